@@ -1,0 +1,389 @@
+"""Benchmark of the triangular solve L X = alpha B on one GB300 (or N replicas).
+
+Default workload: the varlen batch of 8192 independent complex128 solves with
+m, n uniform in [8, 64], alpha = (1.5, -0.5), non-unit diagonal, seed 0
+(synthetic data from the seeded generator), one batched call per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched_c128|single_fp64_64|large_fp64|large_c128|mixed_r32|mixed_ir|serve]
+
+Prints one JSON line.  Metric: GFLOP/s counted as m^2 n real flops per solve
+(x4 for complex), whole job.  Under torchrun each rank solves its own batch
+(seed offset by rank, "weak" scaling) with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TRSM GFLOP/s (m²n) and % roofline; mixed solves/s with p50/p99 latency"
+# FP64 peak derived from the unit count: GB300's nominal 1.25 TFLOP/s FP64 is
+# 2 FP64 FMA per clock per SM: 2 FMA x 2 flop x 152 SMs x 2070 MHz.
+FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2070e6 / 1e9
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (timing only; no collective on the data path)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float, device="cpu") -> float:
+        if self.pg is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float, device="cpu") -> float:
+        if self.pg is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+def shard_seed(base_seed: int, rank: int) -> int:
+    """Each rank solves its own batch: the seed is offset by the rank."""
+    return base_seed + 1000003 * rank
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.window = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu=timestamp,{self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.samples
+        if self.window:
+            inside = [r for (t, r) in rows if self.window[0] - 0.05 <= t <= self.window[1] + 0.05]
+            rows = inside if inside else [r for (_, r) in rows]
+        else:
+            rows = [r for (_, r) in rows]
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                mx = max(mx, float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 6 + k and r[6 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(name: str, files):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256_16") != source_sha(files):
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+SMALL_SOURCES = ["paper_2608_25469_gb300/csrc/small.cu", "paper_2608_25469_gb300/csrc/common.cuh"]
+
+
+def batched_inputs(seed, batch=8192):
+    from paper_2608_25469_gb300 import inputs as I
+    ms, ns = I.batched_sizes(seed, batch)
+    As = [I.gen_A(seed, int(m), I.C128, inst=b) for b, m in enumerate(ms)]
+    Bs = [I.gen_B(seed, int(m), int(n), I.C128, inst=b) for b, (m, n) in enumerate(zip(ms, ns))]
+    flops = float(sum(4.0 * float(m) * m * n for m, n in zip(ms, ns)))
+    # algorithmic bytes: lower triangle of A read, B read, X written
+    abytes = float(sum(16 * (m * (m + 1) // 2) + 2 * 16 * m * n for m, n in zip(ms, ns)))
+    return As, Bs, ms, ns, flops, abytes
+
+
+def cpu_baseline_batched(As, Bs, alpha, min_seconds=3.0):
+    import oracle
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.solve_batch(As, Bs, alpha)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return reps, el, oracle.num_threads()
+
+
+def run_batched(args, dist, device):
+    import torch
+    from paper_2608_25469_gb300 import hsma as H
+    alpha = 1.5 - 0.5j
+    seed = shard_seed(args.seed, dist.rank)
+    As, Bs, ms, ns, flops, abytes = batched_inputs(seed)
+    batch = len(As)
+    es = 16
+    # pack: one buffer for all A (lda = m), one for all B (ldb = m)
+    offA = np.concatenate([[0], np.cumsum(ms.astype(np.int64) ** 2)[:-1]])
+    offB = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns)[:-1]])
+    hostA = np.concatenate([a.ravel(order="F") for a in As])
+    hostB = np.concatenate([b.ravel(order="F") for b in Bs])
+    pinA = torch.from_numpy(hostA).pin_memory()
+    pinB = torch.from_numpy(hostB).pin_memory()
+    outB = torch.empty_like(pinB).pin_memory()
+    dA = pinA.to(device)
+    dB = pinB.to(device)
+    pa = torch.from_numpy((dA.data_ptr() + offA * es).astype(np.int64)).to(device)
+    pb = torch.from_numpy((dB.data_ptr() + offB * es).astype(np.int64)).to(device)
+    dm = torch.from_numpy(ms.astype(np.int32)).to(device)
+    dn = torch.from_numpy(ns.astype(np.int32)).to(device)
+    dld = dm.clone()
+    st = torch.cuda.current_stream()
+    sp = int(st.cuda_stream)
+
+    def step():
+        H.hsma_trsm_llnn_vbatched(H.C128, 0, batch, dm.data_ptr(), dn.data_ptr(), alpha, pa.data_ptr(),
+                                  dld.data_ptr(), pb.data_ptr(), dld.data_ptr(), 64, 64, 0, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if dist.rank == 0 else None
+    if sampler:
+        sampler.start()
+    H.hsma_trace_reset()
+    H.hsma_trace_enable(True)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    dist.barrier()
+    H.hsma_trace_enable(False)
+    ms_total = e0.elapsed_time(e1)
+    solve_ms, solve_cnt = H.hsma_trace_read("vbatched_solve")
+    launches = H.hsma_trace_launches()
+    clocks = None
+    if sampler:
+        sampler.mark(t0, t1)
+        clocks = sampler.stop()
+    ms_max = dist.max(ms_total, device=device)
+
+    # end to end through the C ABI with host buffers: H2D of A and B, solve, D2H of X
+    def e2e_step():
+        dA.copy_(pinA, non_blocking=True)
+        dB.copy_(pinB, non_blocking=True)
+        step()
+        outB.copy_(dB, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 50))
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0.record(st)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = dist.max(e0.elapsed_time(e1), device=device)
+    total_flops = dist.sum(flops, device=device)
+    value = total_flops * args.steps / (ms_max * 1e-3) / 1e9
+    e2e_value = total_flops * e2e_steps / (e2e_ms * 1e-3) / 1e9
+
+    kernel_ms = solve_ms / max(solve_cnt, 1)
+    achieved = flops / (kernel_ms * 1e-3) / 1e9
+    traffic = profile_traffic("vbatched_solve_c128_8192.txt", SMALL_SOURCES)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "batched_small_c128: 8192 complex128 solves per GPU, m,n ~ U{8..64}, "
+                               "alpha=(1.5,-0.5), non-unit, one varlen batched call per step",
+                   "batch_per_gpu": batch, "seed": args.seed, "global_batch": batch * dist.world,
+                   "l2": f"inputs larger than L2 ({abytes / 1e6:.0f} MB algorithmic per step)",
+                   "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
+                     "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
+                     "kernel": "vbatched_solve_kernel<cplx>", "kernel_ms": round(kernel_ms, 5),
+                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+                     "hbm_frac": round(abytes / (kernel_ms * 1e-3) / 1e9 / load_peaks()[0]["hbm_gbs"], 4)},
+        "e2e": {"value": round(e2e_value, 3), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int(hostA.nbytes + hostB.nbytes), "d2h_bytes_per_step": int(hostB.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        reps, el, cores = cpu_baseline_batched(As, Bs, alpha, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": round(flops * reps / el / 1e9, 4), "unit": "GFLOP/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"the full 8192-instance batch, {reps} pass(es) in {el:.2f} s"}
+    return out
+
+
+def run_reference(args, dist):
+    """The oracle, as it stands, on the host cores: same metric and workload."""
+    import oracle
+    if dist.rank != 0:
+        return None
+    alpha = 1.5 - 0.5j
+    As, Bs, ms, ns, flops, _ = batched_inputs(args.seed)
+    # each step: a bounded sample of the batch (the first instances, about 1/8)
+    k = len(As) // 8
+    sflops = float(sum(4.0 * float(m) * m * n for m, n in zip(ms[:k], ns[:k])))
+    for _ in range(args.warmup):
+        oracle.solve_batch(As[:k], Bs[:k], alpha)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve_batch(As[:k], Bs[:k], alpha)
+    el = time.perf_counter() - t0
+    v = sflops * args.steps / el / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "batched_small_c128: 8192 complex128 solves, m,n ~ U{8..64}, alpha=(1.5,-0.5)",
+                   "sample_per_step": f"first {k} of 8192 instances", "seed": args.seed},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"first {k} of the 8192 instances per step"},
+        "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_c128")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=3.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    dist = Dist()
+    if args.impl == "reference":
+        out = run_reference(args, dist)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return 0
+    import torch
+    torch.cuda.set_device(dist.local)
+    device = torch.device("cuda", dist.local)
+    dist.init("nccl")
+    from paper_2608_25469_gb300 import build as B
+    B.build()
+    if args.workload == "batched_c128":
+        out = run_batched(args, dist, device)
+    else:
+        from paper_2608_25469_gb300 import benchlib
+        out = benchlib.run(args.workload, args, dist, device)
+    if dist.rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

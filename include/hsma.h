@@ -1,0 +1,214 @@
+/*
+ * hsma.h - C ABI of the GB300 library for the left / lower / no-transpose
+ * triangular solve with multiple right-hand sides,
+ *
+ *     A X = alpha B,   A (m x m) lower triangular,  B (m x n) overwritten by X,
+ *
+ * after "Hierarchical Shared Memory-Aware Optimization for TRSM on GPU
+ * Platforms" (HSMA-TRSM).  The operation is defined in Section 2.1 by the
+ * forward-substitution formula
+ *
+ *     x_ij = (alpha b_ij - sum_{k<i} a_ik x_kj) / a_ii .
+ *
+ * Conventions shared by every entry point (those of the BLAS xTRSM routine,
+ * which the paper follows; the paper itself fixes no calling convention):
+ *
+ *  - Layout: column-major.  Element (i, j) of A is A[i + j*lda], of B is
+ *    B[i + j*ldb].  Complex data (HSMA_C128) is interleaved (re, im) doubles,
+ *    i.e. the memory layout of C99 `double complex` / numpy complex128.
+ *  - Ownership: A and B are device memory owned by the caller.  Only the lower
+ *    triangle of A is read; with HSMA_UNIT only its strict lower triangle (the
+ *    diagonal is taken as 1).  Rows m..ldb-1 of B are never written.  The
+ *    library keeps no pointer to A or B after the work it enqueued completes.
+ *  - Asynchrony: all work is enqueued on `stream` (a cudaStream_t; NULL means
+ *    the legacy default stream).  A returned HSMA_OK means "validated and
+ *    enqueued"; the result is ready once the stream reaches that point.
+ *  - alpha: HOST pointer to one double (real dtypes) or two doubles (re, im)
+ *    for HSMA_C128.
+ *  - Argument errors return HSMA_ERR_INVALID_ARG and enqueue nothing:
+ *    m < 0, n < 0, lda < max(1, m), ldb < max(1, m), a NULL A/B/alpha when
+ *    m*n > 0, an unknown dtype or diag.
+ *  - Quick returns: m == 0 or n == 0 is a no-op; alpha == 0 sets B := 0 and does
+ *    not read A.
+ *  - A singular A (a zero on the diagonal) is not detected; IEEE infinities and
+ *    NaNs propagate, as in BLAS.
+ *  - Workspace (diagonal-block inverses, refinement copies, batch schedules)
+ *    is taken from CUDA's stream-ordered allocator on `stream` and released on
+ *    the same stream; HSMA_ERR_NO_MEMORY if that fails.  Nothing is allocated
+ *    on the small path of hsma_trsm_llnn.
+ *  - CUDA errors surfacing at enqueue time return HSMA_ERR_CUDA.
+ *  - Thread safety: calls on different streams may run concurrently; the
+ *    tuning table is read-only after hsma_tuning_load.
+ */
+#ifndef HSMA_H
+#define HSMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HSMA_API __attribute__((visibility("default")))
+#else
+#define HSMA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HSMA_R64 = 0,      /* double                                                */
+  HSMA_C128 = 1,     /* double complex                                        */
+  HSMA_R32_BF16 = 2, /* float result; trailing updates in BF16 on tensor cores
+                        with FP32 accumulation                                */
+  HSMA_R64_IR = 3    /* double result from FP32-result solves plus FP64
+                        iterative refinement                                  */
+} hsma_dtype_t;
+
+typedef enum { HSMA_NON_UNIT = 0, HSMA_UNIT = 1 } hsma_diag_t;
+
+typedef enum {
+  HSMA_OK = 0,
+  HSMA_ERR_INVALID_ARG = 1,
+  HSMA_ERR_UNSUPPORTED = 2,
+  HSMA_ERR_NO_MEMORY = 3,
+  HSMA_ERR_CUDA = 4,
+  HSMA_ERR_TIMEOUT = 5,
+  HSMA_ERR_NOT_CONVERGED = 6,
+  HSMA_ERR_BUSY = 7
+} hsma_status_t;
+
+typedef enum { HSMA_PATH_AUTO = 0, HSMA_PATH_SMALL = 1, HSMA_PATH_BLOCKED = 2 } hsma_path_t;
+
+/* Bits OR-ed into a caller-provided device status word by the batched kernel. */
+#define HSMA_DEVERR_BAD_SIZE 0x1u  /* an instance had m<0, n<0, m>64 or ld < max(1,m) */
+#define HSMA_DEVERR_NULL_PTR 0x2u  /* an instance with m*n > 0 had a NULL A or B      */
+
+/* Plan chosen for one solve (Section 4.1's dispatcher and Section 4.3.2's
+ * configuration lookup). */
+typedef struct {
+  int32_t path;      /* hsma_path_t: SMALL (m <= 64) or BLOCKED                     */
+  int32_t nb;        /* BLOCKED: diagonal block size (the paper's N_B)              */
+  int32_t groups;    /* SMALL: row groups per warp G; a warp holds 32/G columns    */
+  int32_t reserved;
+} hsma_plan_t;
+
+/* Options for hsma_trsm_llnn_ex; zero-initialise for defaults. */
+typedef struct {
+  int32_t path;        /* hsma_path_t; AUTO lets the planner choose                 */
+  int32_t nb;          /* BLOCKED: force N_B (16..512, a multiple of 16); 0 = table */
+  int32_t groups;      /* SMALL: force G in {1,2,4,8,16,32}; 0 = planner            */
+  int32_t ir_max_iter; /* R64_IR: refinement steps at most; 0 = 10                   */
+  double ir_tol;       /* R64_IR: stop when ||alpha B - L X||_F / (||L||_F ||X||_F +
+                          |alpha| ||B||_F) <= ir_tol; 0 = 1e-15                    */
+  int32_t bf16_terms;  /* R32_BF16 / R64_IR: BF16 products per update (1 = plain,
+                          3 = hi/lo split of both operands); 0 = planner           */
+  int32_t reserved;
+} hsma_opts_t;
+
+/* Filled by hsma_trsm_llnn_ex (host memory).  Fields describing the device
+ * result (ir_iters, ir_residual) are valid after the stream is synchronised. */
+typedef struct {
+  hsma_plan_t plan;
+  int32_t ir_iters;     /* R64_IR: refinement steps taken                          */
+  int32_t converged;    /* R64_IR: 1 if ir_tol was reached                         */
+  double ir_residual;   /* R64_IR: final normwise residual ratio                   */
+} hsma_info_t;
+
+/* Human-readable name of a status code (static storage). */
+HSMA_API const char *hsma_status_string(int status);
+
+/* Library version "major.minor.patch" (static storage). */
+HSMA_API const char *hsma_version(void);
+
+/*
+ * Single solve  A X = alpha B  (Section 2.1; dispatch of Section 4.1).
+ *
+ * dtype  HSMA_R64 / HSMA_C128: A, B are double / interleaved complex double.
+ *        HSMA_R32_BF16: A, B are float; the result is FP32.
+ *        HSMA_R64_IR: A, B are double; FP32-result solves refined in FP64.
+ * diag   HSMA_NON_UNIT or HSMA_UNIT.
+ * Paths: m <= 64 runs the small direct solve (Section 4.2; triangle in shared
+ * memory, columns of X in registers, warp-shuffle forward substitution);
+ * larger m runs the blocked two-phase algorithm (Section 4.3): parallel
+ * inversion of the N_B x N_B diagonal blocks (Algorithm 2, O(N_B) shared
+ * memory), then for each block row the solve product X_r = D_r^{-1} B_r and the
+ * trailing update with tensor-core (DMMA) products.
+ */
+HSMA_API hsma_status_t hsma_trsm_llnn(int dtype, int diag, int64_t m, int64_t n, const void *alpha,
+                             const void *A, int64_t lda, void *B, int64_t ldb, void *stream);
+
+/* As hsma_trsm_llnn with options (may be NULL) and a host info record (may be NULL). */
+HSMA_API hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const void *alpha,
+                                const void *A, int64_t lda, void *B, int64_t ldb, void *stream,
+                                const hsma_opts_t *opts, hsma_info_t *info);
+
+/*
+ * Varlen batch of independent small solves in one persistent launch (batched
+ * TRSM is the paper's future work, Section 6; each instance is the Section 2.1
+ * solve done by the small kernel of Section 4.2).
+ *
+ * dtype  HSMA_R64 or HSMA_C128 (one dtype and one alpha for the whole batch).
+ * batch  number of instances (>= 0).
+ * d_m, d_n, d_lda, d_ldb: DEVICE arrays of `batch` int32 sizes.
+ * d_A, d_B: DEVICE arrays of `batch` device pointers.
+ * max_m  host upper bound on every m_i: 1..64, or 0 for "unknown" (taken as
+ *        64); a larger value returns HSMA_ERR_UNSUPPORTED (use hsma_trsm_llnn
+ *        per instance for m > 64).
+ * max_n  host upper bound on every n_i, or 0 if unknown (only a hint).
+ * d_status: optional DEVICE uint32 word; the kernel ORs HSMA_DEVERR_* bits into
+ *        it for instances it skips as invalid.  May be NULL.
+ * Instances are scheduled longest first; each instance's arithmetic does not
+ * depend on the others, so results are bit-identical to solving it alone
+ * through this entry point with batch = 1.
+ */
+HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const int32_t *d_m,
+                                      const int32_t *d_n, const void *alpha, const void *const *d_A,
+                                      const int32_t *d_lda, void *const *d_B, const int32_t *d_ldb,
+                                      int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream);
+
+/* Planner query (host only, no GPU needed): the path, N_B and G that
+ * hsma_trsm_llnn would use for (dtype, m, n). */
+HSMA_API hsma_status_t hsma_plan(int dtype, int64_t m, int64_t n, hsma_plan_t *out);
+
+/* Estimated FP64 (or FP32) warp instructions of the small path for one solve
+ * with G row groups (the cost model the planner minimises); host only. */
+HSMA_API double hsma_small_cost(int dtype, int64_t m, int64_t n, int32_t groups);
+
+/* Replace the compiled block-size table with the one in `path` (a text file of
+ * lines "dtype m n nb"; see Section 4.3.2: nearest tested scale wins).  NULL
+ * restores the compiled table. */
+HSMA_API hsma_status_t hsma_tuning_load(const char *path);
+
+/*
+ * Fill a device matrix with the seeded synthetic workload (not part of the
+ * solve; used to build inputs on the device).  kind 0 = A (lower triangular:
+ * off-diagonal (2u-1)/m, diagonal 1+u, zeros above), kind 1 = B (2u-1), drawn
+ * from the counter-based SplitMix64 streams described in inputs.py.  `inst` is
+ * the instance id (-1 for a single solve).  rows x cols written at `dst` with
+ * leading dimension ld (>= rows); dtype HSMA_R64 or HSMA_C128.
+ */
+HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64_t inst, int64_t m,
+                              int64_t cols, void *dst, int64_t ld, void *stream);
+
+/*
+ * Phase tracing (off by default; also switched on by HSMA_PHASE_TIMING=1 in
+ * the environment).  When on, the library records a pair of CUDA events
+ * around every kernel it launches, named by phase: "small_single",
+ * "vbatched_schedule", "vbatched_solve", "diag_inverse", "solve_gemm",
+ * "update_gemm", "convert", "residual", ...  Launches captured into a CUDA
+ * graph are not traced.
+ */
+HSMA_API hsma_status_t hsma_trace_enable(int on);
+/* Total device milliseconds and launch count of `phase` since the last reset
+ * (waits for the recorded events). */
+HSMA_API hsma_status_t hsma_trace_read(const char *phase, double *total_ms, long long *count);
+/* Launches of every phase since the last reset. */
+HSMA_API long long hsma_trace_launches(void);
+HSMA_API void hsma_trace_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSMA_H */

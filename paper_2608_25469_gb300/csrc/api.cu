@@ -1,0 +1,248 @@
+// C ABI of the library (include/hsma.h): argument checks, quick returns, the
+// dispatcher of Section 4.1 and the block-size lookup of Section 4.3.2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hsma.h"
+#include "blocked.h"
+#include "common.cuh"
+#include "gen.h"
+#include "mixed.h"
+#include "small.h"
+#include "workspace.h"
+
+namespace {
+
+bool valid_dtype(int d) { return d >= HSMA_R64 && d <= HSMA_R64_IR; }
+bool valid_diag(int d) { return d == HSMA_NON_UNIT || d == HSMA_UNIT; }
+
+// ---------------------------------------------------------------------------
+// Block-size table (Section 4.3.2): offline profiling keeps the best N_B per
+// (dtype, scale); at run time the nearest profiled scale wins.  Distance is
+// measured in (log m, log n).  Entries come from the autotuner's sweep on this
+// GPU (tuning/gb300.txt); hsma_tuning_load replaces them.
+// ---------------------------------------------------------------------------
+struct TuneEntry {
+  int dtype;
+  int64_t m, n;
+  int nb;
+};
+
+#include "tuning_table.inc"
+
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;  // empty = compiled table
+
+int lookup_nb(int dtype, int64_t m, int64_t n) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const TuneEntry *tab = g_tune.empty() ? kCompiledTable : g_tune.data();
+  const size_t cnt = g_tune.empty() ? sizeof(kCompiledTable) / sizeof(kCompiledTable[0]) : g_tune.size();
+  // R64_IR tunes as R32 (its solves run in FP32); fall back to R64 entries if a dtype has none
+  const int want = dtype == HSMA_R64_IR ? HSMA_R32_BF16 : dtype;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int d = pass == 0 ? want : HSMA_R64;
+    double best = 1e300;
+    int nb = 0;
+    for (size_t k = 0; k < cnt; ++k) {
+      if (tab[k].dtype != d) continue;
+      const double dm = std::log((double)std::max<int64_t>(m, 1)) - std::log((double)tab[k].m);
+      const double dn = std::log((double)std::max<int64_t>(n, 1)) - std::log((double)tab[k].n);
+      const double dist = dm * dm + dn * dn;
+      if (dist < best) {
+        best = dist;
+        nb = tab[k].nb;
+      }
+    }
+    if (nb > 0) return nb;
+  }
+  return 128;
+}
+
+hsma_status_t make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts, hsma_plan_t *p) {
+  std::memset(p, 0, sizeof(*p));
+  int path = opts ? opts->path : HSMA_PATH_AUTO;
+  if (path < HSMA_PATH_AUTO || path > HSMA_PATH_BLOCKED) return HSMA_ERR_INVALID_ARG;
+  const bool small_ok = m <= 64 && (dtype == HSMA_R64 || dtype == HSMA_C128);
+  if (path == HSMA_PATH_AUTO) path = small_ok ? HSMA_PATH_SMALL : HSMA_PATH_BLOCKED;
+  if (path == HSMA_PATH_SMALL && !small_ok) return HSMA_ERR_UNSUPPORTED;
+  p->path = path;
+  if (path == HSMA_PATH_SMALL) {
+    const bool cplx_ = dtype == HSMA_C128;
+    int g = opts ? opts->groups : 0;
+    if (g != 0) {
+      if (g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return HSMA_ERR_INVALID_ARG;
+      if (!hsma_small_g_ok(g, (int)m, cplx_)) return HSMA_ERR_INVALID_ARG;
+    } else {
+      g = hsma_small_pick_g_single((int)std::max<int64_t>(m, 1), (int)std::min<int64_t>(n, 1 << 30), cplx_, 152);
+    }
+    p->groups = g;
+  } else {
+    int nb = opts ? opts->nb : 0;
+    if (nb != 0 && (nb < 16 || nb > 512 || nb % 16 != 0)) return HSMA_ERR_INVALID_ARG;
+    if (nb == 0) nb = lookup_nb(dtype, m, n);
+    p->nb = nb;
+  }
+  return HSMA_OK;
+}
+
+size_t elem_bytes(int dtype) {
+  switch (dtype) {
+    case HSMA_C128: return 16;
+    case HSMA_R32_BF16: return 4;
+    default: return 8;
+  }
+}
+
+bool alpha_is_zero(int dtype, const void *alpha) {
+  const double *a = static_cast<const double *>(alpha);
+  if (dtype == HSMA_C128) return a[0] == 0.0 && a[1] == 0.0;
+  return a[0] == 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hsma_status_string(int s) {
+  switch (s) {
+    case HSMA_OK: return "HSMA_OK";
+    case HSMA_ERR_INVALID_ARG: return "HSMA_ERR_INVALID_ARG";
+    case HSMA_ERR_UNSUPPORTED: return "HSMA_ERR_UNSUPPORTED";
+    case HSMA_ERR_NO_MEMORY: return "HSMA_ERR_NO_MEMORY";
+    case HSMA_ERR_CUDA: return "HSMA_ERR_CUDA";
+    case HSMA_ERR_TIMEOUT: return "HSMA_ERR_TIMEOUT";
+    case HSMA_ERR_NOT_CONVERGED: return "HSMA_ERR_NOT_CONVERGED";
+    case HSMA_ERR_BUSY: return "HSMA_ERR_BUSY";
+    default: return "HSMA_ERR_UNKNOWN";
+  }
+}
+
+const char *hsma_version(void) { return "0.1.0"; }
+
+hsma_status_t hsma_plan(int dtype, int64_t m, int64_t n, hsma_plan_t *out) {
+  if (!valid_dtype(dtype) || m < 0 || n < 0 || out == nullptr) return HSMA_ERR_INVALID_ARG;
+  return make_plan(dtype, m, n, nullptr, out);
+}
+
+double hsma_small_cost(int dtype, int64_t m, int64_t n, int32_t groups) {
+  if (m < 1 || m > 64 || n < 0 || (dtype != HSMA_R64 && dtype != HSMA_C128)) return -1.0;
+  if (groups != 1 && groups != 2 && groups != 4 && groups != 8 && groups != 16 && groups != 32) return -1.0;
+  if (!hsma_small_g_ok(groups, (int)m, dtype == HSMA_C128)) return -1.0;
+  return hsma_small_total_instr((int)m, (int)n, groups, dtype == HSMA_C128);
+}
+
+hsma_status_t hsma_tuning_load(const char *path) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (path == nullptr) {
+    g_tune.clear();
+    return HSMA_OK;
+  }
+  FILE *f = std::fopen(path, "r");
+  if (!f) return HSMA_ERR_INVALID_ARG;
+  std::vector<TuneEntry> t;
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int d, nb;
+    long long m, n;
+    if (std::sscanf(line, "%d %lld %lld %d", &d, &m, &n, &nb) != 4 || !valid_dtype(d) || m < 1 || n < 1 ||
+        nb < 16 || nb > 512 || nb % 16 != 0) {
+      std::fclose(f);
+      return HSMA_ERR_INVALID_ARG;
+    }
+    t.push_back(TuneEntry{d, m, n, nb});
+  }
+  std::fclose(f);
+  if (t.empty()) return HSMA_ERR_INVALID_ARG;
+  g_tune.swap(t);
+  return HSMA_OK;
+}
+
+hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const void *alpha, const void *A,
+                                int64_t lda, void *B, int64_t ldb, void *stream, const hsma_opts_t *opts,
+                                hsma_info_t *info) {
+  if (!valid_dtype(dtype) || !valid_diag(diag)) return HSMA_ERR_INVALID_ARG;
+  if (m < 0 || n < 0) return HSMA_ERR_INVALID_ARG;
+  const int64_t lo = std::max<int64_t>(1, m);
+  if (lda < lo || ldb < lo) return HSMA_ERR_INVALID_ARG;
+  if (m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (m == 0 || n == 0) return HSMA_OK;
+  if (alpha == nullptr || A == nullptr || B == nullptr) return HSMA_ERR_INVALID_ARG;
+  hsma_plan_t plan;
+  hsma_status_t s = make_plan(dtype, m, n, opts, &plan);
+  if (s != HSMA_OK) return s;
+  if (info) info->plan = plan;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (alpha_is_zero(dtype, alpha)) {
+    const size_t eb = elem_bytes(dtype);
+    HSMA_CUDA_TRY(cudaMemset2DAsync(B, (size_t)ldb * eb, 0, (size_t)m * eb, (size_t)n, st));
+    return HSMA_OK;
+  }
+  const int unit = diag == HSMA_UNIT;
+  const double *al = static_cast<const double *>(alpha);
+  switch (dtype) {
+    case HSMA_R64:
+    case HSMA_C128:
+      if (plan.path == HSMA_PATH_SMALL)
+        return hsma_small_single(dtype, plan.groups, A, lda, B, ldb, (int)m, (int)n, al, unit, st);
+      return hsma_blocked_solve(dtype, plan.nb, A, lda, B, ldb, m, n, al, unit, st);
+    case HSMA_R32_BF16:
+      return hsma_mixed_r32(plan.nb, opts ? opts->bf16_terms : 0, static_cast<const float *>(A), lda,
+                            static_cast<float *>(B), ldb, m, n, al[0], unit, st);
+    case HSMA_R64_IR:
+      return hsma_mixed_ir(plan.nb, opts, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb, m,
+                           n, al[0], unit, st, info);
+    default:
+      return HSMA_ERR_INVALID_ARG;
+  }
+}
+
+hsma_status_t hsma_trsm_llnn(int dtype, int diag, int64_t m, int64_t n, const void *alpha, const void *A,
+                             int64_t lda, void *B, int64_t ldb, void *stream) {
+  return hsma_trsm_llnn_ex(dtype, diag, m, n, alpha, A, lda, B, ldb, stream, nullptr, nullptr);
+}
+
+hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const int32_t *d_m, const int32_t *d_n,
+                                      const void *alpha, const void *const *d_A, const int32_t *d_lda,
+                                      void *const *d_B, const int32_t *d_ldb, int32_t max_m, int32_t max_n,
+                                      uint32_t *d_status, void *stream) {
+  if (dtype != HSMA_R64 && dtype != HSMA_C128) {
+    return valid_dtype(dtype) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
+  }
+  if (!valid_diag(diag) || batch < 0 || max_m < 0 || max_n < 0) return HSMA_ERR_INVALID_ARG;
+  if (max_m > 64) return HSMA_ERR_UNSUPPORTED;
+  if (batch > (1 << 24) - 1) return HSMA_ERR_UNSUPPORTED;
+  if (batch == 0) return HSMA_OK;
+  if (alpha == nullptr || d_m == nullptr || d_n == nullptr || d_A == nullptr || d_lda == nullptr ||
+      d_B == nullptr || d_ldb == nullptr)
+    return HSMA_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *scratch = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
+  if (s != HSMA_OK) return s;
+  s = hsma_small_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda, d_B, d_ldb,
+                          diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st);
+  hsma_status_t f = hsma_ws_free(scratch, st);
+  return s != HSMA_OK ? s : f;
+}
+
+hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64_t inst, int64_t m, int64_t cols, void *dst,
+                              int64_t ld, void *stream) {
+  if ((dtype != HSMA_R64 && dtype != HSMA_C128) || (kind != 0 && kind != 1)) return HSMA_ERR_INVALID_ARG;
+  if (m < 0 || cols < 0 || ld < std::max<int64_t>(1, m) || inst < -1) return HSMA_ERR_INVALID_ARG;
+  if (kind == 0 && cols != m) return HSMA_ERR_INVALID_ARG;
+  if (m * cols > 0 && dst == nullptr) return HSMA_ERR_INVALID_ARG;
+  return hsma_gen_launch(dtype, kind, seed, inst, m, cols, dst, ld, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+// Internal helpers shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hsma.h"
+
+#define HSMA_CUDA_TRY(expr)                                  \
+  do {                                                       \
+    cudaError_t hsma_e_ = (expr);                            \
+    if (hsma_e_ != cudaSuccess) return hsma_from_cuda(hsma_e_); \
+  } while (0)
+
+static inline hsma_status_t hsma_from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return HSMA_OK;
+  if (e == cudaErrorMemoryAllocation) return HSMA_ERR_NO_MEMORY;
+  return HSMA_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Element types.  `cplx` is the interleaved (re, im) layout of complex128.
+// ---------------------------------------------------------------------------
+struct cplx {
+  double re, im;
+};
+
+template <class T>
+struct Elem;
+
+template <>
+struct Elem<double> {
+  static constexpr int kFlopsPerFma = 1;  // DFMA instructions per multiply-add
+  __device__ __forceinline__ static double zero() { return 0.0; }
+  __device__ __forceinline__ static double one() { return 1.0; }
+  __device__ __forceinline__ static double mul(double a, double b) { return a * b; }
+  // s - a*x, one fused multiply-add
+  __device__ __forceinline__ static double fms(double a, double x, double s) { return fma(-a, x, s); }
+  __device__ __forceinline__ static double recip(double a) { return 1.0 / a; }
+  __device__ __forceinline__ static double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  __device__ __forceinline__ static double ld(const double *p) { return __ldg(p); }
+  __device__ __forceinline__ static void st(double *p, double v) { *p = v; }
+  __device__ __forceinline__ static bool is_zero(double a) { return a == 0.0; }
+};
+
+template <>
+struct Elem<cplx> {
+  static constexpr int kFlopsPerFma = 4;
+  __device__ __forceinline__ static cplx zero() { return cplx{0.0, 0.0}; }
+  __device__ __forceinline__ static cplx one() { return cplx{1.0, 0.0}; }
+  __device__ __forceinline__ static cplx mul(cplx a, cplx b) {
+    cplx r;
+    r.re = fma(a.re, b.re, -(a.im * b.im));
+    r.im = fma(a.re, b.im, a.im * b.re);
+    return r;
+  }
+  // s - a*x with four fused multiply-adds
+  __device__ __forceinline__ static cplx fms(cplx a, cplx x, cplx s) {
+    s.re = fma(-a.re, x.re, s.re);
+    s.re = fma(a.im, x.im, s.re);
+    s.im = fma(-a.re, x.im, s.im);
+    s.im = fma(-a.im, x.re, s.im);
+    return s;
+  }
+  // 1/a, scaled by the larger component of a (Smith's division with numerator 1)
+  __device__ __forceinline__ static cplx recip(cplx a) {
+    cplx r;
+    if (fabs(a.re) >= fabs(a.im)) {
+      double t = a.im / a.re;
+      double d = a.re + a.im * t;
+      r.re = 1.0 / d;
+      r.im = -t / d;
+    } else {
+      double t = a.re / a.im;
+      double d = a.re * t + a.im;
+      r.re = t / d;
+      r.im = -1.0 / d;
+    }
+    return r;
+  }
+  __device__ __forceinline__ static cplx shfl(cplx v, int src) {
+    cplx r;
+    r.re = __shfl_sync(0xffffffffu, v.re, src);
+    r.im = __shfl_sync(0xffffffffu, v.im, src);
+    return r;
+  }
+  __device__ __forceinline__ static cplx ld(const cplx *p) {
+    const double *q = reinterpret_cast<const double *>(p);
+    return cplx{__ldg(q), __ldg(q + 1)};
+  }
+  __device__ __forceinline__ static void st(cplx *p, cplx v) {
+    double *q = reinterpret_cast<double *>(p);
+    q[0] = v.re;
+    q[1] = v.im;
+  }
+  __device__ __forceinline__ static bool is_zero(cplx a) { return a.re == 0.0 && a.im == 0.0; }
+};
+
+// ---------------------------------------------------------------------------
+// Small-path cost model (Section 4.2 kernel as laid out on this GPU).
+//
+// A warp holds C = 32/G columns of X; each column's rows are spread over G
+// lanes (row r lives in lane group r % G, register slot r / G).  FP64 lanes
+// that are masked off still occupy the FP64 pipe, so the cost of a solve is
+// the number of warp-wide FP64 instructions it issues:
+//   per column tile: K * ( R + sum_{i=0}^{m-2} (R - floor((i+1)/G)) ),
+//   R = ceil(m/G) register slots, K = FP64 instructions per multiply-add
+//   (1 real, 4 complex); the first R term is the alpha*diag^{-1} scaling.
+// Staging the scaled triangle costs K * sum_i ceil((R*G - 1 - i)/32) per CTA.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int hsma_small_rmax(int g, bool cplx_) {
+  // register slots available per lane: 64 rows for any G, except complex G=1
+  // which is limited to 32 rows (128 registers of X per lane)
+  return (cplx_ && g == 1) ? 32 : 64 / g;
+}
+
+__host__ __device__ inline bool hsma_small_g_ok(int g, int m, bool cplx_) {
+  return m <= hsma_small_rmax(g, cplx_) * g;
+}
+
+__host__ __device__ inline double hsma_small_tile_instr(int m, int g, bool cplx_) {
+  const int K = cplx_ ? 4 : 1;
+  const long R = (m + g - 1) / g;
+  long s = R;
+  for (int i = 0; i + 1 < m; ++i) s += R - (i + 1) / g;
+  return (double)K * (double)s;
+}
+
+__host__ __device__ inline double hsma_small_stage_instr(int m, int g, bool cplx_) {
+  const int K = cplx_ ? 4 : 1;
+  const int RG = ((m + g - 1) / g) * g;
+  long s = 0;
+  for (int i = 0; i < m; ++i) s += (RG - 1 - i + 31) / 32;
+  return (double)K * (double)s;
+}
+
+// total FP64 warp instructions for one (m, n) solve with row groups g
+__host__ __device__ inline double hsma_small_total_instr(int m, int n, int g, bool cplx_) {
+  const int C = 32 / g;
+  const int tiles = (n + C - 1) / C;
+  return tiles * hsma_small_tile_instr(m, g, cplx_) + hsma_small_stage_instr(m, g, cplx_);
+}
+
+// Row-group choices compiled into the batched kernel.
+__host__ __device__ inline int hsma_small_pick_g_batched(int m, int n, bool cplx_) {
+  const int cands[4] = {1, 2, 4, 8};
+  int best = 0;
+  double bc = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    const int g = cands[k];
+    if (!hsma_small_g_ok(g, m, cplx_)) continue;
+    const double c = hsma_small_total_instr(m, n, g, cplx_);
+    if (best == 0 || c < bc) {
+      best = g;
+      bc = c;
+    }
+  }
+  return best;
+}
+
+// Device constants of this GPU's FP64 pipe used by the latency-aware choice
+// for a single solve: a warp-wide FP64 instruction occupies a sub-partition
+// for 64 cycles; a dependent step costs one FP64 latency plus, for G > 1, a
+// shuffle round trip.
+__host__ __device__ inline double hsma_small_time_model(int m, int n, int g, bool cplx_, int nsm) {
+  const double tile = hsma_small_tile_instr(m, g, cplx_);
+  const int C = 32 / g;
+  const int tiles = (n + C - 1) / C;
+  const double stage = hsma_small_stage_instr(m, g, cplx_);
+  // every CTA (two warps) stages the triangle once
+  const double total = tiles * tile + stage * ((tiles + 1) / 2);
+  // whole-GPU pipe: 4 sub-partitions per SM, ~84% of nominal measured
+  const double tput = total * 64.0 / (4.0 * nsm * 0.84);
+  // one warp alone on its sub-partition, with staging split over two warps
+  const double warp = (tile + 0.5 * stage) * 64.0;
+  // dependent chain: per step one multiply-add latency (two for complex) plus a shuffle
+  const double chain = (m - 1) * ((cplx_ ? 128.0 : 64.0) + (g > 1 ? 40.0 : 0.0));
+  const double busy = tput > warp ? tput : warp;
+  return busy > chain ? busy : chain;
+}
+
+__host__ __device__ inline int hsma_small_pick_g_single(int m, int n, bool cplx_, int nsm) {
+  const int cands[6] = {1, 2, 4, 8, 16, 32};
+  int best = 0;
+  double bc = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    const int g = cands[k];
+    if (!hsma_small_g_ok(g, m, cplx_)) continue;
+    const double c = hsma_small_time_model(m, n, g, cplx_, nsm);
+    if (best == 0 || c < bc) {
+      best = g;
+      bc = c;
+    }
+  }
+  return best;
+}
+
+// One flag per device (e.g. "kernel attribute already set on this device").
+struct DeviceFlags {
+  static constexpr int kMax = 64;
+  volatile int flag[kMax] = {0};
+  bool test() const {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMax) return false;
+    return flag[d] != 0;
+  }
+  void set() {
+    int d = 0;
+    if (cudaGetDevice(&d) == cudaSuccess && d >= 0 && d < kMax) flag[d] = 1;
+  }
+};

@@ -1,0 +1,14 @@
+// Internal interface of the reduced-precision modes (mixed.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hsma.h"
+
+// FP32-result solve with BF16 tensor-core trailing updates (FP32 accumulate).
+hsma_status_t hsma_mixed_r32(int nb, int bf16_terms, const float *A, int64_t lda, float *B, int64_t ldb, int64_t m,
+                             int64_t n, double alpha, int unit, cudaStream_t st);
+
+// FP64-result solve: FP32-result solve plus FP64 iterative refinement.
+hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, int64_t lda, double *B, int64_t ldb,
+                            int64_t m, int64_t n, double alpha, int unit, cudaStream_t st, hsma_info_t *info);

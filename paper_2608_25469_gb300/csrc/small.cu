@@ -1,0 +1,447 @@
+// Small-case direct solve (m <= 64), single and varlen-batched.
+//
+// Section 4.2.1: the triangle of A stays in shared memory, the columns of B
+// (becoming X) stay in registers, and rows are solved in order; each solved
+// row x_i updates the rows below it with column i of A.  On this GPU the FP64
+// pipe, not memory, bounds the work (a warp-wide FP64 instruction occupies a
+// sub-partition for 64 cycles and masked lanes still pay), so the layout is
+// chosen to keep FP64 lanes busy:
+//
+//  * a warp owns C = 32/G columns; the rows of each column are spread over G
+//    lanes (row r in lane group r % G, register slot r / G).  G is chosen per
+//    instance by a cost model counting warp-wide FP64 instructions;
+//  * the diagonal is folded in while staging: row r of the strict lower
+//    triangle is stored pre-multiplied by 1/a_rr and B's row r by alpha/a_rr,
+//    so a solved value needs no further arithmetic before it is broadcast
+//    (warp shuffle when G > 1);
+//  * the substitution is fully unrolled so X stays in registers; steps past
+//    m and slots past ceil(m/G) are skipped with warp-uniform branches.
+//
+// The per-instance arithmetic is independent of the batch it sits in.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "small.h"
+#include "trace.h"
+
+namespace {
+
+constexpr int kWarpsPerCta = 2;
+constexpr int kThreads = 32 * kWarpsPerCta;
+
+// packed strict-lower triangle: column i holds rows i+1 .. MMAX-1
+__host__ __device__ constexpr int col_off(int i, int mmax) { return i * (mmax - 1) - (i * (i - 1)) / 2; }
+__host__ __device__ constexpr int tri_elems(int mmax) { return col_off(mmax, mmax); }
+
+template <class T>
+struct SmemLayout {
+  // triangle, then c_r = alpha/a_rr, then 1/a_rr
+  __host__ __device__ static constexpr size_t bytes(int mmax) { return sizeof(T) * (tri_elems(mmax) + 2 * mmax); }
+};
+
+// Stage one instance: 1/a_rr and alpha/a_rr for r < m, then the scaled strict
+// lower triangle for rows < rows_used (rows >= m are zero).  All threads of
+// the CTA take part; ends with a CTA barrier.
+template <class T, int MMAX>
+__device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict__ A, int64_t lda, int m,
+                                      int rows_used, T alpha, bool unit) {
+  using E = Elem<T>;
+  const int tid = threadIdx.x;
+  for (int r = tid; r < MMAX; r += kThreads) {
+    T rv = E::one();
+    if (r < m && !unit) rv = E::recip(E::ld(A + r + (int64_t)r * lda));
+    sR[r] = rv;
+    sC[r] = (r < m) ? E::mul(alpha, rv) : E::zero();
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int i = warp; i < m; i += kWarpsPerCta) {
+    T *col = sTri + col_off(i, MMAX) - i - 1;  // col[r], r > i
+    const T *acol = A + (int64_t)i * lda;
+    for (int r = i + 1 + lane; r < rows_used; r += 32) {
+      T v = E::zero();
+      if (r < m) v = E::mul(sR[r], E::ld(acol + r));
+      col[r] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// One warp solves one column tile (up to 32/G columns starting at Bt).
+template <class T, int G, int MMAX>
+__device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, int64_t ldb, int m, int ncols) {
+  using E = Elem<T>;
+  constexpr int R = MMAX / G;
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G, c = lane / G;
+  const bool colok = c < ncols;
+  T *Bp = Bt + (int64_t)(colok ? c : 0) * ldb;
+
+  T s[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int r = g + t * G;
+    s[t] = E::zero();
+    if (t * G < m) {
+      if (colok && r < m) s[t] = E::mul(sC[r], E::ld(Bp + r));
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < MMAX - 1; ++i) {
+    if (i >= m - 1) break;  // warp-uniform: the last row updates nothing
+    const int tb = i / G, gi = i % G;
+    const T x = (G == 1) ? s[tb] : E::shfl(s[tb], c * G + gi);
+    const T *col = sTri + col_off(i, MMAX) - i - 1;
+    if (G > 1 && gi < G - 1) {
+      // boundary slot: only rows strictly below i update
+      const int r = g + tb * G;
+      const int ra = r > i ? r : i + 1;
+      const T ns = E::fms(col[ra], x, s[tb]);
+      if (r > i) s[tb] = ns;
+    }
+#pragma unroll
+    for (int t = tb + 1; t < R; ++t) {
+      if (t * G >= m) break;  // warp-uniform
+      s[t] = E::fms(col[g + t * G], x, s[t]);
+    }
+  }
+
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int r = g + t * G;
+    if (t * G < m) {
+      if (colok && r < m) E::st(Bp + r, s[t]);
+    }
+  }
+}
+
+template <class T, int G, int MMAX>
+__device__ __forceinline__ void solve_tiles(const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n, int tile0,
+                                            int tile_step) {
+  constexpr int C = 32 / G;
+  const int warp = threadIdx.x >> 5;
+  const int ntiles = (n + C - 1) / C;
+  for (int t = tile0 + warp; t < ntiles; t += tile_step) {
+    const int col0 = t * C;
+    const int nc = (n - col0) < C ? (n - col0) : C;
+    warp_solve<T, G, MMAX>(sTri, sC, B + (int64_t)col0 * ldb, ldb, m, nc);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void zero_tiles(T *B, int64_t ldb, int m, int n) {
+  for (int j = threadIdx.x >> 5; j < n; j += kWarpsPerCta)
+    for (int r = threadIdx.x & 31; r < m; r += 32) Elem<T>::st(B + r + (int64_t)j * ldb, Elem<T>::zero());
+}
+
+// Dispatch over the row-group variants compiled for a dtype.
+template <class T>
+struct Variants;
+
+template <>
+struct Variants<double> {
+  __device__ __forceinline__ static void run(int g, const double *sTri, const double *sC, double *B, int64_t ldb,
+                                             int m, int n, int tile0, int step) {
+    switch (g) {
+      case 1: solve_tiles<double, 1, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+      case 2: solve_tiles<double, 2, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+      case 4: solve_tiles<double, 4, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+      default: solve_tiles<double, 8, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+    }
+  }
+};
+
+template <>
+struct Variants<cplx> {
+  __device__ __forceinline__ static void run(int g, const cplx *sTri, const cplx *sC, cplx *B, int64_t ldb, int m,
+                                             int n, int tile0, int step) {
+    switch (g) {
+      case 1: solve_tiles<cplx, 1, 32>(sTri, sC, B, ldb, m, n, tile0, step); break;
+      case 2: solve_tiles<cplx, 2, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+      case 4: solve_tiles<cplx, 4, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+      default: solve_tiles<cplx, 8, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+    }
+  }
+};
+
+// The triangle's packed layout uses MMAX = 64 for every variant except the
+// complex G = 1 one (MMAX = 32); stage with the variant's MMAX.
+template <class T>
+__device__ __forceinline__ int variant_mmax(int g) {
+  return (sizeof(T) == sizeof(cplx) && g == 1) ? 32 : 64;
+}
+
+template <class T>
+__device__ __forceinline__ void stage_any(int g, T *sTri, T *sC, T *sR, const T *A, int64_t lda, int m, T alpha,
+                                          bool unit) {
+  const int rows_used = ((m + g - 1) / g) * g;
+  if (variant_mmax<T>(g) == 32)
+    stage<T, 32>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
+  else
+    stage<T, 64>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
+}
+
+template <class T>
+__device__ __forceinline__ void smem_parts(unsigned char *smem, T *&sTri, T *&sC, T *&sR) {
+  sTri = reinterpret_cast<T *>(smem);
+  sC = sTri + tri_elems(64);
+  sR = sC + 64;
+}
+
+// ---------------------------------------------------------------------------
+// Single solve: CTA k stages the instance and its warps take column tiles
+// k*W, k*W+1, ... (W warps per CTA).
+// ---------------------------------------------------------------------------
+template <class T, int G, int MMAX>
+__global__ void __launch_bounds__(kThreads) small_single_kernel(const T *__restrict__ A, int64_t lda, T *B,
+                                                                 int64_t ldb, int m, int n, T alpha, int unit) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sTri, *sC, *sR;
+  smem_parts<T>(smem, sTri, sC, sR);
+  const int rows_used = ((m + G - 1) / G) * G;
+  stage<T, MMAX>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0);
+  solve_tiles<T, G, MMAX>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsPerCta, gridDim.x * kWarpsPerCta);
+}
+
+// ---------------------------------------------------------------------------
+// Varlen batch.  A one-CTA pre-pass validates the instances, picks G per
+// instance and writes a longest-first schedule (bucketed by estimated cost);
+// the persistent kernel then pulls instances from an atomic counter.
+//
+// Scratch layout (int32): [0] next-item counter, [1] number of scheduled
+// items, [2 .. 2+batch) schedule entries (instance | G << 24).
+// ---------------------------------------------------------------------------
+constexpr int kBuckets = 256;
+
+__device__ __forceinline__ int cost_bucket(double cost) {
+  // 8 buckets per octave, 32 octaves
+  int b = (int)(log2(cost > 1.0 ? cost : 1.0) * 8.0);
+  return b < kBuckets ? b : kBuckets - 1;
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, const int32_t *__restrict__ dm,
+                                                                 const int32_t *__restrict__ dn,
+                                                                 const int32_t *__restrict__ dlda,
+                                                                 const int32_t *__restrict__ dldb,
+                                                                 const void *const *__restrict__ dA,
+                                                                 void *const *__restrict__ dB, int32_t *scratch,
+                                                                 uint32_t *status) {
+  __shared__ int hist[kBuckets];
+  __shared__ int offs[kBuckets];
+  const bool cplx_ = sizeof(T) == sizeof(cplx);
+  for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
+  uint32_t err = 0;
+  for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+    const int m = dm[b], n = dn[b];
+    const int lo = m > 1 ? m : 1;
+    if (m < 0 || n < 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) {
+      err |= HSMA_DEVERR_BAD_SIZE;
+      continue;
+    }
+    if (m == 0 || n == 0) continue;
+    if (dA[b] == nullptr || dB[b] == nullptr) {
+      err |= HSMA_DEVERR_NULL_PTR;
+      continue;
+    }
+    const int g = hsma_small_pick_g_batched(m, n, cplx_);
+    atomicAdd(&hist[cost_bucket(hsma_small_total_instr(m, n, g, cplx_))], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = kBuckets - 1; k >= 0; --k) {  // most expensive first
+      offs[k] = run;
+      run += hist[k];
+    }
+    scratch[0] = 0;
+    scratch[1] = run;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+    const int m = dm[b], n = dn[b];
+    const int lo = m > 1 ? m : 1;
+    if (m <= 0 || n <= 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) continue;
+    if (dA[b] == nullptr || dB[b] == nullptr) continue;
+    const int g = hsma_small_pick_g_batched(m, n, cplx_);
+    const int pos = atomicAdd(&offs[cost_bucket(hsma_small_total_instr(m, n, g, cplx_))], 1);
+    scratch[2 + pos] = b | (g << 24);
+  }
+  if (err != 0 && status != nullptr) atomicOr(status, err);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) vbatched_solve_kernel(const int32_t *__restrict__ dm,
+                                                                  const int32_t *__restrict__ dn,
+                                                                  const int32_t *__restrict__ dlda,
+                                                                  const int32_t *__restrict__ dldb,
+                                                                  const void *const *__restrict__ dA,
+                                                                  void *const *__restrict__ dB, T alpha, int unit,
+                                                                  int32_t *scratch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  T *sTri, *sC, *sR;
+  smem_parts<T>(smem, sTri, sC, sR);
+  const int nitems = *(volatile int32_t *)(scratch + 1);
+  const bool azero = Elem<T>::is_zero(alpha);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(scratch, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= nitems) break;
+    const int e = scratch[2 + item];
+    const int b = e & 0xffffff, g = e >> 24;
+    const int m = dm[b], n = dn[b];
+    const T *A = static_cast<const T *>(dA[b]);
+    T *B = static_cast<T *>(dB[b]);
+    const int64_t lda = dlda[b], ldb = dldb[b];
+    if (azero) {
+      zero_tiles<T>(B, ldb, m, n);
+      continue;
+    }
+    stage_any<T>(g, sTri, sC, sR, A, lda, m, alpha, unit != 0);
+    Variants<T>::run(g, sTri, sC, B, ldb, m, n, 0, kWarpsPerCta);
+    __syncthreads();  // the next item restages shared memory
+  }
+}
+
+template <class T>
+int persistent_grid(int dev) {
+  static int cached[64] = {0};
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  int nsm = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_solve_kernel<T>, kThreads,
+                                                SmemLayout<T>::bytes(64));
+  int grid = nsm * (per_sm > 0 ? per_sm : 1);
+  if (dev >= 0 && dev < 64) cached[dev] = grid;
+  return grid;
+}
+
+template <class T>
+hsma_status_t set_smem_attrs() {
+  const int bytes = (int)SmemLayout<T>::bytes(64);
+  HSMA_CUDA_TRY(cudaFuncSetAttribute(vbatched_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return HSMA_OK;
+}
+
+template <class T, int G, int MMAX>
+hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m, int n, T alpha, int unit,
+                              int nsm, cudaStream_t st) {
+  constexpr int C = 32 / G;
+  const int tiles = (n + C - 1) / C;
+  int grid = (tiles + kWarpsPerCta - 1) / kWarpsPerCta;
+  const int cap = nsm * 16;
+  if (grid > cap) grid = cap;
+  const size_t bytes = SmemLayout<T>::bytes(64);
+  static DeviceFlags attr_done;
+  if (!attr_done.test()) {
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(small_single_kernel<T, G, MMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    attr_done.set();
+  }
+  HsmaTraceScope ts("small_single", st);
+  small_single_kernel<T, G, MMAX><<<grid, kThreads, bytes, st>>>(A, lda, B, ldb, m, n, alpha, unit);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host entry points (internal; the C ABI validates arguments first).
+// ---------------------------------------------------------------------------
+template <class T>
+static hsma_status_t small_single_impl(int g, const void *A, int64_t lda, void *B, int64_t ldb, int m, int n,
+                                       const double *alpha, int unit, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  HSMA_CUDA_TRY(cudaGetDevice(&dev));
+  HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const bool cplx_ = sizeof(T) == sizeof(cplx);
+  if (g == 0) g = hsma_small_pick_g_single(m, n, cplx_, nsm);
+  if (!hsma_small_g_ok(g, m, cplx_)) return HSMA_ERR_INVALID_ARG;
+  T al;
+  if constexpr (sizeof(T) == sizeof(cplx)) {
+    al = T{alpha[0], alpha[1]};
+  } else {
+    al = alpha[0];
+  }
+  const T *a = static_cast<const T *>(A);
+  T *b = static_cast<T *>(B);
+  if constexpr (sizeof(T) == sizeof(cplx)) {
+    switch (g) {
+      case 1: return launch_single_g<T, 1, 32>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 2: return launch_single_g<T, 2, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 4: return launch_single_g<T, 4, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 8: return launch_single_g<T, 8, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 16: return launch_single_g<T, 16, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 32: return launch_single_g<T, 32, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      default: return HSMA_ERR_INVALID_ARG;
+    }
+  } else {
+    switch (g) {
+      case 1: return launch_single_g<T, 1, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 2: return launch_single_g<T, 2, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 4: return launch_single_g<T, 4, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 8: return launch_single_g<T, 8, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 16: return launch_single_g<T, 16, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 32: return launch_single_g<T, 32, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      default: return HSMA_ERR_INVALID_ARG;
+    }
+  }
+}
+
+hsma_status_t hsma_small_single(int dtype, int g, const void *A, int64_t lda, void *B, int64_t ldb, int m, int n,
+                                const double *alpha, int unit, cudaStream_t st) {
+  if (dtype == HSMA_C128) return small_single_impl<cplx>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+  return small_single_impl<double>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+}
+
+template <class T>
+static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32_t *dn, const double *alpha,
+                                   const void *const *dA, const int32_t *dlda, void *const *dB,
+                                   const int32_t *dldb, int unit, uint32_t *status, int32_t *scratch,
+                                   cudaStream_t st) {
+  int dev = 0;
+  HSMA_CUDA_TRY(cudaGetDevice(&dev));
+  static DeviceFlags attr_done;
+  if (!attr_done.test()) {
+    hsma_status_t s = set_smem_attrs<T>();
+    if (s != HSMA_OK) return s;
+    attr_done.set();
+  }
+  T al;
+  if constexpr (sizeof(T) == sizeof(cplx)) {
+    al = T{alpha[0], alpha[1]};
+  } else {
+    al = alpha[0];
+  }
+  {
+    HsmaTraceScope ts("vbatched_schedule", st);
+    vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status);
+  }
+  HSMA_CUDA_TRY(cudaGetLastError());
+  int grid = persistent_grid<T>(dev);
+  if (grid > batch) grid = batch;
+  {
+    HsmaTraceScope ts("vbatched_solve", st);
+    vbatched_solve_kernel<T><<<grid, kThreads, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dA, dB, al,
+                                                                               unit, scratch);
+  }
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+size_t hsma_vbatched_scratch_bytes(int32_t batch) { return sizeof(int32_t) * (2 + (size_t)(batch > 0 ? batch : 0)); }
+
+hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
+                                  const double *alpha, const void *const *dA, const int32_t *dlda,
+                                  void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
+                                  int32_t *scratch, cudaStream_t st) {
+  if (dtype == HSMA_C128)
+    return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+  return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+}

@@ -1,0 +1,21 @@
+// Internal interface of the small-case kernels (small.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/hsma.h"
+
+// One solve with m <= 64 (g = 0: planner choice).  Arguments already validated.
+hsma_status_t hsma_small_single(int dtype, int g, const void *A, int64_t lda, void *B, int64_t ldb, int m, int n,
+                                const double *alpha, int unit, cudaStream_t st);
+
+// Bytes of device scratch the varlen batch needs for `batch` instances.
+size_t hsma_vbatched_scratch_bytes(int32_t batch);
+
+// Varlen batch (schedule pre-pass + persistent solve).  `scratch` holds
+// hsma_vbatched_scratch_bytes(batch) bytes of device memory.
+hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
+                                  const double *alpha, const void *const *dA, const int32_t *dlda,
+                                  void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
+                                  int32_t *scratch, cudaStream_t st);

@@ -1,0 +1,206 @@
+"""Thin ctypes binding of ``libhsma.so`` (include/hsma.h), same names as the C ABI.
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  There is no CPU fallback; if the library has not been built, loading
+this module raises ``RuntimeError``.
+
+Pointers are plain integers (e.g. ``tensor.data_ptr()``); streams are raw
+``cudaStream_t`` values (e.g. ``torch.cuda.current_stream().cuda_stream``).
+Helpers at the end move column-major numpy arrays to and from torch CUDA
+tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhsma.so")
+
+R64, C128, R32_BF16, R64_IR = 0, 1, 2, 3
+NON_UNIT, UNIT = 0, 1
+PATH_AUTO, PATH_SMALL, PATH_BLOCKED = 0, 1, 2
+OK = 0
+DEVERR_BAD_SIZE, DEVERR_NULL_PTR = 0x1, 0x2
+STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTED", 3: "HSMA_ERR_NO_MEMORY",
+                4: "HSMA_ERR_CUDA", 5: "HSMA_ERR_TIMEOUT", 6: "HSMA_ERR_NOT_CONVERGED", 7: "HSMA_ERR_BUSY"}
+
+# Every function include/hsma.h declares (checked by the tests against the header).
+EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_llnn_ex",
+           "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
+           "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset"]
+
+
+class HsmaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("ir_max_iter", ctypes.c_int32), ("ir_tol", ctypes.c_double), ("bf16_terms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("plan", Plan), ("ir_iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("ir_residual", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhsma.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
+                           "python paper_2608_25469_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, u32p, vp, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double
+    c_int = ctypes.c_int
+    lib.hsma_status_string.argtypes = [c_int]
+    lib.hsma_status_string.restype = ctypes.c_char_p
+    lib.hsma_version.restype = ctypes.c_char_p
+    lib.hsma_trsm_llnn.argtypes = [c_int, c_int, i64, i64, vp, vp, i64, vp, i64, vp]
+    lib.hsma_trsm_llnn.restype = c_int
+    lib.hsma_trsm_llnn_ex.argtypes = [c_int, c_int, i64, i64, vp, vp, i64, vp, i64, vp,
+                                      ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    lib.hsma_trsm_llnn_ex.restype = c_int
+    lib.hsma_trsm_llnn_vbatched.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p, vp]
+    lib.hsma_trsm_llnn_vbatched.restype = c_int
+    lib.hsma_plan.argtypes = [c_int, i64, i64, ctypes.POINTER(Plan)]
+    lib.hsma_plan.restype = c_int
+    lib.hsma_small_cost.argtypes = [c_int, i64, i64, i32]
+    lib.hsma_small_cost.restype = dbl
+    lib.hsma_tuning_load.argtypes = [ctypes.c_char_p]
+    lib.hsma_tuning_load.restype = c_int
+    lib.hsma_gen_matrix.argtypes = [c_int, c_int, ctypes.c_uint64, i64, i64, i64, vp, i64, vp]
+    lib.hsma_gen_matrix.restype = c_int
+    lib.hsma_trace_enable.argtypes = [c_int]
+    lib.hsma_trace_enable.restype = c_int
+    lib.hsma_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_longlong)]
+    lib.hsma_trace_read.restype = c_int
+    lib.hsma_trace_launches.restype = ctypes.c_longlong
+    lib.hsma_trace_reset.restype = None
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise HsmaError(status, where)
+
+
+def _alpha_buf(alpha):
+    a = complex(alpha)
+    return (ctypes.c_double * 2)(a.real, a.imag)
+
+
+def hsma_status_string(status: int) -> str:
+    return _lib.hsma_status_string(status).decode()
+
+
+def hsma_version() -> str:
+    return _lib.hsma_version().decode()
+
+
+def hsma_trsm_llnn(dtype, diag, m, n, alpha, A, lda, B, ldb, stream=0, check=True) -> int:
+    """Raw call; A and B are device pointers (ints).  Returns the status."""
+    s = _lib.hsma_trsm_llnn(dtype, diag, m, n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), A, lda, B, ldb,
+                            stream)
+    if check:
+        _check(s, "hsma_trsm_llnn")
+    return s
+
+
+def hsma_trsm_llnn_ex(dtype, diag, m, n, alpha, A, lda, B, ldb, stream=0, opts: Opts | None = None,
+                      info: Info | None = None, check=True) -> int:
+    s = _lib.hsma_trsm_llnn_ex(dtype, diag, m, n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), A, lda, B, ldb,
+                               stream, ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(info) if info is not None else None)
+    if check:
+        _check(s, "hsma_trsm_llnn_ex")
+    return s
+
+
+def hsma_trsm_llnn_vbatched(dtype, diag, batch, d_m, d_n, alpha, d_A, d_lda, d_B, d_ldb, max_m=0, max_n=0,
+                            d_status=0, stream=0, check=True) -> int:
+    s = _lib.hsma_trsm_llnn_vbatched(dtype, diag, batch, d_m, d_n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p),
+                                     d_A, d_lda, d_B, d_ldb, max_m, max_n, d_status or None, stream)
+    if check:
+        _check(s, "hsma_trsm_llnn_vbatched")
+    return s
+
+
+def hsma_plan(dtype, m, n) -> Plan:
+    p = Plan()
+    _check(_lib.hsma_plan(dtype, m, n, ctypes.byref(p)), "hsma_plan")
+    return p
+
+
+def hsma_small_cost(dtype, m, n, groups) -> float:
+    return _lib.hsma_small_cost(dtype, m, n, groups)
+
+
+def hsma_tuning_load(path: str | None) -> int:
+    return _lib.hsma_tuning_load(path.encode() if path is not None else None)
+
+
+def hsma_gen_matrix(dtype, kind, seed, inst, m, cols, dst, ld, stream=0, check=True) -> int:
+    s = _lib.hsma_gen_matrix(dtype, kind, seed, inst, m, cols, dst, ld, stream)
+    if check:
+        _check(s, "hsma_gen_matrix")
+    return s
+
+
+def hsma_trace_enable(on: bool) -> int:
+    return _lib.hsma_trace_enable(int(bool(on)))
+
+
+def hsma_trace_read(phase: str):
+    """(total device ms, launch count) of a traced phase since the last reset."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_longlong()
+    _check(_lib.hsma_trace_read(phase.encode(), ctypes.byref(ms), ctypes.byref(cnt)), "hsma_trace_read")
+    return ms.value, cnt.value
+
+
+def hsma_trace_launches() -> int:
+    return _lib.hsma_trace_launches()
+
+
+def hsma_trace_reset() -> None:
+    _lib.hsma_trace_reset()
+
+
+# ---------------------------------------------------------------------------
+# Column-major helpers (torch only moves memory).
+# ---------------------------------------------------------------------------
+def to_device(X: np.ndarray, device="cuda"):
+    """Fortran-ordered (ld, cols) numpy array -> CUDA tensor with the same column-major bytes.
+
+    The tensor has shape (cols, ld) in torch's row-major convention."""
+    import torch
+    Xf = np.asfortranarray(X)
+    return torch.from_numpy(np.ascontiguousarray(Xf.T)).to(device)
+
+
+def from_device(t) -> np.ndarray:
+    """Inverse of ``to_device``: returns a Fortran-ordered (ld, cols) numpy array."""
+    return np.asfortranarray(t.cpu().numpy().T)
+
+
+def stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)

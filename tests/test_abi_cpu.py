@@ -1,0 +1,115 @@
+"""The C-ABI library loads, exports what include/hsma.h declares, and validates
+arguments on the host before touching the GPU (CPU only)."""
+import os
+import re
+
+import pytest
+
+from paper_2608_25469_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def H():
+    B.build()
+    from paper_2608_25469_gb300 import hsma
+    return hsma
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "hsma.h")).read()
+    return sorted(set(re.findall(r"HSMA_API[^;(]*?\b(hsma_\w+)\s*\(", text)))
+
+
+def test_exports_match_header(H):
+    declared = header_functions()
+    assert declared, "no declarations found"
+    out = os.popen(f"nm -D --defined-only {H.LIB_PATH}").read()
+    exported = set(re.findall(r"\bT (hsma_\w+)", out))
+    missing = [f for f in declared if f not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    assert sorted(H.EXPORTS) == declared, "binding and header disagree"
+    for f in declared:
+        assert hasattr(H.lib(), f)
+
+
+def test_version_and_status_strings(H):
+    assert re.match(r"\d+\.\d+\.\d+", H.hsma_version())
+    for s, name in H.STATUS_NAMES.items():
+        assert H.hsma_status_string(s) == name
+    assert H.hsma_status_string(999) == "HSMA_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize("args", [
+    dict(dtype=0, diag=0, m=-1, n=4, lda=4, ldb=4),     # m < 0
+    dict(dtype=0, diag=0, m=4, n=-1, lda=4, ldb=4),     # n < 0
+    dict(dtype=0, diag=0, m=4, n=4, lda=3, ldb=4),      # lda < m
+    dict(dtype=1, diag=0, m=4, n=4, lda=4, ldb=3),      # ldb < m
+    dict(dtype=9, diag=0, m=4, n=4, lda=4, ldb=4),      # dtype
+    dict(dtype=0, diag=2, m=4, n=4, lda=4, ldb=4),      # diag
+    dict(dtype=0, diag=0, m=0, n=4, lda=0, ldb=1),      # lda < max(1, m)
+])
+def test_invalid_arguments_rejected_without_launch(H, args):
+    s = H.hsma_trsm_llnn(args["dtype"], args["diag"], args["m"], args["n"], 1.0, 0, args["lda"], 0, args["ldb"],
+                         check=False)
+    assert s == 1  # HSMA_ERR_INVALID_ARG
+
+
+def test_null_pointers_rejected(H):
+    assert H.hsma_trsm_llnn(0, 0, 4, 4, 1.0, 0, 4, 0, 4, check=False) == 1
+
+
+def test_quick_return_empty(H):
+    # m == 0 or n == 0: no-op, no pointer is touched, no CUDA call made
+    assert H.hsma_trsm_llnn(0, 0, 0, 5, 1.0, 0, 1, 0, 1, check=False) == 0
+    assert H.hsma_trsm_llnn(1, 1, 7, 0, 1.0, 0, 7, 0, 7, check=False) == 0
+    assert H.hsma_trsm_llnn_vbatched(1, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, check=False) == 0
+
+
+def test_vbatched_argument_checks(H):
+    assert H.hsma_trsm_llnn_vbatched(2, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 2   # dtype unsupported
+    assert H.hsma_trsm_llnn_vbatched(7, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 1   # dtype unknown
+    assert H.hsma_trsm_llnn_vbatched(0, 0, -1, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 1  # batch < 0
+    assert H.hsma_trsm_llnn_vbatched(0, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, max_m=65, check=False) == 2
+    assert H.hsma_trsm_llnn_vbatched(0, 0, 4, 0, 1, 1.0, 1, 1, 1, 1, check=False) == 1   # NULL d_m
+
+
+def test_plan_dispatch(H):
+    # Section 4.1: 64 is the boundary between the direct solve and the blocked path
+    assert H.hsma_plan(H.R64, 64, 64).path == H.PATH_SMALL
+    assert H.hsma_plan(H.C128, 64, 4096).path == H.PATH_SMALL
+    assert H.hsma_plan(H.R64, 65, 64).path == H.PATH_BLOCKED
+    assert H.hsma_plan(H.R32_BF16, 32, 32).path == H.PATH_BLOCKED
+    p = H.hsma_plan(H.R64, 16384, 16384)
+    assert p.nb in (32, 64, 128, 256, 512)
+
+
+def test_tuning_table_nearest_match(H, tmp_path):
+    # Section 4.3.2: offline table, nearest tested scale at run time
+    f = tmp_path / "t.txt"
+    f.write_text("# dtype m n nb\n0 100 100 32\n0 2000 2000 64\n0 30000 30000 512\n")
+    try:
+        assert H.hsma_tuning_load(str(f)) == 0
+        assert H.hsma_plan(H.R64, 120, 120).nb == 32
+        assert H.hsma_plan(H.R64, 3000, 1500).nb == 64
+        assert H.hsma_plan(H.R64, 16384, 16384).nb == 512
+        assert H.hsma_plan(H.C128, 120, 120).nb == 32  # no C128 rows: falls back to R64 rows
+        bad = tmp_path / "bad.txt"
+        bad.write_text("0 100 100 33\n")
+        assert H.hsma_tuning_load(str(bad)) == 1
+        assert H.hsma_plan(H.R64, 120, 120).nb == 32  # unchanged after a rejected load
+    finally:
+        assert H.hsma_tuning_load(None) == 0
+
+
+def test_small_cost_model(H):
+    # fp64, G = 1, one tile: R + sum_{i<m-1} (R - (i+1)) with R = m, plus staging
+    m = 64
+    tile = m + sum(m - (i + 1) for i in range(m - 1))
+    stage = sum((m - 1 - i + 31) // 32 for i in range(m))
+    assert H.hsma_small_cost(H.R64, m, 32, 1) == tile + stage
+    # complex costs four FP64 instructions per multiply-add
+    assert H.hsma_small_cost(H.C128, 32, 32, 1) == 4 * H.hsma_small_cost(H.R64, 32, 32, 1)
+    assert H.hsma_small_cost(H.C128, 33, 8, 1) == -1.0   # complex G=1 holds 32 rows at most
+    assert H.hsma_small_cost(H.R64, 65, 8, 2) == -1.0

@@ -1,0 +1,195 @@
+"""Small-case path (m <= 64) and varlen batch against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_25469_gb300 import inputs as I
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12  # relative Frobenius forward error, fp64 and complex128
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    assert torch.cuda.is_available()
+    return U.lib()
+
+
+def _np_dt(code):
+    return np.float64 if code == I.R64 else np.complex128
+
+
+def _solve_single(H, code, A, B, alpha, unit=False, groups=0):
+    """A: (lda, m) Fortran, B: (ldb, n) Fortran; returns the device result as numpy."""
+    import torch
+    dA, dB = H.to_device(A), H.to_device(B)
+    opts = H.Opts()
+    opts.groups = groups
+    H.hsma_trsm_llnn_ex(code, int(unit), A.shape[1], B.shape[1], alpha, dA.data_ptr(), A.shape[0], dB.data_ptr(),
+                        B.shape[0], H.stream_ptr(), opts=opts)
+    torch.cuda.synchronize()
+    return H.from_device(dB)
+
+
+def test_config0_single_fp64_64(H):
+    """One fp64 solve, m = n = 64, lda = ldb = 64, alpha = 1.5, seed 0."""
+    A, B = I.gen_A(0, 64, I.R64), I.gen_B(0, 64, 64, I.R64)
+    X = _solve_single(H, I.R64, A, B, 1.5)
+    ref = oracle.solve(A, B, 1.5)
+    assert oracle.forward_error(X, ref) <= TOL
+    assert oracle.backward_error(A, B, X, 1.5) <= 1e-14
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+def test_small_sweep_every_m_and_variant(H, code):
+    """Every m in 1..64, ragged n, every row-group variant the single path has."""
+    import torch
+    rng = np.random.default_rng(11)
+    dt = _np_dt(code)
+    alpha = 1.5 if code == I.R64 else 1.5 - 0.5j
+    cases = []
+    for m in range(1, 65):
+        for n in (1, 5, 33, 64, 97):
+            for g in (0, 1, 2, 4, 8, 16, 32):
+                if g and H.hsma_small_cost(code, m, n, g) < 0:
+                    continue
+                cases.append((m, n, g))
+    # fixed inputs per (m, n); all launches on one stream, one sync
+    data = {}
+    jobs = []
+    for (m, n, g) in cases:
+        if (m, n) not in data:
+            seed = int(rng.integers(1 << 30))
+            data[(m, n)] = (I.gen_A(seed, m, code), I.gen_B(seed, m, n, code))
+        A, B = data[(m, n)]
+        dA, dB = H.to_device(A), H.to_device(B)
+        opts = H.Opts()
+        opts.groups = g
+        H.hsma_trsm_llnn_ex(code, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts)
+        jobs.append((m, n, g, dA, dB))
+    torch.cuda.synchronize()
+    refs = {k: oracle.solve(A, B, alpha) for k, (A, B) in data.items()}
+    worst = 0.0
+    for (m, n, g, dA, dB) in jobs:
+        err = oracle.forward_error(H.from_device(dB), refs[(m, n)])
+        worst = max(worst, err)
+        assert err <= TOL, (m, n, g, err)
+    assert worst < 1e-14
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+def test_poison_and_canaries(H, code):
+    """Upper triangle and (unit) diagonal are never read; padding rows of B are never written."""
+    dt = _np_dt(code)
+    m, n, pad = 45, 19, 5
+    alpha = 0.5 if code == I.R64 else 0.5 + 2j
+    A0, B0 = I.gen_A(3, m, code), I.gen_B(3, m, n, code)
+    A = np.full((m + pad, m), np.nan, dtype=dt, order="F")
+    A[:m] = A0
+    A[:m][np.triu_indices(m, 1)] = np.nan
+    Bb = I.embed(B0, m + pad, fill=np.nan)
+    X = _solve_single(H, code, A, Bb, alpha)
+    assert np.all(np.isnan(X[m:])), "padding rows of B were written"
+    ref = oracle.solve(A0, B0, alpha)
+    assert oracle.forward_error(X[:m], ref) <= TOL
+    # unit diagonal: diagonal holds NaN and must not be read
+    Au = A.copy()
+    np.fill_diagonal(Au[:m], np.nan)
+    Xu = _solve_single(H, code, Au, Bb, alpha, unit=True)
+    A1 = A0.copy()
+    np.fill_diagonal(A1, 1.0)
+    refu = oracle.solve(A1, B0, alpha)
+    assert oracle.forward_error(Xu[:m], refu) <= TOL
+    # alpha = 0: B := 0, A not read
+    Anan = np.full((m, m), np.nan, dtype=dt, order="F")
+    X0 = _solve_single(H, code, Anan, Bb, 0.0)
+    assert np.all(X0[:m] == 0) and np.all(np.isnan(X0[m:]))
+
+
+def _config1(code=I.C128, batch=8192, seed=0):
+    ms, ns = I.batched_sizes(seed, batch)
+    As = [I.gen_A(seed, int(m), code, inst=b) for b, m in enumerate(ms)]
+    Bs = [I.gen_B(seed, int(m), int(n), code, inst=b) for b, (m, n) in enumerate(zip(ms, ns))]
+    return As, Bs
+
+
+def _run_batch(H, code, As, Bs, alpha, unit=False, max_m=64):
+    import torch
+    bt = U.Batch(As, Bs)
+    H.hsma_trsm_llnn_vbatched(code, int(unit), bt.batch, bt.args()[0], bt.args()[1], alpha, bt.args()[2],
+                              bt.args()[3], bt.args()[4], bt.args()[5], max_m=max_m, max_n=0,
+                              d_status=bt.d_status.data_ptr(), stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    return bt
+
+
+def test_config1_batched_c128_parity(H):
+    """8192 complex128 instances, m, n uniform in [8, 64], alpha = (1.5, -0.5), one varlen launch."""
+    alpha = 1.5 - 0.5j
+    As, Bs = _config1()
+    bt = _run_batch(H, I.C128, As, Bs, alpha)
+    assert bt.status() == 0
+    Xs = bt.results()
+    refs = oracle.solve_batch(As, Bs, alpha)
+    errs = [oracle.forward_error(X, R) for X, R in zip(Xs, refs)]
+    assert max(errs) <= TOL, max(errs)
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+def test_batched_alone_equals_in_mix(H, code):
+    """Each instance solved alone is bit-identical to its result inside the batch."""
+    alpha = 1.5 if code == I.R64 else 1.5 - 0.5j
+    As, Bs = _config1(code, batch=300, seed=5)
+    mix = _run_batch(H, code, As, Bs, alpha).results()
+    refs = oracle.solve_batch(As, Bs, alpha)
+    for b in range(0, 300, 7):
+        alone = _run_batch(H, code, [As[b]], [Bs[b]], alpha).results()[0]
+        assert np.array_equal(alone, mix[b]), b
+        assert oracle.forward_error(mix[b], refs[b]) <= TOL
+
+
+def test_batched_edge_instances(H):
+    """Empty instances are skipped; invalid ones are skipped and flagged; the rest are solved."""
+    code = I.R64
+    alpha = -2.0
+    As, Bs = [], []
+    for m, n in [(5, 3), (0, 4), (7, 0), (64, 64), (1, 1), (13, 29)]:
+        As.append(I.gen_A(9, m, code) if m else np.zeros((0, 0), order="F"))
+        Bs.append(I.gen_B(9, m, n, code) if m else np.zeros((0, n), order="F"))
+    bt = _run_batch(H, code, As, Bs, alpha)
+    assert bt.status() == 0
+    for A, B, X in zip(As, Bs, bt.results()):
+        if A.shape[1] == 0 or B.shape[1] == 0:
+            continue
+        assert oracle.forward_error(X, oracle.solve(A, B, alpha)) <= TOL
+    # an instance with m > 64 and one with ldb < m: skipped, flagged
+    import torch
+    As2 = [I.gen_A(1, 8, code), I.gen_A(1, 8, code)]
+    Bs2 = [I.gen_B(1, 8, 3, code), I.gen_B(1, 8, 3, code)]
+    bt = U.Batch(As2, Bs2)
+    bt.d_m[1] = 80
+    H.hsma_trsm_llnn_vbatched(code, 0, 2, *bt.args()[:2], alpha, *bt.args()[2:], max_m=0, max_n=0,
+                              d_status=bt.d_status.data_ptr(), stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    assert bt.status() & H.DEVERR_BAD_SIZE
+    X = bt.results()
+    assert oracle.forward_error(X[0], oracle.solve(As2[0], Bs2[0], alpha)) <= TOL
+    assert np.array_equal(X[1], Bs2[1])  # untouched
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+def test_device_generator_matches_host(H, code):
+    import torch
+    dt = U.torch_dtype(_np_dt(code))
+    for kind, (m, cols), inst in [(0, (37, 37), -1), (1, (37, 11), 4), (0, (64, 64), 12)]:
+        ld = m + 3
+        t = torch.full((cols, ld), 7.0, dtype=dt, device="cuda")
+        H.hsma_gen_matrix(code, kind, 42, inst, m, cols, t.data_ptr(), ld, H.stream_ptr())
+        torch.cuda.synchronize()
+        got = H.from_device(t)
+        ref = I.gen_A(42, m, code, inst=inst) if kind == 0 else I.gen_B(42, m, cols, code, inst=inst)
+        assert np.array_equal(got[:m], ref)
+        assert np.all(got[m:] == 7.0)

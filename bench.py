@@ -320,6 +320,123 @@ def run_batched(args, dist, device):
     return out
 
 
+LARGE_SOURCES = ["paper_2608_25469_gb300/csrc/blocked.cu", "paper_2608_25469_gb300/csrc/tma.cuh",
+                 "paper_2608_25469_gb300/csrc/common.cuh"]
+
+
+def run_large(args, dist, device, code, m):
+    """One blocked solve per step: fp64 m = n = 16384 or complex128 m = n = 8192, alpha = 1."""
+    import torch
+    from paper_2608_25469_gb300 import hsma as H
+    n = m
+    cplx_ = code == H.C128
+    dt = torch.complex128 if cplx_ else torch.float64
+    es = 16 if cplx_ else 8
+    seed = shard_seed(args.seed, dist.rank)
+    dA = torch.empty((m, m), dtype=dt, device=device)
+    dB = torch.empty((n, m), dtype=dt, device=device)
+    st = torch.cuda.current_stream()
+    sp = int(st.cuda_stream)
+    H.hsma_gen_matrix(code, 0, seed, -1, m, m, dA.data_ptr(), m, sp)
+    H.hsma_gen_matrix(code, 1, seed, -1, m, n, dB.data_ptr(), m, sp)
+    flops = (4.0 if cplx_ else 1.0) * float(m) * m * n
+    abytes = es * (m * (m + 1) / 2 + 2.0 * m * n)
+
+    def step():
+        H.hsma_trsm_llnn(code, 0, m, n, 1.0, dA.data_ptr(), m, dB.data_ptr(), m, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if dist.rank == 0 else None
+    if sampler:
+        sampler.start()
+    H.hsma_trace_reset()
+    H.hsma_trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    H.hsma_trace_enable(False)
+    ms_max = dist.max(e0.elapsed_time(e1), device=device)
+    phases = {ph: H.hsma_trace_read(ph) for ph in ("diag_inverse", "copy", "solve_gemm", "update_gemm")}
+    launches = H.hsma_trace_launches()
+    clocks = None
+    if sampler:
+        sampler.mark(t0, t1)
+        clocks = sampler.stop()
+    upd_ms, upd_cnt = phases["update_gemm"]
+    tot_phase = sum(v[0] for v in phases.values())
+    # the update products' algorithmic flops: the trailing part of m^2 n not done by the solve products
+    nb = H.hsma_plan(code, m, n).nb
+    upd_flops = (4.0 if cplx_ else 1.0) * float(n) * (m * m - m * nb)
+    achieved = upd_flops / args.steps / (upd_ms / max(args.steps, 1) * 1e-3) / 1e9
+    total_flops = dist.sum(flops, device=device)
+    value = total_flops * args.steps / (ms_max * 1e-3) / 1e9
+    name = "large_c128" if cplx_ else "large_fp64"
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx_ else "f64", "data": "synthetic",
+        "config": {"workload": f"{name}: one blocked solve m=n={m}, alpha=1, non-unit, N_B={nb}", "m": m, "n": n,
+                   "nb": nb, "l2": f"inputs larger than L2 ({abytes / 1e9:.2f} GB)"},
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
+                     "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                     "traffic": profile_traffic(f"update_gemm_{name}.txt", LARGE_SOURCES),
+                     "kernel": "gemm_kernel (update_gemm, DMMA m8n8k4)",
+                     "peak_source": "derived FP64 (DMMA shares the FP64 budget): 2 FMA/clk/SM x 152 x 2070 MHz"},
+        "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phases.items()},
+        "phase_share": {k: round(v[0] / tot_phase, 4) for k, v in phases.items()} if tot_phase else None,
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+
+
+def run_single64(args, dist, device):
+    """Latency of one fp64 solve, m = n = 64, alpha = 1.5 (p50/p99 over the steps, graph-free launches)."""
+    import torch
+    from paper_2608_25469_gb300 import hsma as H
+    from paper_2608_25469_gb300 import inputs as I
+    A, Bm = I.gen_A(args.seed, 64, I.R64), I.gen_B(args.seed, 64, 64, I.R64)
+    dA, dB = H.to_device(A), H.to_device(Bm)
+    st = torch.cuda.current_stream()
+    sp = int(st.cuda_stream)
+
+    def step():
+        H.hsma_trsm_llnn(H.R64, 0, 64, 64, 1.5, dA.data_ptr(), 64, dB.data_ptr(), 64, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    H.hsma_trace_reset()
+    H.hsma_trace_enable(True)
+    lat = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step()
+        e1.record(st)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    H.hsma_trace_enable(False)
+    kms, kc = H.hsma_trace_read("small_single")
+    lat = np.sort(np.array(lat))
+    flops = 64.0 ** 3
+    return {
+        "metric": METRIC, "value": round(flops / (np.median(lat) * 1e-3) / 1e9, 4), "unit": "GFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.median(lat)), 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "single_fp64_64: one fp64 solve m=n=64, lda=ldb=64, alpha=1.5"},
+        "latency_us": {"p50": round(float(np.percentile(lat, 50)) * 1e3, 2),
+                       "p99": round(float(np.percentile(lat, 99)) * 1e3, 2),
+                       "kernel_avg": round(kms / max(kc, 1) * 1e3, 2)},
+    }
+
+
 def run_reference(args, dist):
     """The oracle, as it stands, on the host cores: same metric and workload."""
     import oracle
@@ -374,11 +491,17 @@ def main(argv=None):
     dist.init("nccl")
     from paper_2608_25469_gb300 import build as B
     B.build()
+    from paper_2608_25469_gb300 import hsma as H
     if args.workload == "batched_c128":
         out = run_batched(args, dist, device)
+    elif args.workload == "large_fp64":
+        out = run_large(args, dist, device, H.R64, 16384)
+    elif args.workload == "large_c128":
+        out = run_large(args, dist, device, H.C128, 8192)
+    elif args.workload == "single_fp64_64":
+        out = run_single64(args, dist, device)
     else:
-        from paper_2608_25469_gb300 import benchlib
-        out = benchlib.run(args.workload, args, dist, device)
+        raise SystemExit(f"unknown workload {args.workload}")
     if dist.rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     dist.close()

@@ -192,6 +192,14 @@ HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64
                               int64_t cols, void *dst, int64_t ld, void *stream);
 
 /*
+ * Device-side error bits the library's kernels raise (a bounded wait that ran
+ * out: HSMA_DEVERR_TIMEOUT).  Synchronises the device, returns the bits
+ * accumulated since the last call in *out, and clears them.
+ */
+#define HSMA_DEVERR_TIMEOUT 0x4u
+HSMA_API hsma_status_t hsma_device_status(unsigned int *out);
+
+/*
  * Phase tracing (off by default; also switched on by HSMA_PHASE_TIMING=1 in
  * the environment).  When on, the library records a pair of CUDA events
  * around every kernel it launches, named by phase: "small_single",

@@ -1,5 +1,563 @@
+// Large-case blocked solve (Section 4.3), fp64 and complex128.
+//
+// Phase 1 (Section 4.3, "parallel diagonal block inversion"): the N_B x N_B
+// diagonal blocks D_t are inverted independently, all in one launch.  Each CTA
+// produces a group of columns of D_t^{-1} by forward substitution against the
+// identity (Section 4.3.1): the columns of D_t are streamed through a two-slot
+// shared-memory buffer (Algorithm 2's double buffering: column k+1 is staged
+// while column k is used), so shared memory is O(N_B).  The columns of the
+// inverse live in registers: lane group g of a warp holds rows g, g+G, ...,
+// and the register window slides down by one slot every G steps.
+//
+// Phase 2 (Section 4.3, "sequential GEMM update and solve"), for r = 0..k:
+//   X_r = D_r^{-1} B_r                       (solve product, triangular)
+//   B_{r+1:} = beta B_{r+1:} - A_{r+1:,r} X_r (trailing update)
+// This is the right-looking order of the same arithmetic; the paper's
+// left-looking update B_r -= A_{r,0:r} X_{0:r} accumulates the same products.
+// alpha is folded in once: X_0 = alpha D_0^{-1} B_0 and beta = alpha at r = 0.
+//
+// Both products run on the FP64 tensor path (mma.sync m8n8k4 .f64, "DMMA"),
+// complex as four real products, with operand tiles brought into shared memory
+// by TMA (cp.async.bulk.tensor) behind mbarriers, or by plain loads when a
+// leading dimension rules TMA out (an odd fp64 leading dimension).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
 #include "blocked.h"
-hsma_status_t hsma_blocked_solve(int, int, const void *, int64_t, void *, int64_t, int64_t, int64_t, const double *,
-                                 int, cudaStream_t) {
-  return HSMA_ERR_UNSUPPORTED;
+#include "common.cuh"
+#include "tma.cuh"
+#include "trace.h"
+#include "workspace.h"
+
+__device__ unsigned int g_hsma_dev_error = 0;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Phase 1: diagonal-block inversion
+// ---------------------------------------------------------------------------
+constexpr int kInvSlots = 32;  // register slots per lane: N_B = 32 * G
+
+template <class T, int G>
+__global__ void __launch_bounds__(256) diag_inverse_kernel(const T *__restrict__ A, int64_t lda, int64_t m, int unit,
+                                                            T *__restrict__ Dinv) {
+  using E = Elem<T>;
+  constexpr int R = kInvSlots, NB = 32 * G, C = 32 / G;
+  __shared__ T sRinv[NB];
+  __shared__ T sCol[2][NB];
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int CT = (nthr / 32) * C;
+  const int64_t r0 = (int64_t)blockIdx.x * NB;
+  const int s = (int)((m - r0) < NB ? (m - r0) : NB);
+  const int j0 = blockIdx.y * CT;
+  T *Y = Dinv + (int64_t)blockIdx.x * NB * NB;
+  const T *D = A + r0 + r0 * lda;
+
+  for (int r = tid; r < NB; r += nthr) sRinv[r] = (r < s) ? (unit ? E::one() : E::recip(E::ld(D + r + (int64_t)r * lda))) : E::zero();
+  // zeros outside the computed region: whole columns >= s, rows < j0 and rows >= s
+  for (int e = tid; e < CT * NB; e += nthr) {
+    const int col = j0 + e / NB, row = e % NB;
+    if (col < NB && (col >= s || row < j0 || row >= s)) Y[row + (int64_t)col * NB] = E::zero();
+  }
+  __syncthreads();
+  if (j0 >= s) return;
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = lane % G, c = lane / G;
+  const int j = j0 + warp * C + c;
+  const bool colok = j < s;
+  const int q0 = j0 / G;
+
+  T x[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) x[t] = (colok && g + G * (t + q0) == j) ? sRinv[j] : E::zero();
+
+  // loader role: rows tid, tid + nthr (N_B <= 2 * nthr)
+  auto fetch = [&](int k, T *pf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = tid + h * nthr;
+      pf[h] = (r > k && r < s && k < s) ? E::ld(D + r + (int64_t)k * lda) : E::zero();
+    }
+  };
+  auto put = [&](int k, const T *pf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = tid + h * nthr;
+      if (r < NB) sCol[k & 1][r] = E::mul(sRinv[r < s ? r : 0], pf[h]);
+    }
+  };
+  T pf[2];
+  fetch(j0, pf);
+  put(j0, pf);
+  fetch(j0 + 1, pf);
+  __syncthreads();
+
+  for (int q = q0; q * G < s; ++q) {
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int k = q * G + u;
+      if (k >= s) break;
+      if (k + 1 < s) put(k + 1, pf);
+      if (k + 2 < s) fetch(k + 2, pf);
+      const T *dc = sCol[k & 1];
+      const T xk = (G == 1) ? x[0] : E::shfl(x[0], c * G + u);
+      if (u < G - 1) {
+        const T nv = E::fms(dc[g + G * q], xk, x[0]);
+        if (g > u) x[0] = nv;
+      }
+#pragma unroll
+      for (int t = 1; t < R; ++t) {
+        if ((q + t) * G >= s) break;
+        x[t] = E::fms(dc[g + G * (q + t)], xk, x[t]);
+      }
+      __syncthreads();
+    }
+    const int row = g + G * q;
+    if (colok && row < s) Y[row + (int64_t)j * NB] = x[0];
+#pragma unroll
+    for (int t = 0; t < R - 1; ++t) x[t] = x[t + 1];
+    x[R - 1] = E::zero();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase 2 products on the FP64 tensor path
+// ---------------------------------------------------------------------------
+constexpr int BM = 64, BN = 64, STAGES = 3, GEMM_THREADS = 128;
+
+template <class T>
+struct GemmK;
+template <>
+struct GemmK<double> {
+  static constexpr int BK = 32;
+};
+template <>
+struct GemmK<cplx> {
+  static constexpr int BK = 16;
+};
+
+enum { MODE_UPDATE = 0, MODE_SCALE = 1 };
+
+template <class T>
+struct GemmArgs {
+  const T *A;  // M x K (column-major, lda)
+  int64_t lda;
+  const T *Bm;  // K x N (column-major, ldb)
+  int64_t ldb;
+  T *C;  // M x N (column-major, ldc)
+  int64_t ldc;
+  int M, N, K;
+  int mode;  // UPDATE: C = beta*C - A*B;  SCALE: C = beta*(A*B)
+  T beta;
+  int tri;  // A is lower triangular: row tile i0 needs k < i0 + BM only
+  unsigned int *err;
+  uint64_t limit_ns;
+};
+
+template <class T>
+constexpr int stage_bytes() {
+  return (GemmK<T>::BK * BM + BN * GemmK<T>::BK) * (int)sizeof(T);
+}
+
+__device__ __forceinline__ void dmma884(double &d0, double &d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+// Accumulators of one warp's 32 x 32 tile: 4 x 4 blocks of 8 x 8.
+template <class T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double v[4][4][2];
+};
+template <>
+struct Acc<cplx> {
+  double re[4][4][2];
+  double im[4][4][2];
+};
+
+// one BK-deep slice from shared memory: sA[k][BM], sB[BN][k]
+__device__ __forceinline__ void mma_slice(Acc<double> &acc, const double *sA, const double *sB, int wm, int wn,
+                                          int g, int t) {
+  constexpr int BK = GemmK<double>::BK;
+#pragma unroll
+  for (int kk = 0; kk < BK; kk += 4) {
+    double a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = sA[(kk + t) * BM + wm * 32 + i * 8 + g];
+#pragma unroll
+    for (int jn = 0; jn < 4; ++jn) b[jn] = sB[(wn * 32 + jn * 8 + g) * BK + kk + t];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jn = 0; jn < 4; ++jn) dmma884(acc.v[i][jn][0], acc.v[i][jn][1], a[i], b[jn]);
+  }
+}
+
+__device__ __forceinline__ void mma_slice(Acc<cplx> &acc, const cplx *sA, const cplx *sB, int wm, int wn, int g,
+                                          int t) {
+  constexpr int BK = GemmK<cplx>::BK;
+#pragma unroll
+  for (int kk = 0; kk < BK; kk += 4) {
+    cplx a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = sA[(kk + t) * BM + wm * 32 + i * 8 + g];
+#pragma unroll
+    for (int jn = 0; jn < 4; ++jn) b[jn] = sB[(wn * 32 + jn * 8 + g) * BK + kk + t];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jn = 0; jn < 4; ++jn) {
+        dmma884(acc.re[i][jn][0], acc.re[i][jn][1], a[i].re, b[jn].re);
+        dmma884(acc.re[i][jn][0], acc.re[i][jn][1], -a[i].im, b[jn].im);
+        dmma884(acc.im[i][jn][0], acc.im[i][jn][1], a[i].re, b[jn].im);
+        dmma884(acc.im[i][jn][0], acc.im[i][jn][1], a[i].im, b[jn].re);
+      }
+  }
+}
+
+__device__ __forceinline__ void acc_zero(Acc<double> &a) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a.v[i][j][0] = a.v[i][j][1] = 0.0;
+}
+__device__ __forceinline__ void acc_zero(Acc<cplx> &a) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a.re[i][j][0] = a.re[i][j][1] = a.im[i][j][0] = a.im[i][j][1] = 0.0;
+}
+__device__ __forceinline__ double acc_get(const Acc<double> &a, int i, int j, int q) { return a.v[i][j][q]; }
+__device__ __forceinline__ cplx acc_get(const Acc<cplx> &a, int i, int j, int q) {
+  return cplx{a.re[i][j][q], a.im[i][j][q]};
+}
+__device__ __forceinline__ double sub(double a, double b) { return a - b; }
+__device__ __forceinline__ cplx sub(cplx a, cplx b) { return cplx{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ bool is_one(double a) { return a == 1.0; }
+__device__ __forceinline__ bool is_one(cplx a) { return a.re == 1.0 && a.im == 0.0; }
+
+template <class T>
+__device__ __forceinline__ void epilogue(const GemmArgs<T> &p, const Acc<T> &acc, int m0, int n0, int wm, int wn,
+                                         int g, int t) {
+  using E = Elem<T>;
+  const bool b1 = is_one(p.beta);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = m0 + wm * 32 + i * 8 + g;
+    if (row >= p.M) continue;
+#pragma unroll
+    for (int jn = 0; jn < 4; ++jn)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int col = n0 + wn * 32 + jn * 8 + 2 * t + q;
+        if (col >= p.N) continue;
+        T *cp = p.C + row + (int64_t)col * p.ldc;
+        const T v = acc_get(acc, i, jn, q);
+        if (p.mode == MODE_UPDATE) {
+          const T old = *cp;
+          *cp = sub(b1 ? old : E::mul(p.beta, old), v);
+        } else {
+          *cp = b1 ? v : E::mul(p.beta, v);
+        }
+      }
+  }
+}
+
+// words per element for the 8-byte TMA view of T
+template <class T>
+constexpr int words() {
+  return (int)(sizeof(T) / 8);
+}
+
+template <class T, bool kTma>
+__global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const GemmArgs<T> p,
+                                                            const __grid_constant__ CUtensorMap mapA,
+                                                            const __grid_constant__ CUtensorMap mapB) {
+  constexpr int BK = GemmK<T>::BK;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ int s_abort;
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  auto sA = [&](int s) { return reinterpret_cast<T *>(smem + s * stage_bytes<T>()); };
+  auto sB = [&](int s) { return reinterpret_cast<T *>(smem + s * stage_bytes<T>() + BK * BM * sizeof(T)); };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp & 1, wn = warp >> 1, g = lane >> 2, t = lane & 3;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kend = p.tri ? min(p.K, m0 + BM) : p.K;
+  const int nk = (kend + BK - 1) / BK;
+
+  Acc<T> acc;
+  acc_zero(acc);
+
+  if constexpr (kTma) {
+    if (tid == 0) {
+      for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+      fence_mbar_init();
+      s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int kt, int s) {
+      mbar_arrive_expect_tx(&full[s], stage_bytes<T>());
+      tma_load_2d(sA(s), &mapA, &full[s], m0 * words<T>(), kt * BK);
+      tma_load_2d(sB(s), &mapB, &full[s], kt * BK * words<T>(), n0);
+    };
+    if (tid == 0)
+      for (int s = 0; s < STAGES && s < nk; ++s) issue(s, s);
+    int kt = 0;
+    for (; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      const bool ok = mbar_wait_bounded(&full[s], (kt / STAGES) & 1, p.limit_ns, p.err);
+      if (__syncthreads_or(!ok)) break;
+      mma_slice(acc, sA(s), sB(s), wm, wn, g, t);
+      __syncthreads();
+      if (tid == 0 && kt + STAGES < nk) issue(kt + STAGES, s);
+    }
+    if (kt < nk) {
+      // timed out: let the copies this CTA issued land (bounded) before leaving
+      if (tid == 0)
+        for (int k2 = kt; k2 < nk && k2 < kt + STAGES; ++k2)
+          mbar_wait_bounded(&full[k2 % STAGES], (k2 / STAGES) & 1, p.limit_ns, p.err);
+      return;
+    }
+  } else {
+    using E = Elem<T>;
+    for (int kt = 0; kt < nk; ++kt) {
+      T *a = sA(0), *b = sB(0);
+      const int k0 = kt * BK;
+      for (int e = tid; e < BK * BM; e += GEMM_THREADS) {
+        const int kk = e / BM, mm = e % BM;
+        const int row = m0 + mm, col = k0 + kk;
+        a[e] = (row < p.M && col < p.K) ? E::ld(p.A + row + (int64_t)col * p.lda) : E::zero();
+      }
+      for (int e = tid; e < BN * BK; e += GEMM_THREADS) {
+        const int nn = e / BK, kk = e % BK;
+        const int row = k0 + kk, col = n0 + nn;
+        b[e] = (row < p.K && col < p.N) ? E::ld(p.Bm + row + (int64_t)col * p.ldb) : E::zero();
+      }
+      __syncthreads();
+      mma_slice(acc, a, b, wm, wn, g, t);
+      __syncthreads();
+    }
+  }
+  epilogue(p, acc, m0, n0, wm, wn, g, t);
+}
+
+template <class T>
+size_t gemm_smem_bytes(bool tma) {
+  return (size_t)(tma ? STAGES : 1) * stage_bytes<T>() + 128;
+}
+
+template <class T>
+hsma_status_t gemm_attrs() {
+  static DeviceFlags done;
+  if (done.test()) return HSMA_OK;
+  HSMA_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)gemm_smem_bytes<T>(true)));
+  HSMA_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)gemm_smem_bytes<T>(false)));
+  done.set();
+  return HSMA_OK;
+}
+
+template <class T>
+bool tma_ok(const void *p, int64_t ld) {
+  return ((uintptr_t)p % 16 == 0) && ((ld * (int64_t)sizeof(T)) % 16 == 0);
+}
+
+unsigned int *dev_error_ptr() {
+  static unsigned int *p = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (p == nullptr) cudaGetSymbolAddress((void **)&p, g_hsma_dev_error);
+  return p;
+}
+
+// Launch one product.  `phase` names it for the tracer.
+template <class T>
+hsma_status_t gemm(const GemmArgs<T> &p0, const char *phase, cudaStream_t st) {
+  if (p0.M <= 0 || p0.N <= 0) return HSMA_OK;
+  hsma_status_t s = gemm_attrs<T>();
+  if (s != HSMA_OK) return s;
+  GemmArgs<T> p = p0;
+  p.err = dev_error_ptr();
+  if (p.limit_ns == 0) p.limit_ns = 4000000000ull;  // 4 s of wall time per barrier wait
+  const bool use_tma = tma_ok<T>(p.A, p.lda) && tma_ok<T>(p.Bm, p.ldb);
+  CUtensorMap ma, mb;
+  std::memset(&ma, 0, sizeof ma);
+  std::memset(&mb, 0, sizeof mb);
+  if (use_tma) {
+    constexpr int BK = GemmK<T>::BK;
+    constexpr int w = words<T>();
+    if (!hsma_make_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, p.A, (uint64_t)p.M * w, (uint64_t)p.K,
+                          (uint64_t)p.lda * w, BM * w, BK) ||
+        !hsma_make_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, p.Bm, (uint64_t)p.K * w, (uint64_t)p.N,
+                          (uint64_t)p.ldb * w, BK * w, BN))
+      return HSMA_ERR_CUDA;
+  }
+  dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN);
+  if (grid.y > 65535) return HSMA_ERR_UNSUPPORTED;
+  HsmaTraceScope ts(phase, st);
+  if (use_tma)
+    gemm_kernel<T, true><<<grid, GEMM_THREADS, gemm_smem_bytes<T>(true), st>>>(p, ma, mb);
+  else
+    gemm_kernel<T, false><<<grid, GEMM_THREADS, gemm_smem_bytes<T>(false), st>>>(p, ma, mb);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+template <class T, int G>
+hsma_status_t launch_inverse_g(const T *A, int64_t lda, int64_t m, int unit, T *Dinv, cudaStream_t st) {
+  constexpr int NB = 32 * G, C = 32 / G;
+  const int warps = std::min(8, NB / C);
+  const int CT = warps * C;
+  dim3 grid((unsigned)((m + NB - 1) / NB), (unsigned)(NB / CT));
+  HsmaTraceScope ts("diag_inverse", st);
+  diag_inverse_kernel<T, G><<<grid, warps * 32, 0, st>>>(A, lda, m, unit, Dinv);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+template <class T>
+hsma_status_t launch_inverse(int nb, const T *A, int64_t lda, int64_t m, int unit, T *Dinv, cudaStream_t st) {
+  switch (nb) {
+    case 32: return launch_inverse_g<T, 1>(A, lda, m, unit, Dinv, st);
+    case 64: return launch_inverse_g<T, 2>(A, lda, m, unit, Dinv, st);
+    case 128: return launch_inverse_g<T, 4>(A, lda, m, unit, Dinv, st);
+    case 256: return launch_inverse_g<T, 8>(A, lda, m, unit, Dinv, st);
+    case 512: return launch_inverse_g<T, 16>(A, lda, m, unit, Dinv, st);
+    default: return HSMA_ERR_UNSUPPORTED;
+  }
+}
+
+template <class T>
+T make_scalar(const double *a);
+template <>
+double make_scalar<double>(const double *a) {
+  return a[0];
+}
+template <>
+cplx make_scalar<cplx>(const double *a) {
+  return cplx{a[0], a[1]};
+}
+
+template <class T>
+hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, int64_t m, int64_t n,
+                           const double *alpha, int unit, cudaStream_t st) {
+  const int64_t nblk = (m + nb - 1) / nb;
+  const T al = make_scalar<T>(alpha);
+  const T one = make_scalar<T>((const double[2]){1.0, 0.0});
+  void *ws = nullptr;
+  const size_t dinv_bytes = sizeof(T) * (size_t)nblk * nb * nb;
+  const size_t w_bytes = sizeof(T) * (size_t)nb * n;
+  hsma_status_t s = hsma_ws_alloc(&ws, dinv_bytes + w_bytes, st);
+  if (s != HSMA_OK) return s;
+  T *Dinv = static_cast<T *>(ws);
+  T *W = reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + dinv_bytes);
+  s = launch_inverse<T>(nb, A, lda, m, unit, Dinv, st);
+  for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
+    const int64_t r0 = r * nb;
+    const int sr = (int)std::min<int64_t>(nb, m - r0);
+    // X_r = D_r^{-1} (scale * B_r): B_r is copied to W so the product can write B_r
+    {
+      HsmaTraceScope ts("copy", st);
+      cudaError_t e = cudaMemcpy2DAsync(W, sizeof(T) * nb, B + r0, sizeof(T) * ldb, sizeof(T) * sr, n,
+                                        cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) {
+        s = hsma_from_cuda(e);
+        break;
+      }
+    }
+    GemmArgs<T> ps{};
+    ps.A = Dinv + (size_t)r * nb * nb;
+    ps.lda = nb;
+    ps.Bm = W;
+    ps.ldb = nb;
+    ps.C = B + r0;
+    ps.ldc = ldb;
+    ps.M = sr;
+    ps.N = (int)n;
+    ps.K = sr;
+    ps.mode = MODE_SCALE;
+    ps.beta = r == 0 ? al : one;
+    ps.tri = 1;
+    s = gemm<T>(ps, "solve_gemm", st);
+    if (s != HSMA_OK || r0 + sr >= m) break;
+    // B_{r+1:} = beta B_{r+1:} - A_{r+1:, r} X_r
+    GemmArgs<T> pu{};
+    pu.A = A + (r0 + sr) + r0 * lda;
+    pu.lda = lda;
+    pu.Bm = B + r0;
+    pu.ldb = ldb;
+    pu.C = B + r0 + sr;
+    pu.ldc = ldb;
+    pu.M = (int)(m - r0 - sr);
+    pu.N = (int)n;
+    pu.K = sr;
+    pu.mode = MODE_UPDATE;
+    pu.beta = r == 0 ? al : one;
+    pu.tri = 0;
+    s = gemm<T>(pu, "update_gemm", st);
+  }
+  hsma_status_t f = hsma_ws_free(ws, st);
+  return s != HSMA_OK ? s : f;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+PFN_encodeTiled hsma_encode_fn() {
+  static PFN_encodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(p);
+  });
+  return fn;
+}
+
+bool hsma_make_map_2d(CUtensorMap *map, CUtensorMapDataType dt, int elem_bytes, const void *base, uint64_t rows,
+                      uint64_t cols, uint64_t ld_elems, uint32_t box_rows, uint32_t box_cols, CUtensorMapSwizzle swz) {
+  PFN_encodeTiled enc = hsma_encode_fn();
+  if (enc == nullptr) return false;
+  if ((uintptr_t)base % 16 != 0 || (ld_elems * elem_bytes) % 16 != 0) return false;
+  const cuuint64_t dims[2] = {rows, cols};
+  const cuuint64_t strides[1] = {ld_elems * (uint64_t)elem_bytes};
+  const cuuint32_t box[2] = {box_rows, box_cols};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+hsma_status_t hsma_blocked_solve(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
+                                 int64_t n, const double *alpha, int unit, cudaStream_t st) {
+  if (n > INT32_MAX || m > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  if (dtype == HSMA_C128)
+    return blocked_impl<cplx>(nb, static_cast<const cplx *>(A), lda, static_cast<cplx *>(B), ldb, m, n, alpha, unit,
+                              st);
+  return blocked_impl<double>(nb, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb, m, n, alpha,
+                              unit, st);
+}
+
+extern "C" HSMA_API hsma_status_t hsma_device_status(unsigned int *out) {
+  if (out == nullptr) return HSMA_ERR_INVALID_ARG;
+  unsigned int v = 0, z = 0;
+  HSMA_CUDA_TRY(cudaDeviceSynchronize());
+  HSMA_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_hsma_dev_error, sizeof v));
+  HSMA_CUDA_TRY(cudaMemcpyToSymbol(g_hsma_dev_error, &z, sizeof z));
+  *out = v;
+  return HSMA_OK;
 }

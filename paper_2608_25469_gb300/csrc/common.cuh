@@ -118,38 +118,57 @@ __host__ __device__ inline bool hsma_small_g_ok(int g, int m, bool cplx_) {
   return m <= hsma_small_rmax(g, cplx_) * g;
 }
 
-__host__ __device__ inline double hsma_small_tile_instr(int m, int g, bool cplx_) {
-  const int K = cplx_ ? 4 : 1;
-  const long R = (m + g - 1) / g;
-  long s = R;
-  for (int i = 0; i + 1 < m; ++i) s += R - (i + 1) / g;
-  return (double)K * (double)s;
+// closed form of sum_{k=1}^{N} floor(k/g)
+__host__ __device__ inline long long hsma_sum_floor(long long N, long long g) {
+  if (N <= 0) return 0;
+  const long long q = N / g, r = N % g;
+  return g * q * (q - 1) / 2 + q * (r + 1);
 }
 
-__host__ __device__ inline double hsma_small_stage_instr(int m, int g, bool cplx_) {
-  const int K = cplx_ ? 4 : 1;
-  const int RG = ((m + g - 1) / g) * g;
-  long s = 0;
-  for (int i = 0; i < m; ++i) s += (RG - 1 - i + 31) / 32;
-  return (double)K * (double)s;
+// closed form of sum_{v=0}^{V} ceil(v/32)  (0 for V < 0)
+__host__ __device__ inline long long hsma_sum_ceil32(long long V) {
+  if (V <= 0) return 0;
+  const long long a = V / 32, b = V % 32;
+  return 32 * a * (a + 1) / 2 + (a + 1) * b;
 }
 
-// total FP64 warp instructions for one (m, n) solve with row groups g
-__host__ __device__ inline double hsma_small_total_instr(int m, int n, int g, bool cplx_) {
+__host__ __device__ inline long long hsma_small_tile_instr(int m, int g, bool cplx_) {
+  const long long K = cplx_ ? 4 : 1;
+  const long long R = (m + g - 1) / g;
+  return K * (R + (long long)(m - 1) * R - hsma_sum_floor(m - 1, g));
+}
+
+__host__ __device__ inline long long hsma_small_stage_instr(int m, int g, bool cplx_) {
+  const long long K = cplx_ ? 4 : 1;
+  const long long RG = (long long)((m + g - 1) / g) * g;
+  return K * (hsma_sum_ceil32(RG - 1) - hsma_sum_ceil32(RG - m - 1));
+}
+
+// FP64 warp instructions issued for one (m, n) solve with row groups g
+__host__ __device__ inline long long hsma_small_total_instr(int m, int n, int g, bool cplx_) {
   const int C = 32 / g;
-  const int tiles = (n + C - 1) / C;
+  const long long tiles = (n + C - 1) / C;
   return tiles * hsma_small_tile_instr(m, g, cplx_) + hsma_small_stage_instr(m, g, cplx_);
 }
 
-// Row-group choices compiled into the batched kernel.
-__host__ __device__ inline int hsma_small_pick_g_batched(int m, int n, bool cplx_) {
-  const int cands[4] = {1, 2, 4, 8};
+// As above, but with the tiles dealt round-robin to the W warps of a CTA that
+// share one staged triangle: the CTA holds its warps until the busiest is done.
+__host__ __device__ inline long long hsma_small_cta_instr(int m, int n, int g, bool cplx_, int W) {
+  const int C = 32 / g;
+  const long long tiles = (n + C - 1) / C;
+  const long long rounds = (tiles + W - 1) / W;
+  return rounds * W * hsma_small_tile_instr(m, g, cplx_) + hsma_small_stage_instr(m, g, cplx_);
+}
+
+// Row-group choice of the batched kernel: the allowed set is a bit mask
+// (bit log2(G)), the cost the CTA-level one above.
+__host__ __device__ inline int hsma_small_pick_g_batched(int m, int n, bool cplx_, int W, unsigned gmask) {
   int best = 0;
-  double bc = 0.0;
-  for (int k = 0; k < 4; ++k) {
-    const int g = cands[k];
-    if (!hsma_small_g_ok(g, m, cplx_)) continue;
-    const double c = hsma_small_total_instr(m, n, g, cplx_);
+  long long bc = 0;
+  for (int lg = 0; lg < 6; ++lg) {
+    const int g = 1 << lg;
+    if (!(gmask & (1u << lg)) || !hsma_small_g_ok(g, m, cplx_)) continue;
+    const long long c = hsma_small_cta_instr(m, n, g, cplx_, W);
     if (best == 0 || c < bc) {
       best = g;
       bc = c;
@@ -163,10 +182,10 @@ __host__ __device__ inline int hsma_small_pick_g_batched(int m, int n, bool cplx
 // for 64 cycles; a dependent step costs one FP64 latency plus, for G > 1, a
 // shuffle round trip.
 __host__ __device__ inline double hsma_small_time_model(int m, int n, int g, bool cplx_, int nsm) {
-  const double tile = hsma_small_tile_instr(m, g, cplx_);
+  const double tile = (double)hsma_small_tile_instr(m, g, cplx_);
   const int C = 32 / g;
   const int tiles = (n + C - 1) / C;
-  const double stage = hsma_small_stage_instr(m, g, cplx_);
+  const double stage = (double)hsma_small_stage_instr(m, g, cplx_);
   // every CTA (two warps) stages the triangle once
   const double total = tiles * tile + stage * ((tiles + 1) / 2);
   // whole-GPU pipe: 4 sub-partitions per SM, ~84% of nominal measured

@@ -26,8 +26,21 @@
 
 namespace {
 
-constexpr int kWarpsPerCta = 2;
-constexpr int kThreads = 32 * kWarpsPerCta;
+// Warps per CTA of the single-solve kernel and of the batched kernel, the
+// batched kernel's minimum resident CTAs per SM (register cap; 0 = none) and
+// its set of row-group variants (bit log2(G)).  Defaults chosen by measurement.
+#ifndef HSMA_VB_WARPS
+#define HSMA_VB_WARPS 2
+#endif
+#ifndef HSMA_VB_MINB
+#define HSMA_VB_MINB 0
+#endif
+#ifndef HSMA_VB_GMASK
+#define HSMA_VB_GMASK 0xFu
+#endif
+constexpr int kWarpsSingle = 2;
+constexpr int kWarpsBatched = HSMA_VB_WARPS;
+constexpr unsigned kBatchedGMask = HSMA_VB_GMASK;
 
 // packed strict-lower triangle: column i holds rows i+1 .. MMAX-1
 __host__ __device__ constexpr int col_off(int i, int mmax) { return i * (mmax - 1) - (i * (i - 1)) / 2; }
@@ -42,12 +55,12 @@ struct SmemLayout {
 // Stage one instance: 1/a_rr and alpha/a_rr for r < m, then the scaled strict
 // lower triangle for rows < rows_used (rows >= m are zero).  All threads of
 // the CTA take part; ends with a CTA barrier.
-template <class T, int MMAX>
+template <class T, int MMAX, int W>
 __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict__ A, int64_t lda, int m,
                                       int rows_used, T alpha, bool unit) {
   using E = Elem<T>;
   const int tid = threadIdx.x;
-  for (int r = tid; r < MMAX; r += kThreads) {
+  for (int r = tid; r < MMAX; r += 32 * W) {
     T rv = E::one();
     if (r < m && !unit) rv = E::recip(E::ld(A + r + (int64_t)r * lda));
     sR[r] = rv;
@@ -55,7 +68,7 @@ __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  for (int i = warp; i < m; i += kWarpsPerCta) {
+  for (int i = warp; i < m; i += W) {
     T *col = sTri + col_off(i, MMAX) - i - 1;  // col[r], r > i
     const T *acol = A + (int64_t)i * lda;
     for (int r = i + 1 + lane; r < rows_used; r += 32) {
@@ -129,38 +142,41 @@ __device__ __forceinline__ void solve_tiles(const T *sTri, const T *sC, T *B, in
   }
 }
 
-template <class T>
+template <class T, int W>
 __device__ __forceinline__ void zero_tiles(T *B, int64_t ldb, int m, int n) {
-  for (int j = threadIdx.x >> 5; j < n; j += kWarpsPerCta)
+  for (int j = threadIdx.x >> 5; j < n; j += W)
     for (int r = threadIdx.x & 31; r < m; r += 32) Elem<T>::st(B + r + (int64_t)j * ldb, Elem<T>::zero());
 }
 
-// Dispatch over the row-group variants compiled for a dtype.
+// Dispatch over the row-group variants compiled into the batched kernel.
 template <class T>
-struct Variants;
-
-template <>
-struct Variants<double> {
-  __device__ __forceinline__ static void run(int g, const double *sTri, const double *sC, double *B, int64_t ldb,
-                                             int m, int n, int tile0, int step) {
-    switch (g) {
-      case 1: solve_tiles<double, 1, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
-      case 2: solve_tiles<double, 2, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
-      case 4: solve_tiles<double, 4, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
-      default: solve_tiles<double, 8, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+struct Variants {
+  static constexpr bool kCplx = sizeof(T) == sizeof(cplx);
+  __device__ __forceinline__ static void run(int g, const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n,
+                                             int tile0, int step) {
+    if constexpr ((kBatchedGMask & 1u) != 0) {
+      if (g == 1) {
+        solve_tiles<T, 1, kCplx ? 32 : 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
     }
-  }
-};
-
-template <>
-struct Variants<cplx> {
-  __device__ __forceinline__ static void run(int g, const cplx *sTri, const cplx *sC, cplx *B, int64_t ldb, int m,
-                                             int n, int tile0, int step) {
-    switch (g) {
-      case 1: solve_tiles<cplx, 1, 32>(sTri, sC, B, ldb, m, n, tile0, step); break;
-      case 2: solve_tiles<cplx, 2, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
-      case 4: solve_tiles<cplx, 4, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
-      default: solve_tiles<cplx, 8, 64>(sTri, sC, B, ldb, m, n, tile0, step); break;
+    if constexpr ((kBatchedGMask & 2u) != 0) {
+      if (g == 2) {
+        solve_tiles<T, 2, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
+    }
+    if constexpr ((kBatchedGMask & 4u) != 0) {
+      if (g == 4) {
+        solve_tiles<T, 4, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
+    }
+    if constexpr ((kBatchedGMask & 8u) != 0) {
+      if (g == 8) {
+        solve_tiles<T, 8, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
     }
   }
 };
@@ -172,14 +188,14 @@ __device__ __forceinline__ int variant_mmax(int g) {
   return (sizeof(T) == sizeof(cplx) && g == 1) ? 32 : 64;
 }
 
-template <class T>
+template <class T, int W>
 __device__ __forceinline__ void stage_any(int g, T *sTri, T *sC, T *sR, const T *A, int64_t lda, int m, T alpha,
                                           bool unit) {
   const int rows_used = ((m + g - 1) / g) * g;
   if (variant_mmax<T>(g) == 32)
-    stage<T, 32>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
+    stage<T, 32, W>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
   else
-    stage<T, 64>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
+    stage<T, 64, W>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
 }
 
 template <class T>
@@ -194,14 +210,14 @@ __device__ __forceinline__ void smem_parts(unsigned char *smem, T *&sTri, T *&sC
 // k*W, k*W+1, ... (W warps per CTA).
 // ---------------------------------------------------------------------------
 template <class T, int G, int MMAX>
-__global__ void __launch_bounds__(kThreads) small_single_kernel(const T *__restrict__ A, int64_t lda, T *B,
+__global__ void __launch_bounds__(32 * kWarpsSingle) small_single_kernel(const T *__restrict__ A, int64_t lda, T *B,
                                                                  int64_t ldb, int m, int n, T alpha, int unit) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *sTri, *sC, *sR;
   smem_parts<T>(smem, sTri, sC, sR);
   const int rows_used = ((m + G - 1) / G) * G;
-  stage<T, MMAX>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0);
-  solve_tiles<T, G, MMAX>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsPerCta, gridDim.x * kWarpsPerCta);
+  stage<T, MMAX, kWarpsSingle>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0);
+  solve_tiles<T, G, MMAX>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsSingle, gridDim.x * kWarpsSingle);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,9 +230,11 @@ __global__ void __launch_bounds__(kThreads) small_single_kernel(const T *__restr
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 256;
 
-__device__ __forceinline__ int cost_bucket(double cost) {
-  // 8 buckets per octave, 32 octaves
-  int b = (int)(log2(cost > 1.0 ? cost : 1.0) * 8.0);
+__device__ __forceinline__ int cost_bucket(long long cost) {
+  // 8 buckets per octave: the octave and the three bits below the leading one
+  if (cost < 16) return 0;
+  const int lead = 63 - __clzll(cost);
+  const int b = lead * 8 + (int)((cost >> (lead - 3)) & 7);
   return b < kBuckets ? b : kBuckets - 1;
 }
 
@@ -246,8 +264,8 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
       err |= HSMA_DEVERR_NULL_PTR;
       continue;
     }
-    const int g = hsma_small_pick_g_batched(m, n, cplx_);
-    atomicAdd(&hist[cost_bucket(hsma_small_total_instr(m, n, g, cplx_))], 1);
+    const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
+    atomicAdd(&hist[cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched))], 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -265,15 +283,15 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
     const int lo = m > 1 ? m : 1;
     if (m <= 0 || n <= 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) continue;
     if (dA[b] == nullptr || dB[b] == nullptr) continue;
-    const int g = hsma_small_pick_g_batched(m, n, cplx_);
-    const int pos = atomicAdd(&offs[cost_bucket(hsma_small_total_instr(m, n, g, cplx_))], 1);
+    const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
+    const int pos = atomicAdd(&offs[cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched))], 1);
     scratch[2 + pos] = b | (g << 24);
   }
   if (err != 0 && status != nullptr) atomicOr(status, err);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) vbatched_solve_kernel(const int32_t *__restrict__ dm,
+__global__ void __launch_bounds__(32 * kWarpsBatched, HSMA_VB_MINB) vbatched_solve_kernel(const int32_t *__restrict__ dm,
                                                                   const int32_t *__restrict__ dn,
                                                                   const int32_t *__restrict__ dlda,
                                                                   const int32_t *__restrict__ dldb,
@@ -299,11 +317,11 @@ __global__ void __launch_bounds__(kThreads) vbatched_solve_kernel(const int32_t 
     T *B = static_cast<T *>(dB[b]);
     const int64_t lda = dlda[b], ldb = dldb[b];
     if (azero) {
-      zero_tiles<T>(B, ldb, m, n);
+      zero_tiles<T, kWarpsBatched>(B, ldb, m, n);
       continue;
     }
-    stage_any<T>(g, sTri, sC, sR, A, lda, m, alpha, unit != 0);
-    Variants<T>::run(g, sTri, sC, B, ldb, m, n, 0, kWarpsPerCta);
+    stage_any<T, kWarpsBatched>(g, sTri, sC, sR, A, lda, m, alpha, unit != 0);
+    Variants<T>::run(g, sTri, sC, B, ldb, m, n, 0, kWarpsBatched);
     __syncthreads();  // the next item restages shared memory
   }
 }
@@ -314,7 +332,7 @@ int persistent_grid(int dev) {
   if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
   int nsm = 0, per_sm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_solve_kernel<T>, kThreads,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_solve_kernel<T>, 32 * kWarpsBatched,
                                                 SmemLayout<T>::bytes(64));
   int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (dev >= 0 && dev < 64) cached[dev] = grid;
@@ -333,7 +351,7 @@ hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m,
                               int nsm, cudaStream_t st) {
   constexpr int C = 32 / G;
   const int tiles = (n + C - 1) / C;
-  int grid = (tiles + kWarpsPerCta - 1) / kWarpsPerCta;
+  int grid = (tiles + kWarpsSingle - 1) / kWarpsSingle;
   const int cap = nsm * 16;
   if (grid > cap) grid = cap;
   const size_t bytes = SmemLayout<T>::bytes(64);
@@ -344,7 +362,7 @@ hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m,
     attr_done.set();
   }
   HsmaTraceScope ts("small_single", st);
-  small_single_kernel<T, G, MMAX><<<grid, kThreads, bytes, st>>>(A, lda, B, ldb, m, n, alpha, unit);
+  small_single_kernel<T, G, MMAX><<<grid, 32 * kWarpsSingle, bytes, st>>>(A, lda, B, ldb, m, n, alpha, unit);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
@@ -428,8 +446,8 @@ static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32
   if (grid > batch) grid = batch;
   {
     HsmaTraceScope ts("vbatched_solve", st);
-    vbatched_solve_kernel<T><<<grid, kThreads, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dA, dB, al,
-                                                                               unit, scratch);
+    vbatched_solve_kernel<T><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dA,
+                                                                                          dB, al, unit, scratch);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;

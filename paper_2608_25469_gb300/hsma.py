@@ -23,14 +23,15 @@ R64, C128, R32_BF16, R64_IR = 0, 1, 2, 3
 NON_UNIT, UNIT = 0, 1
 PATH_AUTO, PATH_SMALL, PATH_BLOCKED = 0, 1, 2
 OK = 0
-DEVERR_BAD_SIZE, DEVERR_NULL_PTR = 0x1, 0x2
+DEVERR_BAD_SIZE, DEVERR_NULL_PTR, DEVERR_TIMEOUT = 0x1, 0x2, 0x4
 STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTED", 3: "HSMA_ERR_NO_MEMORY",
                 4: "HSMA_ERR_CUDA", 5: "HSMA_ERR_TIMEOUT", 6: "HSMA_ERR_NOT_CONVERGED", 7: "HSMA_ERR_BUSY"}
 
 # Every function include/hsma.h declares (checked by the tests against the header).
 EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_llnn_ex",
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
-           "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset"]
+           "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
+           "hsma_device_status"]
 
 
 class HsmaError(RuntimeError):
@@ -86,6 +87,8 @@ def _load():
     lib.hsma_trace_read.restype = c_int
     lib.hsma_trace_launches.restype = ctypes.c_longlong
     lib.hsma_trace_reset.restype = None
+    lib.hsma_device_status.argtypes = [ctypes.POINTER(ctypes.c_uint)]
+    lib.hsma_device_status.restype = c_int
     return lib
 
 
@@ -161,6 +164,13 @@ def hsma_gen_matrix(dtype, kind, seed, inst, m, cols, dst, ld, stream=0, check=T
     if check:
         _check(s, "hsma_gen_matrix")
     return s
+
+
+def hsma_device_status() -> int:
+    """Device error bits raised since the last call (synchronises the device)."""
+    v = ctypes.c_uint()
+    _check(_lib.hsma_device_status(ctypes.byref(v)), "hsma_device_status")
+    return v.value
 
 
 def hsma_trace_enable(on: bool) -> int:

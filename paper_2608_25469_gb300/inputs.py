@@ -119,6 +119,18 @@ def gen_B(seed: int, m: int, n: int, dtype: int = R64, inst: int = -1) -> np.nda
     return np.asfortranarray(re + 1j * im)
 
 
+def gen_B_cols(seed: int, m: int, cols, dtype: int = R64, inst: int = -1) -> np.ndarray:
+    """Selected columns of B (the same values gen_B would give), shape (m, len(cols))."""
+    cols = np.asarray(cols, dtype=np.uint64)
+    idx = (np.arange(m, dtype=np.uint64)[:, None] + cols[None, :] * np.uint64(m)).ravel(order="F")
+    shape = (m, len(cols))
+    re = (2.0 * u01(seed, stream_id(B_RE, inst), idx) - 1.0).reshape(shape, order="F")
+    if dtype == R64:
+        return np.asfortranarray(re)
+    im = (2.0 * u01(seed, stream_id(B_IM, inst), idx) - 1.0).reshape(shape, order="F")
+    return np.asfortranarray(re + 1j * im)
+
+
 def batched_sizes(seed: int, batch: int, lo: int = 8, hi: int = 64):
     """(m_i, n_i) for the varlen batched workload: each uniform on {lo, ..., hi}."""
     idx = np.arange(batch, dtype=np.uint64)
@@ -163,7 +175,7 @@ def flops_trsm(m, n, complex_: bool) -> float:
 
 
 __all__ = [
-    "u64", "u01", "key", "stream_id", "gen_A", "gen_B", "batched_sizes",
+    "u64", "u01", "key", "stream_id", "gen_A", "gen_B", "gen_B_cols", "batched_sizes",
     "serving_requests", "embed", "flops_trsm", "R64", "C128",
     "A_RE", "B_RE", "A_IM", "B_IM",
 ]

@@ -59,3 +59,9 @@ def test_serving_stream():
     assert np.all(np.diff(t) >= 0)
     assert abs(20000 / t[-1] - 2000) < 60
     assert abs((dt == I.R64).mean() - 0.7) < 0.02
+
+
+def test_gen_B_cols_matches_gen_B():
+    B = I.gen_B(4, 29, 13, I.C128, inst=2)
+    cols = [0, 12, 5]
+    assert np.array_equal(I.gen_B_cols(4, 29, cols, I.C128, inst=2), B[:, cols])

@@ -96,10 +96,10 @@ def test_poison_and_canaries(H, code):
     ref = oracle.solve(A0, B0, alpha)
     assert oracle.forward_error(X[:m], ref) <= TOL
     # unit diagonal: diagonal holds NaN and must not be read
-    Au = A.copy()
+    Au = np.array(A, order="F")
     np.fill_diagonal(Au[:m], np.nan)
     Xu = _solve_single(H, code, Au, Bb, alpha, unit=True)
-    A1 = A0.copy()
+    A1 = np.array(A0, order="F")
     np.fill_diagonal(A1, 1.0)
     refu = oracle.solve(A1, B0, alpha)
     assert oracle.forward_error(Xu[:m], refu) <= TOL

@@ -192,6 +192,16 @@ HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64
                               int64_t cols, void *dst, int64_t ld, void *stream);
 
 /*
+ * BF16 tensor-core update used by HSMA_R32_BF16 (exposed for direct use and
+ * testing): C = beta*C - A * Bt^T with A (M x K) and Bt (N x K) row-major
+ * BF16 (K contiguous; K a positive multiple of 64) and C (M x N) column-major
+ * FP32 with leading dimension ldc.  Products accumulate in FP32 in tensor
+ * memory (tcgen05.mma kind::f16).  Device pointers; A and Bt 16-byte aligned.
+ */
+HSMA_API hsma_status_t hsma_gemm_bf16_update(int64_t M, int64_t N, int64_t K, const void *A, const void *Bt,
+                                             float beta, float *C, int64_t ldc, void *stream);
+
+/*
  * Device-side error bits the library's kernels raise (a bounded wait that ran
  * out: HSMA_DEVERR_TIMEOUT).  Synchronises the device, returns the bits
  * accumulated since the last call in *out, and clears them.

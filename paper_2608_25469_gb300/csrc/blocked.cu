@@ -154,7 +154,10 @@ struct GemmArgs {
   int M, N, K;
   int mode;  // UPDATE: C = beta*C - A*B;  SCALE: C = beta*(A*B)
   T beta;
-  int tri;  // A is lower triangular: row tile i0 needs k < i0 + BM only
+  int tri;     // A is lower triangular: row tile i0 needs k < i0 + BM only
+  int mask;    // read only A's lower triangle (zeros above; ones on the diagonal if unit); plain loads
+  int unit;
+  const int *skip;  // device flag: when set, the launch does nothing
   unsigned int *err;
   uint64_t limit_ns;
 };
@@ -289,6 +292,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const GemmArgs<T> p,
   auto sA = [&](int s) { return reinterpret_cast<T *>(smem + s * stage_bytes<T>()); };
   auto sB = [&](int s) { return reinterpret_cast<T *>(smem + s * stage_bytes<T>() + BK * BM * sizeof(T)); };
 
+  if (p.skip != nullptr && *(volatile const int *)p.skip != 0) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wm = warp & 1, wn = warp >> 1, g = lane >> 2, t = lane & 3;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -336,7 +340,9 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const GemmArgs<T> p,
       for (int e = tid; e < BK * BM; e += GEMM_THREADS) {
         const int kk = e / BM, mm = e % BM;
         const int row = m0 + mm, col = k0 + kk;
-        a[e] = (row < p.M && col < p.K) ? E::ld(p.A + row + (int64_t)col * p.lda) : E::zero();
+        T v = (row < p.M && col < p.K && !(p.mask && col > row)) ? E::ld(p.A + row + (int64_t)col * p.lda) : E::zero();
+        if (p.mask && p.unit && col == row && row < p.M) v = E::one();
+        a[e] = v;
       }
       for (int e = tid; e < BN * BK; e += GEMM_THREADS) {
         const int nn = e / BK, kk = e % BK;
@@ -373,13 +379,6 @@ bool tma_ok(const void *p, int64_t ld) {
   return ((uintptr_t)p % 16 == 0) && ((ld * (int64_t)sizeof(T)) % 16 == 0);
 }
 
-unsigned int *dev_error_ptr() {
-  static unsigned int *p = nullptr;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lk(mu);
-  if (p == nullptr) cudaGetSymbolAddress((void **)&p, g_hsma_dev_error);
-  return p;
-}
 
 // Launch one product.  `phase` names it for the tracer.
 template <class T>
@@ -388,9 +387,10 @@ hsma_status_t gemm(const GemmArgs<T> &p0, const char *phase, cudaStream_t st) {
   hsma_status_t s = gemm_attrs<T>();
   if (s != HSMA_OK) return s;
   GemmArgs<T> p = p0;
-  p.err = dev_error_ptr();
+  p.err = hsma_dev_error_ptr();
+  if (p.err == nullptr) return HSMA_ERR_CUDA;
   if (p.limit_ns == 0) p.limit_ns = 4000000000ull;  // 4 s of wall time per barrier wait
-  const bool use_tma = tma_ok<T>(p.A, p.lda) && tma_ok<T>(p.Bm, p.ldb);
+  const bool use_tma = !p.mask && tma_ok<T>(p.A, p.lda) && tma_ok<T>(p.Bm, p.ldb);
   CUtensorMap ma, mb;
   std::memset(&ma, 0, sizeof ma);
   std::memset(&mb, 0, sizeof mb);
@@ -512,6 +512,51 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
 }
 
 }  // namespace
+
+unsigned int *hsma_dev_error_ptr() {
+  static unsigned int *ptr[64] = {nullptr};
+  static std::mutex mu;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (ptr[d] == nullptr && cudaGetSymbolAddress((void **)&ptr[d], g_hsma_dev_error) != cudaSuccess) ptr[d] = nullptr;
+  return ptr[d];
+}
+
+hsma_status_t hsma_diag_inverse(int dtype, int nb, const void *A, int64_t lda, int64_t m, int unit, void *Dinv,
+                                cudaStream_t st) {
+  switch (dtype) {
+    case HSMA_C128:
+      return launch_inverse<cplx>(nb, static_cast<const cplx *>(A), lda, m, unit, static_cast<cplx *>(Dinv), st);
+    case HSMA_R32_BF16:
+      return launch_inverse<float>(nb, static_cast<const float *>(A), lda, m, unit, static_cast<float *>(Dinv), st);
+    default:
+      return launch_inverse<double>(nb, static_cast<const double *>(A), lda, m, unit, static_cast<double *>(Dinv),
+                                    st);
+  }
+}
+
+hsma_status_t hsma_residual_f64(const double *A, int64_t lda, int unit, const double *X, int64_t ldx, double *C,
+                                int64_t ldc, int64_t m, int64_t n, double beta, const int *skip, cudaStream_t st) {
+  if (m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  GemmArgs<double> p{};
+  p.A = A;
+  p.lda = lda;
+  p.Bm = X;
+  p.ldb = ldx;
+  p.C = C;
+  p.ldc = ldc;
+  p.M = (int)m;
+  p.N = (int)n;
+  p.K = (int)m;
+  p.mode = MODE_UPDATE;
+  p.beta = beta;
+  p.tri = 1;
+  p.mask = 1;
+  p.unit = unit;
+  p.skip = skip;
+  return gemm<double>(p, "residual", st);
+}
 
 // ---------------------------------------------------------------------------
 PFN_encodeTiled hsma_encode_fn() {

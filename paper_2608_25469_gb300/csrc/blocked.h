@@ -9,3 +9,21 @@
 // diagonal block size nb.  Arguments already validated; alpha != 0.
 hsma_status_t hsma_blocked_solve(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
                                  int64_t n, const double *alpha, int unit, cudaStream_t st);
+
+// Phase 1 alone: invert the N_B x N_B diagonal blocks of the lower triangle of
+// A (dtype HSMA_R64, HSMA_C128 or HSMA_R32_BF16 for float data) into Dinv
+// (ceil(m/nb) blocks of nb x nb, column-major, ld nb, zeros above the diagonal
+// and outside a partial last block).  nb in {32, 64, 128, 256, 512}.
+hsma_status_t hsma_diag_inverse(int dtype, int nb, const void *A, int64_t lda, int64_t m, int unit, void *Dinv,
+                                cudaStream_t st);
+
+// FP64 product used by the refinement residual: C = beta*C - L*X with L the
+// lower triangle of A (unit diagonal if unit), all column-major fp64 (m x m,
+// m x n).  If skip is non-NULL and *skip != 0 on the device, the launch does
+// nothing.
+hsma_status_t hsma_residual_f64(const double *A, int64_t lda, int unit, const double *X, int64_t ldx, double *C,
+                                int64_t ldc, int64_t m, int64_t n, double beta, const int *skip, cudaStream_t st);
+
+// Device address (current device) of the library's device error word, whose
+// HSMA_DEVERR_* bits kernels raise; NULL on a CUDA error.
+unsigned int *hsma_dev_error_ptr();

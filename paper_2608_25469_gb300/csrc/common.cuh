@@ -44,6 +44,20 @@ struct Elem<double> {
 };
 
 template <>
+struct Elem<float> {
+  static constexpr int kFlopsPerFma = 1;
+  __device__ __forceinline__ static float zero() { return 0.0f; }
+  __device__ __forceinline__ static float one() { return 1.0f; }
+  __device__ __forceinline__ static float mul(float a, float b) { return a * b; }
+  __device__ __forceinline__ static float fms(float a, float x, float s) { return fmaf(-a, x, s); }
+  __device__ __forceinline__ static float recip(float a) { return 1.0f / a; }
+  __device__ __forceinline__ static float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  __device__ __forceinline__ static float ld(const float *p) { return __ldg(p); }
+  __device__ __forceinline__ static void st(float *p, float v) { *p = v; }
+  __device__ __forceinline__ static bool is_zero(float a) { return a == 0.0f; }
+};
+
+template <>
 struct Elem<cplx> {
   static constexpr int kFlopsPerFma = 4;
   __device__ __forceinline__ static cplx zero() { return cplx{0.0, 0.0}; }

@@ -1,9 +1,533 @@
+// Reduced-precision modes of the blocked solve (the paper lists mixed
+// precision as future work, Section 6; the blocked algorithm is Section 4.3).
+//
+// FP32-result mode (HSMA_R32_BF16): phase 1 inverts the diagonal blocks in
+// FP32; phase 2 forms X_r = D_r^{-1} B_r with FP32 FMAs and applies the
+// trailing update B_{r+1:} -= A_{r+1:,r} X_r on the 5th-generation tensor
+// cores: operands in BF16, products accumulated in FP32 in tensor memory
+// (tcgen05.mma kind::f16, cta_group::1, 128 x 256 tiles, TMA loads with
+// 128-byte swizzle).  With three terms per update the operands are split,
+// a = hi(a) + lo(a), and the products hi*hi + hi*lo + lo*hi are accumulated in
+// one pass by concatenating along K: [A_hi A_hi A_lo] [X_hi; X_lo; X_hi].
+//
+// FP64-result mode (HSMA_R64_IR): X_0 from the FP32-result solve of the
+// rounded data, then iterative refinement: R = alpha B - L X in FP64 (FP64
+// tensor products), C from the FP32-result solve of L C = R, X += C in FP64,
+// until ||R||_F / (||L||_F ||X||_F + |alpha| ||B||_F) <= tol.  Every
+// refinement kernel checks a device-side "converged" flag first, so the host
+// enqueues the maximum number of steps without waiting on the device.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "blocked.h"
+#include "common.cuh"
 #include "mixed.h"
-hsma_status_t hsma_mixed_r32(int, int, const float *, int64_t, float *, int64_t, int64_t, int64_t, double, int,
-                             cudaStream_t) {
-  return HSMA_ERR_UNSUPPORTED;
+#include "tma.cuh"
+#include "trace.h"
+#include "workspace.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// tcgen05 BF16 x BF16 -> FP32 update:  C (M x N, column-major fp32) =
+// beta*C - A' B'^T with A' (M x K) and B' (N x K) row-major BF16 (K-major).
+// ---------------------------------------------------------------------------
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;
+constexpr uint32_t TC_TMEM_COLS = 256;
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in groups of 8 (1024 bytes apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;              // leading-dimension offset (unused with this swizzle)
+  d |= (uint64_t)(1024u >> 4) << 32;    // stride between 8-row groups
+  d |= (uint64_t)1u << 46;              // descriptor version
+  d |= (uint64_t)2u << 61;              // 128-byte swizzle
+  return d;
 }
-hsma_status_t hsma_mixed_ir(int, const hsma_opts_t *, const double *, int64_t, double *, int64_t, int64_t, int64_t,
-                            double, int, cudaStream_t, hsma_info_t *) {
-  return HSMA_ERR_UNSUPPORTED;
+
+// Instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__global__ void __launch_bounds__(128, 1) bf16_update_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                             const __grid_constant__ CUtensorMap mapB, float *C,
+                                                             int64_t ldc, int M, int N, int K, float beta,
+                                                             unsigned int *err, uint64_t limit_ns) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[TC_STAGES];
+  __shared__ __align__(8) uint64_t empty[TC_STAGES];
+  __shared__ __align__(8) uint64_t accum;
+  __shared__ uint32_t tmem_base;
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const int nk = K / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads into a ring of stages
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (kb >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((kb / TC_STAGES) - 1) & 1, limit_ns, err)) break;
+      unsigned char *sa = smem + s * TC_STAGE_BYTES;
+      mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+      tma_load_2d(sa, &mapA, &full[s], kb * TC_BK, m0);
+      tma_load_2d(sa + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: four K = 16 steps per stage; each stage is released by a commit
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (!mbar_wait_bounded(&full[s], (kb / TC_STAGES) & 1, limit_ns, err)) break;
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
+      const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TC_A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da + 2ull * kk), "l"(db + 2ull * kk), "r"(tc_idesc()), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty[s]))
+                   : "memory");
+    }
+    // signals the epilogue once every issued product has landed in tensor memory
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&accum))
+                 : "memory");
+  }
+  __syncwarp();
+
+  // epilogue: thread = one row of the 128-row tile (its tensor-memory lane)
+  // tcgen05.ld is warp-collective: the whole warp takes the same branch
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accum, 0, limit_ns, err));
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+            "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) {
+            float *cp = C + row + (int64_t)col * ldc;
+            const float a = __uint_as_float(v[j]);
+            *cp = (beta == 1.0f) ? (*cp - a) : fmaf(beta, *cp, -a);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 products on the CUDA cores: C = beta*(A*B), A optionally lower
+// triangular (row tile i0 reads k < i0 + 64 only).  64 x 64 tiles, 4 x 4 per
+// thread.
+// ---------------------------------------------------------------------------
+constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16;
+
+__global__ void __launch_bounds__(256) sgemm_scale_kernel(const float *__restrict__ A, int64_t lda,
+                                                          const float *__restrict__ Bm, int64_t ldb, float *C,
+                                                          int64_t ldc, int M, int N, int K, float beta, int tri) {
+  __shared__ float sA[SG_BK][SG_BM];
+  __shared__ float sB[SG_BN][SG_BK + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.x * SG_BM, n0 = blockIdx.y * SG_BN;
+  const int kend = tri ? min(K, m0 + SG_BM) : K;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < kend; k0 += SG_BK) {
+    for (int e = tid; e < SG_BK * SG_BM; e += 256) {
+      const int kk = e / SG_BM, mm = e % SG_BM;
+      const int row = m0 + mm, col = k0 + kk;
+      sA[kk][mm] = (row < M && col < K) ? A[row + (int64_t)col * lda] : 0.0f;
+    }
+    for (int e = tid; e < SG_BN * SG_BK; e += 256) {
+      const int nn = e / SG_BK, kk = e % SG_BK;
+      const int row = k0 + kk, col = n0 + nn;
+      sB[nn][kk] = (row < K && col < N) ? Bm[row + (int64_t)col * ldb] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[ty + 16 * j][kk];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = m0 + tx + 16 * i, col = n0 + ty + 16 * j;
+      if (row < M && col < N) C[row + (int64_t)col * ldc] = beta * acc[i][j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Conversions to the tensor-core operand layouts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// A panel (rows x nb, column-major fp32, lda) -> A' rows x Kp row-major BF16:
+// terms 1: [hi], terms 3: [hi | hi | lo]; columns past terms*nb are zero.
+__global__ void __launch_bounds__(256) convert_panel_kernel(const float *__restrict__ A, int64_t lda, int rows,
+                                                            int nb, int terms, int Kp, __nv_bfloat16 *out) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int kk = ty; kk < 32; kk += 8) {
+    const int i = i0 + tx, k = k0 + kk;
+    tile[kk][tx] = (i < rows && k < nb) ? A[i + (int64_t)k * lda] : 0.0f;
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, k = k0 + tx;
+    if (i >= rows) continue;
+    __nv_bfloat16 *o = out + (int64_t)i * Kp;
+    if (k < nb) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(tile[tx][ii], hi, lo);
+      o[k] = hi;
+      if (terms == 3) {
+        o[nb + k] = hi;
+        o[2 * nb + k] = lo;
+      }
+    }
+    // zero padding columns [terms*nb, Kp)
+    for (int kp = terms * nb + k0 + tx; kp < Kp && blockIdx.y == 0; kp += 32) o[kp] = __float2bfloat16_rn(0.0f);
+  }
+}
+
+// X_r (nb x n, column-major fp32, ldx) -> X' n x Kp row-major BF16:
+// terms 1: [hi], terms 3: [hi | lo | hi]; zero padding to Kp.
+__global__ void __launch_bounds__(256) convert_x_kernel(const float *__restrict__ X, int64_t ldx, int nb, int n,
+                                                        int terms, int Kp, __nv_bfloat16 *out) {
+  const int64_t total = (int64_t)n * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / Kp), kp = (int)(e % Kp);
+    const int part = kp / nb, k = kp % nb;
+    float v = 0.0f;
+    if (part < terms) {
+      const float x = X[k + (int64_t)j * ldx];
+      __nv_bfloat16 hi, lo;
+      split_bf16(x, hi, lo);
+      out[e] = (terms == 3 && part == 1) ? lo : hi;
+      continue;
+    }
+    out[e] = __float2bfloat16_rn(v);
+  }
+}
+
+int g_launch_grid(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32);
+}
+
+hsma_status_t bf16_update(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, int M, int N, int Kp, float beta, float *C,
+                          int64_t ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return HSMA_OK;
+  if (Kp % TC_BK != 0 || Kp <= 0) return HSMA_ERR_INVALID_ARG;
+  static DeviceFlags attr;
+  if (!attr.test()) {
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(bf16_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    attr.set();
+  }
+  CUtensorMap ma, mb;
+  if (!hsma_make_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Ap, (uint64_t)Kp, (uint64_t)M, (uint64_t)Kp, TC_BK,
+                        TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !hsma_make_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bp, (uint64_t)Kp, (uint64_t)N, (uint64_t)Kp, TC_BK,
+                        TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
+    return HSMA_ERR_CUDA;
+  unsigned int *err = hsma_dev_error_ptr();
+  if (err == nullptr) return HSMA_ERR_CUDA;
+  dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
+  HsmaTraceScope ts("update_bf16", st);
+  bf16_update_kernel<<<grid, 128, TC_SMEM, st>>>(ma, mb, C, ldc, M, N, Kp, beta, err, 4000000000ull);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+hsma_status_t sgemm_scale(const float *A, int64_t lda, const float *Bm, int64_t ldb, float *C, int64_t ldc, int M,
+                          int N, int K, float beta, int tri, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return HSMA_OK;
+  dim3 grid((M + SG_BM - 1) / SG_BM, (N + SG_BN - 1) / SG_BN);
+  if (grid.y > 65535) return HSMA_ERR_UNSUPPORTED;
+  HsmaTraceScope ts("solve_sgemm", st);
+  sgemm_scale_kernel<<<grid, 256, 0, st>>>(A, lda, Bm, ldb, C, ldc, M, N, K, beta, tri);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// FP32-result blocked solve in place on B (fp32).  Workspace from the pool.
+hsma_status_t r32_solve(int nb, int terms, const float *A, int64_t lda, float *B, int64_t ldb, int64_t m, int64_t n,
+                        float alpha, int unit, cudaStream_t st) {
+  if (nb < 32) nb = 32;
+  const int64_t nblk = (m + nb - 1) / nb;
+  const int Kp = round_up(terms * nb, TC_BK);
+  const int64_t rows_max = std::max<int64_t>(m - nb, 1);
+  const size_t dinv_b = sizeof(float) * (size_t)nblk * nb * nb;
+  const size_t w_b = sizeof(float) * (size_t)nb * n;
+  const size_t a_b = sizeof(__nv_bfloat16) * (size_t)rows_max * Kp;
+  const size_t x_b = sizeof(__nv_bfloat16) * (size_t)n * Kp;
+  auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+  void *ws = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&ws, al(dinv_b) + al(w_b) + al(a_b) + al(x_b), st);
+  if (s != HSMA_OK) return s;
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  float *Dinv = reinterpret_cast<float *>(base);
+  float *W = reinterpret_cast<float *>(base + al(dinv_b));
+  __nv_bfloat16 *Ap = reinterpret_cast<__nv_bfloat16 *>(base + al(dinv_b) + al(w_b));
+  __nv_bfloat16 *Xp = reinterpret_cast<__nv_bfloat16 *>(base + al(dinv_b) + al(w_b) + al(a_b));
+  s = hsma_diag_inverse(HSMA_R32_BF16, nb, A, lda, m, unit, Dinv, st);
+  for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
+    const int64_t r0 = r * nb;
+    const int sr = (int)std::min<int64_t>(nb, m - r0);
+    {
+      HsmaTraceScope ts("copy", st);
+      cudaError_t e = cudaMemcpy2DAsync(W, sizeof(float) * nb, B + r0, sizeof(float) * ldb, sizeof(float) * sr, n,
+                                        cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) {
+        s = hsma_from_cuda(e);
+        break;
+      }
+    }
+    s = sgemm_scale(Dinv + (size_t)r * nb * nb, nb, W, nb, B + r0, ldb, sr, (int)n, sr, r == 0 ? alpha : 1.0f, 1, st);
+    if (s != HSMA_OK || r0 + sr >= m) break;
+    const int rows = (int)(m - r0 - sr);
+    {
+      HsmaTraceScope ts("convert", st);
+      dim3 g1((rows + 31) / 32, (nb + 31) / 32);
+      convert_panel_kernel<<<g1, 256, 0, st>>>(A + (r0 + sr) + r0 * lda, lda, rows, nb, terms, Kp, Ap);
+      convert_x_kernel<<<g_launch_grid((int64_t)n * Kp), 256, 0, st>>>(B + r0, ldb, nb, (int)n, terms, Kp, Xp);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        s = hsma_from_cuda(e);
+        break;
+      }
+    }
+    s = bf16_update(Ap, Xp, rows, (int)n, Kp, r == 0 ? alpha : 1.0f, B + r0 + sr, ldb, st);
+  }
+  hsma_status_t f = hsma_ws_free(ws, st);
+  return s != HSMA_OK ? s : f;
+}
+
+// ---------------------------------------------------------------------------
+// Refinement helpers (each returns at once when *flag is set)
+// ---------------------------------------------------------------------------
+__global__ void f64_to_f32_kernel(const double *__restrict__ src, int64_t lds, float *dst, int64_t ldd, int64_t rows,
+                                  int64_t cols, int lower, const int *flag) {
+  if (flag != nullptr && *(volatile const int *)flag) return;
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    if (lower && i < j) continue;
+    dst[i + j * ldd] = (float)src[i + j * lds];
+  }
+}
+
+// X += (double) C   (or X = (double) C when assign)
+__global__ void accumulate_kernel(double *X, int64_t ldx, const float *__restrict__ Cc, int64_t ldc, int64_t rows,
+                                  int64_t cols, int assign, const int *flag) {
+  if (flag != nullptr && *(volatile const int *)flag) return;
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    const double c = (double)Cc[i + j * ldc];
+    X[i + j * ldx] = assign ? c : X[i + j * ldx] + c;
+  }
+}
+
+// sums[slot] += sum of squares (lower triangle only when lower; unit diagonal counts 1)
+__global__ void sumsq_kernel(const double *__restrict__ M_, int64_t ld, int64_t rows, int64_t cols, int lower,
+                             int unit, double *sums, int slot, const int *flag) {
+  if (flag != nullptr && *(volatile const int *)flag) return;
+  double acc = 0.0;
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    if (lower && i < j) continue;
+    const double v = (lower && unit && i == j) ? 1.0 : M_[i + j * ld];
+    acc = fma(v, v, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&sums[slot], acc);
+}
+
+// sums: [0] ||L||^2, [1] ||B||^2, [2] ||R||^2, [3] ||X||^2; state: [0] converged, [1] steps, [2..3] eta (double)
+__global__ void check_kernel(double *sums, int *state, double alpha_abs, double tol, int step) {
+  if (state[0]) return;
+  const double nr = sqrt(sums[2]), den = sqrt(sums[0]) * sqrt(sums[3]) + alpha_abs * sqrt(sums[1]);
+  const double eta = den > 0.0 ? nr / den : nr;
+  *reinterpret_cast<double *>(state + 2) = eta;
+  state[1] = step;
+  if (eta <= tol) state[0] = 1;
+  sums[2] = 0.0;
+  sums[3] = 0.0;
+}
+
+}  // namespace
+
+hsma_status_t hsma_mixed_r32(int nb, int bf16_terms, const float *A, int64_t lda, float *B, int64_t ldb, int64_t m,
+                             int64_t n, double alpha, int unit, cudaStream_t st) {
+  const int terms = bf16_terms == 0 ? 3 : bf16_terms;
+  if (terms != 1 && terms != 3) return HSMA_ERR_INVALID_ARG;
+  if (m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  return r32_solve(nb, terms, A, lda, B, ldb, m, n, (float)alpha, unit, st);
+}
+
+hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, int64_t lda, double *B, int64_t ldb,
+                            int64_t m, int64_t n, double alpha, int unit, cudaStream_t st, hsma_info_t *info) {
+  const int terms = (opts && opts->bf16_terms) ? opts->bf16_terms : 3;
+  const int itmax = (opts && opts->ir_max_iter > 0) ? opts->ir_max_iter : 10;
+  const double tol = (opts && opts->ir_tol > 0.0) ? opts->ir_tol : 1e-15;
+  if (terms != 1 && terms != 3) return HSMA_ERR_INVALID_ARG;
+  if (m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+  const size_t a32_b = sizeof(float) * (size_t)m * m;
+  const size_t r32_b = sizeof(float) * (size_t)m * n;
+  const size_t b0_b = sizeof(double) * (size_t)m * n;
+  const size_t r64_b = b0_b;
+  const size_t st_b = 1024;
+  void *ws = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&ws, al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b, st);
+  if (s != HSMA_OK) return s;
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  float *A32 = reinterpret_cast<float *>(base);
+  float *R32 = reinterpret_cast<float *>(base + al(a32_b));
+  double *B0 = reinterpret_cast<double *>(base + al(a32_b) + al(r32_b));
+  double *R64 = reinterpret_cast<double *>(base + al(a32_b) + al(r32_b) + al(b0_b));
+  double *sums = reinterpret_cast<double *>(base + al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b));
+  int *state = reinterpret_cast<int *>(sums + 8);
+  const int grid = g_launch_grid(m * n);
+  auto fail = [&](cudaError_t e) { return e == cudaSuccess ? HSMA_OK : hsma_from_cuda(e); };
+  do {
+    if ((s = fail(cudaMemsetAsync(sums, 0, st_b, st))) != HSMA_OK) break;
+    if ((s = fail(cudaMemcpy2DAsync(B0, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, n,
+                                    cudaMemcpyDeviceToDevice, st))) != HSMA_OK)
+      break;
+    {
+      HsmaTraceScope ts("convert", st);
+      f64_to_f32_kernel<<<g_launch_grid(m * m), 256, 0, st>>>(A, lda, A32, m, m, m, 1, nullptr);
+      f64_to_f32_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 0, nullptr);
+      sumsq_kernel<<<g_launch_grid(m * m), 256, 0, st>>>(A, lda, m, m, 1, unit, sums, 0, nullptr);
+      sumsq_kernel<<<grid, 256, 0, st>>>(B0, m, m, n, 0, 0, sums, 1, nullptr);
+      if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
+    }
+    // X_0 from the FP32-result solve of the rounded data
+    if ((s = r32_solve(nb, terms, A32, m, R32, m, m, n, (float)alpha, unit, st)) != HSMA_OK) break;
+    accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 1, nullptr);
+    for (int it = 0; it <= itmax && s == HSMA_OK; ++it) {
+      // R = alpha B - L X in FP64, then the stopping test
+      if ((s = fail(cudaMemcpy2DAsync(R64, sizeof(double) * m, B0, sizeof(double) * m, sizeof(double) * m, n,
+                                      cudaMemcpyDeviceToDevice, st))) != HSMA_OK)
+        break;
+      if ((s = hsma_residual_f64(A, lda, unit, B, ldb, R64, m, m, n, alpha, state, st)) != HSMA_OK) break;
+      {
+        HsmaTraceScope ts("refine", st);
+        sumsq_kernel<<<grid, 256, 0, st>>>(R64, m, m, n, 0, 0, sums, 2, state);
+        sumsq_kernel<<<grid, 256, 0, st>>>(B, ldb, m, n, 0, 0, sums, 3, state);
+        check_kernel<<<1, 1, 0, st>>>(sums, state, std::fabs(alpha), tol, it);
+        if (it == itmax) break;
+        f64_to_f32_kernel<<<grid, 256, 0, st>>>(R64, m, R32, m, m, n, 0, state);
+        if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
+      }
+      // correction C from the FP32-result solve of L C = R (alpha = 1), X += C
+      if ((s = r32_solve(nb, terms, A32, m, R32, m, m, n, 1.0f, unit, st)) != HSMA_OK) break;
+      accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 0, state);
+      if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
+    }
+    if (s == HSMA_OK && info != nullptr) {
+      int h[4] = {0, 0, 0, 0};
+      if ((s = fail(cudaMemcpyAsync(h, state, sizeof h, cudaMemcpyDeviceToHost, st))) != HSMA_OK) break;
+      if ((s = fail(cudaStreamSynchronize(st))) != HSMA_OK) break;
+      info->converged = h[0];
+      info->ir_iters = h[1];
+      std::memcpy(&info->ir_residual, h + 2, sizeof(double));
+    }
+  } while (0);
+  hsma_status_t f = hsma_ws_free(ws, st);
+  if (s == HSMA_OK && info != nullptr && !info->converged) s = HSMA_ERR_NOT_CONVERGED;
+  return s != HSMA_OK ? s : f;
+}
+
+extern "C" HSMA_API hsma_status_t hsma_gemm_bf16_update(int64_t M, int64_t N, int64_t K, const void *A,
+                                                        const void *Bt, float beta, float *C, int64_t ldc,
+                                                        void *stream) {
+  if (M < 0 || N < 0 || K < 0 || ldc < std::max<int64_t>(1, M)) return HSMA_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return HSMA_OK;
+  if (A == nullptr || Bt == nullptr || C == nullptr || K == 0 || K % TC_BK != 0) return HSMA_ERR_INVALID_ARG;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  return bf16_update(static_cast<const __nv_bfloat16 *>(A), static_cast<const __nv_bfloat16 *>(Bt), (int)M, (int)N,
+                     (int)K, beta, C, ldc, static_cast<cudaStream_t>(stream));
 }

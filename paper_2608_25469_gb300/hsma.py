@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTE
 EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_llnn_ex",
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
-           "hsma_device_status"]
+           "hsma_device_status", "hsma_gemm_bf16_update"]
 
 
 class HsmaError(RuntimeError):
@@ -87,6 +87,8 @@ def _load():
     lib.hsma_trace_read.restype = c_int
     lib.hsma_trace_launches.restype = ctypes.c_longlong
     lib.hsma_trace_reset.restype = None
+    lib.hsma_gemm_bf16_update.argtypes = [i64, i64, i64, vp, vp, ctypes.c_float, vp, i64, vp]
+    lib.hsma_gemm_bf16_update.restype = c_int
     lib.hsma_device_status.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.hsma_device_status.restype = c_int
     return lib
@@ -163,6 +165,13 @@ def hsma_gen_matrix(dtype, kind, seed, inst, m, cols, dst, ld, stream=0, check=T
     s = _lib.hsma_gen_matrix(dtype, kind, seed, inst, m, cols, dst, ld, stream)
     if check:
         _check(s, "hsma_gen_matrix")
+    return s
+
+
+def hsma_gemm_bf16_update(M, N, K, A, Bt, beta, C, ldc, stream=0, check=True) -> int:
+    s = _lib.hsma_gemm_bf16_update(M, N, K, A, Bt, beta, C, ldc, stream)
+    if check:
+        _check(s, "hsma_gemm_bf16_update")
     return s
 
 

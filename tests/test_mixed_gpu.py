@@ -1,0 +1,114 @@
+"""Reduced-precision modes: the BF16 tensor-core update (tcgen05), the FP32-result
+solve (<= 2e-5 against the FP64 oracle of the FP64 data) and the FP64-result
+solve by iterative refinement (<= 1e-12)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_25469_gb300 import inputs as I
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    assert torch.cuda.is_available()
+    return U.lib()
+
+
+def _bf16_values(rng, shape):
+    """float32 values exactly representable in BF16 (8-bit significands)."""
+    mant = rng.integers(-128, 128, shape).astype(np.float32)
+    expo = rng.integers(-6, 2, shape).astype(np.float32)
+    return (mant * np.exp2(expo - 7)).astype(np.float32)
+
+
+def _bf16_bits(x32):
+    return (x32.view(np.uint32) >> 16).astype(np.uint16)
+
+
+@pytest.mark.parametrize("M,N,K,beta", [(300, 600, 192, 1.0), (128, 256, 64, 0.5), (77, 5, 128, 1.0),
+                                        (1000, 513, 768, 1.0)])
+def test_bf16_update_parity(H, M, N, K, beta):
+    import torch
+    rng = np.random.default_rng(M + N + K)
+    A = _bf16_values(rng, (M, K))
+    Bt = _bf16_values(rng, (N, K))
+    C0 = rng.uniform(-1, 1, (M, N)).astype(np.float32)
+    ldc = M + 3
+    Cb = np.full((ldc, N), 5.0, dtype=np.float32, order="F")
+    Cb[:M] = C0
+    dA = torch.from_numpy(_bf16_bits(A)).cuda()       # row-major M x K
+    dB = torch.from_numpy(_bf16_bits(Bt)).cuda()      # row-major N x K
+    dC = H.to_device(Cb)
+    H.hsma_gemm_bf16_update(M, N, K, dA.data_ptr(), dB.data_ptr(), beta, dC.data_ptr(), ldc, H.stream_ptr())
+    torch.cuda.synchronize()
+    got = H.from_device(dC)
+    ref = beta * C0.astype(np.float64) - A.astype(np.float64) @ Bt.astype(np.float64).T
+    scale = np.abs(C0) + np.abs(A.astype(np.float64)) @ np.abs(Bt.astype(np.float64)).T
+    assert np.all(np.abs(got[:M] - ref) <= 1e-5 * scale + 1e-30), np.max(np.abs(got[:M] - ref) / scale)
+    assert np.all(got[M:] == 5.0)
+    assert H.hsma_device_status() == 0
+
+
+def _r32(H, A64, B64, alpha, terms=0, nb=0):
+    import torch
+    A32 = np.asfortranarray(A64.astype(np.float32))
+    B32 = np.asfortranarray(B64.astype(np.float32))
+    dA, dB = H.to_device(A32), H.to_device(B32)
+    opts = H.Opts()
+    opts.bf16_terms = terms
+    opts.nb = nb
+    m, n = B64.shape
+    H.hsma_trsm_llnn_ex(H.R32_BF16, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts)
+    torch.cuda.synchronize()
+    return H.from_device(dB).astype(np.float64)
+
+
+@pytest.mark.parametrize("m,n,nb", [(1000, 300, 128), (517, 77, 64), (64, 64, 64), (2048, 100, 256)])
+def test_r32_mode_accuracy(H, m, n, nb):
+    A, B = I.gen_A(7, m, I.R64), I.gen_B(7, m, n, I.R64)
+    X = _r32(H, A, B, 1.5, terms=3, nb=nb)
+    err = oracle.forward_error(X, oracle.solve(A, B, 1.5))
+    assert err <= 2e-5, err
+    assert H.hsma_device_status() == 0
+
+
+def test_r32_mode_config3_sampled(H):
+    """m = 8192, n = 4096 FP32-result mode, split BF16 (3 terms), sampled columns."""
+    import torch
+    m, n = 8192, 4096
+    A = I.gen_A(0, m, I.R64)
+    B = I.gen_B(0, m, n, I.R64)
+    X = _r32(H, A, B, 1.0)
+    cols = np.arange(0, n, 64)
+    ref = oracle.solve_cols(A, B, 1.0, cols)
+    err = oracle.forward_error(X[:, cols], ref)
+    assert err <= 2e-5, err
+
+
+def _ir(H, A, B, alpha, **kw):
+    import torch
+    dA, dB = H.to_device(A), H.to_device(B)
+    opts = H.Opts()
+    for k, v in kw.items():
+        setattr(opts, k, v)
+    info = H.Info()
+    m, n = B.shape
+    H.hsma_trsm_llnn_ex(H.R64_IR, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts,
+                        info=info)
+    torch.cuda.synchronize()
+    return H.from_device(dB), info
+
+
+@pytest.mark.parametrize("m,n", [(1000, 300), (300, 1000), (129, 1)])
+def test_ir_mode_reaches_fp64_accuracy(H, m, n):
+    A, B = I.gen_A(9, m, I.R64), I.gen_B(9, m, n, I.R64)
+    X, info = _ir(H, A, B, 1.5)
+    assert info.converged == 1 and 1 <= info.ir_iters <= 10
+    assert info.ir_residual <= 1e-15
+    err = oracle.forward_error(X, oracle.solve(A, B, 1.5))
+    assert err <= 1e-12, err
+    assert oracle.backward_error(A, B, X, 1.5) <= 1e-14

@@ -375,7 +375,7 @@ def run_large(args, dist, device, code, m):
     # the update products' algorithmic flops: the trailing part of m^2 n not done by the solve products
     nb = H.hsma_plan(code, m, n).nb
     upd_flops = (4.0 if cplx_ else 1.0) * float(n) * (m * m - m * nb)
-    achieved = upd_flops / args.steps / (upd_ms / max(args.steps, 1) * 1e-3) / 1e9
+    achieved = upd_flops / (upd_ms / max(args.steps, 1) * 1e-3) / 1e9
     total_flops = dist.sum(flops, device=device)
     value = total_flops * args.steps / (ms_max * 1e-3) / 1e9
     name = "large_c128" if cplx_ else "large_fp64"

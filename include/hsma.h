@@ -167,6 +167,32 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batc
                                       const int32_t *d_lda, void *const *d_B, const int32_t *d_ldb,
                                       int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream);
 
+/*
+ * Allocation-free form of hsma_trsm_llnn_vbatched (same arguments, same
+ * results bit for bit).  It has no counterpart in the paper; it exists for
+ * callers that cannot have the library allocate device memory during a
+ * solve: a serving loop that reserved all device memory up front, an
+ * application whose own allocator owns every byte of the GPU, or code that
+ * runs where a call into the CUDA allocator is not allowed.
+ *
+ * The batch schedule is kept in one static device array inside the library
+ * instead of stream-ordered workspace; every GPU that loads the library holds
+ * that array (about 256 KB) until the process exits.  Limit: batch <= 65536
+ * instances; a larger batch returns HSMA_ERR_UNSUPPORTED without launching.
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress per device, made with that device current); make that
+ * first call before any stream capture.  The call itself allocates and frees
+ * nothing.  All calls share the one array: each call resets the counters it
+ * needs, but calls whose work overlaps on the GPU (on different streams, or
+ * from different threads, without ordering between them) race on the array
+ * and must be serialised by the caller.
+ */
+HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_noalloc(int dtype, int diag, int32_t batch, const int32_t *d_m,
+                                                       const int32_t *d_n, const void *alpha,
+                                                       const void *const *d_A, const int32_t *d_lda,
+                                                       void *const *d_B, const int32_t *d_ldb, int32_t max_m,
+                                                       int32_t max_n, uint32_t *d_status, void *stream);
+
 /* Planner query (host only, no GPU needed): the path, N_B and G that
  * hsma_trsm_llnn would use for (dtype, m, n). */
 HSMA_API hsma_status_t hsma_plan(int dtype, int64_t m, int64_t n, hsma_plan_t *out);

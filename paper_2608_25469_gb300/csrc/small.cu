@@ -20,6 +20,8 @@
 // The per-instance arithmetic is independent of the batch it sits in.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "small.h"
 #include "trace.h"
@@ -462,4 +464,64 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
   if (dtype == HSMA_C128)
     return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
   return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free varlen batch.  The schedule scratch (next-item counter,
+// item count and the per-instance schedule) lives in this file-scope device
+// array instead of the stream-ordered pool.  Every GPU that loads the library
+// keeps the array until the process exits.  Host code never hands the array's
+// name to a kernel: it first looks up the array's device address, once per
+// device, with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int32_t kNoAllocMaxBatch = 65536;
+__device__ __align__(256) int32_t g_noalloc_scratch[2 + kNoAllocMaxBatch];
+
+int32_t *noalloc_scratch(cudaError_t *err) {
+  static int32_t *addr[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (addr[dev] == nullptr) {
+    int32_t *p = nullptr;
+    *err = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+}  // namespace
+
+extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_noalloc(int dtype, int diag, int32_t batch,
+                                                                  const int32_t *d_m, const int32_t *d_n,
+                                                                  const void *alpha, const void *const *d_A,
+                                                                  const int32_t *d_lda, void *const *d_B,
+                                                                  const int32_t *d_ldb, int32_t max_m,
+                                                                  int32_t max_n, uint32_t *d_status,
+                                                                  void *stream) {
+  if (dtype != HSMA_R64 && dtype != HSMA_C128) {
+    return (dtype == HSMA_R32_BF16 || dtype == HSMA_R64_IR) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
+  }
+  if ((diag != HSMA_NON_UNIT && diag != HSMA_UNIT) || batch < 0 || max_m < 0 || max_n < 0)
+    return HSMA_ERR_INVALID_ARG;
+  if (max_m > 64 || batch > kNoAllocMaxBatch) return HSMA_ERR_UNSUPPORTED;
+  if (batch == 0) return HSMA_OK;
+  if (alpha == nullptr || d_m == nullptr || d_n == nullptr || d_A == nullptr || d_lda == nullptr ||
+      d_B == nullptr || d_ldb == nullptr)
+    return HSMA_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  int32_t *scratch = noalloc_scratch(&e);
+  if (scratch == nullptr) return hsma_from_cuda(e);
+  // the schedule pre-pass rewrites the counter and the item count on every call
+  return hsma_small_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda, d_B, d_ldb,
+                             diag == HSMA_UNIT, d_status, scratch, static_cast<cudaStream_t>(stream));
 }

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTE
 EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_llnn_ex",
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
-           "hsma_device_status", "hsma_gemm_bf16_update"]
+           "hsma_device_status", "hsma_gemm_bf16_update", "hsma_trsm_llnn_vbatched_noalloc"]
 
 
 class HsmaError(RuntimeError):
@@ -73,6 +73,9 @@ def _load():
     lib.hsma_trsm_llnn_ex.restype = c_int
     lib.hsma_trsm_llnn_vbatched.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p, vp]
     lib.hsma_trsm_llnn_vbatched.restype = c_int
+    lib.hsma_trsm_llnn_vbatched_noalloc.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p,
+                                                    vp]
+    lib.hsma_trsm_llnn_vbatched_noalloc.restype = c_int
     lib.hsma_plan.argtypes = [c_int, i64, i64, ctypes.POINTER(Plan)]
     lib.hsma_plan.restype = c_int
     lib.hsma_small_cost.argtypes = [c_int, i64, i64, i32]
@@ -144,6 +147,17 @@ def hsma_trsm_llnn_vbatched(dtype, diag, batch, d_m, d_n, alpha, d_A, d_lda, d_B
                                      d_A, d_lda, d_B, d_ldb, max_m, max_n, d_status or None, stream)
     if check:
         _check(s, "hsma_trsm_llnn_vbatched")
+    return s
+
+
+def hsma_trsm_llnn_vbatched_noalloc(dtype, diag, batch, d_m, d_n, alpha, d_A, d_lda, d_B, d_ldb, max_m=0,
+                                    max_n=0, d_status=0, stream=0, check=True) -> int:
+    """Allocation-free varlen batch: schedule scratch in a static device array (batch <= 65536)."""
+    s = _lib.hsma_trsm_llnn_vbatched_noalloc(dtype, diag, batch, d_m, d_n,
+                                             ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), d_A, d_lda, d_B,
+                                             d_ldb, max_m, max_n, d_status or None, stream)
+    if check:
+        _check(s, "hsma_trsm_llnn_vbatched_noalloc")
     return s
 
 

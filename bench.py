@@ -437,6 +437,166 @@ def run_single64(args, dist, device):
     }
 
 
+def run_serve(args, dist, device):
+    """Serving stream: Poisson arrivals at 2000/s, m log-U[16,4096], n log-U[1,512], 70% fp64,
+    16 GB admission budget, inputs generated on the device per request; p50/p99 latency."""
+    import torch
+    from paper_2608_25469_gb300 import hsma as H
+    from paper_2608_25469_gb300 import inputs as I
+    count = args.requests
+    seed = shard_seed(args.seed, dist.rank)
+    t_arr, ms, ns, dts = I.serving_requests(seed, count)
+    flops = float(sum(I.flops_trsm(m, n, d == I.C128) for m, n, d in zip(ms, ns, dts)))
+    s = H.hsma_server_create(16 << 30, 4, 0)
+    reqs = []
+    for k in range(count):
+        r = H.Request()
+        r.dtype, r.diag, r.m, r.n = int(dts[k]), 0, int(ms[k]), int(ns[k])
+        r.alpha[0], r.alpha[1] = 1.0, 0.0
+        r.gen_seed, r.gen_inst = seed, k
+        reqs.append(r)
+    # warm-up: the first few requests' shapes, not timed
+    for k in range(min(args.warmup * 4, count)):
+        H.hsma_server_submit(s, reqs[k])
+    H.hsma_server_drain(s, 600.0)
+    base = H.hsma_server_stats(s).submitted
+    H.hsma_trace_reset()
+    H.hsma_trace_enable(True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    tickets = []
+    t0 = time.perf_counter()
+    for k in range(count):
+        target = t0 + t_arr[k]
+        while True:
+            d = target - time.perf_counter()
+            if d <= 0:
+                break
+            time.sleep(d if d > 0.002 else 0)
+        tickets.append(H.hsma_server_submit(s, reqs[k]))
+    H.hsma_server_drain(s, 3600.0)
+    t1 = time.perf_counter()
+    sampler.mark(t0, t1)
+    clocks = sampler.stop()
+    H.hsma_trace_enable(False)
+    launches = H.hsma_trace_launches()
+    lat = np.array([H.hsma_server_poll(s, t)[1] for t in tickets])
+    st = H.hsma_server_stats(s)
+    H.hsma_server_destroy(s)
+    makespan = t1 - t0
+    # the same requests one at a time with the plain solve (a sample), service time only
+    k_seq = min(count, args.seq_sample)
+    st_ = torch.cuda.current_stream()
+    sp = int(st_.cuda_stream)
+    seq = []
+    for k in range(k_seq):
+        m, n, d = int(ms[k]), int(ns[k]), int(dts[k])
+        dt = torch.complex128 if d == I.C128 else torch.float64
+        A = torch.empty((m, m), dtype=dt, device=device)
+        B = torch.empty((n, m), dtype=dt, device=device)
+        H.hsma_gen_matrix(d, 0, seed, k, m, m, A.data_ptr(), m, sp)
+        H.hsma_gen_matrix(d, 1, seed, k, m, n, B.data_ptr(), m, sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st_)
+        H.hsma_trsm_llnn(d, 0, m, n, 1.0, A.data_ptr(), m, B.data_ptr(), m, sp)
+        e1.record(st_)
+        e1.synchronize()
+        seq.append(e0.elapsed_time(e1) * 1e-3)
+    seq = np.array(seq)
+    seq_flops = float(sum(I.flops_trsm(m, n, d == I.C128) for m, n, d in zip(ms[:k_seq], ns[:k_seq], dts[:k_seq])))
+    return {
+        "metric": METRIC, "value": round(count / makespan, 2), "unit": "solves/s", "n_gpus": dist.world,
+        "steps": count, "warmup": base, "ms_per_step": round(makespan * 1e3 / count, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+c128", "data": "synthetic",
+        "config": {"workload": f"serve: {count} requests, Poisson 2000/s, m log-U[16,4096], n log-U[1,512], "
+                               "70% fp64 / 30% c128, 16 GB budget, device-generated inputs"},
+        "gflops": round(flops / makespan / 1e9, 2), "offered_gflops": round(flops / t_arr[-1] / 1e9, 2),
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                       "p99": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                       "max": round(float(lat.max()) * 1e3, 3)},
+        "one_at_a_time": {"sample": k_seq, "solves_per_s": round(k_seq / seq.sum(), 2),
+                          "gflops": round(seq_flops / seq.sum() / 1e9, 2),
+                          "service_ms_p50": round(float(np.percentile(seq, 50)) * 1e3, 3),
+                          "service_ms_p99": round(float(np.percentile(seq, 99)) * 1e3, 3)},
+        "server": {"peak_bytes": int(st.peak_bytes_in_use), "budget_bytes": int(st.budget_bytes),
+                   "batched_launches": int(st.batched_launches), "blocked_launches": int(st.blocked_launches)},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+
+
+def run_mixed(args, dist, device, mode):
+    """m = 8192, n = 4096: FP32-result (BF16 tensor-core updates) or FP64-result (IR), beside plain fp64."""
+    import torch
+    from paper_2608_25469_gb300 import hsma as H
+    m, n = 8192, 4096
+    seed = shard_seed(args.seed, dist.rank)
+    st = torch.cuda.current_stream()
+    sp = int(st.cuda_stream)
+    A64 = torch.empty((m, m), dtype=torch.float64, device=device)
+    B64 = torch.empty((n, m), dtype=torch.float64, device=device)
+    H.hsma_gen_matrix(H.R64, 0, seed, -1, m, m, A64.data_ptr(), m, sp)
+    H.hsma_gen_matrix(H.R64, 1, seed, -1, m, n, B64.data_ptr(), m, sp)
+    flops = float(m) * m * n
+    if mode == "r32":
+        A = A64.float()
+        B0 = B64.float()
+        code = H.R32_BF16
+    else:
+        A = A64
+        B0 = B64
+        code = H.R64_IR
+    B = B0.clone()
+    info = H.Info()
+
+    def step():
+        B.copy_(B0)
+        H.hsma_trsm_llnn_ex(code, 0, m, n, 1.0, A.data_ptr(), m, B.data_ptr(), m, sp,
+                            info=info if code == H.R64_IR else None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    H.hsma_trace_reset()
+    H.hsma_trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(args.steps):
+        e0.record(st)
+        step()
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    H.hsma_trace_enable(False)
+    phases = {}
+    for ph in ("diag_inverse", "copy", "solve_sgemm", "convert", "update_bf16", "residual", "refine"):
+        ms_, c = H.hsma_trace_read(ph)
+        if c:
+            phases[ph] = round(ms_ / args.steps, 4)
+    ms_med = float(np.median(times))
+    out = {
+        "metric": METRIC, "value": round(flops / (ms_med * 1e-3) / 1e9, 3), "unit": "GFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_med, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32(bf16 updates)" if mode == "r32" else "f64 (IR)",
+        "data": "synthetic",
+        "config": {"workload": f"mixed_{mode}: m=8192, n=4096, alpha=1, non-unit",
+                   "step_includes": "a device copy of B (268 MB or 134 MB) to restore the input"},
+        "phases_ms_per_step": phases,
+    }
+    if mode == "ir":
+        out["ir"] = {"iterations": int(info.ir_iters), "converged": int(info.converged),
+                     "residual": float(info.ir_residual)}
+    # the plain fp64 solve of the same data on the same GPU
+    B.copy_(B64)
+    torch.cuda.synchronize()
+    e0.record(st)
+    H.hsma_trsm_llnn(H.R64, 0, m, n, 1.0, A64.data_ptr(), m, B.data_ptr(), m, sp)
+    e1.record(st)
+    e1.synchronize()
+    pms = e0.elapsed_time(e1)
+    out["plain_fp64"] = {"ms": round(pms, 3), "gflops": round(flops / (pms * 1e-3) / 1e9, 3)}
+    return out
+
+
 def run_reference(args, dist):
     """The oracle, as it stands, on the host cores: same metric and workload."""
     import oracle
@@ -476,6 +636,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--seq-sample", type=int, default=1000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
@@ -500,6 +662,10 @@ def main(argv=None):
         out = run_large(args, dist, device, H.C128, 8192)
     elif args.workload == "single_fp64_64":
         out = run_single64(args, dist, device)
+    elif args.workload == "serve":
+        out = run_serve(args, dist, device)
+    elif args.workload in ("mixed_r32", "mixed_ir"):
+        out = run_mixed(args, dist, device, args.workload.split("_")[1])
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     if dist.rank == 0 and out is not None:

@@ -218,6 +218,64 @@ HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64
                               int64_t cols, void *dst, int64_t ld, void *stream);
 
 /*
+ * Serving loop (the benchmark spec's continuous-batching server; batched TRSM is
+ * the paper's future work, Section 6).  A server owns a scheduler thread, a
+ * ring of CUDA streams and a device memory pool on the current device.
+ * Submitted requests are admitted in arrival order while their device memory
+ * (A, B and the blocked path's workspace) fits `budget_bytes`; admitted
+ * requests with m <= 64 that are ready together run as one varlen batched
+ * launch, larger ones run the blocked path on the streams, overlapping on the
+ * device.  Memory is freed when a request's completion event fires; latency is
+ * measured from submission to that event.  Each result equals the request
+ * solved alone (up to the rounding of the path chosen for its size).
+ */
+typedef struct hsma_server hsma_server_t;
+
+#define HSMA_SERVER_FAKE_DEVICE 0x1u /* no GPU: launches complete after a modelled time (tests) */
+
+typedef struct {
+  int32_t dtype;  /* HSMA_R64 or HSMA_C128                                        */
+  int32_t diag;
+  int64_t m, n;   /* >= 1                                                           */
+  double alpha[2];
+  /* inputs: copied from host memory when A_host != NULL (column-major, lda/ldb
+     >= m; pinned memory makes the copy asynchronous), otherwise generated on
+     the device from (gen_seed, gen_inst) as hsma_gen_matrix does             */
+  const void *A_host;
+  int64_t lda;
+  const void *B_host;
+  int64_t ldb;
+  uint64_t gen_seed;
+  int64_t gen_inst;
+  /* output: copied to X_host (ldx >= m) before the request completes, or
+     discarded when X_host == NULL                                            */
+  void *X_host;
+  int64_t ldx;
+} hsma_request_t;
+
+typedef struct {
+  uint64_t submitted, admitted, completed;
+  uint64_t bytes_in_use, peak_bytes_in_use, budget_bytes;
+  uint64_t batched_launches, blocked_launches;
+} hsma_server_stats_t;
+
+/* Create a server on the current device (flags: 0 or HSMA_SERVER_FAKE_DEVICE). */
+HSMA_API hsma_status_t hsma_server_create(size_t budget_bytes, int n_streams, unsigned int flags,
+                                          hsma_server_t **out);
+/* Enqueue a request (thread-safe, non-blocking); *ticket identifies it.  Host
+ * buffers must stay valid until the request completes.  A request that can
+ * never fit the budget completes with HSMA_ERR_NO_MEMORY. */
+HSMA_API hsma_status_t hsma_server_submit(hsma_server_t *s, const hsma_request_t *req, uint64_t *ticket);
+/* *done = 1 once the request completed; then *latency_s is submission-to-
+ * completion time and the return value is the request's own status. */
+HSMA_API hsma_status_t hsma_server_poll(hsma_server_t *s, uint64_t ticket, int *done, double *latency_s);
+/* Wait until every submitted request completed (timeout_s <= 0: no limit). */
+HSMA_API hsma_status_t hsma_server_drain(hsma_server_t *s, double timeout_s);
+HSMA_API hsma_status_t hsma_server_stats(hsma_server_t *s, hsma_server_stats_t *out);
+/* Finish outstanding work, then free the server. */
+HSMA_API hsma_status_t hsma_server_destroy(hsma_server_t *s);
+
+/*
  * BF16 tensor-core update used by HSMA_R32_BF16 (exposed for direct use and
  * testing): C = beta*C - A * Bt^T with A (M x K) and Bt (N x K) row-major
  * BF16 (K contiguous; K a positive multiple of 64) and C (M x N) column-major

@@ -32,10 +32,10 @@ namespace {
 // batched kernel's minimum resident CTAs per SM (register cap; 0 = none) and
 // its set of row-group variants (bit log2(G)).  Defaults chosen by measurement.
 #ifndef HSMA_VB_WARPS
-#define HSMA_VB_WARPS 2
+#define HSMA_VB_WARPS 4
 #endif
 #ifndef HSMA_VB_MINB
-#define HSMA_VB_MINB 0
+#define HSMA_VB_MINB 3
 #endif
 #ifndef HSMA_VB_GMASK
 #define HSMA_VB_GMASK 0xFu
@@ -69,15 +69,26 @@ __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict
     sC[r] = (r < m) ? E::mul(alpha, rv) : E::zero();
   }
   __syncthreads();
+  // U columns per warp in flight, P row chunks of 32 per column: the loads of
+  // a batch are issued before any of them is used
   const int warp = tid >> 5, lane = tid & 31;
-  for (int i = warp; i < m; i += W) {
-    T *col = sTri + col_off(i, MMAX) - i - 1;  // col[r], r > i
-    const T *acol = A + (int64_t)i * lda;
-    for (int r = i + 1 + lane; r < rows_used; r += 32) {
-      T v = E::zero();
-      if (r < m) v = E::mul(sR[r], E::ld(acol + r));
-      col[r] = v;
-    }
+  constexpr int U = 4, P = (MMAX + 31) / 32;
+  for (int i0 = warp; i0 < m; i0 += W * U) {
+    T v[U][P];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int i = i0 + u * W, r = lane + 32 * p;
+        v[u][p] = (i < m && r > i && r < m) ? E::ld(A + r + (int64_t)i * lda) : E::zero();
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int i = i0 + u * W, r = lane + 32 * p;
+        if (i < m && r > i && r < rows_used) sTri[col_off(i, MMAX) - i - 1 + r] = E::mul(sR[r], v[u][p]);
+      }
   }
   __syncthreads();
 }

@@ -31,7 +31,9 @@ STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTE
 EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_llnn_ex",
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
-           "hsma_device_status", "hsma_gemm_bf16_update", "hsma_trsm_llnn_vbatched_noalloc"]
+           "hsma_device_status", "hsma_gemm_bf16_update", "hsma_trsm_llnn_vbatched_noalloc",
+           "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
+           "hsma_server_destroy"]
 
 
 class HsmaError(RuntimeError):
@@ -49,6 +51,22 @@ class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("ir_max_iter", ctypes.c_int32), ("ir_tol", ctypes.c_double), ("bf16_terms", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("diag", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("alpha", ctypes.c_double * 2), ("A_host", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B_host", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("gen_seed", ctypes.c_uint64),
+                ("gen_inst", ctypes.c_int64), ("X_host", ctypes.c_void_p), ("ldx", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "admitted", "completed", "bytes_in_use",
+                                               "peak_bytes_in_use", "budget_bytes", "batched_launches",
+                                               "blocked_launches")]
+
+
+SERVER_FAKE_DEVICE = 0x1
 
 
 class Info(ctypes.Structure):
@@ -92,6 +110,18 @@ def _load():
     lib.hsma_trace_reset.restype = None
     lib.hsma_gemm_bf16_update.argtypes = [i64, i64, i64, vp, vp, ctypes.c_float, vp, i64, vp]
     lib.hsma_gemm_bf16_update.restype = c_int
+    lib.hsma_server_create.argtypes = [ctypes.c_size_t, c_int, ctypes.c_uint, ctypes.POINTER(ctypes.c_void_p)]
+    lib.hsma_server_create.restype = c_int
+    lib.hsma_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.hsma_server_submit.restype = c_int
+    lib.hsma_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(c_int), ctypes.POINTER(dbl)]
+    lib.hsma_server_poll.restype = c_int
+    lib.hsma_server_drain.argtypes = [vp, dbl]
+    lib.hsma_server_drain.restype = c_int
+    lib.hsma_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.hsma_server_stats.restype = c_int
+    lib.hsma_server_destroy.argtypes = [vp]
+    lib.hsma_server_destroy.restype = c_int
     lib.hsma_device_status.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.hsma_device_status.restype = c_int
     return lib
@@ -159,6 +189,40 @@ def hsma_trsm_llnn_vbatched_noalloc(dtype, diag, batch, d_m, d_n, alpha, d_A, d_
     if check:
         _check(s, "hsma_trsm_llnn_vbatched_noalloc")
     return s
+
+
+def hsma_server_create(budget_bytes: int, n_streams: int = 4, flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.hsma_server_create(budget_bytes, n_streams, flags, ctypes.byref(h)), "hsma_server_create")
+    return h.value
+
+
+def hsma_server_submit(server: int, req: Request) -> int:
+    t = ctypes.c_uint64()
+    _check(_lib.hsma_server_submit(server, ctypes.byref(req), ctypes.byref(t)), "hsma_server_submit")
+    return t.value
+
+
+def hsma_server_poll(server: int, ticket: int):
+    """(done, latency_s, status) of a request."""
+    d = ctypes.c_int()
+    lat = ctypes.c_double()
+    s = _lib.hsma_server_poll(server, ticket, ctypes.byref(d), ctypes.byref(lat))
+    return bool(d.value), lat.value, s
+
+
+def hsma_server_drain(server: int, timeout_s: float = 0.0) -> int:
+    return _lib.hsma_server_drain(server, timeout_s)
+
+
+def hsma_server_stats(server: int) -> ServerStats:
+    st = ServerStats()
+    _check(_lib.hsma_server_stats(server, ctypes.byref(st)), "hsma_server_stats")
+    return st
+
+
+def hsma_server_destroy(server: int) -> int:
+    return _lib.hsma_server_destroy(server)
 
 
 def hsma_plan(dtype, m, n) -> Plan:

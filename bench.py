@@ -447,7 +447,7 @@ def run_serve(args, dist, device):
     seed = shard_seed(args.seed, dist.rank)
     t_arr, ms, ns, dts = I.serving_requests(seed, count)
     flops = float(sum(I.flops_trsm(m, n, d == I.C128) for m, n, d in zip(ms, ns, dts)))
-    s = H.hsma_server_create(16 << 30, 4, 0)
+    s = H.hsma_server_create(16 << 30, args.streams, 0)
     reqs = []
     for k in range(count):
         r = H.Request()
@@ -509,7 +509,8 @@ def run_serve(args, dist, device):
         "steps": count, "warmup": base, "ms_per_step": round(makespan * 1e3 / count, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+c128", "data": "synthetic",
         "config": {"workload": f"serve: {count} requests, Poisson 2000/s, m log-U[16,4096], n log-U[1,512], "
-                               "70% fp64 / 30% c128, 16 GB budget, device-generated inputs"},
+                               "70% fp64 / 30% c128, 16 GB budget, device-generated inputs",
+                   "streams": args.streams},
         "gflops": round(flops / makespan / 1e9, 2), "offered_gflops": round(flops / t_arr[-1] / 1e9, 2),
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)) * 1e3, 3),
                        "p99": round(float(np.percentile(lat, 99)) * 1e3, 3),
@@ -585,11 +586,11 @@ def run_mixed(args, dist, device, mode):
     if mode == "ir":
         out["ir"] = {"iterations": int(info.ir_iters), "converged": int(info.converged),
                      "residual": float(info.ir_residual)}
-    # the plain fp64 solve of the same data on the same GPU
-    B.copy_(B64)
+    # the plain fp64 solve of the same data on the same GPU (its own fp64 buffer)
+    Bp = B64.clone()
     torch.cuda.synchronize()
     e0.record(st)
-    H.hsma_trsm_llnn(H.R64, 0, m, n, 1.0, A64.data_ptr(), m, B.data_ptr(), m, sp)
+    H.hsma_trsm_llnn(H.R64, 0, m, n, 1.0, A64.data_ptr(), m, Bp.data_ptr(), m, sp)
     e1.record(st)
     e1.synchronize()
     pms = e0.elapsed_time(e1)
@@ -638,6 +639,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--seq-sample", type=int, default=1000)
+    ap.add_argument("--streams", type=int, default=16)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) diag_inverse_kernel(const T *__restrict__
 // ---------------------------------------------------------------------------
 // Phase 2 products on the FP64 tensor path
 // ---------------------------------------------------------------------------
-constexpr int BM = 64, BN = 64, STAGES = 3, GEMM_THREADS = 128;
+constexpr int GEMM_THREADS = 128;
 
 template <class T>
 struct GemmK;
@@ -141,7 +141,20 @@ struct GemmK<cplx> {
   static constexpr int BK = 16;
 };
 
-enum { MODE_UPDATE = 0, MODE_SCALE = 1 };
+// CTA tile: WARPS_M x WARPS_N warps, each owning WM x WN blocks of 8 x 8.
+// Narrow tiles keep the tensor lanes busy when n is small.
+template <int WARPS_M_, int WARPS_N_, int WM_, int WN_>
+struct Tile {
+  static constexpr int WARPS_M = WARPS_M_, WARPS_N = WARPS_N_, WM = WM_, WN = WN_;
+  static constexpr int BM = WARPS_M * WM * 8, BN = WARPS_N * WN * 8;
+};
+using TileWide = Tile<2, 2, 4, 4>;  // 64 x 64
+using TileN16 = Tile<4, 1, 4, 2>;   // 128 x 16
+using TileN8 = Tile<4, 1, 4, 1>;    // 128 x 8
+
+// UPDATE: C = beta*C - A*B;  SCALE: C = beta*(A*B);  PARTIAL: P[z] = A*B over
+// this launch's z-th K chunk (a later fixed-order sum finishes the product)
+enum { MODE_UPDATE = 0, MODE_SCALE = 1, MODE_PARTIAL = 2 };
 
 template <class T>
 struct GemmArgs {
@@ -152,20 +165,23 @@ struct GemmArgs {
   T *C;  // M x N (column-major, ldc)
   int64_t ldc;
   int M, N, K;
-  int mode;  // UPDATE: C = beta*C - A*B;  SCALE: C = beta*(A*B)
+  int mode;
   T beta;
   int tri;     // A is lower triangular: row tile i0 needs k < i0 + BM only
   int mask;    // read only A's lower triangle (zeros above; ones on the diagonal if unit); plain loads
   int unit;
+  int kchunk;  // K per z-slice (a multiple of BK); K when not split
+  T *P;        // PARTIAL: slices of M x N (ld M)
   const int *skip;  // device flag: when set, the launch does nothing
   unsigned int *err;
   uint64_t limit_ns;
 };
 
-template <class T>
+template <class T, class TL>
 constexpr int stage_bytes() {
-  return (GemmK<T>::BK * BM + BN * GemmK<T>::BK) * (int)sizeof(T);
+  return (GemmK<T>::BK * TL::BM + TL::BN * GemmK<T>::BK) * (int)sizeof(T);
 }
+constexpr int kStages = 3;
 
 __device__ __forceinline__ void dmma884(double &d0, double &d1, double a, double b) {
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
@@ -173,51 +189,66 @@ __device__ __forceinline__ void dmma884(double &d0, double &d1, double a, double
                : "d"(a), "d"(b));
 }
 
-// Accumulators of one warp's 32 x 32 tile: 4 x 4 blocks of 8 x 8.
-template <class T>
+template <class T, class TL>
 struct Acc;
-template <>
-struct Acc<double> {
-  double v[4][4][2];
+template <class TL>
+struct Acc<double, TL> {
+  double v[TL::WM][TL::WN][2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < TL::WM; ++i)
+#pragma unroll
+      for (int j = 0; j < TL::WN; ++j) v[i][j][0] = v[i][j][1] = 0.0;
+  }
+  __device__ __forceinline__ double get(int i, int j, int q) const { return v[i][j][q]; }
 };
-template <>
-struct Acc<cplx> {
-  double re[4][4][2];
-  double im[4][4][2];
+template <class TL>
+struct Acc<cplx, TL> {
+  double re[TL::WM][TL::WN][2];
+  double im[TL::WM][TL::WN][2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < TL::WM; ++i)
+#pragma unroll
+      for (int j = 0; j < TL::WN; ++j) re[i][j][0] = re[i][j][1] = im[i][j][0] = im[i][j][1] = 0.0;
+  }
+  __device__ __forceinline__ cplx get(int i, int j, int q) const { return cplx{re[i][j][q], im[i][j][q]}; }
 };
 
 // one BK-deep slice from shared memory: sA[k][BM], sB[BN][k]
-__device__ __forceinline__ void mma_slice(Acc<double> &acc, const double *sA, const double *sB, int wm, int wn,
+template <class TL>
+__device__ __forceinline__ void mma_slice(Acc<double, TL> &acc, const double *sA, const double *sB, int wm, int wn,
                                           int g, int t) {
   constexpr int BK = GemmK<double>::BK;
 #pragma unroll
   for (int kk = 0; kk < BK; kk += 4) {
-    double a[4], b[4];
+    double a[TL::WM], b[TL::WN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = sA[(kk + t) * BM + wm * 32 + i * 8 + g];
+    for (int i = 0; i < TL::WM; ++i) a[i] = sA[(kk + t) * TL::BM + wm * TL::WM * 8 + i * 8 + g];
 #pragma unroll
-    for (int jn = 0; jn < 4; ++jn) b[jn] = sB[(wn * 32 + jn * 8 + g) * BK + kk + t];
+    for (int jn = 0; jn < TL::WN; ++jn) b[jn] = sB[(wn * TL::WN * 8 + jn * 8 + g) * BK + kk + t];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TL::WM; ++i)
 #pragma unroll
-      for (int jn = 0; jn < 4; ++jn) dmma884(acc.v[i][jn][0], acc.v[i][jn][1], a[i], b[jn]);
+      for (int jn = 0; jn < TL::WN; ++jn) dmma884(acc.v[i][jn][0], acc.v[i][jn][1], a[i], b[jn]);
   }
 }
 
-__device__ __forceinline__ void mma_slice(Acc<cplx> &acc, const cplx *sA, const cplx *sB, int wm, int wn, int g,
+template <class TL>
+__device__ __forceinline__ void mma_slice(Acc<cplx, TL> &acc, const cplx *sA, const cplx *sB, int wm, int wn, int g,
                                           int t) {
   constexpr int BK = GemmK<cplx>::BK;
 #pragma unroll
   for (int kk = 0; kk < BK; kk += 4) {
-    cplx a[4], b[4];
+    cplx a[TL::WM], b[TL::WN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = sA[(kk + t) * BM + wm * 32 + i * 8 + g];
+    for (int i = 0; i < TL::WM; ++i) a[i] = sA[(kk + t) * TL::BM + wm * TL::WM * 8 + i * 8 + g];
 #pragma unroll
-    for (int jn = 0; jn < 4; ++jn) b[jn] = sB[(wn * 32 + jn * 8 + g) * BK + kk + t];
+    for (int jn = 0; jn < TL::WN; ++jn) b[jn] = sB[(wn * TL::WN * 8 + jn * 8 + g) * BK + kk + t];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TL::WM; ++i)
 #pragma unroll
-      for (int jn = 0; jn < 4; ++jn) {
+      for (int jn = 0; jn < TL::WN; ++jn) {
         dmma884(acc.re[i][jn][0], acc.re[i][jn][1], a[i].re, b[jn].re);
         dmma884(acc.re[i][jn][0], acc.re[i][jn][1], -a[i].im, b[jn].im);
         dmma884(acc.im[i][jn][0], acc.im[i][jn][1], a[i].re, b[jn].im);
@@ -226,50 +257,45 @@ __device__ __forceinline__ void mma_slice(Acc<cplx> &acc, const cplx *sA, const 
   }
 }
 
-__device__ __forceinline__ void acc_zero(Acc<double> &a) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a.v[i][j][0] = a.v[i][j][1] = 0.0;
-}
-__device__ __forceinline__ void acc_zero(Acc<cplx> &a) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a.re[i][j][0] = a.re[i][j][1] = a.im[i][j][0] = a.im[i][j][1] = 0.0;
-}
-__device__ __forceinline__ double acc_get(const Acc<double> &a, int i, int j, int q) { return a.v[i][j][q]; }
-__device__ __forceinline__ cplx acc_get(const Acc<cplx> &a, int i, int j, int q) {
-  return cplx{a.re[i][j][q], a.im[i][j][q]};
-}
 __device__ __forceinline__ double sub(double a, double b) { return a - b; }
 __device__ __forceinline__ cplx sub(cplx a, cplx b) { return cplx{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ cplx add(cplx a, cplx b) { return cplx{a.re + b.re, a.im + b.im}; }
 __device__ __forceinline__ bool is_one(double a) { return a == 1.0; }
 __device__ __forceinline__ bool is_one(cplx a) { return a.re == 1.0 && a.im == 0.0; }
 
+// out = beta*C - v (UPDATE) or beta*v (SCALE)
 template <class T>
-__device__ __forceinline__ void epilogue(const GemmArgs<T> &p, const Acc<T> &acc, int m0, int n0, int wm, int wn,
-                                         int g, int t) {
+__device__ __forceinline__ void finish_elem(int mode, T beta, bool b1, T *cp, T v) {
   using E = Elem<T>;
+  if (mode == MODE_UPDATE) {
+    const T old = *cp;
+    *cp = sub(b1 ? old : E::mul(beta, old), v);
+  } else {
+    *cp = b1 ? v : E::mul(beta, v);
+  }
+}
+
+template <class T, class TL>
+__device__ __forceinline__ void epilogue(const GemmArgs<T> &p, const Acc<T, TL> &acc, int m0, int n0, int wm, int wn,
+                                         int g, int t) {
   const bool b1 = is_one(p.beta);
+  T *P = p.P + (size_t)blockIdx.z * p.M * p.N;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = m0 + wm * 32 + i * 8 + g;
+  for (int i = 0; i < TL::WM; ++i) {
+    const int row = m0 + wm * TL::WM * 8 + i * 8 + g;
     if (row >= p.M) continue;
 #pragma unroll
-    for (int jn = 0; jn < 4; ++jn)
+    for (int jn = 0; jn < TL::WN; ++jn)
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int col = n0 + wn * 32 + jn * 8 + 2 * t + q;
+        const int col = n0 + wn * TL::WN * 8 + jn * 8 + 2 * t + q;
         if (col >= p.N) continue;
-        T *cp = p.C + row + (int64_t)col * p.ldc;
-        const T v = acc_get(acc, i, jn, q);
-        if (p.mode == MODE_UPDATE) {
-          const T old = *cp;
-          *cp = sub(b1 ? old : E::mul(p.beta, old), v);
-        } else {
-          *cp = b1 ? v : E::mul(p.beta, v);
-        }
+        const T v = acc.get(i, jn, q);
+        if (p.mode == MODE_PARTIAL)
+          P[row + (size_t)col * p.M] = v;
+        else
+          finish_elem(p.mode, p.beta, b1, p.C + row + (int64_t)col * p.ldc, v);
       }
   }
 }
@@ -280,67 +306,69 @@ constexpr int words() {
   return (int)(sizeof(T) / 8);
 }
 
-template <class T, bool kTma>
+template <class T, class TL, bool kTma>
 __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const GemmArgs<T> p,
                                                             const __grid_constant__ CUtensorMap mapA,
                                                             const __grid_constant__ CUtensorMap mapB) {
-  constexpr int BK = GemmK<T>::BK;
+  constexpr int BK = GemmK<T>::BK, BM = TL::BM, BN = TL::BN;
+  constexpr int SB = stage_bytes<T, TL>();
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[STAGES];
-  __shared__ int s_abort;
-  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  auto sA = [&](int s) { return reinterpret_cast<T *>(smem + s * stage_bytes<T>()); };
-  auto sB = [&](int s) { return reinterpret_cast<T *>(smem + s * stage_bytes<T>() + BK * BM * sizeof(T)); };
-
+  __shared__ __align__(8) uint64_t full[kStages];
   if (p.skip != nullptr && *(volatile const int *)p.skip != 0) return;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp & 1, wn = warp >> 1, g = lane >> 2, t = lane & 3;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kend = p.tri ? min(p.K, m0 + BM) : p.K;
-  const int nk = (kend + BK - 1) / BK;
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  auto sA = [&](int s) { return reinterpret_cast<T *>(smem + s * SB); };
+  auto sB = [&](int s) { return reinterpret_cast<T *>(smem + s * SB + BK * BM * sizeof(T)); };
 
-  Acc<T> acc;
-  acc_zero(acc);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp % TL::WARPS_M, wn = warp / TL::WARPS_M, g = lane >> 2, t = lane & 3;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kall = p.tri ? min(p.K, m0 + BM) : p.K;
+  const int kbeg = blockIdx.z * p.kchunk;
+  const int kend = min(kall, kbeg + p.kchunk);
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+
+  Acc<T, TL> acc;
+  acc.zero();
 
   if constexpr (kTma) {
     if (tid == 0) {
-      for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+      for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
       fence_mbar_init();
-      s_abort = 0;
     }
     __syncthreads();
     auto issue = [&](int kt, int s) {
-      mbar_arrive_expect_tx(&full[s], stage_bytes<T>());
-      tma_load_2d(sA(s), &mapA, &full[s], m0 * words<T>(), kt * BK);
-      tma_load_2d(sB(s), &mapB, &full[s], kt * BK * words<T>(), n0);
+      mbar_arrive_expect_tx(&full[s], SB);
+      tma_load_2d(sA(s), &mapA, &full[s], m0 * words<T>(), kbeg + kt * BK);
+      tma_load_2d(sB(s), &mapB, &full[s], (kbeg + kt * BK) * words<T>(), n0);
     };
     if (tid == 0)
-      for (int s = 0; s < STAGES && s < nk; ++s) issue(s, s);
+      for (int s = 0; s < kStages && s < nk; ++s) issue(s, s);
     int kt = 0;
     for (; kt < nk; ++kt) {
-      const int s = kt % STAGES;
-      const bool ok = mbar_wait_bounded(&full[s], (kt / STAGES) & 1, p.limit_ns, p.err);
+      const int s = kt % kStages;
+      const bool ok = mbar_wait_bounded(&full[s], (kt / kStages) & 1, p.limit_ns, p.err);
       if (__syncthreads_or(!ok)) break;
       mma_slice(acc, sA(s), sB(s), wm, wn, g, t);
       __syncthreads();
-      if (tid == 0 && kt + STAGES < nk) issue(kt + STAGES, s);
+      if (tid == 0 && kt + kStages < nk) issue(kt + kStages, s);
     }
     if (kt < nk) {
       // timed out: let the copies this CTA issued land (bounded) before leaving
       if (tid == 0)
-        for (int k2 = kt; k2 < nk && k2 < kt + STAGES; ++k2)
-          mbar_wait_bounded(&full[k2 % STAGES], (k2 / STAGES) & 1, p.limit_ns, p.err);
+        for (int k2 = kt; k2 < nk && k2 < kt + kStages; ++k2)
+          mbar_wait_bounded(&full[k2 % kStages], (k2 / kStages) & 1, p.limit_ns, p.err);
       return;
     }
   } else {
     using E = Elem<T>;
     for (int kt = 0; kt < nk; ++kt) {
       T *a = sA(0), *b = sB(0);
-      const int k0 = kt * BK;
+      const int k0 = kbeg + kt * BK;
       for (int e = tid; e < BK * BM; e += GEMM_THREADS) {
         const int kk = e / BM, mm = e % BM;
         const int row = m0 + mm, col = k0 + kk;
-        T v = (row < p.M && col < p.K && !(p.mask && col > row)) ? E::ld(p.A + row + (int64_t)col * p.lda) : E::zero();
+        T v = (row < p.M && col < p.K && !(p.mask && col > row)) ? E::ld(p.A + row + (int64_t)col * p.lda)
+                                                                   : E::zero();
         if (p.mask && p.unit && col == row && row < p.M) v = E::one();
         a[e] = v;
       }
@@ -357,19 +385,33 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const GemmArgs<T> p,
   epilogue(p, acc, m0, n0, wm, wn, g, t);
 }
 
+// C = mode(beta C, sum_z P[z]) over the M x N region, z in increasing order
 template <class T>
-size_t gemm_smem_bytes(bool tma) {
-  return (size_t)(tma ? STAGES : 1) * stage_bytes<T>() + 128;
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const T *__restrict__ P, int S, int M, int N, T *C,
+                                                              int64_t ldc, int mode, T beta) {
+  const int64_t total = (int64_t)M * N;
+  const bool b1 = is_one(beta);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    T v = P[e];
+    for (int z = 1; z < S; ++z) v = add(v, P[e + (int64_t)z * total]);
+    const int row = (int)(e % M), col = (int)(e / M);
+    finish_elem(mode, beta, b1, C + row + (int64_t)col * ldc, v);
+  }
 }
 
-template <class T>
+template <class T, class TL>
+size_t gemm_smem_bytes(bool tma) {
+  return (size_t)(tma ? kStages : 1) * stage_bytes<T, TL>() + 128;
+}
+
+template <class T, class TL>
 hsma_status_t gemm_attrs() {
   static DeviceFlags done;
   if (done.test()) return HSMA_OK;
-  HSMA_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)gemm_smem_bytes<T>(true)));
-  HSMA_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)gemm_smem_bytes<T>(false)));
+  HSMA_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<T, TL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)gemm_smem_bytes<T, TL>(true)));
+  HSMA_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<T, TL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)gemm_smem_bytes<T, TL>(false)));
   done.set();
   return HSMA_OK;
 }
@@ -379,39 +421,84 @@ bool tma_ok(const void *p, int64_t ld) {
   return ((uintptr_t)p % 16 == 0) && ((ld * (int64_t)sizeof(T)) % 16 == 0);
 }
 
+int sm_count() {
+  static int n[64] = {0};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 152;
+  if (n[d] == 0) cudaDeviceGetAttribute(&n[d], cudaDevAttrMultiProcessorCount, d);
+  return n[d] > 0 ? n[d] : 152;
+}
 
-// Launch one product.  `phase` names it for the tracer.
-template <class T>
-hsma_status_t gemm(const GemmArgs<T> &p0, const char *phase, cudaStream_t st) {
-  if (p0.M <= 0 || p0.N <= 0) return HSMA_OK;
-  hsma_status_t s = gemm_attrs<T>();
+// Elements of partial-product workspace the split products of one solve may need.
+size_t partial_elems_max() { return (size_t)2 * 152 * 64 * 64 + (size_t)2 * 152 * 128 * 16; }
+
+template <class T, class TL>
+hsma_status_t gemm_tiled(const GemmArgs<T> &p0, const char *phase, cudaStream_t st, T *P, size_t P_elems) {
+  hsma_status_t s = gemm_attrs<T, TL>();
   if (s != HSMA_OK) return s;
+  constexpr int BK = GemmK<T>::BK;
   GemmArgs<T> p = p0;
   p.err = hsma_dev_error_ptr();
   if (p.err == nullptr) return HSMA_ERR_CUDA;
   if (p.limit_ns == 0) p.limit_ns = 4000000000ull;  // 4 s of wall time per barrier wait
+  const int tiles_m = (p.M + TL::BM - 1) / TL::BM, tiles_n = (p.N + TL::BN - 1) / TL::BN;
+  // split K while the tiles alone leave the GPU short of two CTAs per SM
+  int S = 1;
+  const int target = 2 * sm_count();
+  if (P != nullptr && (int64_t)tiles_m * tiles_n < target) {
+    S = target / (tiles_m * tiles_n);
+    S = std::min(S, std::max(1, p.K / (2 * BK)));
+    S = std::min(S, 16);
+    while (S > 1 && (size_t)S * p.M * p.N > P_elems) --S;
+  }
+  p.kchunk = S > 1 ? ((p.K + S - 1) / S + BK - 1) / BK * BK : p.K;
+  if (S > 1) S = (p.K + p.kchunk - 1) / p.kchunk;
+  const int final_mode = p.mode;
+  if (S > 1) {
+    p.mode = MODE_PARTIAL;
+    p.P = P;
+  }
   const bool use_tma = !p.mask && tma_ok<T>(p.A, p.lda) && tma_ok<T>(p.Bm, p.ldb);
   CUtensorMap ma, mb;
   std::memset(&ma, 0, sizeof ma);
   std::memset(&mb, 0, sizeof mb);
   if (use_tma) {
-    constexpr int BK = GemmK<T>::BK;
     constexpr int w = words<T>();
     if (!hsma_make_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, p.A, (uint64_t)p.M * w, (uint64_t)p.K,
-                          (uint64_t)p.lda * w, BM * w, BK) ||
+                          (uint64_t)p.lda * w, TL::BM * w, BK) ||
         !hsma_make_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, p.Bm, (uint64_t)p.K * w, (uint64_t)p.N,
-                          (uint64_t)p.ldb * w, BK * w, BN))
+                          (uint64_t)p.ldb * w, BK * w, TL::BN))
       return HSMA_ERR_CUDA;
   }
-  dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN);
+  dim3 grid(tiles_m, tiles_n, S);
   if (grid.y > 65535) return HSMA_ERR_UNSUPPORTED;
-  HsmaTraceScope ts(phase, st);
-  if (use_tma)
-    gemm_kernel<T, true><<<grid, GEMM_THREADS, gemm_smem_bytes<T>(true), st>>>(p, ma, mb);
-  else
-    gemm_kernel<T, false><<<grid, GEMM_THREADS, gemm_smem_bytes<T>(false), st>>>(p, ma, mb);
+  {
+    HsmaTraceScope ts(phase, st);
+    if (use_tma)
+      gemm_kernel<T, TL, true><<<grid, GEMM_THREADS, gemm_smem_bytes<T, TL>(true), st>>>(p, ma, mb);
+    else
+      gemm_kernel<T, TL, false><<<grid, GEMM_THREADS, gemm_smem_bytes<T, TL>(false), st>>>(p, ma, mb);
+  }
   HSMA_CUDA_TRY(cudaGetLastError());
+  if (S > 1) {
+    const int64_t total = (int64_t)p.M * p.N;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4 * sm_count());
+    HsmaTraceScope ts("reduce", st);
+    reduce_partials_kernel<T><<<blocks, 256, 0, st>>>(P, S, p.M, p.N, p.C, p.ldc, final_mode, p.beta);
+    HSMA_CUDA_TRY(cudaGetLastError());
+  }
   return HSMA_OK;
+}
+
+// Launch one product (tile shape by n; K split across CTAs when the output
+// alone has too few tiles and a partial-product workspace P is given).
+// `phase` names it for the tracer.
+template <class T>
+hsma_status_t gemm(const GemmArgs<T> &p, const char *phase, cudaStream_t st, T *P = nullptr, size_t P_elems = 0) {
+  if (p.M <= 0 || p.N <= 0) return HSMA_OK;
+  if (p.N <= 8) return gemm_tiled<T, TileN8>(p, phase, st, P, P_elems);
+  if (p.N <= 48) return gemm_tiled<T, TileN16>(p, phase, st, P, P_elems);
+  return gemm_tiled<T, TileWide>(p, phase, st, P, P_elems);
 }
 
 template <class T, int G>
@@ -458,10 +545,13 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
   void *ws = nullptr;
   const size_t dinv_bytes = sizeof(T) * (size_t)nblk * nb * nb;
   const size_t w_bytes = sizeof(T) * (size_t)nb * n;
-  hsma_status_t s = hsma_ws_alloc(&ws, dinv_bytes + w_bytes, st);
+  // partial products of split-K launches (only when n is small)
+  const size_t p_elems = (size_t)n * 64 < (size_t)2 * 152 * 64 * 64 ? partial_elems_max() : 0;
+  hsma_status_t s = hsma_ws_alloc(&ws, dinv_bytes + w_bytes + sizeof(T) * p_elems, st);
   if (s != HSMA_OK) return s;
   T *Dinv = static_cast<T *>(ws);
   T *W = reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + dinv_bytes);
+  T *Pw = p_elems ? reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + dinv_bytes + w_bytes) : nullptr;
   s = launch_inverse<T>(nb, A, lda, m, unit, Dinv, st);
   for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
     const int64_t r0 = r * nb;
@@ -489,7 +579,7 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
     ps.mode = MODE_SCALE;
     ps.beta = r == 0 ? al : one;
     ps.tri = 1;
-    s = gemm<T>(ps, "solve_gemm", st);
+    s = gemm<T>(ps, "solve_gemm", st, Pw, p_elems);
     if (s != HSMA_OK || r0 + sr >= m) break;
     // B_{r+1:} = beta B_{r+1:} - A_{r+1:, r} X_r
     GemmArgs<T> pu{};
@@ -505,7 +595,7 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
     pu.mode = MODE_UPDATE;
     pu.beta = r == 0 ? al : one;
     pu.tri = 0;
-    s = gemm<T>(pu, "update_gemm", st);
+    s = gemm<T>(pu, "update_gemm", st, Pw, p_elems);
   }
   hsma_status_t f = hsma_ws_free(ws, st);
   return s != HSMA_OK ? s : f;

@@ -460,8 +460,7 @@ def run_serve(args, dist, device):
         H.hsma_server_submit(s, reqs[k])
     H.hsma_server_drain(s, 600.0)
     base = H.hsma_server_stats(s).submitted
-    H.hsma_trace_reset()
-    H.hsma_trace_enable(True)
+    H.hsma_trace_reset()  # launch counter only: per-launch events stay off while serving
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     tickets = []
@@ -478,7 +477,6 @@ def run_serve(args, dist, device):
     t1 = time.perf_counter()
     sampler.mark(t0, t1)
     clocks = sampler.stop()
-    H.hsma_trace_enable(False)
     launches = H.hsma_trace_launches()
     lat = np.array([H.hsma_server_poll(s, t)[1] for t in tickets])
     st = H.hsma_server_stats(s)

@@ -177,7 +177,7 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batc
  *
  * The batch schedule is kept in one static device array inside the library
  * instead of stream-ordered workspace; every GPU that loads the library holds
- * that array (about 512 KB) until the process exits.  Limit: batch <= 65536
+ * that array (about 256 KB) until the process exits.  Limit: batch <= 65536
  * instances; a larger batch returns HSMA_ERR_UNSUPPORTED without launching.
  * The first call on a device looks up the array's device address (one
  * cudaGetSymbolAddress per device, made with that device current); make that
@@ -305,7 +305,8 @@ HSMA_API hsma_status_t hsma_trace_enable(int on);
 /* Total device milliseconds and launch count of `phase` since the last reset
  * (waits for the recorded events). */
 HSMA_API hsma_status_t hsma_trace_read(const char *phase, double *total_ms, long long *count);
-/* Launches of every phase since the last reset. */
+/* Kernel launches made by the library since the last reset (counted whether
+ * or not tracing is on; captured launches included). */
 HSMA_API long long hsma_trace_launches(void);
 HSMA_API void hsma_trace_reset(void);
 

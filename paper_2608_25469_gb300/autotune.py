@@ -3,7 +3,8 @@
 For every (dtype, m, n) point of a grid, time the blocked solve for each
 candidate diagonal block size N_B, keep the fastest, and write the
 "scale x dtype -> block" table: ``csrc/tuning_table.inc`` (compiled into the
-library) and a text copy loadable at run time with ``hsma_tuning_load``.  At
+library) plus ``tuning/tuning_gb300.txt`` (loadable at run time with
+``hsma_tuning_load``) and ``tuning/tuning_gb300.json`` (every candidate's time).  At
 run time the planner picks the entry nearest to the input in (log m, log n).
 
     python -m paper_2608_25469_gb300.autotune [--quick] [--out-dir DIR]
@@ -87,7 +88,7 @@ def sweep(quick=False, reps=3, budget_s=900.0):
     return rows
 
 
-def write_table(rows, out_dir):
+def write_table(rows, out_dir, data_dir=None):
     names = {0: "HSMA_R64", 1: "HSMA_C128", 2: "HSMA_R32_BF16"}
     inc = ["// Block-size table (dtype, m, n, N_B): fastest N_B per profiled point on GB300,",
            "// written by paper_2608_25469_gb300/autotune.py (Section 4.3.2's offline profiling).",
@@ -96,23 +97,26 @@ def write_table(rows, out_dir):
     inc.append("};")
     with open(os.path.join(out_dir, "tuning_table.inc"), "w") as f:
         f.write("\n".join(inc) + "\n")
-    with open(os.path.join(out_dir, "tuning_gb300.txt"), "w") as f:
+    data_dir = data_dir or out_dir
+    os.makedirs(data_dir, exist_ok=True)
+    with open(os.path.join(data_dir, "tuning_gb300.txt"), "w") as f:
         f.write("# dtype m n nb  (fastest N_B per point; per-candidate ms in tuning_gb300.json)\n")
         for r in rows:
             f.write(f"{r['dtype']} {r['m']} {r['n']} {r['nb']}\n")
-    with open(os.path.join(out_dir, "tuning_gb300.json"), "w") as f:
+    with open(os.path.join(data_dir, "tuning_gb300.json"), "w") as f:
         json.dump(rows, f, indent=1)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true")
-    ap.add_argument("--out-dir", default=os.path.join(HERE, "csrc"))
+    ap.add_argument("--out-dir", default=os.path.join(HERE, "csrc"), help="where tuning_table.inc goes")
+    ap.add_argument("--data-dir", default=os.path.join(HERE, "tuning"), help="text and JSON copies of the sweep")
     ap.add_argument("--budget-s", type=float, default=900.0)
     a = ap.parse_args()
     rows = sweep(a.quick, budget_s=a.budget_s)
     os.makedirs(a.out_dir, exist_ok=True)
-    write_table(rows, a.out_dir)
+    write_table(rows, a.out_dir, a.data_dir)
 
 
 if __name__ == "__main__":

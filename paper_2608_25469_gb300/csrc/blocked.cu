@@ -172,6 +172,9 @@ struct GemmArgs {
   int unit;
   int kchunk;  // K per z-slice (a multiple of BK); K when not split
   T *P;        // PARTIAL: slices of M x N (ld M)
+  T *C2;       // rows < split_rows are written to C2 (ld ldc2) instead of C; old values still come from C
+  int64_t ldc2;
+  int split_rows;
   const int *skip;  // device flag: when set, the launch does nothing
   unsigned int *err;
   uint64_t limit_ns;
@@ -279,12 +282,35 @@ __device__ __forceinline__ void finish_elem(int mode, T beta, bool b1, T *cp, T 
 template <class T, class TL>
 __device__ __forceinline__ void epilogue(const GemmArgs<T> &p, const Acc<T, TL> &acc, int m0, int n0, int wm, int wn,
                                          int g, int t) {
+  using E = Elem<T>;
   const bool b1 = is_one(p.beta);
   T *P = p.P + (size_t)blockIdx.z * p.M * p.N;
 #pragma unroll
   for (int i = 0; i < TL::WM; ++i) {
     const int row = m0 + wm * TL::WM * 8 + i * 8 + g;
     if (row >= p.M) continue;
+    if (p.mode == MODE_PARTIAL) {
+#pragma unroll
+      for (int jn = 0; jn < TL::WN; ++jn)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int col = n0 + wn * TL::WN * 8 + jn * 8 + 2 * t + q;
+          if (col < p.N) P[row + (size_t)col * p.M] = acc.get(i, jn, q);
+        }
+      continue;
+    }
+    // this row's old values of C first, then the results (loads do not wait behind stores)
+    T old[TL::WN][2];
+    if (p.mode == MODE_UPDATE) {
+#pragma unroll
+      for (int jn = 0; jn < TL::WN; ++jn)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int col = n0 + wn * TL::WN * 8 + jn * 8 + 2 * t + q;
+          old[jn][q] = col < p.N ? p.C[row + (int64_t)col * p.ldc] : E::zero();
+        }
+    }
+    const bool redirect = row < p.split_rows;
 #pragma unroll
     for (int jn = 0; jn < TL::WN; ++jn)
 #pragma unroll
@@ -292,10 +318,11 @@ __device__ __forceinline__ void epilogue(const GemmArgs<T> &p, const Acc<T, TL> 
         const int col = n0 + wn * TL::WN * 8 + jn * 8 + 2 * t + q;
         if (col >= p.N) continue;
         const T v = acc.get(i, jn, q);
-        if (p.mode == MODE_PARTIAL)
-          P[row + (size_t)col * p.M] = v;
+        T *cp = redirect ? p.C2 + row + (int64_t)col * p.ldc2 : p.C + row + (int64_t)col * p.ldc;
+        if (p.mode == MODE_UPDATE)
+          *cp = sub(b1 ? old[jn][q] : E::mul(p.beta, old[jn][q]), v);
         else
-          finish_elem(p.mode, p.beta, b1, p.C + row + (int64_t)col * p.ldc, v);
+          *cp = b1 ? v : E::mul(p.beta, v);
       }
   }
 }
@@ -388,14 +415,21 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const GemmArgs<T> p,
 // C = mode(beta C, sum_z P[z]) over the M x N region, z in increasing order
 template <class T>
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const T *__restrict__ P, int S, int M, int N, T *C,
-                                                              int64_t ldc, int mode, T beta) {
+                                                              int64_t ldc, T *C2, int64_t ldc2, int split_rows,
+                                                              int mode, T beta) {
+  using E = Elem<T>;
   const int64_t total = (int64_t)M * N;
   const bool b1 = is_one(beta);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     T v = P[e];
     for (int z = 1; z < S; ++z) v = add(v, P[e + (int64_t)z * total]);
     const int row = (int)(e % M), col = (int)(e / M);
-    finish_elem(mode, beta, b1, C + row + (int64_t)col * ldc, v);
+    const T *src = C + row + (int64_t)col * ldc;
+    T *dst = row < split_rows ? C2 + row + (int64_t)col * ldc2 : C + row + (int64_t)col * ldc;
+    if (mode == MODE_UPDATE)
+      *dst = sub(b1 ? *src : E::mul(beta, *src), v);
+    else
+      *dst = b1 ? v : E::mul(beta, v);
   }
 }
 
@@ -484,7 +518,8 @@ hsma_status_t gemm_tiled(const GemmArgs<T> &p0, const char *phase, cudaStream_t 
     const int64_t total = (int64_t)p.M * p.N;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4 * sm_count());
     HsmaTraceScope ts("reduce", st);
-    reduce_partials_kernel<T><<<blocks, 256, 0, st>>>(P, S, p.M, p.N, p.C, p.ldc, final_mode, p.beta);
+    reduce_partials_kernel<T><<<blocks, 256, 0, st>>>(P, S, p.M, p.N, p.C, p.ldc, p.C2, p.ldc2, p.split_rows,
+                                                      final_mode, p.beta);
     HSMA_CUDA_TRY(cudaGetLastError());
   }
   return HSMA_OK;
@@ -553,19 +588,20 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
   T *W = reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + dinv_bytes);
   T *Pw = p_elems ? reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + dinv_bytes + w_bytes) : nullptr;
   s = launch_inverse<T>(nb, A, lda, m, unit, Dinv, st);
+  // W holds the current block row's right-hand side: copied from B for the
+  // first block, written by the previous trailing update for the others, so
+  // the solve product can write X_r straight into B_r.
+  if (s == HSMA_OK) {
+    HsmaTraceScope ts("copy", st);
+    const int s0 = (int)std::min<int64_t>(nb, m);
+    cudaError_t e = cudaMemcpy2DAsync(W, sizeof(T) * nb, B, sizeof(T) * ldb, sizeof(T) * s0, n,
+                                      cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) s = hsma_from_cuda(e);
+  }
   for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
     const int64_t r0 = r * nb;
     const int sr = (int)std::min<int64_t>(nb, m - r0);
-    // X_r = D_r^{-1} (scale * B_r): B_r is copied to W so the product can write B_r
-    {
-      HsmaTraceScope ts("copy", st);
-      cudaError_t e = cudaMemcpy2DAsync(W, sizeof(T) * nb, B + r0, sizeof(T) * ldb, sizeof(T) * sr, n,
-                                        cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess) {
-        s = hsma_from_cuda(e);
-        break;
-      }
-    }
+    // X_r = D_r^{-1} (scale * W)
     GemmArgs<T> ps{};
     ps.A = Dinv + (size_t)r * nb * nb;
     ps.lda = nb;
@@ -581,7 +617,7 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
     ps.tri = 1;
     s = gemm<T>(ps, "solve_gemm", st, Pw, p_elems);
     if (s != HSMA_OK || r0 + sr >= m) break;
-    // B_{r+1:} = beta B_{r+1:} - A_{r+1:, r} X_r
+    // B_{r+1:} = beta B_{r+1:} - A_{r+1:, r} X_r; the next block row goes to W
     GemmArgs<T> pu{};
     pu.A = A + (r0 + sr) + r0 * lda;
     pu.lda = lda;
@@ -589,6 +625,9 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
     pu.ldb = ldb;
     pu.C = B + r0 + sr;
     pu.ldc = ldb;
+    pu.C2 = W;
+    pu.ldc2 = nb;
+    pu.split_rows = (int)std::min<int64_t>(nb, m - r0 - sr);
     pu.M = (int)(m - r0 - sr);
     pu.N = (int)n;
     pu.K = sr;

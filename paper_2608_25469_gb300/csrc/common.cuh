@@ -165,75 +165,28 @@ __host__ __device__ inline long long hsma_small_total_instr(int m, int n, int g,
   return tiles * hsma_small_tile_instr(m, g, cplx_) + hsma_small_stage_instr(m, g, cplx_);
 }
 
-// Tile plan of the batched kernel: the n columns of an instance are covered
-// by c[lg] tiles of 32 >> lg columns with G = 1 << lg row groups (lg = 0..3),
-// laid out in that order (widest first); the counts are packed 5 bits each.
-__host__ __device__ inline unsigned hsma_plan_pack(const int c[4]) {
-  return (unsigned)c[0] | ((unsigned)c[1] << 5) | ((unsigned)c[2] << 10) | ((unsigned)c[3] << 15);
+// As above, but with the tiles dealt round-robin to the W warps of a CTA that
+// share one staged triangle: the CTA holds its warps until the busiest is done.
+__host__ __device__ inline long long hsma_small_cta_instr(int m, int n, int g, bool cplx_, int W) {
+  const int C = 32 / g;
+  const long long tiles = (n + C - 1) / C;
+  const long long rounds = (tiles + W - 1) / W;
+  return rounds * W * hsma_small_tile_instr(m, g, cplx_) + hsma_small_stage_instr(m, g, cplx_);
 }
 
-__host__ __device__ inline void hsma_plan_unpack(unsigned p, int c[4]) {
-  for (int k = 0; k < 4; ++k) c[k] = (int)((p >> (5 * k)) & 31u);
-}
-
-// Cost of a plan: tiles dealt round-robin, widest (costliest) first, to the W
-// warps of a CTA; W = 1 counts issued instructions only.
-__host__ __device__ inline long long hsma_plan_cost(int m, const int c[4], bool cplx_, int W) {
-  long long loads[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  long long total = 0;
-  int k = 0, gmax = 1;
-  for (int lg = 0; lg < 4; ++lg) {
-    if (c[lg] == 0) continue;
-    const long long tc = hsma_small_tile_instr(m, 1 << lg, cplx_);
-    for (int t = 0; t < c[lg]; ++t) {
-      loads[k % W] += tc;
-      ++k;
+// Row-group choice of the batched kernel: the allowed set is a bit mask
+// (bit log2(G)), the cost the CTA-level one above.
+__host__ __device__ inline int hsma_small_pick_g_batched(int m, int n, bool cplx_, int W, unsigned gmask) {
+  int best = 0;
+  long long bc = 0;
+  for (int lg = 0; lg < 6; ++lg) {
+    const int g = 1 << lg;
+    if (!(gmask & (1u << lg)) || !hsma_small_g_ok(g, m, cplx_)) continue;
+    const long long c = hsma_small_cta_instr(m, n, g, cplx_, W);
+    if (best == 0 || c < bc) {
+      best = g;
+      bc = c;
     }
-    total += tc * c[lg];
-    gmax = 1 << lg;
-  }
-  long long mk = 0;
-  for (int w = 0; w < W; ++w) mk = loads[w] > mk ? loads[w] : mk;
-  return (W == 1 ? total : mk * W) + hsma_small_stage_instr(m, gmax, cplx_);
-}
-
-// Cheapest plan covering n columns: for each allowed main G, as many full
-// tiles as fit, the remainder either padded into one more main tile or
-// covered by up to three narrower tiles.
-__host__ __device__ inline unsigned hsma_plan_pick(int m, int n, bool cplx_, int W, unsigned gmask) {
-  unsigned best = 0;
-  long long bc = -1;
-  for (int lgm = 0; lgm < 4; ++lgm) {
-    const int gm = 1 << lgm;
-    if (!(gmask & (1u << lgm)) || !hsma_small_g_ok(gm, m, cplx_)) continue;
-    const int C = 32 / gm, k = n / C, r = n - k * C;
-    int c[4] = {0, 0, 0, 0};
-    c[lgm] = k + (r > 0 ? 1 : 0);
-    long long cost = hsma_plan_cost(m, c, cplx_, W);
-    if (bc < 0 || cost < bc) {
-      bc = cost;
-      best = hsma_plan_pack(c);
-    }
-    if (r == 0) continue;
-    for (int a2 = 0; a2 <= 3; ++a2)
-      for (int a4 = 0; a4 <= 3 - a2; ++a4)
-        for (int a8 = 0; a8 <= 3 - a2 - a4; ++a8) {
-          if (a2 + a4 + a8 == 0 || 16 * a2 + 8 * a4 + 4 * a8 < r) continue;
-          if ((a2 && (!(gmask & 2u) || !hsma_small_g_ok(2, m, cplx_))) ||
-              (a4 && (!(gmask & 4u) || !hsma_small_g_ok(4, m, cplx_))) ||
-              (a8 && (!(gmask & 8u) || !hsma_small_g_ok(8, m, cplx_))))
-            continue;
-          int d[4] = {0, 0, 0, 0};
-          d[lgm] = k;
-          d[1] += a2;
-          d[2] += a4;
-          d[3] += a8;
-          cost = hsma_plan_cost(m, d, cplx_, W);
-          if (cost < bc) {
-            bc = cost;
-            best = hsma_plan_pack(d);
-          }
-        }
   }
   return best;
 }

@@ -157,13 +157,19 @@ __global__ void __launch_bounds__(128, 1) bf16_update_kernel(const __grid_consta
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < M) {
+        // all 32 loads of C first, then the stores (no load waits behind a store)
+        float old[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          old[j] = (col < N) ? __ldcs(C + row + (int64_t)col * ldc) : 0.0f;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + c0 + j;
           if (col < N) {
-            float *cp = C + row + (int64_t)col * ldc;
             const float a = __uint_as_float(v[j]);
-            *cp = (beta == 1.0f) ? (*cp - a) : fmaf(beta, *cp, -a);
+            __stcs(C + row + (int64_t)col * ldc, (beta == 1.0f) ? (old[j] - a) : fmaf(beta, old[j], -a));
           }
         }
       }

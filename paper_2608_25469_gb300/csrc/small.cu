@@ -40,18 +40,9 @@ namespace {
 #ifndef HSMA_VB_GMASK
 #define HSMA_VB_GMASK 0xFu
 #endif
-#ifndef HSMA_VB_COSTW
-#define HSMA_VB_COSTW 1
-#endif
 constexpr int kWarpsSingle = 2;
 constexpr int kWarpsBatched = HSMA_VB_WARPS;
-// complex G = 1 would need the 32-row triangle layout: not used in batches
-template <class T>
-constexpr unsigned batched_gmask() {
-  return sizeof(T) == sizeof(cplx) ? (HSMA_VB_GMASK & 0xEu) : HSMA_VB_GMASK;
-}
-// warps the plan cost balances tiles over (1: issued instructions only)
-constexpr int kPlanCostWarps = HSMA_VB_COSTW;
+constexpr unsigned kBatchedGMask = HSMA_VB_GMASK;
 
 // packed strict-lower triangle: column i holds rows i+1 .. MMAX-1
 __host__ __device__ constexpr int col_off(int i, int mmax) { return i * (mmax - 1) - (i * (i - 1)) / 2; }
@@ -170,39 +161,54 @@ __device__ __forceinline__ void zero_tiles(T *B, int64_t ldb, int m, int n) {
     for (int r = threadIdx.x & 31; r < m; r += 32) Elem<T>::st(B + r + (int64_t)j * ldb, Elem<T>::zero());
 }
 
-// The warps of a CTA take the tiles of an instance's plan round-robin, widest
-// first; each tile runs the variant of its row-group size.
+// Dispatch over the row-group variants compiled into the batched kernel.
 template <class T>
-__device__ __forceinline__ void run_plan(unsigned plan, const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n) {
-  constexpr unsigned mask = batched_gmask<T>();
-  int c[4];
-  hsma_plan_unpack(plan, c);
-  const int ntiles = c[0] + c[1] + c[2] + c[3];
-  for (int t = threadIdx.x >> 5; t < ntiles; t += kWarpsBatched) {
-    int rest = t, col0 = 0, lg = 0;
-    for (; lg < 3; ++lg) {
-      if (rest < c[lg]) break;
-      rest -= c[lg];
-      col0 += c[lg] * (32 >> lg);
+struct Variants {
+  static constexpr bool kCplx = sizeof(T) == sizeof(cplx);
+  __device__ __forceinline__ static void run(int g, const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n,
+                                             int tile0, int step) {
+    if constexpr ((kBatchedGMask & 1u) != 0) {
+      if (g == 1) {
+        solve_tiles<T, 1, kCplx ? 32 : 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
     }
-    col0 += rest * (32 >> lg);
-    const int width = 32 >> lg;
-    const int nc = (n - col0) < width ? (n - col0) : width;
-    if (nc <= 0) continue;
-    T *Bt = B + (int64_t)col0 * ldb;
-    if constexpr ((mask & 1u) != 0) {
-      if (lg == 0) warp_solve<T, 1, 64>(sTri, sC, Bt, ldb, m, nc);
+    if constexpr ((kBatchedGMask & 2u) != 0) {
+      if (g == 2) {
+        solve_tiles<T, 2, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
     }
-    if constexpr ((mask & 2u) != 0) {
-      if (lg == 1) warp_solve<T, 2, 64>(sTri, sC, Bt, ldb, m, nc);
+    if constexpr ((kBatchedGMask & 4u) != 0) {
+      if (g == 4) {
+        solve_tiles<T, 4, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
     }
-    if constexpr ((mask & 4u) != 0) {
-      if (lg == 2) warp_solve<T, 4, 64>(sTri, sC, Bt, ldb, m, nc);
-    }
-    if constexpr ((mask & 8u) != 0) {
-      if (lg == 3) warp_solve<T, 8, 64>(sTri, sC, Bt, ldb, m, nc);
+    if constexpr ((kBatchedGMask & 8u) != 0) {
+      if (g == 8) {
+        solve_tiles<T, 8, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        return;
+      }
     }
   }
+};
+
+// The triangle's packed layout uses MMAX = 64 for every variant except the
+// complex G = 1 one (MMAX = 32); stage with the variant's MMAX.
+template <class T>
+__device__ __forceinline__ int variant_mmax(int g) {
+  return (sizeof(T) == sizeof(cplx) && g == 1) ? 32 : 64;
+}
+
+template <class T, int W>
+__device__ __forceinline__ void stage_any(int g, T *sTri, T *sC, T *sR, const T *A, int64_t lda, int m, T alpha,
+                                          bool unit) {
+  const int rows_used = ((m + g - 1) / g) * g;
+  if (variant_mmax<T>(g) == 32)
+    stage<T, 32, W>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
+  else
+    stage<T, 64, W>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
 }
 
 template <class T>
@@ -233,8 +239,7 @@ __global__ void __launch_bounds__(32 * kWarpsSingle) small_single_kernel(const T
 // the persistent kernel then pulls instances from an atomic counter.
 //
 // Scratch layout (int32): [0] next-item counter, [1] number of scheduled
-// items, [2 .. 2+batch) scheduled instance ids, [2+batch .. 2+2*batch) their
-// tile plans.
+// items, [2 .. 2+batch) schedule entries (instance | G << 24).
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 256;
 
@@ -272,10 +277,8 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
       err |= HSMA_DEVERR_NULL_PTR;
       continue;
     }
-    const unsigned plan = hsma_plan_pick(m, n, cplx_, kPlanCostWarps, batched_gmask<T>());
-    int c[4];
-    hsma_plan_unpack(plan, c);
-    atomicAdd(&hist[cost_bucket(hsma_plan_cost(m, c, cplx_, kPlanCostWarps))], 1);
+    const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
+    atomicAdd(&hist[cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched))], 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -293,12 +296,9 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
     const int lo = m > 1 ? m : 1;
     if (m <= 0 || n <= 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) continue;
     if (dA[b] == nullptr || dB[b] == nullptr) continue;
-    const unsigned plan = hsma_plan_pick(m, n, cplx_, kPlanCostWarps, batched_gmask<T>());
-    int c[4];
-    hsma_plan_unpack(plan, c);
-    const int pos = atomicAdd(&offs[cost_bucket(hsma_plan_cost(m, c, cplx_, kPlanCostWarps))], 1);
-    scratch[2 + pos] = b;
-    scratch[2 + batch + pos] = (int32_t)plan;
+    const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
+    const int pos = atomicAdd(&offs[cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched))], 1);
+    scratch[2 + pos] = b | (g << 24);
   }
   if (err != 0 && status != nullptr) atomicOr(status, err);
 }
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(32 * kWarpsBatched, HSMA_VB_MINB) vbatched_sol
                                                                   const int32_t *__restrict__ dldb,
                                                                   const void *const *__restrict__ dA,
                                                                   void *const *__restrict__ dB, T alpha, int unit,
-                                                                  int32_t *scratch, int nbatch) {
+                                                                  int32_t *scratch) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   T *sTri, *sC, *sR;
@@ -323,11 +323,8 @@ __global__ void __launch_bounds__(32 * kWarpsBatched, HSMA_VB_MINB) vbatched_sol
     const int item = s_item;
     __syncthreads();
     if (item >= nitems) break;
-    const int b = scratch[2 + item];
-    const unsigned plan = (unsigned)scratch[2 + nbatch + item];
-    int c[4];
-    hsma_plan_unpack(plan, c);
-    const int gmax = c[3] ? 8 : c[2] ? 4 : c[1] ? 2 : 1;
+    const int e = scratch[2 + item];
+    const int b = e & 0xffffff, g = e >> 24;
     const int m = dm[b], n = dn[b];
     const T *A = static_cast<const T *>(dA[b]);
     T *B = static_cast<T *>(dB[b]);
@@ -336,8 +333,8 @@ __global__ void __launch_bounds__(32 * kWarpsBatched, HSMA_VB_MINB) vbatched_sol
       zero_tiles<T, kWarpsBatched>(B, ldb, m, n);
       continue;
     }
-    stage<T, 64, kWarpsBatched>(sTri, sC, sR, A, lda, m, ((m + gmax - 1) / gmax) * gmax, alpha, unit != 0);
-    run_plan<T>(plan, sTri, sC, B, ldb, m, n);
+    stage_any<T, kWarpsBatched>(g, sTri, sC, sR, A, lda, m, alpha, unit != 0);
+    Variants<T>::run(g, sTri, sC, B, ldb, m, n, 0, kWarpsBatched);
     __syncthreads();  // the next item restages shared memory
   }
 }
@@ -463,16 +460,13 @@ static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32
   {
     HsmaTraceScope ts("vbatched_solve", st);
     vbatched_solve_kernel<T><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dA,
-                                                                                          dB, al, unit, scratch,
-                                                                                          batch);
+                                                                                          dB, al, unit, scratch);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
 
-size_t hsma_vbatched_scratch_bytes(int32_t batch) {
-  return sizeof(int32_t) * (2 + 2 * (size_t)(batch > 0 ? batch : 0));
-}
+size_t hsma_vbatched_scratch_bytes(int32_t batch) { return sizeof(int32_t) * (2 + (size_t)(batch > 0 ? batch : 0)); }
 
 hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
@@ -494,7 +488,7 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
 namespace {
 
 constexpr int32_t kNoAllocMaxBatch = 65536;
-__device__ __align__(256) int32_t g_noalloc_scratch[2 + 2 * kNoAllocMaxBatch];
+__device__ __align__(256) int32_t g_noalloc_scratch[2 + kNoAllocMaxBatch];
 
 int32_t *noalloc_scratch(cudaError_t *err) {
   static int32_t *addr[64] = {nullptr};

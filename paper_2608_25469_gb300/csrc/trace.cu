@@ -1,4 +1,5 @@
 // Phase tracer (see trace.h): per-phase launch counts and device time.
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -22,18 +23,19 @@ struct Totals {
 };
 
 std::mutex g_mu;
-int g_enabled = -1;  // -1: not yet read from the environment
+std::atomic<int> g_enabled{-1};  // -1: not yet read from the environment
+std::atomic<long long> g_launches{0};  // every launch site, traced or not
 std::vector<Pending> g_open;  // indexed by slot
 std::vector<int> g_free_slots;
 std::vector<int> g_done;  // slots recorded, not yet folded into totals
 std::map<std::string, Totals> g_totals;
 
 bool enabled_locked() {
-  if (g_enabled < 0) {
+  if (g_enabled.load() < 0) {
     const char *e = std::getenv("HSMA_PHASE_TIMING");
-    g_enabled = (e != nullptr && e[0] == '1') ? 1 : 0;
+    g_enabled.store((e != nullptr && e[0] == '1') ? 1 : 0);
   }
-  return g_enabled == 1;
+  return g_enabled.load() == 1;
 }
 
 // fold finished records into the totals (waits for their events)
@@ -54,6 +56,8 @@ void drain_locked() {
 }  // namespace
 
 HsmaTraceScope::HsmaTraceScope(const char *phase, cudaStream_t st) : phase_(phase), st_(st), slot_(-1) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (g_enabled.load(std::memory_order_relaxed) == 0) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!enabled_locked()) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -88,7 +92,7 @@ extern "C" {
 
 HSMA_API hsma_status_t hsma_trace_enable(int on) {
   std::lock_guard<std::mutex> lk(g_mu);
-  g_enabled = on ? 1 : 0;
+  g_enabled.store(on ? 1 : 0);
   return HSMA_OK;
 }
 
@@ -102,18 +106,13 @@ HSMA_API hsma_status_t hsma_trace_read(const char *phase, double *total_ms, long
   return HSMA_OK;
 }
 
-HSMA_API long long hsma_trace_launches(void) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  drain_locked();
-  long long c = 0;
-  for (auto &kv : g_totals) c += kv.second.count;
-  return c;
-}
+HSMA_API long long hsma_trace_launches(void) { return g_launches.load(); }
 
 HSMA_API void hsma_trace_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   drain_locked();
   g_totals.clear();
+  g_launches.store(0);
 }
 
 }  // extern "C"

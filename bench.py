@@ -638,6 +638,7 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--seq-sample", type=int, default=1000)
     ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--m", type=int, default=0, help="large_*: m = n (default 16384 fp64, 8192 c128)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
@@ -657,9 +658,9 @@ def main(argv=None):
     if args.workload == "batched_c128":
         out = run_batched(args, dist, device)
     elif args.workload == "large_fp64":
-        out = run_large(args, dist, device, H.R64, 16384)
+        out = run_large(args, dist, device, H.R64, args.m or 16384)
     elif args.workload == "large_c128":
-        out = run_large(args, dist, device, H.C128, 8192)
+        out = run_large(args, dist, device, H.C128, args.m or 8192)
     elif args.workload == "single_fp64_64":
         out = run_single64(args, dist, device)
     elif args.workload == "serve":

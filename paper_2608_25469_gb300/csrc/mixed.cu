@@ -64,7 +64,7 @@ __host__ __device__ constexpr uint32_t tc_idesc() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__global__ void __launch_bounds__(128, 1) bf16_update_kernel(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(256, 1) bf16_update_kernel(const __grid_constant__ CUtensorMap mapA,
                                                              const __grid_constant__ CUtensorMap mapB, float *C,
                                                              int64_t ldc, int M, int N, int K, float beta,
                                                              unsigned int *err, uint64_t limit_ns) {
@@ -136,16 +136,31 @@ __global__ void __launch_bounds__(128, 1) bf16_update_kernel(const __grid_consta
   }
   __syncwarp();
 
-  // epilogue: thread = one row of the 128-row tile (its tensor-memory lane)
-  // tcgen05.ld is warp-collective: the whole warp takes the same branch
+  // epilogue: thread = one row of the 128-row tile (its tensor-memory lane);
+  // warps w and w+4 share lane quarter w%4 and split the columns.  The C loads
+  // of the next 32-column chunk are issued before this chunk's stores.
   const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accum, 0, limit_ns, err));
   tc_fence_after();
-  const int row = m0 + warp * 32 + lane;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = m0 + quarter * 32 + lane;
+  const int cbeg = half * (TC_BN / 2);
   if (ok) {
+    float old[32], nxt[32];
+    auto load_chunk = [&](int c0, float *dst) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = n0 + c0 + j;
+        dst[j] = (row < M && col < N) ? __ldcs(C + row + (int64_t)col * ldc) : 0.0f;
+      }
+    };
+    load_chunk(cbeg, nxt);
 #pragma unroll 1
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+    for (int c0 = cbeg; c0 < cbeg + TC_BN / 2; c0 += 32) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) old[j] = nxt[j];
+      if (c0 + 32 < cbeg + TC_BN / 2) load_chunk(c0 + 32, nxt);
       uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -157,13 +172,6 @@ __global__ void __launch_bounds__(128, 1) bf16_update_kernel(const __grid_consta
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < M) {
-        // all 32 loads of C first, then the stores (no load waits behind a store)
-        float old[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          old[j] = (col < N) ? __ldcs(C + row + (int64_t)col * ldc) : 0.0f;
-        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + c0 + j;
@@ -316,7 +324,7 @@ hsma_status_t bf16_update(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, int 
   if (err == nullptr) return HSMA_ERR_CUDA;
   dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
   HsmaTraceScope ts("update_bf16", st);
-  bf16_update_kernel<<<grid, 128, TC_SMEM, st>>>(ma, mb, C, ldc, M, N, Kp, beta, err, 4000000000ull);
+  bf16_update_kernel<<<grid, 256, TC_SMEM, st>>>(ma, mb, C, ldc, M, N, Kp, beta, err, 4000000000ull);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }

@@ -379,6 +379,18 @@ def run_large(args, dist, device, code, m):
     total_flops = dist.sum(flops, device=device)
     value = total_flops * args.steps / (ms_max * 1e-3) / 1e9
     name = "large_c128" if cplx_ else "large_fp64"
+    # the other phases' algorithmic rates: triangular solve products (sum_r s_r(s_r+1) n flops)
+    # and the diagonal-block inversion (about s_r^3/3 flops per block), x4 for complex
+    kf = 4.0 if cplx_ else 1.0
+    blocks = [min(nb, m - r0) for r0 in range(0, m, nb)]
+    solve_flops = kf * sum(sr * (sr + 1) * float(n) for sr in blocks)
+    inv_flops = kf * sum(sr ** 3 / 3.0 for sr in blocks)
+    phase_rates = {}
+    for ph, fl in (("solve_gemm", solve_flops), ("diag_inverse", inv_flops)):
+        ms_, c = phases[ph]
+        if ms_ > 0:
+            rate = fl * args.steps / (ms_ * 1e-3) / 1e9
+            phase_rates[ph] = {"gflops": round(rate, 2), "frac_of_fp64_peak": round(rate / FP64_PEAK_GFLOPS, 4)}
     return {
         "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
@@ -392,6 +404,7 @@ def run_large(args, dist, device, code, m):
                      "peak_source": "derived FP64 (DMMA shares the FP64 budget): 2 FMA/clk/SM x 152 x 2070 MHz"},
         "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phases.items()},
         "phase_share": {k: round(v[0] / tot_phase, 4) for k, v in phases.items()} if tot_phase else None,
+        "phase_rates": phase_rates,
         "gpu_launches": int(launches), "clocks": clocks,
     }
 
@@ -572,6 +585,20 @@ def run_mixed(args, dist, device, mode):
         if c:
             phases[ph] = round(ms_ / args.steps, 4)
     ms_med = float(np.median(times))
+    rates = {}
+    if mode == "r32":
+        nb = H.hsma_plan(H.R32_BF16, m, n).nb
+        kp = -(-3 * nb // 64) * 64
+        starts = list(range(0, m, nb))
+        upd = sum(2.0 * (m - r0 - min(nb, m - r0)) * n * kp for r0 in starts)
+        sol = sum(min(nb, m - r0) * (min(nb, m - r0) + 1) * float(n) for r0 in starts)
+        peaks, src = load_peaks()
+        for ph, fl, pk, unit in (("update_bf16", upd, peaks["bf16_tflops"] * 1e3, "bf16 tensor (measured burst)"),
+                                 ("solve_sgemm", sol, 152 * 128 * 2 * 2.07, "FP32 FFMA (derived: 128 FMA/clk/SM)")):
+            if ph in phases and phases[ph] > 0:
+                rate = fl / (phases[ph] * 1e-3) / 1e9
+                rates[ph] = {"gflops": round(rate, 1), "peak_gflops": round(pk, 1), "frac": round(rate / pk, 4),
+                             "peak_source": f"{unit}, {src}"}
     out = {
         "metric": METRIC, "value": round(flops / (ms_med * 1e-3) / 1e9, 3), "unit": "GFLOP/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_med, 3), "higher_is_better": True,
@@ -580,6 +607,7 @@ def run_mixed(args, dist, device, mode):
         "config": {"workload": f"mixed_{mode}: m=8192, n=4096, alpha=1, non-unit",
                    "step_includes": "a device copy of B (268 MB or 134 MB) to restore the input"},
         "phases_ms_per_step": phases,
+        "phase_rates": rates,
     }
     if mode == "ir":
         out["ir"] = {"iterations": int(info.ir_iters), "converged": int(info.converged),

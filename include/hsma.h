@@ -177,7 +177,7 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batc
  *
  * The batch schedule is kept in one static device array inside the library
  * instead of stream-ordered workspace; every GPU that loads the library holds
- * that array (about 512 KB) until the process exits.  Limit: batch <= 65536
+ * that array (about 256 KB) until the process exits.  Limit: batch <= 65536
  * instances; a larger batch returns HSMA_ERR_UNSUPPORTED without launching.
  * The first call on a device looks up the array's device address (one
  * cudaGetSymbolAddress per device, made with that device current); make that

@@ -191,75 +191,6 @@ __host__ __device__ inline int hsma_small_pick_g_batched(int m, int n, bool cplx
   return best;
 }
 
-// Tile plan of the pooled batched kernel: the n columns of an instance are
-// covered by c[lg] tiles of 32 >> lg columns with G = 1 << lg row groups
-// (lg = 0..3), laid out widest first; counts packed 5 bits each.  The warps
-// of a CTA take tiles independently, so a plan is chosen by the FP64
-// instructions it issues alone.
-__host__ __device__ inline unsigned hsma_plan_pack(const int c[4]) {
-  return (unsigned)c[0] | ((unsigned)c[1] << 5) | ((unsigned)c[2] << 10) | ((unsigned)c[3] << 15);
-}
-
-__host__ __device__ inline void hsma_plan_unpack(unsigned p, int c[4]) {
-  for (int k = 0; k < 4; ++k) c[k] = (int)((p >> (5 * k)) & 31u);
-}
-
-__host__ __device__ inline int hsma_plan_gmax(unsigned p) {
-  int c[4];
-  hsma_plan_unpack(p, c);
-  return c[3] ? 8 : c[2] ? 4 : c[1] ? 2 : 1;
-}
-
-// Cheapest covering plan: for each allowed main G, as many full tiles as fit,
-// the remainder padded into one more main tile or covered by up to three
-// narrower tiles; cost = sum of tile instructions + staging.  *cost_out gets
-// the winning cost.
-__host__ __device__ inline unsigned hsma_plan_pick_issued(int m, int n, bool cplx_, unsigned gmask,
-                                                         long long *cost_out) {
-  long long tc[4], sc[4];
-  bool ok[4];
-  for (int lg = 0; lg < 4; ++lg) {
-    ok[lg] = (gmask & (1u << lg)) && hsma_small_g_ok(1 << lg, m, cplx_);
-    tc[lg] = ok[lg] ? hsma_small_tile_instr(m, 1 << lg, cplx_) : 0;
-    sc[lg] = ok[lg] ? hsma_small_stage_instr(m, 1 << lg, cplx_) : 0;
-  }
-  unsigned best = 0;
-  long long bc = -1;
-  for (int lgm = 0; lgm < 4; ++lgm) {
-    if (!ok[lgm]) continue;
-    const int C = 32 >> lgm, k = n / C, r = n - k * C;
-    {
-      int c[4] = {0, 0, 0, 0};
-      c[lgm] = k + (r > 0 ? 1 : 0);
-      const long long cost = c[lgm] * tc[lgm] + sc[lgm];
-      if (bc < 0 || cost < bc) {
-        bc = cost;
-        best = hsma_plan_pack(c);
-      }
-    }
-    if (r == 0) continue;
-    for (int a2 = 0; a2 <= 3; ++a2)
-      for (int a4 = 0; a4 <= 3 - a2; ++a4)
-        for (int a8 = 0; a8 <= 3 - a2 - a4; ++a8) {
-          if (a2 + a4 + a8 == 0 || 16 * a2 + 8 * a4 + 4 * a8 < r) continue;
-          if ((a2 && !ok[1]) || (a4 && !ok[2]) || (a8 && !ok[3])) continue;
-          int c[4] = {0, 0, 0, 0};
-          c[lgm] = k;
-          c[1] += a2;
-          c[2] += a4;
-          c[3] += a8;
-          const int lgmax = c[3] ? 3 : c[2] ? 2 : c[1] ? 1 : 0;
-          const long long cost = c[0] * tc[0] + c[1] * tc[1] + c[2] * tc[2] + c[3] * tc[3] + sc[lgmax];
-          if (cost < bc) {
-            bc = cost;
-            best = hsma_plan_pack(c);
-          }
-        }
-  }
-  if (cost_out) *cost_out = bc;
-  return best;
-}
-
 // Device constants of this GPU's FP64 pipe used by the latency-aware choice
 // for a single solve: a warp-wide FP64 instruction occupies a sub-partition
 // for 64 cycles; a dependent step costs one FP64 latency plus, for G > 1, a

@@ -193,53 +193,84 @@ __global__ void __launch_bounds__(256, 1) bf16_update_kernel(const __grid_consta
 
 // ---------------------------------------------------------------------------
 // FP32 products on the CUDA cores: C = beta*(A*B), A optionally lower
-// triangular (row tile i0 reads k < i0 + 64 only).  64 x 64 tiles, 4 x 4 per
-// thread.
+// triangular (row tile i0 reads k < i0 + 128 only).  128 x 128 tiles, 8 x 8
+// outputs per thread, K slices of 8 staged in shared memory double-buffered
+// (the next slice is read from global memory into registers while the
+// current one is used).
 // ---------------------------------------------------------------------------
-constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16;
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8;
 
 __global__ void __launch_bounds__(256) sgemm_scale_kernel(const float *__restrict__ A, int64_t lda,
                                                           const float *__restrict__ Bm, int64_t ldb, float *C,
                                                           int64_t ldc, int M, int N, int K, float beta, int tri) {
-  __shared__ float sA[SG_BK][SG_BM];
-  __shared__ float sB[SG_BN][SG_BK + 1];
+  __shared__ __align__(16) float sA[2][SG_BK][SG_BM];
+  __shared__ __align__(16) float sB[2][SG_BK][SG_BN];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.x * SG_BM, n0 = blockIdx.y * SG_BN;
   const int kend = tri ? min(K, m0 + SG_BM) : K;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < kend; k0 += SG_BK) {
-    for (int e = tid; e < SG_BK * SG_BM; e += 256) {
-      const int kk = e / SG_BM, mm = e % SG_BM;
-      const int row = m0 + mm, col = k0 + kk;
-      sA[kk][mm] = (row < M && col < K) ? A[row + (int64_t)col * lda] : 0.0f;
+  // loader mapping: A slice 8 x 128 (k, m): thread -> (k = tid / 32, m = 4 * (tid % 32) .. +3)
+  //                 B slice 8 x 128 (k, n): thread -> (n = tid / 2, k = 4 * (tid % 2) .. +3)
+  const int ak = tid / 32, am = 4 * (tid % 32);
+  const int bn = tid / 2, bk = 4 * (tid % 2);
+  float ra[4], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = m0 + am + u, col = k0 + ak;
+      ra[u] = (row < M && col < kend) ? __ldg(A + row + (int64_t)col * lda) : 0.0f;
+      const int kr = k0 + bk + u, cn = n0 + bn;
+      rb[u] = (kr < kend && cn < N) ? __ldg(Bm + kr + (int64_t)cn * ldb) : 0.0f;
     }
-    for (int e = tid; e < SG_BN * SG_BK; e += 256) {
-      const int nn = e / SG_BK, kk = e % SG_BK;
-      const int row = k0 + kk, col = n0 + nn;
-      sB[nn][kk] = (row < K && col < N) ? Bm[row + (int64_t)col * ldb] : 0.0f;
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      sA[buf][ak][am + u] = ra[u];
+      sB[buf][bk + u][bn] = rb[u];
     }
-    __syncthreads();
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  const int nk = (kend + SG_BK - 1) / SG_BK;
+  if (nk > 0) {
+    fetch(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) fetch((kt + 1) * SG_BK);
 #pragma unroll
     for (int kk = 0; kk < SG_BK; ++kk) {
-      float a[4], b[4];
+      float a[8], b[8];
+      const float4 a0 = *reinterpret_cast<const float4 *>(&sA[cur][kk][tx * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&sA[cur][kk][64 + tx * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&sB[cur][kk][ty * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&sB[cur][kk][64 + ty * 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[kk][tx + 16 * i];
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = sB[ty + 16 * j][kk];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
+    if (kt + 1 < nk) store(cur ^ 1);
     __syncthreads();
   }
+  // thread rows: tx*4 .. +3 and 64 + tx*4 .. +3; columns: ty*4 .. +3 and 64 + ty*4 .. +3
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int j = 0; j < 8; ++j) {
+    const int col = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+    if (col >= N) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int row = m0 + tx + 16 * i, col = n0 + ty + 16 * j;
-      if (row < M && col < N) C[row + (int64_t)col * ldc] = beta * acc[i][j];
+    for (int i = 0; i < 8; ++i) {
+      const int row = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
+      if (row < M) C[row + (int64_t)col * ldc] = beta * acc[i][j];
     }
+  }
 }
 
 // ---------------------------------------------------------------------------

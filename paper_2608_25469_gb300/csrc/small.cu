@@ -23,17 +23,10 @@
 #include <mutex>
 
 #include "common.cuh"
-#include "blocked.h"
 #include "small.h"
 #include "trace.h"
 
 namespace {
-
-__device__ __forceinline__ uint64_t global_timer_ns_small() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // Warps per CTA of the single-solve kernel and of the batched kernel, the
 // batched kernel's minimum resident CTAs per SM (register cap; 0 = none) and
@@ -47,16 +40,9 @@ __device__ __forceinline__ uint64_t global_timer_ns_small() {
 #ifndef HSMA_VB_GMASK
 #define HSMA_VB_GMASK 0xFu
 #endif
-#ifndef HSMA_VB_POOL
-#define HSMA_VB_POOL 1
-#endif
 constexpr int kWarpsSingle = 2;
 constexpr int kWarpsBatched = HSMA_VB_WARPS;
 constexpr unsigned kBatchedGMask = HSMA_VB_GMASK;
-// pooled batched kernel: warps take column tiles from two staged instances
-constexpr bool kUsePool = HSMA_VB_POOL != 0;
-constexpr int kPoolWarps = 4;
-constexpr int kPoolBufs = 2;
 
 // packed strict-lower triangle: column i holds rows i+1 .. MMAX-1
 __host__ __device__ constexpr int col_off(int i, int mmax) { return i * (mmax - 1) - (i * (i - 1)) / 2; }
@@ -353,301 +339,14 @@ __global__ void __launch_bounds__(32 * kWarpsBatched, HSMA_VB_MINB) vbatched_sol
   }
 }
 
-// ---------------------------------------------------------------------------
-// Pooled varlen batch.  Each CTA keeps two instance buffers in shared memory;
-// every warp independently takes the next column tile of a staged instance,
-// and a warp that finds no tile stages the next instance into a free buffer.
-// No warp waits for the others of its CTA, so the per-instance tile plan can
-// minimise the FP64 instructions issued (tiles of 32, 16, 8 and 4 columns).
-// Scratch (int32): [0] next-item counter, [1] item count, [2 .. 2+batch)
-// instance ids longest first, [2+batch .. 2+2*batch) their tile plans.
-// ---------------------------------------------------------------------------
-enum { PB_FREE = 0, PB_STAGING = 1, PB_READY = 2 };
-constexpr int kNoTile = 1 << 28;
-
-struct PoolCtl {
-  int state;
-  int next_tile;  // >= ntiles while the buffer is not READY
-  int done;
-  int ntiles;
-  int inst, m, n;
-  unsigned plan;
-};
-
-// one warp stages an instance (no CTA barrier)
-template <class T>
-__device__ __forceinline__ void stage_warp(T *sTri, T *sC, T *sR, const T *__restrict__ A, int64_t lda, int m,
-                                           int rows_used, T alpha, bool unit) {
-  using E = Elem<T>;
-  const int lane = threadIdx.x & 31;
-  for (int r = lane; r < 64; r += 32) {
-    T rv = E::one();
-    if (r < m && !unit) rv = E::recip(E::ld(A + r + (int64_t)r * lda));
-    sR[r] = rv;
-    sC[r] = (r < m) ? E::mul(alpha, rv) : E::zero();
-  }
-  __syncwarp();
-  constexpr int U = 8, P = 2;
-  for (int i0 = 0; i0 < m; i0 += U) {
-    T v[U][P];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const int i = i0 + u, r = lane + 32 * p;
-        v[u][p] = (i < m && r > i && r < m) ? E::ld(A + r + (int64_t)i * lda) : E::zero();
-      }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const int i = i0 + u, r = lane + 32 * p;
-        if (i < m && r > i && r < rows_used) sTri[col_off(i, 64) - i - 1 + r] = E::mul(sR[r], v[u][p]);
-      }
-  }
-  __syncwarp();
-}
-
-template <class T>
-__device__ __forceinline__ void pool_tile(unsigned plan, int t, const T *sTri, const T *sC, T *B, int64_t ldb, int m,
-                                          int n) {
-  constexpr unsigned mask = sizeof(T) == sizeof(cplx) ? (kBatchedGMask & 0xEu) : kBatchedGMask;
-  int c[4];
-  hsma_plan_unpack(plan, c);
-  int rest = t, col0 = 0, lg = 0;
-  for (; lg < 3; ++lg) {
-    if (rest < c[lg]) break;
-    rest -= c[lg];
-    col0 += c[lg] * (32 >> lg);
-  }
-  col0 += rest * (32 >> lg);
-  const int width = 32 >> lg;
-  const int nc = (n - col0) < width ? (n - col0) : width;
-  if (nc <= 0) return;
-  T *Bt = B + (int64_t)col0 * ldb;
-  if constexpr ((mask & 1u) != 0) {
-    if (lg == 0) warp_solve<T, 1, 64>(sTri, sC, Bt, ldb, m, nc);
-  }
-  if constexpr ((mask & 2u) != 0) {
-    if (lg == 1) warp_solve<T, 2, 64>(sTri, sC, Bt, ldb, m, nc);
-  }
-  if constexpr ((mask & 4u) != 0) {
-    if (lg == 2) warp_solve<T, 4, 64>(sTri, sC, Bt, ldb, m, nc);
-  }
-  if constexpr ((mask & 8u) != 0) {
-    if (lg == 3) warp_solve<T, 8, 64>(sTri, sC, Bt, ldb, m, nc);
-  }
-}
-
-template <class T>
-__global__ void __launch_bounds__(1024) vbatched_schedule_pool_kernel(int batch, const int32_t *__restrict__ dm,
-                                                                      const int32_t *__restrict__ dn,
-                                                                      const int32_t *__restrict__ dlda,
-                                                                      const int32_t *__restrict__ dldb,
-                                                                      const void *const *__restrict__ dA,
-                                                                      void *const *__restrict__ dB,
-                                                                      int32_t *scratch, uint32_t *status) {
-  __shared__ int hist[kBuckets];
-  __shared__ int offs[kBuckets];
-  constexpr bool cplx_ = sizeof(T) == sizeof(cplx);
-  constexpr unsigned mask = cplx_ ? (kBatchedGMask & 0xEu) : kBatchedGMask;
-  for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) hist[k] = 0;
-  __syncthreads();
-  uint32_t err = 0;
-  for (int b = threadIdx.x; b < batch; b += blockDim.x) {
-    const int m = dm[b], n = dn[b];
-    const int lo = m > 1 ? m : 1;
-    if (m < 0 || n < 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) {
-      err |= HSMA_DEVERR_BAD_SIZE;
-      continue;
-    }
-    if (m == 0 || n == 0) continue;
-    if (dA[b] == nullptr || dB[b] == nullptr) {
-      err |= HSMA_DEVERR_NULL_PTR;
-      continue;
-    }
-    long long cost = 0;
-    hsma_plan_pick_issued(m, n, cplx_, mask, &cost);
-    atomicAdd(&hist[cost_bucket(cost)], 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int k = kBuckets - 1; k >= 0; --k) {
-      offs[k] = run;
-      run += hist[k];
-    }
-    scratch[0] = 0;
-    scratch[1] = run;
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < batch; b += blockDim.x) {
-    const int m = dm[b], n = dn[b];
-    const int lo = m > 1 ? m : 1;
-    if (m <= 0 || n <= 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) continue;
-    if (dA[b] == nullptr || dB[b] == nullptr) continue;
-    long long cost = 0;
-    const unsigned plan = hsma_plan_pick_issued(m, n, cplx_, mask, &cost);
-    const int pos = atomicAdd(&offs[cost_bucket(cost)], 1);
-    scratch[2 + pos] = b;
-    scratch[2 + batch + pos] = (int32_t)plan;
-  }
-  if (err != 0 && status != nullptr) atomicOr(status, err);
-}
-
-template <class T>
-__global__ void __launch_bounds__(32 * kPoolWarps, 3) vbatched_pool_kernel(
-    const int32_t *__restrict__ dm, const int32_t *__restrict__ dn, const int32_t *__restrict__ dlda,
-    const int32_t *__restrict__ dldb, const void *const *__restrict__ dA, void *const *__restrict__ dB, T alpha,
-    int unit, int32_t *scratch, int nbatch, unsigned int *err, uint64_t limit_ns) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ PoolCtl ctl[kPoolBufs];
-  __shared__ int s_exhausted;
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < kPoolBufs; ++k) {
-      ctl[k].state = PB_FREE;
-      ctl[k].next_tile = kNoTile;
-      ctl[k].done = 0;
-      ctl[k].ntiles = 0;
-    }
-    s_exhausted = 0;
-  }
-  __syncthreads();
-  const int nitems = *(volatile int32_t *)(scratch + 1);
-  const bool azero = Elem<T>::is_zero(alpha);
-  uint64_t idle_since = 0;
-  for (;;) {
-    int got_b = -1, got_t = -1;
-    if (lane == 0) {
-      for (int k = 0; k < kPoolBufs && got_b < 0; ++k) {
-        volatile PoolCtl &c = ctl[k];
-        if (c.state == PB_READY && c.next_tile < c.ntiles) {
-          const int t = atomicAdd(&ctl[k].next_tile, 1);
-          if (t < c.ntiles) {
-            got_b = k;
-            got_t = t;
-          }
-        }
-      }
-      if (got_b < 0 && *(volatile int *)&s_exhausted == 0) {
-        for (int k = 0; k < kPoolBufs; ++k)
-          if (atomicCAS(&ctl[k].state, PB_FREE, PB_STAGING) == PB_FREE) {
-            got_b = k;
-            got_t = -2;
-            break;
-          }
-      }
-    }
-    got_b = __shfl_sync(0xffffffffu, got_b, 0);
-    got_t = __shfl_sync(0xffffffffu, got_t, 0);
-    T *sTri = reinterpret_cast<T *>(smem + (size_t)(got_b < 0 ? 0 : got_b) * SmemLayout<T>::bytes(64));
-    T *sC = sTri + tri_elems(64);
-    T *sR = sC + 64;
-    if (got_b >= 0 && got_t >= 0) {
-      // a column tile of a staged instance
-      __threadfence_block();
-      volatile PoolCtl &c = ctl[got_b];
-      const int b = c.inst, m = c.m, n = c.n;
-      const unsigned plan = c.plan;
-      pool_tile<T>(plan, got_t, sTri, sC, static_cast<T *>(dB[b]), dldb[b], m, n);
-      __syncwarp();
-      if (lane == 0) {
-        __threadfence_block();
-        const int d = atomicAdd(&ctl[got_b].done, 1) + 1;
-        if (d == c.ntiles) {  // last tile: release the buffer
-          ctl[got_b].done = 0;
-          atomicExch(&ctl[got_b].next_tile, kNoTile);
-          __threadfence_block();
-          atomicExch(&ctl[got_b].state, PB_FREE);
-        }
-      }
-      idle_since = 0;
-      continue;
-    }
-    if (got_b >= 0) {
-      // stage the next instance into the claimed buffer
-      int item = 0;
-      if (lane == 0) item = atomicAdd(scratch, 1);
-      item = __shfl_sync(0xffffffffu, item, 0);
-      if (item >= nitems) {
-        if (lane == 0) {
-          *(volatile int *)&s_exhausted = 1;
-          __threadfence_block();
-          atomicExch(&ctl[got_b].state, PB_FREE);
-        }
-        continue;
-      }
-      const int b = scratch[2 + item];
-      const unsigned plan = (unsigned)scratch[2 + nbatch + item];
-      const int m = dm[b], n = dn[b];
-      const T *A = static_cast<const T *>(dA[b]);
-      T *B = static_cast<T *>(dB[b]);
-      const int64_t lda = dlda[b], ldb = dldb[b];
-      if (azero) {
-        for (int j = 0; j < n; ++j)
-          for (int r = lane; r < m; r += 32) Elem<T>::st(B + r + (int64_t)j * ldb, Elem<T>::zero());
-        __syncwarp();
-        if (lane == 0) atomicExch(&ctl[got_b].state, PB_FREE);
-        continue;
-      }
-      const int gmax = hsma_plan_gmax(plan);
-      stage_warp<T>(sTri, sC, sR, A, lda, m, ((m + gmax - 1) / gmax) * gmax, alpha, unit != 0);
-      if (lane == 0) {
-        int cc[4];
-        hsma_plan_unpack(plan, cc);
-        volatile PoolCtl &c = ctl[got_b];
-        c.inst = b;
-        c.m = m;
-        c.n = n;
-        c.plan = plan;
-        c.ntiles = cc[0] + cc[1] + cc[2] + cc[3];
-        c.done = 0;
-        __threadfence_block();
-        atomicExch(&ctl[got_b].next_tile, 0);
-        __threadfence_block();
-        atomicExch(&ctl[got_b].state, PB_READY);
-      }
-      __syncwarp();
-      idle_since = 0;
-      continue;
-    }
-    // nothing to take: finished once the queue is empty and no buffer is busy
-    // (decided by lane 0 so the whole warp leaves together)
-    int leave = 0;
-    if (lane == 0) {
-      bool busy = false;
-      for (int k = 0; k < kPoolBufs; ++k) busy |= *(volatile int *)&ctl[k].state != PB_FREE;
-      if (*(volatile int *)&s_exhausted && !busy) {
-        leave = 1;
-      } else {
-        const uint64_t now = global_timer_ns_small();
-        if (idle_since == 0) {
-          idle_since = now;
-        } else if (now - idle_since > limit_ns) {
-          atomicOr(err, HSMA_DEVERR_TIMEOUT);
-          leave = 1;
-        }
-      }
-    }
-    if (__shfl_sync(0xffffffffu, leave, 0)) break;
-    __nanosleep(200);
-  }
-}
-
 template <class T>
 int persistent_grid(int dev) {
   static int cached[64] = {0};
   if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
   int nsm = 0, per_sm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if constexpr (kUsePool) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_pool_kernel<T>, 32 * kPoolWarps,
-                                                  kPoolBufs * SmemLayout<T>::bytes(64));
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_solve_kernel<T>, 32 * kWarpsBatched,
-                                                  SmemLayout<T>::bytes(64));
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_solve_kernel<T>, 32 * kWarpsBatched,
+                                                SmemLayout<T>::bytes(64));
   int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (dev >= 0 && dev < 64) cached[dev] = grid;
   return grid;
@@ -657,8 +356,6 @@ template <class T>
 hsma_status_t set_smem_attrs() {
   const int bytes = (int)SmemLayout<T>::bytes(64);
   HSMA_CUDA_TRY(cudaFuncSetAttribute(vbatched_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  HSMA_CUDA_TRY(cudaFuncSetAttribute(vbatched_pool_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kPoolBufs * bytes));
   return HSMA_OK;
 }
 
@@ -755,33 +452,21 @@ static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32
   }
   {
     HsmaTraceScope ts("vbatched_schedule", st);
-      if constexpr (kUsePool)
-      vbatched_schedule_pool_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status);
-    else
-      vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status);
+    vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   int grid = persistent_grid<T>(dev);
   if (grid > batch) grid = batch;
   {
     HsmaTraceScope ts("vbatched_solve", st);
-    if constexpr (kUsePool) {
-      unsigned int *err = hsma_dev_error_ptr();
-      if (err == nullptr) return HSMA_ERR_CUDA;
-      vbatched_pool_kernel<T><<<grid, 32 * kPoolWarps, kPoolBufs * SmemLayout<T>::bytes(64), st>>>(
-          dm, dn, dlda, dldb, dA, dB, al, unit, scratch, batch, err, 4000000000ull);
-    } else {
-      vbatched_solve_kernel<T><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dA,
-                                                                                            dB, al, unit, scratch);
-    }
+    vbatched_solve_kernel<T><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dA,
+                                                                                          dB, al, unit, scratch);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
 
-size_t hsma_vbatched_scratch_bytes(int32_t batch) {
-  return sizeof(int32_t) * (2 + 2 * (size_t)(batch > 0 ? batch : 0));
-}
+size_t hsma_vbatched_scratch_bytes(int32_t batch) { return sizeof(int32_t) * (2 + (size_t)(batch > 0 ? batch : 0)); }
 
 hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
@@ -803,7 +488,7 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
 namespace {
 
 constexpr int32_t kNoAllocMaxBatch = 65536;
-__device__ __align__(256) int32_t g_noalloc_scratch[2 + 2 * kNoAllocMaxBatch];
+__device__ __align__(256) int32_t g_noalloc_scratch[2 + kNoAllocMaxBatch];
 
 int32_t *noalloc_scratch(cudaError_t *err) {
   static int32_t *addr[64] = {nullptr};

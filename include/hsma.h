@@ -103,7 +103,9 @@ typedef struct {
                           |alpha| ||B||_F) <= ir_tol; 0 = 1e-15                    */
   int32_t bf16_terms;  /* R32_BF16 / R64_IR: BF16 products per update (1 = plain,
                           3 = hi/lo split of both operands); 0 = planner           */
-  int32_t reserved;
+  int32_t ir_residual; /* R64_IR: 0 = residual products emulated in FP64 on the BF16
+                          tensor cores (exact integer slices; m <= 16384, else 1),
+                          1 = FP64 tensor products (DMMA)                          */
 } hsma_opts_t;
 
 /* Filled by hsma_trsm_llnn_ex (host memory).  Fields describing the device

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "blocked.h"
 #include "common.cuh"
@@ -64,19 +65,42 @@ __host__ __device__ constexpr uint32_t tc_idesc() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__global__ void __launch_bounds__(256, 1) bf16_update_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                             const __grid_constant__ CUtensorMap mapB, float *C,
-                                                             int64_t ldc, int M, int N, int K, float beta,
-                                                             unsigned int *err, uint64_t limit_ns) {
+// Epilogues of the tensor-core product:
+//   TC_F32:    C32 = beta*C32 - acc                    (the FP32-result update)
+//   TC_F64ACC: C64 -= w * 2^(rexp[i] + cexp[j]) * acc  (one slice pair of an
+//              emulated FP64 product; acc holds an exact integer)
+enum { TC_F32 = 0, TC_F64ACC = 1 };
+
+struct TcArgs {
+  float *C32;
+  double *C64;
+  int64_t ldc;
+  float beta;
+  double w;
+  const int *rexp;
+  const double *cscale;  // 2^cexp[j]
+  int M, N, K;
+  int tri;          // row tile i0 needs k < i0 + TC_BM only
+  const int *skip;  // device flag: when set, the launch does nothing
+  unsigned int *err;
+  uint64_t limit_ns;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                         const __grid_constant__ CUtensorMap mapB, const TcArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[TC_STAGES];
   __shared__ __align__(8) uint64_t empty[TC_STAGES];
   __shared__ __align__(8) uint64_t accum;
   __shared__ uint32_t tmem_base;
+  if (p.skip != nullptr && *(volatile const int *)p.skip != 0) return;
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-  const int nk = K / TC_BK;
+  const int kall = p.tri ? min(p.K, m0 + TC_BM) : p.K;
+  const int nk = (kall + TC_BK - 1) / TC_BK;
+  const int M = p.M, N = p.N;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -101,7 +125,7 @@ __global__ void __launch_bounds__(256, 1) bf16_update_kernel(const __grid_consta
     // producer: TMA loads into a ring of stages
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % TC_STAGES;
-      if (kb >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((kb / TC_STAGES) - 1) & 1, limit_ns, err)) break;
+      if (kb >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((kb / TC_STAGES) - 1) & 1, p.limit_ns, p.err)) break;
       unsigned char *sa = smem + s * TC_STAGE_BYTES;
       mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
       tma_load_2d(sa, &mapA, &full[s], kb * TC_BK, m0);
@@ -109,10 +133,9 @@ __global__ void __launch_bounds__(256, 1) bf16_update_kernel(const __grid_consta
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: four K = 16 steps per stage; each stage is released by a commit
-    int kb = 0;
-    for (; kb < nk; ++kb) {
+    for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % TC_STAGES;
-      if (!mbar_wait_bounded(&full[s], (kb / TC_STAGES) & 1, limit_ns, err)) break;
+      if (!mbar_wait_bounded(&full[s], (kb / TC_STAGES) & 1, p.limit_ns, p.err)) break;
       tc_fence_after();
       const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
       const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TC_A_BYTES);
@@ -137,20 +160,25 @@ __global__ void __launch_bounds__(256, 1) bf16_update_kernel(const __grid_consta
   __syncwarp();
 
   // epilogue: thread = one row of the 128-row tile (its tensor-memory lane);
-  // warps w and w+4 share lane quarter w%4 and split the columns.  The C loads
-  // of the next 32-column chunk are issued before this chunk's stores.
-  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accum, 0, limit_ns, err));
+  // warps w and w+4 share lane quarter w%4 and split the columns.  The old
+  // values of the next 32-column chunk are loaded before this chunk's stores.
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accum, 0, p.limit_ns, p.err)) && nk > 0;
   tc_fence_after();
   const int quarter = warp & 3, half = warp >> 2;
   const int row = m0 + quarter * 32 + lane;
   const int cbeg = half * (TC_BN / 2);
   if (ok) {
-    float old[32], nxt[32];
-    auto load_chunk = [&](int c0, float *dst) {
+    using V = typename std::conditional<MODE == TC_F32, float, double>::type;
+    V old[32], nxt[32];
+    const double rs = (MODE == TC_F64ACC && row < M) ? ldexp(p.w, p.rexp[row]) : 0.0;
+    auto load_chunk = [&](int c0, V *dst) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int col = n0 + c0 + j;
-        dst[j] = (row < M && col < N) ? __ldcs(C + row + (int64_t)col * ldc) : 0.0f;
+        if constexpr (MODE == TC_F32)
+          dst[j] = (row < M && col < N) ? __ldcs(p.C32 + row + (int64_t)col * p.ldc) : 0.0f;
+        else
+          dst[j] = (row < M && col < N) ? __ldcs(p.C64 + row + (int64_t)col * p.ldc) : 0.0;
       }
     };
     load_chunk(cbeg, nxt);
@@ -177,7 +205,12 @@ __global__ void __launch_bounds__(256, 1) bf16_update_kernel(const __grid_consta
           const int col = n0 + c0 + j;
           if (col < N) {
             const float a = __uint_as_float(v[j]);
-            __stcs(C + row + (int64_t)col * ldc, (beta == 1.0f) ? (old[j] - a) : fmaf(beta, old[j], -a));
+            if constexpr (MODE == TC_F32) {
+              __stcs(p.C32 + row + (int64_t)col * p.ldc,
+                     (p.beta == 1.0f) ? (old[j] - a) : fmaf(p.beta, old[j], -a));
+            } else {
+              __stcs(p.C64 + row + (int64_t)col * p.ldc, fma(-(rs * p.cscale[col]), (double)a, old[j]));
+            }
           }
         }
       }
@@ -336,28 +369,43 @@ int g_launch_grid(int64_t total) {
   return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32);
 }
 
-hsma_status_t bf16_update(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, int M, int N, int Kp, float beta, float *C,
-                          int64_t ldc, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return HSMA_OK;
-  if (Kp % TC_BK != 0 || Kp <= 0) return HSMA_ERR_INVALID_ARG;
+template <int MODE>
+hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, const TcArgs &a0, const char *phase,
+                      cudaStream_t st) {
+  if (a0.M <= 0 || a0.N <= 0) return HSMA_OK;
+  if (a0.K % TC_BK != 0 || a0.K <= 0) return HSMA_ERR_INVALID_ARG;
   static DeviceFlags attr;
   if (!attr.test()) {
-    HSMA_CUDA_TRY(cudaFuncSetAttribute(bf16_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     attr.set();
   }
   CUtensorMap ma, mb;
-  if (!hsma_make_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Ap, (uint64_t)Kp, (uint64_t)M, (uint64_t)Kp, TC_BK,
-                        TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !hsma_make_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bp, (uint64_t)Kp, (uint64_t)N, (uint64_t)Kp, TC_BK,
-                        TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
+  if (!hsma_make_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Ap, (uint64_t)a0.K, (uint64_t)a0.M, (uint64_t)a0.K,
+                        TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !hsma_make_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bp, (uint64_t)a0.K, (uint64_t)a0.N, (uint64_t)a0.K,
+                        TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
     return HSMA_ERR_CUDA;
-  unsigned int *err = hsma_dev_error_ptr();
-  if (err == nullptr) return HSMA_ERR_CUDA;
-  dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
-  HsmaTraceScope ts("update_bf16", st);
-  bf16_update_kernel<<<grid, 256, TC_SMEM, st>>>(ma, mb, C, ldc, M, N, Kp, beta, err, 4000000000ull);
+  TcArgs a = a0;
+  a.err = hsma_dev_error_ptr();
+  if (a.err == nullptr) return HSMA_ERR_CUDA;
+  if (a.limit_ns == 0) a.limit_ns = 4000000000ull;
+  dim3 grid((a.M + TC_BM - 1) / TC_BM, (a.N + TC_BN - 1) / TC_BN);
+  HsmaTraceScope ts(phase, st);
+  tc_gemm_kernel<MODE><<<grid, 256, TC_SMEM, st>>>(ma, mb, a);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
+}
+
+hsma_status_t bf16_update(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, int M, int N, int Kp, float beta, float *C,
+                          int64_t ldc, cudaStream_t st) {
+  TcArgs a{};
+  a.C32 = C;
+  a.ldc = ldc;
+  a.beta = beta;
+  a.M = M;
+  a.N = N;
+  a.K = Kp;
+  return tc_gemm<TC_F32>(Ap, Bp, a, "update_bf16", st);
 }
 
 hsma_status_t sgemm_scale(const float *A, int64_t lda, const float *Bm, int64_t ldb, float *C, int64_t ldc, int M,
@@ -440,6 +488,14 @@ __global__ void f64_to_f32_kernel(const double *__restrict__ src, int64_t lds, f
   }
 }
 
+// dst = alpha * src (m x n, both ld m)
+__global__ void scale_copy_kernel(const double *__restrict__ src, double *dst, int64_t total, double alpha,
+                                  const int *flag) {
+  if (flag != nullptr && *(volatile const int *)flag) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = alpha * src[e];
+}
+
 // X += (double) C   (or X = (double) C when assign)
 __global__ void accumulate_kernel(double *X, int64_t ldx, const float *__restrict__ Cc, int64_t ldc, int64_t rows,
                                   int64_t cols, int assign, const int *flag) {
@@ -481,6 +537,185 @@ __global__ void check_kernel(double *sums, int *state, double alpha_abs, double 
   sums[3] = 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 product emulated on the BF16 tensor cores (Ozaki-style exact slices).
+//
+// Each row i of L is scaled by 2^-e_i and each column j of X by 2^-f_j (powers
+// of two, exact) so that every entry lies in (-1, 1); an entry a is then cut
+// into kOzS signed digits, a = sum_p d_p 2^-b_p + r, b_p = 5 + 6(p-1), with
+// d_p = rint(r_{p-1} 2^b_p) in [-32, 32] and r_p = r_{p-1} - d_p 2^-b_p, all
+// exact in FP64.  A digit is exact in BF16 and a product of two digits is at
+// most 2^10, so for K <= 2^14 every partial sum of a slice-pair product is an
+// integer below 2^24: the FP32 tensor-memory accumulation is exact.  Pairs with
+// p + q <= kOzS + 1 are kept and each is folded into the FP64 result with its
+// weight 2^(e_i + f_j - b_p - b_q).  The dropped pairs and the digit remainders
+// contribute below 2^-60 of |row scale| |column scale| per product.
+// ---------------------------------------------------------------------------
+constexpr int kOzS = 10;
+constexpr int kOzMaxK = 1 << 14;
+constexpr int kOzExpEmpty = -1100;  // exponent of an all-zero row or column
+
+__host__ __device__ constexpr int oz_bits(int p) { return 5 + 6 * (p - 1); }
+
+// e_i = exponent with |L_ik| < 2^e_i over the lower triangle (unit diagonal: 1)
+__global__ void oz_rowexp_kernel(const double *__restrict__ A, int64_t lda, int M, int K, int unit, int *rexp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int k0 = blockIdx.y * 64, k1 = min(K, k0 + 64);
+  double mx = 0.0;
+  for (int k = k0; k < k1 && k <= i; ++k) {
+    const double v = (k == i && unit) ? 1.0 : fabs(A[i + (int64_t)k * lda]);
+    mx = fmax(mx, v);
+  }
+  if (mx > 0.0) {
+    int e;
+    frexp(mx, &e);
+    atomicMax(&rexp[i], e);
+  }
+}
+
+// f_j and 2^f_j for the columns of X (one CTA per column)
+__global__ void __launch_bounds__(256) oz_colexp_kernel(const double *__restrict__ X, int64_t ldx, int K, int *cexp,
+                                                        double *cscale, const int *skip) {
+  if (skip != nullptr && *(volatile const int *)skip) return;
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(X[k + (int64_t)j * ldx]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    cexp[j] = e;
+    cscale[j] = ldexp(1.0, e);
+  }
+}
+
+__device__ __forceinline__ void oz_digits(double a, __nv_bfloat16 *out, size_t stride) {
+  double r = a;
+#pragma unroll
+  for (int p = 1; p <= kOzS; ++p) {
+    const double t = ldexp(r, oz_bits(p));
+    const double d = rint(t);
+    r -= ldexp(d, -oz_bits(p));
+    out[(size_t)(p - 1) * stride] = __float2bfloat16_rn((float)d);
+  }
+}
+
+// slices of L (lower triangle of A): out[p][i][k], row-major M x Kp per slice
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(const double *__restrict__ A, int64_t lda, int M, int K,
+                                                            int Kp, int unit, const int *rexp, __nv_bfloat16 *out) {
+  __shared__ double tile[32][33];
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int kk = ty; kk < 32; kk += 8) {
+    const int i = i0 + tx, k = k0 + kk;
+    double v = 0.0;
+    if (i < M && k < K && k <= i) v = (k == i && unit) ? 1.0 : A[i + (int64_t)k * lda];
+    tile[kk][tx] = v;
+  }
+  __syncthreads();
+  const size_t stride = (size_t)M * Kp;
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, k = k0 + tx;
+    if (i >= M || k >= Kp) continue;
+    const int e = rexp[i];
+    const double a = e == kOzExpEmpty ? 0.0 : ldexp(tile[tx][ii], -e);
+    oz_digits(a, out + (size_t)i * Kp + k, stride);
+  }
+}
+
+// slices of X: out[q][j][k], row-major N x Kp per slice
+__global__ void __launch_bounds__(256) oz_slice_cols_kernel(const double *__restrict__ X, int64_t ldx, int K, int N,
+                                                            int Kp, const int *cexp, __nv_bfloat16 *out,
+                                                            const int *skip) {
+  if (skip != nullptr && *(volatile const int *)skip) return;
+  const int64_t total = (int64_t)N * Kp;
+  const size_t stride = (size_t)N * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / Kp), k = (int)(e % Kp);
+    const double x = k < K ? X[k + (int64_t)j * ldx] : 0.0;
+    oz_digits(ldexp(x, -cexp[j]), out + e, stride);
+  }
+}
+
+__global__ void oz_fill_kernel(int *p, int n, int v) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = v;
+}
+
+struct OzL {  // slices of L, built once per solve
+  __nv_bfloat16 *slices = nullptr;
+  int *rexp = nullptr;
+  int M = 0, Kp = 0;
+};
+
+size_t oz_l_bytes(int64_t m) {
+  const size_t Kp = (size_t)((m + TC_BK - 1) / TC_BK) * TC_BK;
+  return kOzS * (size_t)m * Kp * sizeof(__nv_bfloat16) + 1024 + sizeof(int) * (size_t)m;
+}
+
+size_t oz_x_bytes(int64_t m, int64_t n) {
+  const size_t Kp = (size_t)((m + TC_BK - 1) / TC_BK) * TC_BK;
+  return kOzS * (size_t)n * Kp * sizeof(__nv_bfloat16) + 1024 + (sizeof(int) + sizeof(double)) * (size_t)n + 1024;
+}
+
+hsma_status_t oz_prepare_l(const double *A, int64_t lda, int unit, int64_t m, void *ws, OzL *L, cudaStream_t st) {
+  const int Kp = (int)((m + TC_BK - 1) / TC_BK) * TC_BK;
+  unsigned char *b = static_cast<unsigned char *>(ws);
+  L->slices = reinterpret_cast<__nv_bfloat16 *>(b);
+  L->rexp = reinterpret_cast<int *>(b + ((kOzS * (size_t)m * Kp * sizeof(__nv_bfloat16) + 1023) & ~(size_t)1023));
+  L->M = (int)m;
+  L->Kp = Kp;
+  HsmaTraceScope ts("residual_slices", st);
+  oz_fill_kernel<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(L->rexp, (int)m, kOzExpEmpty);
+  oz_rowexp_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)((m + 63) / 64)), 256, 0, st>>>(A, lda, (int)m,
+                                                                                                 (int)m, unit,
+                                                                                                 L->rexp);
+  oz_slice_rows_kernel<<<dim3((unsigned)((m + 31) / 32), (unsigned)((Kp + 31) / 32)), 256, 0, st>>>(
+      A, lda, (int)m, (int)m, Kp, unit, L->rexp, L->slices);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+// R -= L X in emulated FP64 (R holds alpha B on entry); skip: device flag
+hsma_status_t oz_residual(const OzL &L, const double *X, int64_t ldx, double *R, int64_t ldr, int64_t n, void *ws,
+                          const int *skip, cudaStream_t st) {
+  const int m = L.M, Kp = L.Kp;
+  unsigned char *b = static_cast<unsigned char *>(ws);
+  __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(b);
+  size_t off = (kOzS * (size_t)n * Kp * sizeof(__nv_bfloat16) + 1023) & ~(size_t)1023;
+  int *cexp = reinterpret_cast<int *>(b + off);
+  double *cscale = reinterpret_cast<double *>(b + ((off + sizeof(int) * (size_t)n + 1023) & ~(size_t)1023));
+  {
+    HsmaTraceScope ts("residual_slices", st);
+    oz_colexp_kernel<<<(unsigned)n, 256, 0, st>>>(X, ldx, m, cexp, cscale, skip);
+    oz_slice_cols_kernel<<<g_launch_grid((int64_t)n * Kp), 256, 0, st>>>(X, ldx, m, (int)n, Kp, cexp, XS, skip);
+    HSMA_CUDA_TRY(cudaGetLastError());
+  }
+  for (int pa = 1; pa <= kOzS; ++pa)
+    for (int qb = 1; pa + qb <= kOzS + 1; ++qb) {
+      TcArgs a{};
+      a.C64 = R;
+      a.ldc = ldr;
+      a.w = ldexp(1.0, -(oz_bits(pa) + oz_bits(qb)));
+      a.rexp = L.rexp;
+      a.cscale = cscale;
+      a.M = m;
+      a.N = (int)n;
+      a.K = Kp;
+      a.tri = 1;
+      a.skip = skip;
+      hsma_status_t s = tc_gemm<TC_F64ACC>(L.slices + (size_t)(pa - 1) * m * Kp, XS + (size_t)(qb - 1) * n * Kp, a,
+                                           "residual", st);
+      if (s != HSMA_OK) return s;
+    }
+  return HSMA_OK;
+}
+
 }  // namespace
 
 hsma_status_t hsma_mixed_r32(int nb, int bf16_terms, const float *A, int64_t lda, float *B, int64_t ldb, int64_t m,
@@ -496,16 +731,24 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
   const int terms = (opts && opts->bf16_terms) ? opts->bf16_terms : 3;
   const int itmax = (opts && opts->ir_max_iter > 0) ? opts->ir_max_iter : 10;
   const double tol = (opts && opts->ir_tol > 0.0) ? opts->ir_tol : 1e-15;
+  const int res_mode = opts ? opts->ir_residual : 0;
   if (terms != 1 && terms != 3) return HSMA_ERR_INVALID_ARG;
+  if (res_mode != 0 && res_mode != 1) return HSMA_ERR_INVALID_ARG;
   if (m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  // residual products: emulated FP64 on the BF16 tensor cores unless asked
+  // otherwise or K is beyond the exactness bound of the slice sums
+  const bool emulated = res_mode == 0 && m <= kOzMaxK;
   auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
   const size_t a32_b = sizeof(float) * (size_t)m * m;
   const size_t r32_b = sizeof(float) * (size_t)m * n;
   const size_t b0_b = sizeof(double) * (size_t)m * n;
   const size_t r64_b = b0_b;
   const size_t st_b = 1024;
+  const size_t ozl_b = emulated ? al(oz_l_bytes(m)) : 0;
+  const size_t ozx_b = emulated ? al(oz_x_bytes(m, n)) : 0;
   void *ws = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&ws, al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b, st);
+  hsma_status_t s =
+      hsma_ws_alloc(&ws, al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b + ozl_b + ozx_b, st);
   if (s != HSMA_OK) return s;
   unsigned char *base = static_cast<unsigned char *>(ws);
   float *A32 = reinterpret_cast<float *>(base);
@@ -514,6 +757,9 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
   double *R64 = reinterpret_cast<double *>(base + al(a32_b) + al(r32_b) + al(b0_b));
   double *sums = reinterpret_cast<double *>(base + al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b));
   int *state = reinterpret_cast<int *>(sums + 8);
+  void *ozl_ws = base + al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b;
+  void *ozx_ws = static_cast<unsigned char *>(ozl_ws) + ozl_b;
+  OzL Lsl;
   const int grid = g_launch_grid(m * n);
   auto fail = [&](cudaError_t e) { return e == cudaSuccess ? HSMA_OK : hsma_from_cuda(e); };
   do {
@@ -529,15 +775,24 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
       sumsq_kernel<<<grid, 256, 0, st>>>(B0, m, m, n, 0, 0, sums, 1, nullptr);
       if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     }
+    if (emulated && (s = oz_prepare_l(A, lda, unit, m, ozl_ws, &Lsl, st)) != HSMA_OK) break;
     // X_0 from the FP32-result solve of the rounded data
     if ((s = r32_solve(nb, terms, A32, m, R32, m, m, n, (float)alpha, unit, st)) != HSMA_OK) break;
     accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 1, nullptr);
     for (int it = 0; it <= itmax && s == HSMA_OK; ++it) {
       // R = alpha B - L X in FP64, then the stopping test
-      if ((s = fail(cudaMemcpy2DAsync(R64, sizeof(double) * m, B0, sizeof(double) * m, sizeof(double) * m, n,
-                                      cudaMemcpyDeviceToDevice, st))) != HSMA_OK)
-        break;
-      if ((s = hsma_residual_f64(A, lda, unit, B, ldb, R64, m, m, n, alpha, state, st)) != HSMA_OK) break;
+      if (emulated) {
+        {
+          HsmaTraceScope ts("refine", st);
+          scale_copy_kernel<<<grid, 256, 0, st>>>(B0, R64, m * n, alpha, state);
+        }
+        if ((s = oz_residual(Lsl, B, ldb, R64, m, n, ozx_ws, state, st)) != HSMA_OK) break;
+      } else {
+        if ((s = fail(cudaMemcpy2DAsync(R64, sizeof(double) * m, B0, sizeof(double) * m, sizeof(double) * m, n,
+                                        cudaMemcpyDeviceToDevice, st))) != HSMA_OK)
+          break;
+        if ((s = hsma_residual_f64(A, lda, unit, B, ldb, R64, m, m, n, alpha, state, st)) != HSMA_OK) break;
+      }
       {
         HsmaTraceScope ts("refine", st);
         sumsq_kernel<<<grid, 256, 0, st>>>(R64, m, m, n, 0, 0, sums, 2, state);

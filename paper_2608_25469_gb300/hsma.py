@@ -50,7 +50,7 @@ class Plan(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("ir_max_iter", ctypes.c_int32), ("ir_tol", ctypes.c_double), ("bf16_terms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("ir_residual", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

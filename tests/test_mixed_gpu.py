@@ -103,12 +103,34 @@ def _ir(H, A, B, alpha, **kw):
     return H.from_device(dB), info
 
 
-@pytest.mark.parametrize("m,n", [(1000, 300), (300, 1000), (129, 1)])
-def test_ir_mode_reaches_fp64_accuracy(H, m, n):
+@pytest.mark.parametrize("residual", [0, 1], ids=["emulated", "dmma"])
+@pytest.mark.parametrize("m,n", [(1000, 300), (300, 1000), (129, 1), (2000, 64)])
+def test_ir_mode_reaches_fp64_accuracy(H, m, n, residual):
+    """FP64-result mode; residual products emulated on the BF16 tensor cores (exact
+    integer slices) or FP64 tensor products."""
     A, B = I.gen_A(9, m, I.R64), I.gen_B(9, m, n, I.R64)
-    X, info = _ir(H, A, B, 1.5)
+    X, info = _ir(H, A, B, 1.5, ir_residual=residual)
     assert info.converged == 1 and 1 <= info.ir_iters <= 10
     assert info.ir_residual <= 1e-15
     err = oracle.forward_error(X, oracle.solve(A, B, 1.5))
     assert err <= 1e-12, err
     assert oracle.backward_error(A, B, X, 1.5) <= 1e-14
+    assert H.hsma_device_status() == 0
+
+
+def test_ir_mode_unit_diagonal_emulated(H):
+    m, n = 700, 90
+    A0, B = I.gen_A(12, m, I.R64), I.gen_B(12, m, n, I.R64)
+    A = np.array(A0, order="F")
+    np.fill_diagonal(A, np.nan)  # never read under a unit diagonal
+    import torch
+    dA, dB = H.to_device(A), H.to_device(B)
+    info = H.Info()
+    H.hsma_trsm_llnn_ex(H.R64_IR, 1, m, n, -0.5, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=H.Opts(),
+                        info=info)
+    torch.cuda.synchronize()
+    A1 = np.array(A0, order="F")
+    np.fill_diagonal(A1, 1.0)
+    X = H.from_device(dB)
+    assert info.converged == 1
+    assert oracle.forward_error(X, oracle.solve(A1, B, -0.5)) <= 1e-12

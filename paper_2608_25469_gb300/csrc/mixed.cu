@@ -235,7 +235,9 @@ constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8;
 
 __global__ void __launch_bounds__(256) sgemm_scale_kernel(const float *__restrict__ A, int64_t lda,
                                                           const float *__restrict__ Bm, int64_t ldb, float *C,
-                                                          int64_t ldc, int M, int N, int K, float beta, int tri) {
+                                                          int64_t ldc, int M, int N, int K, float beta, int tri,
+                                                          const int *skip) {
+  if (skip != nullptr && *(volatile const int *)skip) return;
   __shared__ __align__(16) float sA[2][SG_BK][SG_BM];
   __shared__ __align__(16) float sB[2][SG_BK][SG_BN];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -347,7 +349,8 @@ __global__ void __launch_bounds__(256) convert_panel_kernel(const float *__restr
 // X_r (nb x n, column-major fp32, ldx) -> X' n x Kp row-major BF16:
 // terms 1: [hi], terms 3: [hi | lo | hi]; zero padding to Kp.
 __global__ void __launch_bounds__(256) convert_x_kernel(const float *__restrict__ X, int64_t ldx, int nb, int n,
-                                                        int terms, int Kp, __nv_bfloat16 *out) {
+                                                        int terms, int Kp, __nv_bfloat16 *out, const int *skip) {
+  if (skip != nullptr && *(volatile const int *)skip) return;
   const int64_t total = (int64_t)n * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / Kp), kp = (int)(e % Kp);
@@ -409,67 +412,154 @@ hsma_status_t bf16_update(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, int 
 }
 
 hsma_status_t sgemm_scale(const float *A, int64_t lda, const float *Bm, int64_t ldb, float *C, int64_t ldc, int M,
-                          int N, int K, float beta, int tri, cudaStream_t st) {
+                          int N, int K, float beta, int tri, const int *skip, cudaStream_t st) {
   if (M <= 0 || N <= 0) return HSMA_OK;
   dim3 grid((M + SG_BM - 1) / SG_BM, (N + SG_BN - 1) / SG_BN);
   if (grid.y > 65535) return HSMA_ERR_UNSUPPORTED;
   HsmaTraceScope ts("solve_sgemm", st);
-  sgemm_scale_kernel<<<grid, 256, 0, st>>>(A, lda, Bm, ldb, C, ldc, M, N, K, beta, tri);
+  sgemm_scale_kernel<<<grid, 256, 0, st>>>(A, lda, Bm, ldb, C, ldc, M, N, K, beta, tri, skip);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// FP32-result blocked solve in place on B (fp32).  Workspace from the pool.
-hsma_status_t r32_solve(int nb, int terms, const float *A, int64_t lda, float *B, int64_t ldb, int64_t m, int64_t n,
-                        float alpha, int unit, cudaStream_t st) {
-  if (nb < 32) nb = 32;
-  const int64_t nblk = (m + nb - 1) / nb;
-  const int Kp = round_up(terms * nb, TC_BK);
+// Pieces of the FP32-result solve that depend on A only: the FP32 inverses of
+// the diagonal blocks and (when kept) the BF16 operand panels of every
+// trailing update.  The refinement reuses them for all its corrections.
+struct R32Plan {
+  int nb = 0, terms = 0, Kp = 0;
+  int64_t m = 0;
+  const float *A = nullptr;
+  int64_t lda = 0;
+  int unit = 0;
+  float *Dinv = nullptr;
+  __nv_bfloat16 *panels = nullptr;  // step r's panel at panel_off(r), rows x Kp; null: converted per step
+};
+
+int64_t panel_rows(const R32Plan &P, int64_t r) {
+  const int64_t r0 = r * P.nb, sr = std::min<int64_t>(P.nb, P.m - r0);
+  return std::max<int64_t>(P.m - r0 - sr, 0);
+}
+
+size_t panel_off(const R32Plan &P, int64_t r) {
+  size_t off = 0;
+  for (int64_t q = 0; q < r; ++q) off += (size_t)panel_rows(P, q) * P.Kp;
+  return off;
+}
+
+size_t r32_panels_elems(int nb, int terms, int64_t m) {
+  R32Plan P;
+  P.nb = nb;
+  P.m = m;
+  P.Kp = round_up(terms * nb, TC_BK);
+  return panel_off(P, (m + nb - 1) / nb);
+}
+
+// copy rows x cols (column-major) unless *skip is set
+__global__ void copy_f32_kernel(const float *__restrict__ src, int64_t lds, float *dst, int64_t ldd, int rows,
+                                int64_t cols, const int *skip) {
+  if (skip != nullptr && *(volatile const int *)skip) return;
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    dst[i + j * ldd] = src[i + j * lds];
+  }
+}
+
+hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
+  hsma_status_t s = hsma_diag_inverse(HSMA_R32_BF16, P.nb, P.A, P.lda, P.m, P.unit, P.Dinv, st);
+  if (s != HSMA_OK || !keep_panels) return s;
+  const int64_t nblk = (P.m + P.nb - 1) / P.nb;
+  HsmaTraceScope ts("convert", st);
+  for (int64_t r = 0; r + 1 < nblk; ++r) {
+    const int64_t r0 = r * P.nb, sr = std::min<int64_t>(P.nb, P.m - r0);
+    const int rows = (int)panel_rows(P, r);
+    dim3 g1((rows + 31) / 32, (P.nb + 31) / 32);
+    convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, P.nb, P.terms, P.Kp,
+                                             P.panels + panel_off(P, r));
+  }
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+// Phase 2 of the FP32-result solve, in place on B (fp32).  Every launch is
+// skipped once *skip is set on the device (null: never).
+hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, float alpha, const int *skip,
+                        cudaStream_t st) {
+  const int nb = P.nb, Kp = P.Kp;
+  const int64_t m = P.m, nblk = (m + nb - 1) / nb;
   const int64_t rows_max = std::max<int64_t>(m - nb, 1);
-  const size_t dinv_b = sizeof(float) * (size_t)nblk * nb * nb;
   const size_t w_b = sizeof(float) * (size_t)nb * n;
-  const size_t a_b = sizeof(__nv_bfloat16) * (size_t)rows_max * Kp;
+  const size_t a_b = P.panels ? 0 : sizeof(__nv_bfloat16) * (size_t)rows_max * Kp;
   const size_t x_b = sizeof(__nv_bfloat16) * (size_t)n * Kp;
   auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
   void *ws = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&ws, al(dinv_b) + al(w_b) + al(a_b) + al(x_b), st);
+  hsma_status_t s = hsma_ws_alloc(&ws, al(w_b) + al(a_b) + al(x_b), st);
   if (s != HSMA_OK) return s;
   unsigned char *base = static_cast<unsigned char *>(ws);
-  float *Dinv = reinterpret_cast<float *>(base);
-  float *W = reinterpret_cast<float *>(base + al(dinv_b));
-  __nv_bfloat16 *Ap = reinterpret_cast<__nv_bfloat16 *>(base + al(dinv_b) + al(w_b));
-  __nv_bfloat16 *Xp = reinterpret_cast<__nv_bfloat16 *>(base + al(dinv_b) + al(w_b) + al(a_b));
-  s = hsma_diag_inverse(HSMA_R32_BF16, nb, A, lda, m, unit, Dinv, st);
+  float *W = reinterpret_cast<float *>(base);
+  __nv_bfloat16 *Ap = reinterpret_cast<__nv_bfloat16 *>(base + al(w_b));
+  __nv_bfloat16 *Xp = reinterpret_cast<__nv_bfloat16 *>(base + al(w_b) + al(a_b));
   for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
     const int64_t r0 = r * nb;
     const int sr = (int)std::min<int64_t>(nb, m - r0);
     {
       HsmaTraceScope ts("copy", st);
-      cudaError_t e = cudaMemcpy2DAsync(W, sizeof(float) * nb, B + r0, sizeof(float) * ldb, sizeof(float) * sr, n,
-                                        cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess) {
-        s = hsma_from_cuda(e);
-        break;
-      }
+      copy_f32_kernel<<<g_launch_grid((int64_t)sr * n), 256, 0, st>>>(B + r0, ldb, W, nb, sr, n, skip);
     }
-    s = sgemm_scale(Dinv + (size_t)r * nb * nb, nb, W, nb, B + r0, ldb, sr, (int)n, sr, r == 0 ? alpha : 1.0f, 1, st);
+    s = sgemm_scale(P.Dinv + (size_t)r * nb * nb, nb, W, nb, B + r0, ldb, sr, (int)n, sr, r == 0 ? alpha : 1.0f, 1,
+                    skip, st);
     if (s != HSMA_OK || r0 + sr >= m) break;
     const int rows = (int)(m - r0 - sr);
+    const __nv_bfloat16 *panel = P.panels ? P.panels + panel_off(P, r) : Ap;
     {
       HsmaTraceScope ts("convert", st);
-      dim3 g1((rows + 31) / 32, (nb + 31) / 32);
-      convert_panel_kernel<<<g1, 256, 0, st>>>(A + (r0 + sr) + r0 * lda, lda, rows, nb, terms, Kp, Ap);
-      convert_x_kernel<<<g_launch_grid((int64_t)n * Kp), 256, 0, st>>>(B + r0, ldb, nb, (int)n, terms, Kp, Xp);
+      if (!P.panels) {
+        dim3 g1((rows + 31) / 32, (nb + 31) / 32);
+        convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, nb, P.terms, Kp, Ap);
+      }
+      convert_x_kernel<<<g_launch_grid((int64_t)n * Kp), 256, 0, st>>>(B + r0, ldb, nb, (int)n, P.terms, Kp, Xp,
+                                                                       skip);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         s = hsma_from_cuda(e);
         break;
       }
     }
-    s = bf16_update(Ap, Xp, rows, (int)n, Kp, r == 0 ? alpha : 1.0f, B + r0 + sr, ldb, st);
+    TcArgs a{};
+    a.C32 = B + r0 + sr;
+    a.ldc = ldb;
+    a.beta = r == 0 ? alpha : 1.0f;
+    a.M = rows;
+    a.N = (int)n;
+    a.K = Kp;
+    a.skip = skip;
+    s = tc_gemm<TC_F32>(panel, Xp, a, "update_bf16", st);
   }
+  hsma_status_t f = hsma_ws_free(ws, st);
+  return s != HSMA_OK ? s : f;
+}
+
+// FP32-result blocked solve in place on B (fp32).  Workspace from the pool.
+hsma_status_t r32_solve(int nb, int terms, const float *A, int64_t lda, float *B, int64_t ldb, int64_t m, int64_t n,
+                        float alpha, int unit, cudaStream_t st) {
+  if (nb < 32) nb = 32;
+  R32Plan P;
+  P.nb = nb;
+  P.terms = terms;
+  P.Kp = round_up(terms * nb, TC_BK);
+  P.m = m;
+  P.A = A;
+  P.lda = lda;
+  P.unit = unit;
+  const int64_t nblk = (m + nb - 1) / nb;
+  void *ws = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&ws, sizeof(float) * (size_t)nblk * nb * nb, st);
+  if (s != HSMA_OK) return s;
+  P.Dinv = static_cast<float *>(ws);
+  s = r32_prepare(P, false, st);
+  if (s == HSMA_OK) s = r32_apply(P, B, ldb, n, alpha, nullptr, st);
   hsma_status_t f = hsma_ws_free(ws, st);
   return s != HSMA_OK ? s : f;
 }
@@ -746,9 +836,19 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
   const size_t st_b = 1024;
   const size_t ozl_b = emulated ? al(oz_l_bytes(m)) : 0;
   const size_t ozx_b = emulated ? al(oz_x_bytes(m, n)) : 0;
+  // the FP32 inverses and BF16 panels of L, shared by the first solve and every correction
+  R32Plan P;
+  P.nb = nb < 32 ? 32 : nb;
+  P.terms = terms;
+  P.Kp = round_up(terms * P.nb, TC_BK);
+  P.m = m;
+  P.lda = m;
+  P.unit = unit;
+  const size_t dinv_b = al(sizeof(float) * (size_t)((m + P.nb - 1) / P.nb) * P.nb * P.nb);
+  const size_t pan_b = al(sizeof(__nv_bfloat16) * r32_panels_elems(P.nb, terms, m));
   void *ws = nullptr;
-  hsma_status_t s =
-      hsma_ws_alloc(&ws, al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b + ozl_b + ozx_b, st);
+  hsma_status_t s = hsma_ws_alloc(
+      &ws, al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b + ozl_b + ozx_b + dinv_b + pan_b, st);
   if (s != HSMA_OK) return s;
   unsigned char *base = static_cast<unsigned char *>(ws);
   float *A32 = reinterpret_cast<float *>(base);
@@ -760,6 +860,9 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
   void *ozl_ws = base + al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b;
   void *ozx_ws = static_cast<unsigned char *>(ozl_ws) + ozl_b;
   OzL Lsl;
+  P.A = A32;
+  P.Dinv = reinterpret_cast<float *>(static_cast<unsigned char *>(ozx_ws) + ozx_b);
+  P.panels = reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(P.Dinv) + dinv_b);
   const int grid = g_launch_grid(m * n);
   auto fail = [&](cudaError_t e) { return e == cudaSuccess ? HSMA_OK : hsma_from_cuda(e); };
   do {
@@ -777,7 +880,8 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
     }
     if (emulated && (s = oz_prepare_l(A, lda, unit, m, ozl_ws, &Lsl, st)) != HSMA_OK) break;
     // X_0 from the FP32-result solve of the rounded data
-    if ((s = r32_solve(nb, terms, A32, m, R32, m, m, n, (float)alpha, unit, st)) != HSMA_OK) break;
+    if ((s = r32_prepare(P, true, st)) != HSMA_OK) break;
+    if ((s = r32_apply(P, R32, m, n, (float)alpha, nullptr, st)) != HSMA_OK) break;
     accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 1, nullptr);
     for (int it = 0; it <= itmax && s == HSMA_OK; ++it) {
       // R = alpha B - L X in FP64, then the stopping test
@@ -803,7 +907,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
         if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
       }
       // correction C from the FP32-result solve of L C = R (alpha = 1), X += C
-      if ((s = r32_solve(nb, terms, A32, m, R32, m, m, n, 1.0f, unit, st)) != HSMA_OK) break;
+      if ((s = r32_apply(P, R32, m, n, 1.0f, state, st)) != HSMA_OK) break;
       accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 0, state);
       if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     }

@@ -580,7 +580,8 @@ def run_mixed(args, dist, device, mode):
         times.append(e0.elapsed_time(e1))
     H.hsma_trace_enable(False)
     phases = {}
-    for ph in ("diag_inverse", "copy", "solve_sgemm", "convert", "update_bf16", "residual", "refine"):
+    for ph in ("diag_inverse", "copy", "solve_sgemm", "convert", "update_bf16", "residual_slices", "residual",
+               "refine"):
         ms_, c = H.hsma_trace_read(ph)
         if c:
             phases[ph] = round(ms_ / args.steps, 4)

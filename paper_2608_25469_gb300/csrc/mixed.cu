@@ -86,33 +86,63 @@ struct TcArgs {
   uint64_t limit_ns;
 };
 
+// 32 lanes x 16 consecutive 32-bit tensor-memory columns into registers
+// (completion awaited separately with tcgen05.wait::ld).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+// Persistent, warp-specialised product: warp 0 loads operand stages by TMA,
+// warp 1 issues the MMAs, warps 2..9 drain accumulators.  Two accumulators of
+// 256 tensor-memory columns alternate between tiles, so the epilogue of one
+// tile runs while the next tile's products accumulate.  Tiles are dealt
+// round-robin to the CTAs (one per SM).
+constexpr int TC_WARPS = 10;
+constexpr int TC_EPI_WARPS = 8;
+
 template <int MODE>
-__global__ void __launch_bounds__(256, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                         const __grid_constant__ CUtensorMap mapB, const TcArgs p) {
+__global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                                   const __grid_constant__ CUtensorMap mapB,
+                                                                   const TcArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[TC_STAGES];
   __shared__ __align__(8) uint64_t empty[TC_STAGES];
-  __shared__ __align__(8) uint64_t accum;
+  __shared__ __align__(8) uint64_t acc_full[2];
+  __shared__ __align__(8) uint64_t acc_empty[2];
+  __shared__ __align__(8) uint64_t drained;
   __shared__ uint32_t tmem_base;
   if (p.skip != nullptr && *(volatile const int *)p.skip != 0) return;
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-  const int kall = p.tri ? min(p.K, m0 + TC_BM) : p.K;
-  const int nk = (kall + TC_BK - 1) / TC_BK;
   const int M = p.M, N = p.N;
+  const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
+  const int ntiles = tiles_m * tiles_n;
+  auto tile_k = [&](int t, int &m0, int &n0) {  // tile -> origin and K-block count
+    m0 = (t % tiles_m) * TC_BM;
+    n0 = (t / tiles_m) * TC_BN;
+    const int kall = p.tri ? min(p.K, m0 + TC_BM) : p.K;
+    return (kall + TC_BK - 1) / TC_BK;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], TC_EPI_WARPS);
+    }
+    mbar_init(&drained, 1);
     fence_mbar_init();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TC_TMEM_COLS)
+                 "r"(2 * TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -121,106 +151,144 @@ __global__ void __launch_bounds__(256, 1) tc_gemm_kernel(const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    // producer: TMA loads into a ring of stages
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES;
-      if (kb >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((kb / TC_STAGES) - 1) & 1, p.limit_ns, p.err)) break;
-      unsigned char *sa = smem + s * TC_STAGE_BYTES;
-      mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
-      tma_load_2d(sa, &mapA, &full[s], kb * TC_BK, m0);
-      tma_load_2d(sa + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer: four K = 16 steps per stage; each stage is released by a commit
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES;
-      if (!mbar_wait_bounded(&full[s], (kb / TC_STAGES) & 1, p.limit_ns, p.err)) break;
-      tc_fence_after();
-      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
-      const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TC_A_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk) {
-        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(da + 2ull * kk), "l"(db + 2ull * kk), "r"(tc_idesc()), "r"(acc)
-            : "memory");
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: TMA loads into a ring of stages, across tiles
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int m0, n0;
+        const int nk = tile_k(t, m0, n0);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % TC_STAGES;
+          if (it >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((it / TC_STAGES) - 1) & 1, p.limit_ns, p.err)) {
+            ok = false;
+            break;
+          }
+          unsigned char *sa = smem + s * TC_STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+          tma_load_2d(sa, &mapA, &full[s], kb * TC_BK, m0);
+          tma_load_2d(sa + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0);
+        }
       }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: per tile, wait for a drained accumulator, then four K = 16
+      // steps per stage; each stage is released by a commit, the tile by another
+      int it = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        int m0, n0;
+        const int nk = tile_k(t, m0, n0);
+        const int b = i & 1;
+        if (i >= 2 && !mbar_wait_bounded(&acc_empty[b], ((i >> 1) - 1) & 1, p.limit_ns, p.err)) break;
+        tc_fence_after();
+        const uint32_t acc_cols = tmem + (uint32_t)(b * TC_TMEM_COLS);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % TC_STAGES;
+          if (!mbar_wait_bounded(&full[s], (it / TC_STAGES) & 1, p.limit_ns, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
+          const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TC_A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_cols),
+                "l"(da + 2ull * kk), "l"(db + 2ull * kk), "r"(tc_idesc()), "r"(acc)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty[s]))
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&acc_full[b]))
+                     : "memory");
+      }
+      // every issued product has finished before tensor memory is released,
+      // also when a wait above gave up
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&empty[s]))
+                       smem_u32(&drained))
                    : "memory");
+      mbar_wait_bounded(&drained, 0, p.limit_ns, p.err);
     }
-    // signals the epilogue once every issued product has landed in tensor memory
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(&accum))
-                 : "memory");
-  }
-  __syncwarp();
-
-  // epilogue: thread = one row of the 128-row tile (its tensor-memory lane);
-  // warps w and w+4 share lane quarter w%4 and split the columns.  The old
-  // values of the next 32-column chunk are loaded before this chunk's stores.
-  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accum, 0, p.limit_ns, p.err)) && nk > 0;
-  tc_fence_after();
-  const int quarter = warp & 3, half = warp >> 2;
-  const int row = m0 + quarter * 32 + lane;
-  const int cbeg = half * (TC_BN / 2);
-  if (ok) {
+    __syncwarp();
+  } else {
+    // epilogue warps: thread = one row of the 128-row tile (its tensor-memory
+    // lane); two warps per lane quarter split the 256 columns.  The old values
+    // of the next 32-column chunk are loaded before this chunk's stores.
+    const int ew = warp - 2;
+    const int quarter = warp & 3, half = ew >> 2;
+    const int cbeg = half * (TC_BN / 2);
     using V = typename std::conditional<MODE == TC_F32, float, double>::type;
-    V old[32], nxt[32];
-    const double rs = (MODE == TC_F64ACC && row < M) ? ldexp(p.w, p.rexp[row]) : 0.0;
-    auto load_chunk = [&](int c0, V *dst) {
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      int m0, n0;
+      const int nk = tile_k(t, m0, n0);
+      const int b = i & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[b], (i >> 1) & 1, p.limit_ns, p.err));
+      if (!ok) break;
+      tc_fence_after();
+      const int row = m0 + quarter * 32 + lane;
+      const double rs = (MODE == TC_F64ACC && row < M) ? ldexp(p.w, p.rexp[row]) : 0.0;
+      constexpr int CW = 16;  // columns per chunk: keeps ten warps within the register file
+      V old[CW], nxt[CW];
+      auto load_chunk = [&](int c0, V *dst) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = n0 + c0 + j;
-        if constexpr (MODE == TC_F32)
-          dst[j] = (row < M && col < N) ? __ldcs(p.C32 + row + (int64_t)col * p.ldc) : 0.0f;
-        else
-          dst[j] = (row < M && col < N) ? __ldcs(p.C64 + row + (int64_t)col * p.ldc) : 0.0;
-      }
-    };
-    load_chunk(cbeg, nxt);
-#pragma unroll 1
-    for (int c0 = cbeg; c0 < cbeg + TC_BN / 2; c0 += 32) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) old[j] = nxt[j];
-      if (c0 + 32 < cbeg + TC_BN / 2) load_chunk(c0 + 32, nxt);
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-            "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < CW; ++j) {
           const int col = n0 + c0 + j;
-          if (col < N) {
-            const float a = __uint_as_float(v[j]);
-            if constexpr (MODE == TC_F32) {
-              __stcs(p.C32 + row + (int64_t)col * p.ldc,
-                     (p.beta == 1.0f) ? (old[j] - a) : fmaf(p.beta, old[j], -a));
-            } else {
-              __stcs(p.C64 + row + (int64_t)col * p.ldc, fma(-(rs * p.cscale[col]), (double)a, old[j]));
+          if constexpr (MODE == TC_F32)
+            dst[j] = (row < M && col < N) ? __ldcs(p.C32 + row + (int64_t)col * p.ldc) : 0.0f;
+          else
+            dst[j] = (row < M && col < N) ? __ldcs(p.C64 + row + (int64_t)col * p.ldc) : 0.0;
+        }
+      };
+      load_chunk(cbeg, nxt);
+#pragma unroll 1
+      for (int c0 = cbeg; c0 < cbeg + TC_BN / 2; c0 += CW) {
+#pragma unroll
+        for (int j = 0; j < CW; ++j) old[j] = nxt[j];
+        if (c0 + CW < cbeg + TC_BN / 2) load_chunk(c0 + CW, nxt);
+        uint32_t v[CW];
+        const uint32_t taddr = tmem + (uint32_t)(b * TC_TMEM_COLS) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+#pragma unroll
+        for (int h = 0; h < CW / 16; ++h) tmem_ld16(taddr + 16 * h, v + 16 * h);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < M && nk > 0) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < N) {
+              const float a = __uint_as_float(v[j]);
+              if constexpr (MODE == TC_F32) {
+                __stcs(p.C32 + row + (int64_t)col * p.ldc,
+                       (p.beta == 1.0f) ? (old[j] - a) : fmaf(p.beta, old[j], -a));
+              } else {
+                __stcs(p.C64 + row + (int64_t)col * p.ldc, fma(-(rs * p.cscale[col]), (double)a, old[j]));
+              }
             }
           }
         }
       }
+      // this warp is done with accumulator b
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_TMEM_COLS)
+                 : "memory");
   }
 }
 
@@ -392,9 +460,15 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, const Tc
   a.err = hsma_dev_error_ptr();
   if (a.err == nullptr) return HSMA_ERR_CUDA;
   if (a.limit_ns == 0) a.limit_ns = 4000000000ull;
-  dim3 grid((a.M + TC_BM - 1) / TC_BM, (a.N + TC_BN - 1) / TC_BN);
+  const int tiles = ((a.M + TC_BM - 1) / TC_BM) * ((a.N + TC_BN - 1) / TC_BN);
+  static int nsm[64] = {0};
+  int dev = 0;
+  HSMA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return HSMA_ERR_UNSUPPORTED;
+  if (nsm[dev] == 0) HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
+  const int grid = tiles < nsm[dev] ? tiles : nsm[dev];
   HsmaTraceScope ts(phase, st);
-  tc_gemm_kernel<MODE><<<grid, 256, TC_SMEM, st>>>(ma, mb, a);
+  tc_gemm_kernel<MODE><<<grid, 32 * TC_WARPS, TC_SMEM, st>>>(ma, mb, a);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
@@ -882,7 +956,10 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
     // X_0 from the FP32-result solve of the rounded data
     if ((s = r32_prepare(P, true, st)) != HSMA_OK) break;
     if ((s = r32_apply(P, R32, m, n, (float)alpha, nullptr, st)) != HSMA_OK) break;
-    accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 1, nullptr);
+    {
+      HsmaTraceScope ts("refine", st);
+      accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 1, nullptr);
+    }
     for (int it = 0; it <= itmax && s == HSMA_OK; ++it) {
       // R = alpha B - L X in FP64, then the stopping test
       if (emulated) {
@@ -908,7 +985,10 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
       }
       // correction C from the FP32-result solve of L C = R (alpha = 1), X += C
       if ((s = r32_apply(P, R32, m, n, 1.0f, state, st)) != HSMA_OK) break;
-      accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 0, state);
+      {
+        HsmaTraceScope ts("refine", st);
+        accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 0, state);
+      }
       if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     }
     if (s == HSMA_OK && info != nullptr) {

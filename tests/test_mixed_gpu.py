@@ -30,7 +30,7 @@ def _bf16_bits(x32):
 
 
 @pytest.mark.parametrize("M,N,K,beta", [(300, 600, 192, 1.0), (128, 256, 64, 0.5), (77, 5, 128, 1.0),
-                                        (1000, 513, 768, 1.0)])
+                                        (1000, 513, 768, 1.0), (2100, 2600, 128, 1.0), (4000, 5000, 64, 0.5)])
 def test_bf16_update_parity(H, M, N, K, beta):
     import torch
     rng = np.random.default_rng(M + N + K)

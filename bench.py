@@ -322,6 +322,8 @@ def run_batched(args, dist, device):
 
 LARGE_SOURCES = ["paper_2608_25469_gb300/csrc/blocked.cu", "paper_2608_25469_gb300/csrc/tma.cuh",
                  "paper_2608_25469_gb300/csrc/common.cuh"]
+EMU_SOURCES = ["paper_2608_25469_gb300/csrc/mixed.cu", "paper_2608_25469_gb300/csrc/tma.cuh",
+               "paper_2608_25469_gb300/csrc/common.cuh"]
 
 
 def run_large(args, dist, device, code, m):
@@ -341,9 +343,14 @@ def run_large(args, dist, device, code, m):
     H.hsma_gen_matrix(code, 1, seed, -1, m, n, dB.data_ptr(), m, sp)
     flops = (4.0 if cplx_ else 1.0) * float(m) * m * n
     abytes = es * (m * (m + 1) / 2 + 2.0 * m * n)
+    emulated = args.fp64_products == "emulated"
+    opts = H.Opts()
+    opts.fp64_products = 1 if emulated else 0
+    opts.nb = args.nb
+    info = H.Info()
 
     def step():
-        H.hsma_trsm_llnn(code, 0, m, n, 1.0, dA.data_ptr(), m, dB.data_ptr(), m, sp)
+        H.hsma_trsm_llnn_ex(code, 0, m, n, 1.0, dA.data_ptr(), m, dB.data_ptr(), m, sp, opts=opts, info=info)
 
     for _ in range(args.warmup):
         step()
@@ -364,7 +371,8 @@ def run_large(args, dist, device, code, m):
     t1 = time.time()
     H.hsma_trace_enable(False)
     ms_max = dist.max(e0.elapsed_time(e1), device=device)
-    phases = {ph: H.hsma_trace_read(ph) for ph in ("diag_inverse", "copy", "solve_gemm", "update_gemm")}
+    phases = {ph: H.hsma_trace_read(ph) for ph in ("diag_inverse", "copy", "slices", "solve_gemm", "update_gemm")}
+    phases = {k: v for k, v in phases.items() if v[1] or k != "slices"}
     launches = H.hsma_trace_launches()
     clocks = None
     if sampler:
@@ -373,9 +381,18 @@ def run_large(args, dist, device, code, m):
     upd_ms, upd_cnt = phases["update_gemm"]
     tot_phase = sum(v[0] for v in phases.values())
     # the update products' algorithmic flops: the trailing part of m^2 n not done by the solve products
-    nb = H.hsma_plan(code, m, n).nb
+    nb = info.plan.nb
     upd_flops = (4.0 if cplx_ else 1.0) * float(n) * (m * m - m * nb)
     achieved = upd_flops / (upd_ms / max(args.steps, 1) * 1e-3) / 1e9
+    if emulated:
+        # tensor work the emulated update products issue: 55 BF16 slice-pair
+        # products of (W rows) x n x Kp per block step (W = 2 for complex)
+        w = 2 if cplx_ else 1
+        kp = -(-(w * nb) // 64) * 64
+        bf16_flops = 55 * 2.0 * sum(w * (m - r0 - min(nb, m - r0)) * float(n) * kp for r0 in range(0, m, nb))
+        peaks, src = load_peaks()
+        bf16_peak = peaks["bf16_tflops_sustained"] * 1e3
+        bf16_rate = bf16_flops / (upd_ms / max(args.steps, 1) * 1e-3) / 1e9
     total_flops = dist.sum(flops, device=device)
     value = total_flops * args.steps / (ms_max * 1e-3) / 1e9
     name = "large_c128" if cplx_ else "large_fp64"
@@ -394,14 +411,23 @@ def run_large(args, dist, device, code, m):
     return {
         "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx_ else "f64", "data": "synthetic",
-        "config": {"workload": f"{name}: one blocked solve m=n={m}, alpha=1, non-unit, N_B={nb}", "m": m, "n": n,
+        "scaling": "weak", "vs_baseline": None, "dtype": ("c128" if cplx_ else "f64") + (" (emulated: bf16 slices)" if emulated else ""),
+        "data": "synthetic",
+        "config": {"workload": f"{name}: one blocked solve m=n={m}, alpha=1, non-unit, N_B={nb}"
+                               + (", FP64 products emulated on the BF16 tensor cores" if emulated else ""),
+                   "m": m, "n": n,
                    "nb": nb, "l2": f"inputs larger than L2 ({abytes / 1e9:.2f} GB)"},
-        "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
-                     "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                     "traffic": profile_traffic(f"update_gemm_{name}.txt", LARGE_SOURCES),
-                     "kernel": "gemm_kernel (update_gemm, DMMA m8n8k4)",
-                     "peak_source": "derived FP64 (DMMA shares the FP64 budget): 2 FMA/clk/SM x 152 x 2070 MHz"},
+        "roofline": ({"bound": "tensor", "achieved": round(bf16_rate, 1), "peak": round(bf16_peak, 1),
+                      "unit": "GFLOP/s", "frac": round(bf16_rate / bf16_peak, 4),
+                      "traffic": profile_traffic(f"update_emulated_{name}.txt", EMU_SOURCES),
+                      "kernel": "tc_gemm_kernel<TC_OZ> (update_gemm, tcgen05 BF16 slice pairs)",
+                      "peak_source": f"bf16 tensor (sustained), {src}",
+                      "fp64_equivalent_gflops": round(achieved, 1)} if emulated else
+                     {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
+                      "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                      "traffic": profile_traffic(f"update_gemm_{name}.txt", LARGE_SOURCES),
+                      "kernel": "gemm_kernel (update_gemm, DMMA m8n8k4)",
+                      "peak_source": "derived FP64 (DMMA shares the FP64 budget): 2 FMA/clk/SM x 152 x 2070 MHz"}),
         "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phases.items()},
         "phase_share": {k: round(v[0] / tot_phase, 4) for k, v in phases.items()} if tot_phase else None,
         "phase_rates": phase_rates,
@@ -668,6 +694,9 @@ def main(argv=None):
     ap.add_argument("--seq-sample", type=int, default=1000)
     ap.add_argument("--streams", type=int, default=16)
     ap.add_argument("--m", type=int, default=0, help="large_*: m = n (default 16384 fp64, 8192 c128)")
+    ap.add_argument("--fp64-products", default="dmma", choices=["dmma", "emulated"],
+                    help="large_*: FP64 tensor products, or FP64 emulated on the BF16 tensor cores")
+    ap.add_argument("--nb", type=int, default=0, help="large_*: force N_B (0 = planner)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

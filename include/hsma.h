@@ -106,6 +106,14 @@ typedef struct {
   int32_t ir_residual; /* R64_IR: 0 = residual products emulated in FP64 on the BF16
                           tensor cores (exact integer slices; m <= 16384, else 1),
                           1 = FP64 tensor products (DMMA)                          */
+  int32_t fp64_products; /* R64 / C128 blocked path: 0 = FP64 tensor products
+                          (DMMA, IEEE FP64 roundings); 1 = FP64 emulated on the
+                          BF16 tensor cores: both operands cut into 10 exact
+                          6-bit digit slices per row / column scale, slice-pair
+                          products summed exactly in FP32 and folded into the
+                          FP64 result (error below 2^-59 of row max x column
+                          max per product term; N_B <= 512, default 256)      */
+  int32_t reserved;
 } hsma_opts_t;
 
 /* Filled by hsma_trsm_llnn_ex (host memory).  Fields describing the device
@@ -286,6 +294,24 @@ HSMA_API hsma_status_t hsma_server_destroy(hsma_server_t *s);
  */
 HSMA_API hsma_status_t hsma_gemm_bf16_update(int64_t M, int64_t N, int64_t K, const void *A, const void *Bt,
                                              float beta, float *C, int64_t ldc, void *stream);
+
+/*
+ * FP64 product emulated on the BF16 tensor cores, the building block of the
+ * fp64_products = 1 blocked path and of the R64_IR residual (exposed for
+ * direct use and testing): C -= A X with A (M x K), X (K x N) and C (M x N)
+ * column-major FP64 (device pointers, leading dimensions lda, ldx, ldc).  Each
+ * row of A and column of X is scaled by a power of two, cut into 10 signed
+ * 6-bit digit slices (BF16, exact), and the slice pairs with p + q <= 11 are
+ * multiplied with FP32 accumulation that stays exact for K <= 16384; each
+ * group of equal-weight pairs is added to C in FP64.  Error per entry: below
+ * 2^-59 x (max |A row|) x (max |X column|) x K, plus one FP64 rounding per
+ * group (10 groups when K <= 1600).  Errors: INVALID_ARG for negative sizes,
+ * short leading dimensions or null pointers; UNSUPPORTED for K > 16384 or
+ * M, N beyond INT32_MAX.  Workspace comes from the library's stream-ordered
+ * pool.
+ */
+HSMA_API hsma_status_t hsma_gemm_f64_emulated(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                                              const double *X, int64_t ldx, double *C, int64_t ldc, void *stream);
 
 /*
  * Device-side error bits the library's kernels raise (a bounded wait that ran

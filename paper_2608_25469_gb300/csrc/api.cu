@@ -71,6 +71,7 @@ hsma_status_t make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts
   std::memset(p, 0, sizeof(*p));
   int path = opts ? opts->path : HSMA_PATH_AUTO;
   if (path < HSMA_PATH_AUTO || path > HSMA_PATH_BLOCKED) return HSMA_ERR_INVALID_ARG;
+  if (opts && (opts->fp64_products < 0 || opts->fp64_products > 1)) return HSMA_ERR_INVALID_ARG;
   const bool small_ok = m <= 64 && (dtype == HSMA_R64 || dtype == HSMA_C128);
   if (path == HSMA_PATH_AUTO) path = small_ok ? HSMA_PATH_SMALL : HSMA_PATH_BLOCKED;
   if (path == HSMA_PATH_SMALL && !small_ok) return HSMA_ERR_UNSUPPORTED;
@@ -195,6 +196,11 @@ hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const
     case HSMA_C128:
       if (plan.path == HSMA_PATH_SMALL)
         return hsma_small_single(dtype, plan.groups, A, lda, B, ldb, (int)m, (int)n, al, unit, st);
+      if (opts != nullptr && opts->fp64_products == 1) {
+        const int nb = opts->nb != 0 ? opts->nb : 256;
+        if (info) info->plan.nb = nb;
+        return hsma_blocked_emulated(dtype, nb, A, lda, B, ldb, m, n, al, unit, st);
+      }
       return hsma_blocked_solve(dtype, plan.nb, A, lda, B, ldb, m, n, al, unit, st);
     case HSMA_R32_BF16:
       return hsma_mixed_r32(plan.nb, opts ? opts->bf16_terms : 0, static_cast<const float *>(A), lda,

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -66,21 +67,33 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Epilogues of the tensor-core product:
-//   TC_F32:    C32 = beta*C32 - acc                    (the FP32-result update)
-//   TC_F64ACC: C64 -= w * 2^(rexp[i] + cexp[j]) * acc  (one slice pair of an
-//              emulated FP64 product; acc holds an exact integer)
-enum { TC_F32 = 0, TC_F64ACC = 1 };
+//   TC_F32: C32 = beta*C32 - acc                    (the FP32-result update)
+//   TC_OZ:  C64 -/+= 2^(rexp[i] + cexp[j] + uexp[u]) * acc_u for every
+//           accumulation unit u of the tile (an emulated FP64 product; each
+//           acc_u holds an exact integer)
+enum { TC_F32 = 0, TC_OZ = 1 };
+
+// Emulated FP64 products (see the Ozaki section below): kOzS slices per
+// operand, pairs p + q <= kOzS + 1.
+constexpr int kOzS = 10;
+constexpr int kOzPairs = kOzS * (kOzS + 1) / 2;
+constexpr int kOzMaxUnits = 64;
 
 struct TcArgs {
   float *C32;
   double *C64;
   int64_t ldc;
-  float beta;
-  double w;
-  const int *rexp;
-  const double *cscale;  // 2^cexp[j]
+  float beta;      // TC_F32
+  int beta0;       // TC_OZ: 0 = the first unit overwrites C64 (old values not read)
+  int negate;      // TC_OZ: add the product instead of subtracting it
+  const int *rexp;  // TC_OZ: row exponents of A
+  const int *cexp;  // TC_OZ: column exponents of B
   int M, N, K;
   int tri;          // row tile i0 needs k < i0 + TC_BM only
+  int nunits;       // accumulation units per tile (TC_F32: 1)
+  uint8_t ubeg[kOzMaxUnits + 1];  // unit u accumulates pairs ubeg[u] .. ubeg[u+1]-1
+  int8_t uexp[kOzMaxUnits];       // TC_OZ: weight exponent of unit u
+  uint8_t pa[kOzPairs], pb[kOzPairs];  // slice of A and of B for each pair
   const int *skip;  // device flag: when set, the launch does nothing
   unsigned int *err;
   uint64_t limit_ns;
@@ -96,18 +109,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v) {
       : "r"(taddr));
 }
 
+// acc * 2^shift in FP64 for an FP32 accumulator value acc (bits f): the
+// exponent is rebased with integer operations, so the FP64 pipe only sees the
+// final addition; ldexp covers results outside the normal range.
+__device__ __forceinline__ double oz_scale(uint32_t f, int shift) {
+  if ((f & 0x7fffffffu) == 0) return 0.0;
+  const int E = (int)((f >> 23) & 0xffu) + (1023 - 127) + shift;
+  if (E >= 1 && E <= 2046)
+    return __hiloint2double((int)((f & 0x80000000u) | ((uint32_t)E << 20) | ((f & 0x7fffffu) >> 3)), (int)(f << 29));
+  return ldexp((double)__uint_as_float(f), shift);
+}
+
 // Persistent, warp-specialised product: warp 0 loads operand stages by TMA,
-// warp 1 issues the MMAs, warps 2..9 drain accumulators.  Two accumulators of
-// 256 tensor-memory columns alternate between tiles, so the epilogue of one
-// tile runs while the next tile's products accumulate.  Tiles are dealt
-// round-robin to the CTAs (one per SM).
+// warp 1 issues the MMAs, warps 2..9 drain accumulators.  Work items are
+// (tile, accumulation unit); two accumulators of 256 tensor-memory columns
+// alternate between items, so the epilogue of one item runs while the next
+// item's products accumulate.  Tiles are dealt round-robin to the CTAs (one
+// per SM).  Operands are 3-D: (K, rows, slice); a unit sums the products of
+// its slice pairs over the whole K range in one accumulator.
 constexpr int TC_WARPS = 10;
 constexpr int TC_EPI_WARPS = 8;
 
 template <int MODE>
 __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                    const __grid_constant__ CUtensorMap mapB,
-                                                                   const TcArgs p) {
+                                                                   const __grid_constant__ TcArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[TC_STAGES];
   __shared__ __align__(8) uint64_t empty[TC_STAGES];
@@ -118,7 +144,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
   if (p.skip != nullptr && *(volatile const int *)p.skip != 0) return;
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int M = p.M, N = p.N;
+  const int M = p.M, N = p.N, nunits = p.nunits;
   const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
   const int ntiles = tiles_m * tiles_n;
   auto tile_k = [&](int t, int &m0, int &n0) {  // tile -> origin and K-block count
@@ -153,64 +179,75 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: TMA loads into a ring of stages, across tiles
+      // producer: TMA loads into a ring of stages, across items
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int m0, n0;
         const int nk = tile_k(t, m0, n0);
-        for (int kb = 0; kb < nk; ++kb, ++it) {
-          const int s = it % TC_STAGES;
-          if (it >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((it / TC_STAGES) - 1) & 1, p.limit_ns, p.err)) {
-            ok = false;
-            break;
+        for (int q = 0; q < p.ubeg[nunits] && ok; ++q) {
+          const int sa = p.pa[q], sb = p.pb[q];
+          for (int kb = 0; kb < nk; ++kb, ++it) {
+            const int s = it % TC_STAGES;
+            if (it >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((it / TC_STAGES) - 1) & 1, p.limit_ns, p.err)) {
+              ok = false;
+              break;
+            }
+            unsigned char *st = smem + s * TC_STAGE_BYTES;
+            mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+            tma_load_3d(st, &mapA, &full[s], kb * TC_BK, m0, sa);
+            tma_load_3d(st + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0, sb);
           }
-          unsigned char *sa = smem + s * TC_STAGE_BYTES;
-          mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
-          tma_load_2d(sa, &mapA, &full[s], kb * TC_BK, m0);
-          tma_load_2d(sa + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0);
         }
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: per tile, wait for a drained accumulator, then four K = 16
-      // steps per stage; each stage is released by a commit, the tile by another
+      // MMA issuer: per item, wait for a drained accumulator, then four K = 16
+      // steps per stage; each stage is released by a commit, the item by another
       int it = 0, i = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int m0, n0;
         const int nk = tile_k(t, m0, n0);
-        const int b = i & 1;
-        if (i >= 2 && !mbar_wait_bounded(&acc_empty[b], ((i >> 1) - 1) & 1, p.limit_ns, p.err)) break;
-        tc_fence_after();
-        const uint32_t acc_cols = tmem + (uint32_t)(b * TC_TMEM_COLS);
-        for (int kb = 0; kb < nk; ++kb, ++it) {
-          const int s = it % TC_STAGES;
-          if (!mbar_wait_bounded(&full[s], (it / TC_STAGES) & 1, p.limit_ns, p.err)) {
+        for (int u = 0; u < nunits && ok; ++u, ++i) {
+          const int b = i & 1;
+          if (i >= 2 && !mbar_wait_bounded(&acc_empty[b], ((i >> 1) - 1) & 1, p.limit_ns, p.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
-          const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TC_A_BYTES);
+          const uint32_t acc_cols = tmem + (uint32_t)(b * TC_TMEM_COLS);
+          uint32_t accum = 0;
+          for (int q = p.ubeg[u]; q < p.ubeg[u + 1] && ok; ++q) {
+            for (int kb = 0; kb < nk; ++kb, ++it) {
+              const int s = it % TC_STAGES;
+              if (!mbar_wait_bounded(&full[s], (it / TC_STAGES) & 1, p.limit_ns, p.err)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
+              const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TC_A_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk) {
-            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_cols),
-                "l"(da + 2ull * kk), "l"(db + 2ull * kk), "r"(tc_idesc()), "r"(acc)
-                : "memory");
+              for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_cols),
+                    "l"(da + 2ull * kk), "l"(db + 2ull * kk), "r"(tc_idesc()), "r"(accum)
+                    : "memory");
+                accum = 1u;
+              }
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                               smem_u32(&empty[s]))
+                           : "memory");
+            }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&empty[s]))
+                           smem_u32(&acc_full[b]))
                        : "memory");
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&acc_full[b]))
-                     : "memory");
       }
       // every issued product has finished before tensor memory is released,
       // also when a wait above gave up
@@ -223,64 +260,73 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
   } else {
     // epilogue warps: thread = one row of the 128-row tile (its tensor-memory
     // lane); two warps per lane quarter split the 256 columns.  The old values
-    // of the next 32-column chunk are loaded before this chunk's stores.
+    // of the next 16-column chunk are loaded before this chunk's stores.  The
+    // units of a tile are drained in order by the same threads, so each
+    // read-modify-write of C sees the previous unit's stores.
     const int ew = warp - 2;
     const int quarter = warp & 3, half = ew >> 2;
     const int cbeg = half * (TC_BN / 2);
     using V = typename std::conditional<MODE == TC_F32, float, double>::type;
+    constexpr int CW = 16;  // columns per chunk: keeps ten warps within the register file
     int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0;
       const int nk = tile_k(t, m0, n0);
-      const int b = i & 1;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[b], (i >> 1) & 1, p.limit_ns, p.err));
-      if (!ok) break;
-      tc_fence_after();
       const int row = m0 + quarter * 32 + lane;
-      const double rs = (MODE == TC_F64ACC && row < M) ? ldexp(p.w, p.rexp[row]) : 0.0;
-      constexpr int CW = 16;  // columns per chunk: keeps ten warps within the register file
-      V old[CW], nxt[CW];
-      auto load_chunk = [&](int c0, V *dst) {
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          const int col = n0 + c0 + j;
-          if constexpr (MODE == TC_F32)
-            dst[j] = (row < M && col < N) ? __ldcs(p.C32 + row + (int64_t)col * p.ldc) : 0.0f;
-          else
-            dst[j] = (row < M && col < N) ? __ldcs(p.C64 + row + (int64_t)col * p.ldc) : 0.0;
-        }
-      };
-      load_chunk(cbeg, nxt);
-#pragma unroll 1
-      for (int c0 = cbeg; c0 < cbeg + TC_BN / 2; c0 += CW) {
-#pragma unroll
-        for (int j = 0; j < CW; ++j) old[j] = nxt[j];
-        if (c0 + CW < cbeg + TC_BN / 2) load_chunk(c0 + CW, nxt);
-        uint32_t v[CW];
-        const uint32_t taddr = tmem + (uint32_t)(b * TC_TMEM_COLS) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-#pragma unroll
-        for (int h = 0; h < CW / 16; ++h) tmem_ld16(taddr + 16 * h, v + 16 * h);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < M && nk > 0) {
+      const int rx = (MODE == TC_OZ && row < M) ? p.rexp[row] : 0;
+      for (int u = 0; u < nunits; ++u, ++i) {
+        const int b = i & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[b], (i >> 1) & 1, p.limit_ns, p.err));
+        if (!ok) break;
+        tc_fence_after();
+        const bool fresh = MODE == TC_OZ && u == 0 && p.beta0 == 0;
+        const int ushift = MODE == TC_OZ ? rx + p.uexp[u] : 0;
+        V old[CW], nxt[CW];
+        auto load_chunk = [&](int c0, V *dst) {
 #pragma unroll
           for (int j = 0; j < CW; ++j) {
             const int col = n0 + c0 + j;
-            if (col < N) {
-              const float a = __uint_as_float(v[j]);
-              if constexpr (MODE == TC_F32) {
-                __stcs(p.C32 + row + (int64_t)col * p.ldc,
-                       (p.beta == 1.0f) ? (old[j] - a) : fmaf(p.beta, old[j], -a));
-              } else {
-                __stcs(p.C64 + row + (int64_t)col * p.ldc, fma(-(rs * p.cscale[col]), (double)a, old[j]));
+            if constexpr (MODE == TC_F32)
+              dst[j] = (row < M && col < N) ? __ldcs(p.C32 + row + (int64_t)col * p.ldc) : 0.0f;
+            else
+              dst[j] = (!fresh && row < M && col < N) ? p.C64[row + (int64_t)col * p.ldc] : 0.0;
+          }
+        };
+        load_chunk(cbeg, nxt);
+#pragma unroll 1
+        for (int c0 = cbeg; c0 < cbeg + TC_BN / 2; c0 += CW) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) old[j] = nxt[j];
+          if (c0 + CW < cbeg + TC_BN / 2) load_chunk(c0 + CW, nxt);
+          uint32_t v[CW];
+          const uint32_t taddr =
+              tmem + (uint32_t)(b * TC_TMEM_COLS) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+#pragma unroll
+          for (int h = 0; h < CW / 16; ++h) tmem_ld16(taddr + 16 * h, v + 16 * h);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (row < M && nk > 0) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              const int col = n0 + c0 + j;
+              if (col < N) {
+                if constexpr (MODE == TC_F32) {
+                  const float a = __uint_as_float(v[j]);
+                  __stcs(p.C32 + row + (int64_t)col * p.ldc,
+                         (p.beta == 1.0f) ? (old[j] - a) : fmaf(p.beta, old[j], -a));
+                } else {
+                  const double x = oz_scale(v[j], ushift + __ldg(p.cexp + col));
+                  p.C64[row + (int64_t)col * p.ldc] = p.negate ? old[j] + x : old[j] - x;
+                }
               }
             }
           }
         }
+        // this warp is done with accumulator b
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[b]);
       }
-      // this warp is done with accumulator b
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
   }
   tc_fence_before();
@@ -440,9 +486,27 @@ int g_launch_grid(int64_t total) {
   return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32);
 }
 
+// 3-D tensor map over BF16 operand slices (K contiguous, rows, slice), one
+// box = 64 K-values x box_rows rows of one slice, 128-byte swizzle.
+bool make_slice_map(CUtensorMap *map, const void *base, uint64_t K, uint64_t rows, uint64_t slices,
+                    uint32_t box_rows) {
+  PFN_encodeTiled enc = hsma_encode_fn();
+  if (enc == nullptr || (uintptr_t)base % 16 != 0 || (K * 2) % 16 != 0) return false;
+  const cuuint64_t dims[3] = {K, rows, slices};
+  const cuuint64_t strides[2] = {K * 2, K * rows * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)TC_BK, box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launch the persistent product.  A: sa slices of M x K (row-major), B: sb
+// slices of N x K; the unit table of a0 names the slice pairs (TC_F32: one
+// unit, one pair, filled in here).
 template <int MODE>
-hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, const TcArgs &a0, const char *phase,
-                      cudaStream_t st) {
+hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, int sb, const TcArgs &a0,
+                      const char *phase, cudaStream_t st) {
   if (a0.M <= 0 || a0.N <= 0) return HSMA_OK;
   if (a0.K % TC_BK != 0 || a0.K <= 0) return HSMA_ERR_INVALID_ARG;
   static DeviceFlags attr;
@@ -451,12 +515,19 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, const Tc
     attr.set();
   }
   CUtensorMap ma, mb;
-  if (!hsma_make_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Ap, (uint64_t)a0.K, (uint64_t)a0.M, (uint64_t)a0.K,
-                        TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !hsma_make_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bp, (uint64_t)a0.K, (uint64_t)a0.N, (uint64_t)a0.K,
-                        TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
+  if (!make_slice_map(&ma, Ap, (uint64_t)a0.K, (uint64_t)a0.M, (uint64_t)sa, TC_BM) ||
+      !make_slice_map(&mb, Bp, (uint64_t)a0.K, (uint64_t)a0.N, (uint64_t)sb, TC_BN))
     return HSMA_ERR_CUDA;
   TcArgs a = a0;
+  if (MODE == TC_F32) {
+    a.nunits = 1;
+    a.ubeg[0] = 0;
+    a.ubeg[1] = 1;
+    a.pa[0] = a.pb[0] = 0;
+  }
+  if (a.nunits < 1 || a.nunits > kOzMaxUnits) return HSMA_ERR_INVALID_ARG;
+  for (int q = 0; q < a.ubeg[a.nunits]; ++q)
+    if (a.pa[q] >= sa || a.pb[q] >= sb) return HSMA_ERR_INVALID_ARG;
   a.err = hsma_dev_error_ptr();
   if (a.err == nullptr) return HSMA_ERR_CUDA;
   if (a.limit_ns == 0) a.limit_ns = 4000000000ull;
@@ -482,7 +553,7 @@ hsma_status_t bf16_update(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, int 
   a.M = M;
   a.N = N;
   a.K = Kp;
-  return tc_gemm<TC_F32>(Ap, Bp, a, "update_bf16", st);
+  return tc_gemm<TC_F32>(Ap, 1, Bp, 1, a, "update_bf16", st);
 }
 
 hsma_status_t sgemm_scale(const float *A, int64_t lda, const float *Bm, int64_t ldb, float *C, int64_t ldc, int M,
@@ -609,7 +680,7 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
     a.N = (int)n;
     a.K = Kp;
     a.skip = skip;
-    s = tc_gemm<TC_F32>(panel, Xp, a, "update_bf16", st);
+    s = tc_gemm<TC_F32>(panel, 1, Xp, 1, a, "update_bf16", st);
   }
   hsma_status_t f = hsma_ws_free(ws, st);
   return s != HSMA_OK ? s : f;
@@ -702,182 +773,423 @@ __global__ void check_kernel(double *sums, int *state, double alpha_abs, double 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 product emulated on the BF16 tensor cores (Ozaki-style exact slices).
+// FP64 products emulated on the BF16 tensor cores (Ozaki-style exact slices).
 //
-// Each row i of L is scaled by 2^-e_i and each column j of X by 2^-f_j (powers
-// of two, exact) so that every entry lies in (-1, 1); an entry a is then cut
-// into kOzS signed digits, a = sum_p d_p 2^-b_p + r, b_p = 5 + 6(p-1), with
-// d_p = rint(r_{p-1} 2^b_p) in [-32, 32] and r_p = r_{p-1} - d_p 2^-b_p, all
-// exact in FP64.  A digit is exact in BF16 and a product of two digits is at
-// most 2^10, so for K <= 2^14 every partial sum of a slice-pair product is an
-// integer below 2^24: the FP32 tensor-memory accumulation is exact.  Pairs with
-// p + q <= kOzS + 1 are kept and each is folded into the FP64 result with its
-// weight 2^(e_i + f_j - b_p - b_q).  The dropped pairs and the digit remainders
-// contribute below 2^-60 of |row scale| |column scale| per product.
+// Row i of the left operand is scaled by 2^-e_i and column j of the right
+// operand by 2^-f_j (powers of two with |entry| < 2^e), so every scaled entry
+// lies in (-1, 1).  It is rounded to the fixed-point integer I = a 2^(59 - e)
+// (bits below 2^-59 of the row or column scale are dropped) and cut from the
+// top into kOzS signed base-64 digits, I = sum_p d_p 2^(59 - b_p) with
+// b_p = 5 + 6(p-1) and d_p in [-32, 32], using integer operations only.  A
+// digit is exact in BF16 and a product of two digits is at most 2^10, so a sum
+// of g slice-pair products over K terms is an integer below 2^24 whenever
+// g K <= 2^14: the FP32 tensor-memory accumulation is exact.  Pairs with the
+// same p + q share the weight 2^-(b_p + b_q); they are grouped into
+// accumulation units of at most 2^14 / K pairs, and each unit is folded into
+// the FP64 result once, with weight 2^(e_i + f_j - b_p - b_q).  Pairs with
+// p + q > kOzS + 1 are dropped; they and the fixed-point rounding contribute
+// below 2^-59 of |row scale| |column scale| per product term.
 // ---------------------------------------------------------------------------
-constexpr int kOzS = 10;
+constexpr int kOzFrac = 59;
 constexpr int kOzMaxK = 1 << 14;
-constexpr int kOzExpEmpty = -1100;  // exponent of an all-zero row or column
+constexpr int kOzExpEmpty = -1100;  // exponent of an all-zero row
 
 __host__ __device__ constexpr int oz_bits(int p) { return 5 + 6 * (p - 1); }
+static_assert(oz_bits(kOzS) == kOzFrac, "the last digit has weight 2^-kOzFrac");
 
-// e_i = exponent with |L_ik| < 2^e_i over the lower triangle (unit diagonal: 1)
-__global__ void oz_rowexp_kernel(const double *__restrict__ A, int64_t lda, int M, int K, int unit, int *rexp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const int k0 = blockIdx.y * 64, k1 = min(K, k0 + 64);
-  double mx = 0.0;
-  for (int k = k0; k < k1 && k <= i; ++k) {
-    const double v = (k == i && unit) ? 1.0 : fabs(A[i + (int64_t)k * lda]);
-    mx = fmax(mx, v);
-  }
-  if (mx > 0.0) {
-    int e;
-    frexp(mx, &e);
-    atomicMax(&rexp[i], e);
-  }
+// e with |x| < 2^e, from the bits of |x| (x != 0)
+__device__ __forceinline__ int oz_exponent(uint64_t absbits) {
+  const int ea = (int)(absbits >> 52);
+  return ea != 0 ? ea - 1022 : 64 - __clzll((long long)absbits) - 1074;
 }
 
-// f_j and 2^f_j for the columns of X (one CTA per column)
-__global__ void __launch_bounds__(256) oz_colexp_kernel(const double *__restrict__ X, int64_t ldx, int K, int *cexp,
-                                                        double *cscale, const int *skip) {
-  if (skip != nullptr && *(volatile const int *)skip) return;
-  __shared__ double red[8];
-  const int j = blockIdx.x;
-  double mx = 0.0;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(X[k + (int64_t)j * ldx]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
-    cexp[j] = e;
-    cscale[j] = ldexp(1.0, e);
+// round(a 2^(kOzFrac - e)) for |a| < 2^e (ties away from zero)
+__device__ __forceinline__ int64_t oz_fixed(double a, int e) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(a);
+  const int ea = (int)((bits >> 52) & 0x7ff);
+  uint64_t mant = bits & 0xfffffffffffffull;
+  if (ea == 0 && mant == 0) return 0;
+  int ex = -1074;
+  if (ea != 0) {
+    mant |= 1ull << 52;
+    ex = ea - 1075;
   }
+  const int sh = ex - e + kOzFrac;  // a 2^(kOzFrac - e) = mant 2^sh
+  int64_t I = 0;
+  if (sh >= 0)
+    I = (int64_t)(mant << sh);
+  else if (sh > -64)
+    I = (int64_t)((mant + (1ull << (-sh - 1))) >> (-sh));
+  return (bits >> 63) ? -I : I;
 }
 
-__device__ __forceinline__ void oz_digits(double a, __nv_bfloat16 *out, size_t stride) {
-  double r = a;
+// the kOzS digits of I, slice p at out[(p-1) stride]
+__device__ __forceinline__ void oz_put_digits(int64_t I, __nv_bfloat16 *out, size_t stride) {
 #pragma unroll
   for (int p = 1; p <= kOzS; ++p) {
-    const double t = ldexp(r, oz_bits(p));
-    const double d = rint(t);
-    r -= ldexp(d, -oz_bits(p));
-    out[(size_t)(p - 1) * stride] = __float2bfloat16_rn((float)d);
+    const int sh = kOzFrac - oz_bits(p);
+    int64_t d = I;
+    if (sh > 0) {
+      d = (I + (1ll << (sh - 1))) >> sh;
+      I -= d << sh;
+    }
+    out[(size_t)(p - 1) * stride] = __float2bfloat16_rn((float)(int)d);
   }
 }
 
-// slices of L (lower triangle of A): out[p][i][k], row-major M x Kp per slice
-__global__ void __launch_bounds__(256) oz_slice_rows_kernel(const double *__restrict__ A, int64_t lda, int M, int K,
-                                                            int Kp, int unit, const int *rexp, __nv_bfloat16 *out) {
-  __shared__ double tile[32][33];
-  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  for (int kk = ty; kk < 32; kk += 8) {
-    const int i = i0 + tx, k = k0 + kk;
-    double v = 0.0;
-    if (i < M && k < K && k <= i) v = (k == i && unit) ? 1.0 : A[i + (int64_t)k * lda];
-    tile[kk][tx] = v;
+__device__ __forceinline__ uint64_t oz_absbits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// Entry (r, k) of the rows x K block of a column-major matrix (T = double, or
+// complex double as (re, im)) under a mode: 0 = the whole block; 1 = lower
+// triangle (k <= r); 2 = lower triangle with a unit diagonal.
+template <bool CPLX>
+__device__ __forceinline__ void oz_entry(const double *__restrict__ A, int64_t lda, int rows, int K, int mode, int r,
+                                         int k, double &re, double &im) {
+  constexpr int W = CPLX ? 2 : 1;
+  re = 0.0;
+  im = 0.0;
+  if (r >= rows || k >= K || (mode != 0 && k > r)) return;
+  if (mode == 2 && k == r) {
+    re = 1.0;
+    return;
+  }
+  re = A[W * (r + (int64_t)k * lda)];
+  if (CPLX) im = A[W * (r + (int64_t)k * lda) + 1];
+}
+
+// K-balancing exponents: g_k with max_r |A_rk| < 2^g_k over the block (complex:
+// one g per complex column, stored for both real columns 2k and 2k+1).  The
+// left operand is sliced as A_rk 2^-g_k and the right one as X_kj 2^g_k, which
+// leaves the product unchanged and makes the row and column scales of badly
+// scaled operands (D_r L D_c) meaningful.  A column without nonzeros gets
+// kOzExpEmpty and the right operand's row k is then ignored.  One warp per column.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) oz_kexp_kernel(const double *__restrict__ A, int64_t lda, int rows, int K,
+                                                      int mode, int *kexp) {
+  const int k = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (k >= K) return;
+  uint64_t mx = 0;
+  for (int r = (mode != 0 ? k : 0) + lane; r < rows; r += 32) {
+    double re, im;
+    oz_entry<CPLX>(A, lda, rows, K, mode, r, k, re, im);
+    mx = max(mx, max(oz_absbits(re), oz_absbits(im)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_down_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    const int e = mx == 0 ? kOzExpEmpty : oz_exponent(mx);
+    kexp[(CPLX ? 2 : 1) * k] = e;
+    if (CPLX) kexp[2 * k + 1] = e;
+  }
+}
+
+// Slices of a left operand: the rows x K block (mode as in oz_entry; complex
+// expanded to the real 2 rows x 2 K form with [re -im; im re] per entry),
+// balanced by 2^-g_k, as out[p][row][k], rows' x Kp row-major per slice (zero
+// beyond K'), plus the row exponents.  One CTA per 32 rows: a pass for the
+// exponents, a pass for the digits.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) oz_slice_a_kernel(const double *__restrict__ A, int64_t lda, int rows, int K,
+                                                         int Kp, int mode, const int *__restrict__ kexp, int *rexp,
+                                                         __nv_bfloat16 *out, size_t sstride) {
+  constexpr int W = CPLX ? 2 : 1;
+  constexpr int KT = 32 / W;  // source columns per tile
+  __shared__ double sre[KT][33], sim[CPLX ? KT : 1][33];
+  __shared__ int sg[KT];
+  __shared__ int red[8][32];
+  __shared__ int se[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 32;
+  const int i = i0 + tx;
+  int ex = INT_MIN;
+  const int kend = mode != 0 ? min(K, i + 1) : K;
+  for (int k = ty; k < kend && i < rows; k += 8) {
+    double re, im;
+    oz_entry<CPLX>(A, lda, rows, K, mode, i, k, re, im);
+    const uint64_t ab = max(oz_absbits(re), oz_absbits(im));
+    if (ab != 0) ex = max(ex, oz_exponent(ab) - kexp[W * k]);
+  }
+  red[ty][tx] = ex;
+  __syncthreads();
+  if (ty == 0) {
+    for (int w = 1; w < 8; ++w) ex = max(ex, red[w][tx]);
+    const int e = ex == INT_MIN ? kOzExpEmpty : ex;
+    se[tx] = e;
+    if (i < rows) {
+      rexp[W * i] = e;
+      if (CPLX) rexp[W * i + 1] = e;
+    }
   }
   __syncthreads();
-  const size_t stride = (size_t)M * Kp;
-  for (int ii = ty; ii < 32; ii += 8) {
-    const int i = i0 + ii, k = k0 + tx;
-    if (i >= M || k >= Kp) continue;
-    const int e = rexp[i];
-    const double a = e == kOzExpEmpty ? 0.0 : ldexp(tile[tx][ii], -e);
-    oz_digits(a, out + (size_t)i * Kp + k, stride);
+  for (int k0 = 0; k0 < Kp; k0 += 32) {
+    const int kc0 = k0 / W;
+    for (int kk = ty; kk < KT; kk += 8) {
+      double re, im;
+      oz_entry<CPLX>(A, lda, rows, K, mode, i, kc0 + kk, re, im);
+      sre[kk][tx] = re;
+      if (CPLX) sim[kk][tx] = im;
+    }
+    if (threadIdx.x < KT) sg[threadIdx.x] = kc0 + (int)threadIdx.x < K ? kexp[W * (kc0 + threadIdx.x)] : 0;
+    __syncthreads();
+    const int g = sg[tx / W];
+    for (int ii = ty; ii < 32; ii += 8) {
+      const int r = i0 + ii;
+      if (r >= rows) break;
+      const int e = se[ii];
+      const bool zero = e == kOzExpEmpty;
+      if (CPLX) {
+        const double re = sre[tx >> 1][ii], im = sim[tx >> 1][ii];
+        const bool first = (tx & 1) == 0;
+        oz_put_digits(zero ? 0 : oz_fixed(first ? re : -im, e + g), out + (size_t)(2 * r) * Kp + k0 + tx, sstride);
+        oz_put_digits(zero ? 0 : oz_fixed(first ? im : re, e + g), out + (size_t)(2 * r + 1) * Kp + k0 + tx,
+                      sstride);
+      } else {
+        oz_put_digits(zero ? 0 : oz_fixed(sre[tx][ii], e + g), out + (size_t)r * Kp + k0 + tx, sstride);
+      }
+    }
+    __syncthreads();
   }
 }
 
-// slices of X: out[q][j][k], row-major N x Kp per slice
-__global__ void __launch_bounds__(256) oz_slice_cols_kernel(const double *__restrict__ X, int64_t ldx, int K, int N,
-                                                            int Kp, const int *cexp, __nv_bfloat16 *out,
-                                                            const int *skip) {
+// Slices of a right operand: K x N column-major (complex: its real view with
+// 2K rows), balanced by 2^g_k (rows with g_k = kOzExpEmpty are ignored), as
+// out[q][j][k], N x Kp row-major per slice (zero beyond K), plus the column
+// exponents.  One CTA per column.
+__global__ void __launch_bounds__(256) oz_slice_x_kernel(const double *__restrict__ X, int64_t ldx, int K, int N,
+                                                         int Kp, const int *__restrict__ kexp, int *cexp,
+                                                         __nv_bfloat16 *out, size_t sstride, const int *skip) {
   if (skip != nullptr && *(volatile const int *)skip) return;
-  const int64_t total = (int64_t)N * Kp;
-  const size_t stride = (size_t)N * Kp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / Kp), k = (int)(e % Kp);
-    const double x = k < K ? X[k + (int64_t)j * ldx] : 0.0;
-    oz_digits(ldexp(x, -cexp[j]), out + e, stride);
+  __shared__ int red[8];
+  __shared__ int se;
+  for (int j = blockIdx.x; j < N; j += gridDim.x) {
+    const double *x = X + (int64_t)j * ldx;
+    int ex = INT_MIN;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const uint64_t ab = oz_absbits(x[k]);
+      const int g = kexp[k];
+      if (ab != 0 && g != kOzExpEmpty) ex = max(ex, oz_exponent(ab) + g);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_down_sync(0xffffffffu, ex, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ex;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 8; ++w) ex = max(ex, red[w]);
+      se = ex == INT_MIN ? 0 : ex;
+      cexp[j] = se;
+    }
+    __syncthreads();
+    const int e = se;
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+      const int g = k < K ? kexp[k] : kOzExpEmpty;
+      oz_put_digits(g != kOzExpEmpty ? oz_fixed(x[k], e - g) : 0, out + (size_t)j * Kp + k, sstride);
+    }
+    __syncthreads();
   }
 }
 
-__global__ void oz_fill_kernel(int *p, int n, int v) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = v;
-}
-
-struct OzL {  // slices of L, built once per solve
+// One sliced operand: kOzS slices of rows x Kp BF16 digits, an exponent per
+// row, and (left operands) the K-balancing exponents.
+struct OzOperand {
   __nv_bfloat16 *slices = nullptr;
-  int *rexp = nullptr;
-  int M = 0, Kp = 0;
+  int *exps = nullptr;
+  int *kexp = nullptr;
+  int rows = 0, Kp = 0;
 };
 
-size_t oz_l_bytes(int64_t m) {
-  const size_t Kp = (size_t)((m + TC_BK - 1) / TC_BK) * TC_BK;
-  return kOzS * (size_t)m * Kp * sizeof(__nv_bfloat16) + 1024 + sizeof(int) * (size_t)m;
+int oz_kp(int64_t K) { return (int)((K + TC_BK - 1) / TC_BK) * TC_BK; }
+
+size_t oz_slices_bytes(int64_t rows, int Kp) {
+  return (kOzS * (size_t)rows * Kp * sizeof(__nv_bfloat16) + 1023) & ~(size_t)1023;
 }
 
-size_t oz_x_bytes(int64_t m, int64_t n) {
-  const size_t Kp = (size_t)((m + TC_BK - 1) / TC_BK) * TC_BK;
-  return kOzS * (size_t)n * Kp * sizeof(__nv_bfloat16) + 1024 + (sizeof(int) + sizeof(double)) * (size_t)n + 1024;
+size_t oz_operand_bytes(int64_t rows, int Kp) {
+  return oz_slices_bytes(rows, Kp) + ((sizeof(int) * (size_t)rows + 1023) & ~(size_t)1023) +
+         ((sizeof(int) * (size_t)Kp + 1023) & ~(size_t)1023);
 }
 
-hsma_status_t oz_prepare_l(const double *A, int64_t lda, int unit, int64_t m, void *ws, OzL *L, cudaStream_t st) {
-  const int Kp = (int)((m + TC_BK - 1) / TC_BK) * TC_BK;
+OzOperand oz_operand(void *ws, int64_t rows, int Kp) {
+  OzOperand o;
   unsigned char *b = static_cast<unsigned char *>(ws);
-  L->slices = reinterpret_cast<__nv_bfloat16 *>(b);
-  L->rexp = reinterpret_cast<int *>(b + ((kOzS * (size_t)m * Kp * sizeof(__nv_bfloat16) + 1023) & ~(size_t)1023));
-  L->M = (int)m;
-  L->Kp = Kp;
-  HsmaTraceScope ts("residual_slices", st);
-  oz_fill_kernel<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(L->rexp, (int)m, kOzExpEmpty);
-  oz_rowexp_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)((m + 63) / 64)), 256, 0, st>>>(A, lda, (int)m,
-                                                                                                 (int)m, unit,
-                                                                                                 L->rexp);
-  oz_slice_rows_kernel<<<dim3((unsigned)((m + 31) / 32), (unsigned)((Kp + 31) / 32)), 256, 0, st>>>(
-      A, lda, (int)m, (int)m, Kp, unit, L->rexp, L->slices);
+  o.slices = reinterpret_cast<__nv_bfloat16 *>(b);
+  o.exps = reinterpret_cast<int *>(b + oz_slices_bytes(rows, Kp));
+  o.kexp = reinterpret_cast<int *>(b + oz_slices_bytes(rows, Kp) + ((sizeof(int) * (size_t)rows + 1023) & ~(size_t)1023));
+  o.rows = (int)rows;
+  o.Kp = Kp;
+  return o;
+}
+
+// Slice the rows x K block of A (lda in elements of the dtype) into o (o.rows =
+// W rows), with its K-balancing exponents in o.kexp.
+hsma_status_t oz_slice_a(bool cplx, const double *A, int64_t lda, int rows, int K, int mode, OzOperand &o,
+                         cudaStream_t st) {
+  if (rows <= 0 || K <= 0) return HSMA_OK;
+  const size_t ss = (size_t)o.rows * o.Kp;
+  const unsigned kb = (unsigned)((K + 7) / 8);
+  if (cplx) {
+    oz_kexp_kernel<true><<<kb, 256, 0, st>>>(A, lda, rows, K, mode, o.kexp);
+    oz_slice_a_kernel<true><<<(rows + 31) / 32, 256, 0, st>>>(A, lda, rows, K, o.Kp, mode, o.kexp, o.exps, o.slices,
+                                                               ss);
+  } else {
+    oz_kexp_kernel<false><<<kb, 256, 0, st>>>(A, lda, rows, K, mode, o.kexp);
+    oz_slice_a_kernel<false><<<(rows + 31) / 32, 256, 0, st>>>(A, lda, rows, K, o.Kp, mode, o.kexp, o.exps,
+                                                                o.slices, ss);
+  }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
 
+// Slice the K x N real matrix X (complex: its real view) into o (o.rows = N),
+// balanced by the K-balancing exponents of the left operand it multiplies.
+hsma_status_t oz_slice_x(const double *X, int64_t ldx, int K, const int *kexp, OzOperand &o, const int *skip,
+                         cudaStream_t st) {
+  if (o.rows <= 0) return HSMA_OK;
+  const int grid = std::min(o.rows, 152 * 8);
+  oz_slice_x_kernel<<<grid, 256, 0, st>>>(X, ldx, K, o.rows, o.Kp, kexp, o.exps, o.slices, (size_t)o.rows * o.Kp,
+                                          skip);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+// Unit table: pairs of equal p + q, smallest weights first, at most
+// 2^14 / Kp pairs per unit (exact FP32 sums).
+void oz_units(int Kp, TcArgs &a) {
+  const int gmax = std::max(1, kOzMaxK / Kp);
+  int np = 0, nu = 0;
+  for (int s = kOzS + 1; s >= 2; --s) {
+    int in_unit = 0;
+    for (int p = std::max(1, s - kOzS); p <= std::min(kOzS, s - 1); ++p) {
+      if (in_unit == 0) {
+        a.ubeg[nu] = (uint8_t)np;
+        a.uexp[nu] = (int8_t)(-(oz_bits(p) + oz_bits(s - p)));
+        ++nu;
+      }
+      a.pa[np] = (uint8_t)(p - 1);
+      a.pb[np] = (uint8_t)(s - p - 1);
+      ++np;
+      if (++in_unit == gmax) in_unit = 0;
+    }
+  }
+  a.ubeg[nu] = (uint8_t)np;
+  a.nunits = nu;
+}
+
+// C (M x N, column-major FP64) = (beta0 ? C : 0) -/+ L X in emulated FP64,
+// L and X given by their slices; tri: L is lower triangular.
+hsma_status_t oz_product(const OzOperand &L, const OzOperand &X, double *C, int64_t ldc, int beta0, int negate,
+                         int tri, const int *skip, const char *phase, cudaStream_t st) {
+  if (L.Kp != X.Kp || L.Kp > kOzMaxK) return HSMA_ERR_INVALID_ARG;
+  TcArgs a{};
+  a.C64 = C;
+  a.ldc = ldc;
+  a.beta0 = beta0;
+  a.negate = negate;
+  a.rexp = L.exps;
+  a.cexp = X.exps;
+  a.M = L.rows;
+  a.N = X.rows;
+  a.K = L.Kp;
+  a.tri = tri;
+  a.skip = skip;
+  oz_units(L.Kp, a);
+  return tc_gemm<TC_OZ>(L.slices, kOzS, X.slices, kOzS, a, phase, st);
+}
+
 // R -= L X in emulated FP64 (R holds alpha B on entry); skip: device flag
-hsma_status_t oz_residual(const OzL &L, const double *X, int64_t ldx, double *R, int64_t ldr, int64_t n, void *ws,
+hsma_status_t oz_residual(const OzOperand &L, const double *X, int64_t ldx, double *R, int64_t ldr, OzOperand &Xo,
                           const int *skip, cudaStream_t st) {
-  const int m = L.M, Kp = L.Kp;
-  unsigned char *b = static_cast<unsigned char *>(ws);
-  __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(b);
-  size_t off = (kOzS * (size_t)n * Kp * sizeof(__nv_bfloat16) + 1023) & ~(size_t)1023;
-  int *cexp = reinterpret_cast<int *>(b + off);
-  double *cscale = reinterpret_cast<double *>(b + ((off + sizeof(int) * (size_t)n + 1023) & ~(size_t)1023));
   {
     HsmaTraceScope ts("residual_slices", st);
-    oz_colexp_kernel<<<(unsigned)n, 256, 0, st>>>(X, ldx, m, cexp, cscale, skip);
-    oz_slice_cols_kernel<<<g_launch_grid((int64_t)n * Kp), 256, 0, st>>>(X, ldx, m, (int)n, Kp, cexp, XS, skip);
-    HSMA_CUDA_TRY(cudaGetLastError());
+    hsma_status_t s = oz_slice_x(X, ldx, L.rows, L.kexp, Xo, skip, st);
+    if (s != HSMA_OK) return s;
   }
-  for (int pa = 1; pa <= kOzS; ++pa)
-    for (int qb = 1; pa + qb <= kOzS + 1; ++qb) {
-      TcArgs a{};
-      a.C64 = R;
-      a.ldc = ldr;
-      a.w = ldexp(1.0, -(oz_bits(pa) + oz_bits(qb)));
-      a.rexp = L.rexp;
-      a.cscale = cscale;
-      a.M = m;
-      a.N = (int)n;
-      a.K = Kp;
-      a.tri = 1;
-      a.skip = skip;
-      hsma_status_t s = tc_gemm<TC_F64ACC>(L.slices + (size_t)(pa - 1) * m * Kp, XS + (size_t)(qb - 1) * n * Kp, a,
-                                           "residual", st);
-      if (s != HSMA_OK) return s;
+  return oz_product(L, Xo, R, ldr, 1, 0, 1, skip, "residual", st);
+}
+
+__global__ void scale_kernel(double *B, int64_t ldb, int64_t rows, int64_t n, double ar, double ai, int cplx) {
+  const int64_t total = rows * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    if (cplx) {
+      double *p = B + 2 * (i + j * ldb);
+      const double re = p[0], im = p[1];
+      p[0] = ar * re - ai * im;
+      p[1] = ar * im + ai * re;
+    } else {
+      B[i + j * ldb] *= ar;
     }
-  return HSMA_OK;
+  }
+}
+
+
+// Blocked solve (Section 4.3) with both products of every block step, the
+// solve X_r = D_r^{-1} B_r and the trailing update B_{r+1:} -= A_{r+1:,r} X_r,
+// emulated in FP64 on the BF16 tensor cores.  The diagonal blocks are
+// inverted in FP64 (Algorithm 2).  Complex operands run as real products of
+// the expanded forms (rows [re -im; im re] on the left, the interleaved real
+// view on the right and in B), so a complex product is four real ones.
+hsma_status_t blocked_emulated(bool cplx, int nb, const double *A, int64_t lda, double *B, int64_t ldb, int64_t m,
+                               int64_t n, const double *alpha, int unit, cudaStream_t st) {
+  const int W = cplx ? 2 : 1;
+  const int64_t nblk = (m + nb - 1) / nb;
+  const int Kp = oz_kp((int64_t)W * nb);
+  if (Kp > kOzMaxK || (int64_t)W * m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+  const size_t eb = sizeof(double) * W;
+  const size_t dinv_b = al(eb * (size_t)nblk * nb * nb);
+  const size_t w_b = al(eb * (size_t)nb * n);
+  const size_t pa_b = al(oz_operand_bytes((int64_t)W * m, Kp));
+  const size_t pd_b = al(oz_operand_bytes((int64_t)W * nb, Kp));
+  const size_t px_b = al(oz_operand_bytes(n, Kp));
+  void *ws = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&ws, dinv_b + w_b + pa_b + pd_b + px_b, st);
+  if (s != HSMA_OK) return s;
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  double *Dinv = reinterpret_cast<double *>(base);
+  double *Wb = reinterpret_cast<double *>(base + dinv_b);
+  OzOperand Pa = oz_operand(base + dinv_b + w_b, (int64_t)W * m, Kp);
+  OzOperand Pd = oz_operand(base + dinv_b + w_b + pa_b, (int64_t)W * nb, Kp);
+  OzOperand Px = oz_operand(base + dinv_b + w_b + pa_b + pd_b, n, Kp);
+  do {
+    if ((s = hsma_diag_inverse(cplx ? HSMA_C128 : HSMA_R64, nb, A, lda, m, unit, Dinv, st)) != HSMA_OK) break;
+    if (alpha[0] != 1.0 || (cplx && alpha[1] != 0.0)) {
+      HsmaTraceScope ts("copy", st);
+      scale_kernel<<<g_launch_grid(m * n), 256, 0, st>>>(B, ldb, m, n, alpha[0], cplx ? alpha[1] : 0.0, cplx);
+      if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
+    }
+    for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
+      const int64_t r0 = r * nb;
+      const int sr = (int)std::min<int64_t>(nb, m - r0);
+      {
+        HsmaTraceScope ts("copy", st);
+        cudaError_t e = cudaMemcpy2DAsync(Wb, eb * nb, B + W * r0, eb * ldb, eb * sr, n, cudaMemcpyDeviceToDevice, st);
+        if ((s = hsma_from_cuda(e)) != HSMA_OK) break;
+      }
+      // X_r = D_r^{-1} B_r
+      Pd.rows = W * sr;
+      {
+        HsmaTraceScope ts("slices", st);
+        if ((s = oz_slice_a(cplx, Dinv + (size_t)W * r * nb * nb, nb, sr, sr, 1, Pd, st)) != HSMA_OK) break;
+        if ((s = oz_slice_x(Wb, (int64_t)W * nb, W * sr, Pd.kexp, Px, nullptr, st)) != HSMA_OK) break;
+      }
+      if ((s = oz_product(Pd, Px, B + W * r0, (int64_t)W * ldb, 0, 1, 1, nullptr, "solve_gemm", st)) != HSMA_OK)
+        break;
+      if (r0 + sr >= m) break;
+      // B_{r+1:} -= A_{r+1:, r} X_r
+      const int rows = (int)(m - r0 - sr);
+      Pa.rows = W * rows;
+      {
+        HsmaTraceScope ts("slices", st);
+        if ((s = oz_slice_a(cplx, A + W * ((r0 + sr) + r0 * lda), lda, rows, sr, 0, Pa, st)) != HSMA_OK) break;
+        if ((s = oz_slice_x(B + W * r0, (int64_t)W * ldb, W * sr, Pa.kexp, Px, nullptr, st)) != HSMA_OK) break;
+      }
+      s = oz_product(Pa, Px, B + W * (r0 + sr), (int64_t)W * ldb, 1, 0, 0, nullptr, "update_gemm", st);
+    }
+  } while (0);
+  hsma_status_t f = hsma_ws_free(ws, st);
+  return s != HSMA_OK ? s : f;
 }
 
 }  // namespace
@@ -908,8 +1220,9 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
   const size_t b0_b = sizeof(double) * (size_t)m * n;
   const size_t r64_b = b0_b;
   const size_t st_b = 1024;
-  const size_t ozl_b = emulated ? al(oz_l_bytes(m)) : 0;
-  const size_t ozx_b = emulated ? al(oz_x_bytes(m, n)) : 0;
+  const int ozkp = oz_kp(m);
+  const size_t ozl_b = emulated ? al(oz_operand_bytes(m, ozkp)) : 0;
+  const size_t ozx_b = emulated ? al(oz_operand_bytes(n, ozkp)) : 0;
   // the FP32 inverses and BF16 panels of L, shared by the first solve and every correction
   R32Plan P;
   P.nb = nb < 32 ? 32 : nb;
@@ -933,7 +1246,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
   int *state = reinterpret_cast<int *>(sums + 8);
   void *ozl_ws = base + al(a32_b) + al(r32_b) + al(b0_b) + al(r64_b) + st_b;
   void *ozx_ws = static_cast<unsigned char *>(ozl_ws) + ozl_b;
-  OzL Lsl;
+  OzOperand Lsl = oz_operand(ozl_ws, m, ozkp), Xsl = oz_operand(ozx_ws, n, ozkp);
   P.A = A32;
   P.Dinv = reinterpret_cast<float *>(static_cast<unsigned char *>(ozx_ws) + ozx_b);
   P.panels = reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(P.Dinv) + dinv_b);
@@ -952,7 +1265,10 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
       sumsq_kernel<<<grid, 256, 0, st>>>(B0, m, m, n, 0, 0, sums, 1, nullptr);
       if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     }
-    if (emulated && (s = oz_prepare_l(A, lda, unit, m, ozl_ws, &Lsl, st)) != HSMA_OK) break;
+    if (emulated) {
+      HsmaTraceScope ts("residual_slices", st);
+      if ((s = oz_slice_a(false, A, lda, (int)m, (int)m, unit ? 2 : 1, Lsl, st)) != HSMA_OK) break;
+    }
     // X_0 from the FP32-result solve of the rounded data
     if ((s = r32_prepare(P, true, st)) != HSMA_OK) break;
     if ((s = r32_apply(P, R32, m, n, (float)alpha, nullptr, st)) != HSMA_OK) break;
@@ -967,7 +1283,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
           HsmaTraceScope ts("refine", st);
           scale_copy_kernel<<<grid, 256, 0, st>>>(B0, R64, m * n, alpha, state);
         }
-        if ((s = oz_residual(Lsl, B, ldb, R64, m, n, ozx_ws, state, st)) != HSMA_OK) break;
+        if ((s = oz_residual(Lsl, B, ldb, R64, m, Xsl, state, st)) != HSMA_OK) break;
       } else {
         if ((s = fail(cudaMemcpy2DAsync(R64, sizeof(double) * m, B0, sizeof(double) * m, sizeof(double) * m, n,
                                         cudaMemcpyDeviceToDevice, st))) != HSMA_OK)
@@ -1014,4 +1330,34 @@ extern "C" HSMA_API hsma_status_t hsma_gemm_bf16_update(int64_t M, int64_t N, in
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
   return bf16_update(static_cast<const __nv_bfloat16 *>(A), static_cast<const __nv_bfloat16 *>(Bt), (int)M, (int)N,
                      (int)K, beta, C, ldc, static_cast<cudaStream_t>(stream));
+}
+
+hsma_status_t hsma_blocked_emulated(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
+                                    int64_t n, const double *alpha, int unit, cudaStream_t st) {
+  if (dtype != HSMA_R64 && dtype != HSMA_C128) return HSMA_ERR_INVALID_ARG;
+  return blocked_emulated(dtype == HSMA_C128, nb, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb,
+                          m, n, alpha, unit, st);
+}
+
+extern "C" HSMA_API hsma_status_t hsma_gemm_f64_emulated(int64_t M, int64_t N, int64_t K, const double *A,
+                                                         int64_t lda, const double *X, int64_t ldx, double *C,
+                                                         int64_t ldc, void *stream) {
+  if (M < 0 || N < 0 || K < 0 || lda < std::max<int64_t>(1, M) || ldx < std::max<int64_t>(1, K) ||
+      ldc < std::max<int64_t>(1, M))
+    return HSMA_ERR_INVALID_ARG;
+  if (M == 0 || N == 0 || K == 0) return HSMA_OK;
+  if (A == nullptr || X == nullptr || C == nullptr) return HSMA_ERR_INVALID_ARG;
+  if (K > kOzMaxK || M > INT32_MAX || N > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int Kp = oz_kp(K);
+  const size_t a_b = oz_operand_bytes(M, Kp), x_b = oz_operand_bytes(N, Kp);
+  void *ws = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&ws, a_b + x_b, st);
+  if (s != HSMA_OK) return s;
+  OzOperand Ao = oz_operand(ws, M, Kp), Xo = oz_operand(static_cast<unsigned char *>(ws) + a_b, N, Kp);
+  s = oz_slice_a(false, A, lda, (int)M, (int)K, 0, Ao, st);
+  if (s == HSMA_OK) s = oz_slice_x(X, ldx, (int)K, Ao.kexp, Xo, nullptr, st);
+  if (s == HSMA_OK) s = oz_product(Ao, Xo, C, ldc, 1, 0, 0, nullptr, "emulated_gemm", st);
+  hsma_status_t f = hsma_ws_free(ws, st);
+  return s != HSMA_OK ? s : f;
 }

@@ -12,3 +12,8 @@ hsma_status_t hsma_mixed_r32(int nb, int bf16_terms, const float *A, int64_t lda
 // FP64-result solve: FP32-result solve plus FP64 iterative refinement.
 hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, int64_t lda, double *B, int64_t ldb,
                             int64_t m, int64_t n, double alpha, int unit, cudaStream_t st, hsma_info_t *info);
+
+// Blocked FP64 / complex FP64 solve with the solve and trailing-update
+// products emulated in FP64 on the BF16 tensor cores (exact integer slices).
+hsma_status_t hsma_blocked_emulated(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
+                                    int64_t n, const double *alpha, int unit, cudaStream_t st);

@@ -23,6 +23,7 @@ R64, C128, R32_BF16, R64_IR = 0, 1, 2, 3
 NON_UNIT, UNIT = 0, 1
 PATH_AUTO, PATH_SMALL, PATH_BLOCKED = 0, 1, 2
 OK = 0
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_BUSY = range(1, 8)
 DEVERR_BAD_SIZE, DEVERR_NULL_PTR, DEVERR_TIMEOUT = 0x1, 0x2, 0x4
 STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTED", 3: "HSMA_ERR_NO_MEMORY",
                 4: "HSMA_ERR_CUDA", 5: "HSMA_ERR_TIMEOUT", 6: "HSMA_ERR_NOT_CONVERGED", 7: "HSMA_ERR_BUSY"}
@@ -31,7 +32,7 @@ STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTE
 EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_llnn_ex",
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
-           "hsma_device_status", "hsma_gemm_bf16_update", "hsma_trsm_llnn_vbatched_noalloc",
+           "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -50,7 +51,7 @@ class Plan(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("ir_max_iter", ctypes.c_int32), ("ir_tol", ctypes.c_double), ("bf16_terms", ctypes.c_int32),
-                ("ir_residual", ctypes.c_int32)]
+                ("ir_residual", ctypes.c_int32), ("fp64_products", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -110,6 +111,8 @@ def _load():
     lib.hsma_trace_reset.restype = None
     lib.hsma_gemm_bf16_update.argtypes = [i64, i64, i64, vp, vp, ctypes.c_float, vp, i64, vp]
     lib.hsma_gemm_bf16_update.restype = c_int
+    lib.hsma_gemm_f64_emulated.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
+    lib.hsma_gemm_f64_emulated.restype = c_int
     lib.hsma_server_create.argtypes = [ctypes.c_size_t, c_int, ctypes.c_uint, ctypes.POINTER(ctypes.c_void_p)]
     lib.hsma_server_create.restype = c_int
     lib.hsma_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
@@ -250,6 +253,14 @@ def hsma_gemm_bf16_update(M, N, K, A, Bt, beta, C, ldc, stream=0, check=True) ->
     s = _lib.hsma_gemm_bf16_update(M, N, K, A, Bt, beta, C, ldc, stream)
     if check:
         _check(s, "hsma_gemm_bf16_update")
+    return s
+
+
+def hsma_gemm_f64_emulated(M, N, K, A, lda, X, ldx, C, ldc, stream=0, check=True) -> int:
+    """C -= A X in FP64 emulated on the BF16 tensor cores (device pointers, column-major)."""
+    s = _lib.hsma_gemm_f64_emulated(M, N, K, A, lda, X, ldx, C, ldc, stream)
+    if check:
+        _check(s, "hsma_gemm_f64_emulated")
     return s
 
 

@@ -386,10 +386,19 @@ def run_large(args, dist, device, code, m):
     achieved = upd_flops / (upd_ms / max(args.steps, 1) * 1e-3) / 1e9
     if emulated:
         # tensor work the emulated update products issue: 55 BF16 slice-pair
-        # products of (W rows) x n x Kp per block step (W = 2 for complex)
+        # products of (W rows) x n x Kp each (W = 2 for complex); panels of h
+        # blocks: per block an update of the panel's remaining rows (K = N_B),
+        # per panel one update of the rows below it (K = h N_B)
         w = 2 if cplx_ else 1
-        kp = -(-(w * nb) // 64) * 64
-        bf16_flops = 55 * 2.0 * sum(w * (m - r0 - min(nb, m - r0)) * float(n) * kp for r0 in range(0, m, nb))
+        h = max(1, 1024 // (w * nb))
+        kp = lambda k: -(-(w * k) // 64) * 64  # noqa: E731
+        bf16_flops = 0.0
+        for R0 in range(0, m, h * nb):
+            PR = min(h * nb, m - R0)
+            for r0 in range(R0, R0 + PR, nb):
+                sr = min(nb, m - r0)
+                bf16_flops += 55 * 2.0 * w * (R0 + PR - r0 - sr) * float(n) * kp(sr)
+            bf16_flops += 55 * 2.0 * w * (m - R0 - PR) * float(n) * kp(PR)
         peaks, src = load_peaks()
         bf16_peak = peaks["bf16_tflops_sustained"] * 1e3
         bf16_rate = bf16_flops / (upd_ms / max(args.steps, 1) * 1e-3) / 1e9

@@ -112,7 +112,7 @@ typedef struct {
                           6-bit digit slices per row / column scale, slice-pair
                           products summed exactly in FP32 and folded into the
                           FP64 result (error below 2^-59 of row max x column
-                          max per product term; N_B <= 512, default 256)      */
+                          max per product term; N_B <= 512, default 512)      */
   int32_t reserved;
 } hsma_opts_t;
 

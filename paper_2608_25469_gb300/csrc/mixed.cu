@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 
@@ -127,10 +128,15 @@ __device__ __forceinline__ double oz_scale(uint32_t f, int shift) {
 // item's products accumulate.  Tiles are dealt round-robin to the CTAs (one
 // per SM).  Operands are 3-D: (K, rows, slice); a unit sums the products of
 // its slice pairs over the whole K range in one accumulator.
+// CL = 2: clusters of two CTAs own vertically adjacent tiles (m0, m0 + 128)
+// with the same columns; each CTA loads its own A tile and one half of the
+// shared B tile, multicast into both CTAs' shared memory, which cuts the
+// operand traffic from L2 per product by a third.  A stage is refilled only
+// after both CTAs' MMAs released it (commits multicast to both CTAs).
 constexpr int TC_WARPS = 10;
 constexpr int TC_EPI_WARPS = 8;
 
-template <int MODE>
+template <int MODE, int CL>
 __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                    const __grid_constant__ CUtensorMap mapB,
                                                                    const __grid_constant__ TcArgs p) {
@@ -145,19 +151,24 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = p.M, N = p.N, nunits = p.nunits;
+  uint32_t rank = 0;
+  if constexpr (CL > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
   const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
-  const int ntiles = tiles_m * tiles_n;
-  auto tile_k = [&](int t, int &m0, int &n0) {  // tile -> origin and K-block count
-    m0 = (t % tiles_m) * TC_BM;
-    n0 = (t / tiles_m) * TC_BN;
-    const int kall = p.tri ? min(p.K, m0 + TC_BM) : p.K;
+  const int tiles_mc = (tiles_m + CL - 1) / CL;
+  const int ntiles = tiles_mc * tiles_n;  // cluster tiles
+  auto tile_k = [&](int t, int &m0, int &n0) {  // cluster tile -> this CTA's origin and K-block count
+    const int pm = t % tiles_mc;
+    m0 = (pm * CL + (int)rank) * TC_BM;
+    n0 = (t / tiles_mc) * TC_BN;
+    const int kall = p.tri ? min(p.K, (pm + 1) * CL * TC_BM) : p.K;  // the same in every CTA of a cluster
     return (kall + TC_BK - 1) / TC_BK;
   };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -174,6 +185,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL > 1) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
@@ -182,7 +194,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
       // producer: TMA loads into a ring of stages, across items
       int it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int t = cid; t < ntiles && ok; t += ncl) {
         int m0, n0;
         const int nk = tile_k(t, m0, n0);
         for (int q = 0; q < p.ubeg[nunits] && ok; ++q) {
@@ -196,7 +208,11 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
             unsigned char *st = smem + s * TC_STAGE_BYTES;
             mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
             tma_load_3d(st, &mapA, &full[s], kb * TC_BK, m0, sa);
-            tma_load_3d(st + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0, sb);
+            if constexpr (CL == 1)
+              tma_load_3d(st + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0, sb);
+            else
+              tma_load_3d_multicast(st + TC_A_BYTES + rank * (TC_B_BYTES / CL), &mapB, &full[s], kb * TC_BK,
+                                    n0 + (int)rank * (TC_BN / CL), sb, (uint16_t)((1u << CL) - 1));
           }
         }
       }
@@ -208,7 +224,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
       // steps per stage; each stage is released by a commit, the item by another
       int it = 0, i = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int t = cid; t < ntiles && ok; t += ncl) {
         int m0, n0;
         const int nk = tile_k(t, m0, n0);
         for (int u = 0; u < nunits && ok; ++u, ++i) {
@@ -239,9 +255,16 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
                     : "memory");
                 accum = 1u;
               }
-              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                               smem_u32(&empty[s]))
-                           : "memory");
+              if constexpr (CL == 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty[s]))
+                             : "memory");
+              else
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], "
+                    "%1;" ::"r"(smem_u32(&empty[s])),
+                    "h"((uint16_t)((1u << CL) - 1))
+                    : "memory");
             }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -270,7 +293,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
     constexpr int CW = 16;  // columns per chunk: keeps ten warps within the register file
     int i = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int t = cid; t < ntiles && ok; t += ncl) {
       int m0, n0;
       const int nk = tile_k(t, m0, n0);
       const int row = m0 + quarter * 32 + lane;
@@ -336,6 +359,8 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_TMEM_COLS)
                  : "memory");
   }
+  // no CTA leaves while its peer may still signal its barriers
+  if constexpr (CL > 1) cluster_sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -501,9 +526,19 @@ bool make_slice_map(CUtensorMap *map, const void *base, uint64_t K, uint64_t row
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Clusters of two CTAs unless HSMA_TC_CLUSTER=1 (a tuning knob, read once).
+int tc_cluster_pref() {
+  static const int v = [] {
+    const char *e = std::getenv("HSMA_TC_CLUSTER");
+    return (e != nullptr && std::atoi(e) == 1) ? 1 : 2;
+  }();
+  return v;
+}
+
 // Launch the persistent product.  A: sa slices of M x K (row-major), B: sb
 // slices of N x K; the unit table of a0 names the slice pairs (TC_F32: one
-// unit, one pair, filled in here).
+// unit, one pair, filled in here).  Pairs of row tiles run as clusters of two
+// CTAs sharing the B tile.
 template <int MODE>
 hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, int sb, const TcArgs &a0,
                       const char *phase, cudaStream_t st) {
@@ -511,12 +546,17 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   if (a0.K % TC_BK != 0 || a0.K <= 0) return HSMA_ERR_INVALID_ARG;
   static DeviceFlags attr;
   if (!attr.test()) {
-    HSMA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    HSMA_CUDA_TRY(
+        cudaFuncSetAttribute(tc_gemm_kernel<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    HSMA_CUDA_TRY(
+        cudaFuncSetAttribute(tc_gemm_kernel<MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     attr.set();
   }
+  const int tiles_m = (a0.M + TC_BM - 1) / TC_BM, tiles_n = (a0.N + TC_BN - 1) / TC_BN;
+  const int cl = (tiles_m >= 2 && tc_cluster_pref() == 2) ? 2 : 1;
   CUtensorMap ma, mb;
   if (!make_slice_map(&ma, Ap, (uint64_t)a0.K, (uint64_t)a0.M, (uint64_t)sa, TC_BM) ||
-      !make_slice_map(&mb, Bp, (uint64_t)a0.K, (uint64_t)a0.N, (uint64_t)sb, TC_BN))
+      !make_slice_map(&mb, Bp, (uint64_t)a0.K, (uint64_t)a0.N, (uint64_t)sb, TC_BN / cl))
     return HSMA_ERR_CUDA;
   TcArgs a = a0;
   if (MODE == TC_F32) {
@@ -531,15 +571,31 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   a.err = hsma_dev_error_ptr();
   if (a.err == nullptr) return HSMA_ERR_CUDA;
   if (a.limit_ns == 0) a.limit_ns = 4000000000ull;
-  const int tiles = ((a.M + TC_BM - 1) / TC_BM) * ((a.N + TC_BN - 1) / TC_BN);
   static int nsm[64] = {0};
   int dev = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return HSMA_ERR_UNSUPPORTED;
   if (nsm[dev] == 0) HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
-  const int grid = tiles < nsm[dev] ? tiles : nsm[dev];
+  const int ctiles = ((tiles_m + cl - 1) / cl) * tiles_n;
+  const int clusters = std::max(1, std::min(ctiles, nsm[dev] / cl));
   HsmaTraceScope ts(phase, st);
-  tc_gemm_kernel<MODE><<<grid, 32 * TC_WARPS, TC_SMEM, st>>>(ma, mb, a);
+  if (cl == 1) {
+    tc_gemm_kernel<MODE, 1><<<clusters, 32 * TC_WARPS, TC_SMEM, st>>>(ma, mb, a);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * cl));
+    cfg.blockDim = dim3(32 * TC_WARPS);
+    cfg.dynamicSmemBytes = TC_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HSMA_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE, 2>, ma, mb, a));
+  }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
@@ -863,25 +919,33 @@ __device__ __forceinline__ void oz_entry(const double *__restrict__ A, int64_t l
 // one g per complex column, stored for both real columns 2k and 2k+1).  The
 // left operand is sliced as A_rk 2^-g_k and the right one as X_kj 2^g_k, which
 // leaves the product unchanged and makes the row and column scales of badly
-// scaled operands (D_r L D_c) meaningful.  A column without nonzeros gets
-// kOzExpEmpty and the right operand's row k is then ignored.  One warp per column.
+// scaled operands (D_r L D_c) meaningful.  A column without nonzeros keeps
+// kOzExpEmpty and the right operand's row k is then ignored.  A CTA covers 32
+// columns x 256 rows (a warp per column, lanes down the rows) and folds its
+// maxima in with atomicMax over the kOzExpEmpty fill.
+__global__ void oz_fill_kernel(int *p, int n, int v) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = v;
+}
+
 template <bool CPLX>
 __global__ void __launch_bounds__(256) oz_kexp_kernel(const double *__restrict__ A, int64_t lda, int rows, int K,
                                                       int mode, int *kexp) {
-  const int k = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (k >= K) return;
-  uint64_t mx = 0;
-  for (int r = (mode != 0 ? k : 0) + lane; r < rows; r += 32) {
-    double re, im;
-    oz_entry<CPLX>(A, lda, rows, K, mode, r, k, re, im);
-    mx = max(mx, max(oz_absbits(re), oz_absbits(im)));
-  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * 256;
+  for (int k = blockIdx.x * 32 + warp; k < min(K, blockIdx.x * 32 + 32); k += 8) {
+    uint64_t mx = 0;
+    for (int r = r0 + lane; r < min(rows, r0 + 256); r += 32) {
+      double re, im;
+      oz_entry<CPLX>(A, lda, rows, K, mode, r, k, re, im);
+      mx = max(mx, max(oz_absbits(re), oz_absbits(im)));
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_down_sync(0xffffffffu, mx, o));
-  if (lane == 0) {
-    const int e = mx == 0 ? kOzExpEmpty : oz_exponent(mx);
-    kexp[(CPLX ? 2 : 1) * k] = e;
-    if (CPLX) kexp[2 * k + 1] = e;
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0 && mx != 0) {
+      const int e = oz_exponent(mx);
+      atomicMax(&kexp[(CPLX ? 2 : 1) * k], e);
+      if (CPLX) atomicMax(&kexp[2 * k + 1], e);
+    }
   }
 }
 
@@ -956,37 +1020,50 @@ __global__ void __launch_bounds__(256) oz_slice_a_kernel(const double *__restric
 // Slices of a right operand: K x N column-major (complex: its real view with
 // 2K rows), balanced by 2^g_k (rows with g_k = kOzExpEmpty are ignored), as
 // out[q][j][k], N x Kp row-major per slice (zero beyond K), plus the column
-// exponents.  One CTA per column.
+// exponents.  One warp per column; a lane handles two consecutive k, so each
+// slice is written 128 bytes per warp step.
 __global__ void __launch_bounds__(256) oz_slice_x_kernel(const double *__restrict__ X, int64_t ldx, int K, int N,
                                                          int Kp, const int *__restrict__ kexp, int *cexp,
                                                          __nv_bfloat16 *out, size_t sstride, const int *skip) {
   if (skip != nullptr && *(volatile const int *)skip) return;
-  __shared__ int red[8];
-  __shared__ int se;
-  for (int j = blockIdx.x; j < N; j += gridDim.x) {
-    const double *x = X + (int64_t)j * ldx;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; j < N; j += nwarps) {
+    const double *x = X + j * ldx;
     int ex = INT_MIN;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    for (int k = lane; k < K; k += 32) {
       const uint64_t ab = oz_absbits(x[k]);
       const int g = kexp[k];
       if (ab != 0 && g != kOzExpEmpty) ex = max(ex, oz_exponent(ab) + g);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_down_sync(0xffffffffu, ex, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ex;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < 8; ++w) ex = max(ex, red[w]);
-      se = ex == INT_MIN ? 0 : ex;
-      cexp[j] = se;
+    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+    const int e = ex == INT_MIN ? 0 : ex;
+    if (lane == 0) cexp[j] = e;
+    __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(out + (size_t)j * Kp);
+    for (int k = 2 * lane; k < Kp; k += 64) {
+      int64_t I[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int g = k + h < K ? kexp[k + h] : kOzExpEmpty;
+        I[h] = g != kOzExpEmpty ? oz_fixed(x[k + h], e - g) : 0;
+      }
+#pragma unroll
+      for (int p = 1; p <= kOzS; ++p) {
+        const int sh = kOzFrac - oz_bits(p);
+        float d[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int64_t v = I[h];
+          if (sh > 0) {
+            v = (I[h] + (1ll << (sh - 1))) >> sh;
+            I[h] -= v << sh;
+          }
+          d[h] = (float)(int)v;
+        }
+        o2[(size_t)(p - 1) * (sstride / 2) + k / 2] = __floats2bfloat162_rn(d[0], d[1]);
+      }
     }
-    __syncthreads();
-    const int e = se;
-    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
-      const int g = k < K ? kexp[k] : kOzExpEmpty;
-      oz_put_digits(g != kOzExpEmpty ? oz_fixed(x[k], e - g) : 0, out + (size_t)j * Kp + k, sstride);
-    }
-    __syncthreads();
   }
 }
 
@@ -1027,13 +1104,16 @@ hsma_status_t oz_slice_a(bool cplx, const double *A, int64_t lda, int rows, int 
                          cudaStream_t st) {
   if (rows <= 0 || K <= 0) return HSMA_OK;
   const size_t ss = (size_t)o.rows * o.Kp;
-  const unsigned kb = (unsigned)((K + 7) / 8);
+  const dim3 kg((unsigned)((K + 31) / 32), (unsigned)((rows + 255) / 256));
+  if (kg.y > 65535) return HSMA_ERR_UNSUPPORTED;
+  const int kw = (cplx ? 2 : 1) * K;
+  oz_fill_kernel<<<(kw + 255) / 256, 256, 0, st>>>(o.kexp, kw, kOzExpEmpty);
   if (cplx) {
-    oz_kexp_kernel<true><<<kb, 256, 0, st>>>(A, lda, rows, K, mode, o.kexp);
+    oz_kexp_kernel<true><<<kg, 256, 0, st>>>(A, lda, rows, K, mode, o.kexp);
     oz_slice_a_kernel<true><<<(rows + 31) / 32, 256, 0, st>>>(A, lda, rows, K, o.Kp, mode, o.kexp, o.exps, o.slices,
                                                                ss);
   } else {
-    oz_kexp_kernel<false><<<kb, 256, 0, st>>>(A, lda, rows, K, mode, o.kexp);
+    oz_kexp_kernel<false><<<kg, 256, 0, st>>>(A, lda, rows, K, mode, o.kexp);
     oz_slice_a_kernel<false><<<(rows + 31) / 32, 256, 0, st>>>(A, lda, rows, K, o.Kp, mode, o.kexp, o.exps,
                                                                 o.slices, ss);
   }
@@ -1046,7 +1126,7 @@ hsma_status_t oz_slice_a(bool cplx, const double *A, int64_t lda, int rows, int 
 hsma_status_t oz_slice_x(const double *X, int64_t ldx, int K, const int *kexp, OzOperand &o, const int *skip,
                          cudaStream_t st) {
   if (o.rows <= 0) return HSMA_OK;
-  const int grid = std::min(o.rows, 152 * 8);
+  const int grid = std::min((o.rows + 7) / 8, 152 * 16);
   oz_slice_x_kernel<<<grid, 256, 0, st>>>(X, ldx, K, o.rows, o.Kp, kexp, o.exps, o.slices, (size_t)o.rows * o.Kp,
                                           skip);
   HSMA_CUDA_TRY(cudaGetLastError());
@@ -1130,28 +1210,55 @@ __global__ void scale_kernel(double *B, int64_t ldb, int64_t rows, int64_t n, do
 // inverted in FP64 (Algorithm 2).  Complex operands run as real products of
 // the expanded forms (rows [re -im; im re] on the left, the interleaved real
 // view on the right and in B), so a complex product is four real ones.
+//
+// Each emulated product adds every accumulation unit into B once in FP64, so
+// its cost per element of B grows with the number of units, not with K.  The
+// updates are therefore applied per panel of h diagonal blocks (about 1024
+// real columns): inside a panel, each solved block updates only the panel's
+// remaining rows; below the panel, one update with K = h N_B covers all h
+// blocks.  The result is the same product sum, grouped differently.
 hsma_status_t blocked_emulated(bool cplx, int nb, const double *A, int64_t lda, double *B, int64_t ldb, int64_t m,
                                int64_t n, const double *alpha, int unit, cudaStream_t st) {
   const int W = cplx ? 2 : 1;
   const int64_t nblk = (m + nb - 1) / nb;
-  const int Kp = oz_kp((int64_t)W * nb);
-  if (Kp > kOzMaxK || (int64_t)W * m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
+  const int h = std::max(1, 1024 / (W * nb));
+  const int64_t P = (int64_t)h * nb;  // panel width (source columns)
+  const int Kpb = oz_kp((int64_t)W * nb), Kpp = oz_kp(W * P);
+  if (Kpp > kOzMaxK || (int64_t)W * m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
   auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
   const size_t eb = sizeof(double) * W;
   const size_t dinv_b = al(eb * (size_t)nblk * nb * nb);
   const size_t w_b = al(eb * (size_t)nb * n);
-  const size_t pa_b = al(oz_operand_bytes((int64_t)W * m, Kp));
-  const size_t pd_b = al(oz_operand_bytes((int64_t)W * nb, Kp));
-  const size_t px_b = al(oz_operand_bytes(n, Kp));
+  const size_t pa_b = al(oz_operand_bytes((int64_t)W * m, Kpp));
+  const size_t pd_b = al(oz_operand_bytes((int64_t)W * nb, Kpb));
+  const size_t px_b = al(oz_operand_bytes(n, Kpp));
   void *ws = nullptr;
   hsma_status_t s = hsma_ws_alloc(&ws, dinv_b + w_b + pa_b + pd_b + px_b, st);
   if (s != HSMA_OK) return s;
   unsigned char *base = static_cast<unsigned char *>(ws);
   double *Dinv = reinterpret_cast<double *>(base);
   double *Wb = reinterpret_cast<double *>(base + dinv_b);
-  OzOperand Pa = oz_operand(base + dinv_b + w_b, (int64_t)W * m, Kp);
-  OzOperand Pd = oz_operand(base + dinv_b + w_b + pa_b, (int64_t)W * nb, Kp);
-  OzOperand Px = oz_operand(base + dinv_b + w_b + pa_b + pd_b, n, Kp);
+  unsigned char *pa_mem = base + dinv_b + w_b, *px_mem = base + dinv_b + w_b + pa_b + pd_b;
+  // views of the operand buffers for a given K (the buffers hold the widest)
+  auto view = [](unsigned char *mem, int64_t rows_cap, int Kp, int64_t rows) {
+    OzOperand o = oz_operand(mem, rows_cap, Kp);
+    o.rows = (int)rows;
+    return o;
+  };
+  OzOperand Pd = oz_operand(base + dinv_b + w_b + pa_b, (int64_t)W * nb, Kpb);
+  // B rows [rb, rb + rows) -= A[rb : rb + rows, c0 : c0 + k] X[c0 : c0 + k]
+  auto update = [&](int64_t rb, int64_t rows, int64_t c0, int k, const char *phase) -> hsma_status_t {
+    const int Kp = oz_kp((int64_t)W * k);
+    OzOperand Pa = view(pa_mem, (int64_t)W * m, Kp, (int64_t)W * rows);
+    OzOperand Px = view(px_mem, n, Kp, n);
+    {
+      HsmaTraceScope ts("slices", st);
+      hsma_status_t e = oz_slice_a(cplx, A + W * (rb + c0 * lda), lda, (int)rows, k, 0, Pa, st);
+      if (e == HSMA_OK) e = oz_slice_x(B + W * c0, (int64_t)W * ldb, W * k, Pa.kexp, Px, nullptr, st);
+      if (e != HSMA_OK) return e;
+    }
+    return oz_product(Pa, Px, B + W * rb, (int64_t)W * ldb, 1, 0, 0, nullptr, phase, st);
+  };
   do {
     if ((s = hsma_diag_inverse(cplx ? HSMA_C128 : HSMA_R64, nb, A, lda, m, unit, Dinv, st)) != HSMA_OK) break;
     if (alpha[0] != 1.0 || (cplx && alpha[1] != 0.0)) {
@@ -1159,33 +1266,34 @@ hsma_status_t blocked_emulated(bool cplx, int nb, const double *A, int64_t lda, 
       scale_kernel<<<g_launch_grid(m * n), 256, 0, st>>>(B, ldb, m, n, alpha[0], cplx ? alpha[1] : 0.0, cplx);
       if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
     }
-    for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
-      const int64_t r0 = r * nb;
-      const int sr = (int)std::min<int64_t>(nb, m - r0);
-      {
-        HsmaTraceScope ts("copy", st);
-        cudaError_t e = cudaMemcpy2DAsync(Wb, eb * nb, B + W * r0, eb * ldb, eb * sr, n, cudaMemcpyDeviceToDevice, st);
-        if ((s = hsma_from_cuda(e)) != HSMA_OK) break;
+    for (int64_t R0 = 0; R0 < m && s == HSMA_OK; R0 += P) {
+      const int64_t PR = std::min<int64_t>(P, m - R0);
+      for (int64_t r0 = R0; r0 < R0 + PR && s == HSMA_OK; r0 += nb) {
+        const int64_t r = r0 / nb;
+        const int sr = (int)std::min<int64_t>(nb, m - r0);
+        {
+          HsmaTraceScope ts("copy", st);
+          cudaError_t e =
+              cudaMemcpy2DAsync(Wb, eb * nb, B + W * r0, eb * ldb, eb * sr, n, cudaMemcpyDeviceToDevice, st);
+          if ((s = hsma_from_cuda(e)) != HSMA_OK) break;
+        }
+        // X_r = D_r^{-1} B_r
+        Pd.rows = W * sr;
+        OzOperand Px = view(px_mem, n, Kpb, n);
+        {
+          HsmaTraceScope ts("slices", st);
+          if ((s = oz_slice_a(cplx, Dinv + (size_t)W * r * nb * nb, nb, sr, sr, 1, Pd, st)) != HSMA_OK) break;
+          if ((s = oz_slice_x(Wb, (int64_t)W * nb, W * sr, Pd.kexp, Px, nullptr, st)) != HSMA_OK) break;
+        }
+        if ((s = oz_product(Pd, Px, B + W * r0, (int64_t)W * ldb, 0, 1, 1, nullptr, "solve_gemm", st)) != HSMA_OK)
+          break;
+        // the panel's remaining rows
+        const int64_t rin = R0 + PR - (r0 + sr);
+        if (rin > 0) s = update(r0 + sr, rin, r0, sr, "update_gemm");
       }
-      // X_r = D_r^{-1} B_r
-      Pd.rows = W * sr;
-      {
-        HsmaTraceScope ts("slices", st);
-        if ((s = oz_slice_a(cplx, Dinv + (size_t)W * r * nb * nb, nb, sr, sr, 1, Pd, st)) != HSMA_OK) break;
-        if ((s = oz_slice_x(Wb, (int64_t)W * nb, W * sr, Pd.kexp, Px, nullptr, st)) != HSMA_OK) break;
-      }
-      if ((s = oz_product(Pd, Px, B + W * r0, (int64_t)W * ldb, 0, 1, 1, nullptr, "solve_gemm", st)) != HSMA_OK)
-        break;
-      if (r0 + sr >= m) break;
-      // B_{r+1:} -= A_{r+1:, r} X_r
-      const int rows = (int)(m - r0 - sr);
-      Pa.rows = W * rows;
-      {
-        HsmaTraceScope ts("slices", st);
-        if ((s = oz_slice_a(cplx, A + W * ((r0 + sr) + r0 * lda), lda, rows, sr, 0, Pa, st)) != HSMA_OK) break;
-        if ((s = oz_slice_x(B + W * r0, (int64_t)W * ldb, W * sr, Pa.kexp, Px, nullptr, st)) != HSMA_OK) break;
-      }
-      s = oz_product(Pa, Px, B + W * (r0 + sr), (int64_t)W * ldb, 1, 0, 0, nullptr, "update_gemm", st);
+      // every row below the panel, K = the panel's width
+      const int64_t rout = m - (R0 + PR);
+      if (s == HSMA_OK && rout > 0) s = update(R0 + PR, rout, R0, (int)PR, "update_gemm");
     }
   } while (0);
   hsma_status_t f = hsma_ws_free(ws, st);

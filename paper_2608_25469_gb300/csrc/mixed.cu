@@ -92,6 +92,7 @@ struct TcArgs {
   int M, N, K;
   int tri;          // row tile i0 needs k < i0 + TC_BM only
   int nunits;       // accumulation units per tile (TC_F32: 1)
+  int band;         // cluster-tile rows per band of the tile order (set by the launcher)
   uint8_t ubeg[kOzMaxUnits + 1];  // unit u accumulates pairs ubeg[u] .. ubeg[u+1]-1
   int8_t uexp[kOzMaxUnits];       // TC_OZ: weight exponent of unit u
   uint8_t pa[kOzPairs], pb[kOzPairs];  // slice of A and of B for each pair
@@ -157,10 +158,20 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
   const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
   const int tiles_mc = (tiles_m + CL - 1) / CL;
   const int ntiles = tiles_mc * tiles_n;  // cluster tiles
+  // Cluster tiles run in bands of p.band cluster-tile rows, column by column
+  // inside a band.  For short K the host picks 16 tile rows, so the tiles in
+  // flight at once (one per SM) cover about 16 row tiles x 10 column tiles and
+  // their operand slices stay in L2 while every slice pair re-reads them; for
+  // long K one band spans all rows (column-major order), so the right operand's
+  // slices are shared by every row tile in flight.
+  const int G = max(1, p.band);
   auto tile_k = [&](int t, int &m0, int &n0) {  // cluster tile -> this CTA's origin and K-block count
-    const int pm = t % tiles_mc;
+    const int band = t / (G * tiles_n);
+    const int gb = min(G, tiles_mc - band * G);
+    const int idx = t - band * G * tiles_n;
+    const int pm = band * G + idx % gb;
     m0 = (pm * CL + (int)rank) * TC_BM;
-    n0 = (t / tiles_mc) * TC_BN;
+    n0 = (idx / gb) * TC_BN;
     const int kall = p.tri ? min(p.K, (pm + 1) * CL * TC_BM) : p.K;  // the same in every CTA of a cluster
     return (kall + TC_BK - 1) / TC_BK;
   };
@@ -577,6 +588,7 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   if (dev < 0 || dev >= 64) return HSMA_ERR_UNSUPPORTED;
   if (nsm[dev] == 0) HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
   const int ctiles = ((tiles_m + cl - 1) / cl) * tiles_n;
+  a.band = a.K <= 2048 ? 16 / cl : (tiles_m + cl - 1) / cl;
   const int clusters = std::max(1, std::min(ctiles, nsm[dev] / cl));
   HsmaTraceScope ts(phase, st);
   if (cl == 1) {

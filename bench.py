@@ -165,8 +165,12 @@ def source_sha(files):
     return h.hexdigest()[:16]
 
 
-def profile_traffic(name: str, files):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+def profile_traffic(name: str, files, work=None):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current source.
+
+    With `work` (algorithmic units of one launch of the bench's workload) and a
+    summary that records `work_per_launch` for a smaller captured case, the
+    captured bytes are scaled by work / work_per_launch."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         kv = {}
@@ -177,7 +181,10 @@ def profile_traffic(name: str, files):
                     kv[k.strip()] = v.strip()
         if kv.get("source_sha256_16") != source_sha(files):
             return None
-        return float(kv["dram_bytes_per_launch"])
+        dram = float(kv["dram_bytes_per_launch"])
+        if work is not None and "work_per_launch" in kv:
+            return dram * work / float(kv["work_per_launch"])
+        return dram
     except (OSError, KeyError, ValueError):
         return None
 
@@ -428,7 +435,8 @@ def run_large(args, dist, device, code, m):
                    "nb": nb, "l2": f"inputs larger than L2 ({abytes / 1e9:.2f} GB)"},
         "roofline": ({"bound": "tensor", "achieved": round(bf16_rate, 1), "peak": round(bf16_peak, 1),
                       "unit": "GFLOP/s", "frac": round(bf16_rate / bf16_peak, 4),
-                      "traffic": profile_traffic(f"update_emulated_{name}.txt", EMU_SOURCES),
+                      "traffic": profile_traffic(f"update_emulated_{name}.txt", EMU_SOURCES,
+                                                 work=bf16_flops / max(upd_cnt / max(args.steps, 1), 1)),
                       "kernel": "tc_gemm_kernel<TC_OZ> (update_gemm, tcgen05 BF16 slice pairs)",
                       "peak_source": f"bf16 tensor (sustained), {src}",
                       "fp64_equivalent_gflops": round(achieved, 1)} if emulated else
@@ -495,7 +503,8 @@ def run_serve(args, dist, device):
     seed = shard_seed(args.seed, dist.rank)
     t_arr, ms, ns, dts = I.serving_requests(seed, count)
     flops = float(sum(I.flops_trsm(m, n, d == I.C128) for m, n, d in zip(ms, ns, dts)))
-    s = H.hsma_server_create(16 << 30, args.streams, 0)
+    emulated = args.fp64_products == "emulated"
+    s = H.hsma_server_create(16 << 30, args.streams, H.SERVER_FP64_EMULATED if emulated else 0)
     reqs = []
     for k in range(count):
         r = H.Request()
@@ -535,6 +544,8 @@ def run_serve(args, dist, device):
     st_ = torch.cuda.current_stream()
     sp = int(st_.cuda_stream)
     seq = []
+    seq_opts = H.Opts()
+    seq_opts.fp64_products = 1 if emulated else 0
     for k in range(k_seq):
         m, n, d = int(ms[k]), int(ns[k]), int(dts[k])
         dt = torch.complex128 if d == I.C128 else torch.float64
@@ -544,7 +555,7 @@ def run_serve(args, dist, device):
         H.hsma_gen_matrix(d, 1, seed, k, m, n, B.data_ptr(), m, sp)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st_)
-        H.hsma_trsm_llnn(d, 0, m, n, 1.0, A.data_ptr(), m, B.data_ptr(), m, sp)
+        H.hsma_trsm_llnn_ex(d, 0, m, n, 1.0, A.data_ptr(), m, B.data_ptr(), m, sp, opts=seq_opts)
         e1.record(st_)
         e1.synchronize()
         seq.append(e0.elapsed_time(e1) * 1e-3)
@@ -555,7 +566,9 @@ def run_serve(args, dist, device):
         "steps": count, "warmup": base, "ms_per_step": round(makespan * 1e3 / count, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+c128", "data": "synthetic",
         "config": {"workload": f"serve: {count} requests, Poisson 2000/s, m log-U[16,4096], n log-U[1,512], "
-                               "70% fp64 / 30% c128, 16 GB budget, device-generated inputs",
+                               "70% fp64 / 30% c128, 16 GB budget, device-generated inputs"
+                               + ("; blocked requests with FP64 products emulated on the BF16 tensor cores"
+                                  if emulated else ""),
                    "streams": args.streams},
         "gflops": round(flops / makespan / 1e9, 2), "offered_gflops": round(flops / t_arr[-1] / 1e9, 2),
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)) * 1e3, 3),
@@ -615,8 +628,8 @@ def run_mixed(args, dist, device, mode):
         times.append(e0.elapsed_time(e1))
     H.hsma_trace_enable(False)
     phases = {}
-    for ph in ("diag_inverse", "copy", "solve_sgemm", "convert", "update_bf16", "residual_slices", "residual",
-               "refine"):
+    for ph in ("diag_inverse", "copy", "solve_bf16", "solve_sgemm", "convert", "update_bf16", "residual_slices",
+               "residual", "refine"):
         ms_, c = H.hsma_trace_read(ph)
         if c:
             phases[ph] = round(ms_ / args.steps, 4)
@@ -627,10 +640,16 @@ def run_mixed(args, dist, device, mode):
         kp = -(-3 * nb // 64) * 64
         starts = list(range(0, m, nb))
         upd = sum(2.0 * (m - r0 - min(nb, m - r0)) * n * kp for r0 in starts)
-        sol = sum(min(nb, m - r0) * (min(nb, m - r0) + 1) * float(n) for r0 in starts)
+        # solve products: six BF16 slice pairs of (s_r x n x Kd), the row tiles of the
+        # triangular inverse skipping K blocks past their diagonal
+        kd = -(-nb // 64) * 64
+        sol = 0.0
+        for r0 in starts:
+            sr = min(nb, m - r0)
+            sol += sum(6 * 2.0 * 128 * n * min(kd, (i0 // 256 + 1) * 256) for i0 in range(0, sr, 128))
         peaks, src = load_peaks()
         for ph, fl, pk, unit in (("update_bf16", upd, peaks["bf16_tflops"] * 1e3, "bf16 tensor (measured burst)"),
-                                 ("solve_sgemm", sol, 152 * 128 * 2 * 2.07, "FP32 FFMA (derived: 128 FMA/clk/SM)")):
+                                 ("solve_bf16", sol, peaks["bf16_tflops"] * 1e3, "bf16 tensor (measured burst)")):
             if ph in phases and phases[ph] > 0:
                 rate = fl / (phases[ph] * 1e-3) / 1e9
                 rates[ph] = {"gflops": round(rate, 1), "peak_gflops": round(pk, 1), "frac": round(rate / pk, 4),
@@ -704,7 +723,7 @@ def main(argv=None):
     ap.add_argument("--streams", type=int, default=16)
     ap.add_argument("--m", type=int, default=0, help="large_*: m = n (default 16384 fp64, 8192 c128)")
     ap.add_argument("--fp64-products", default="dmma", choices=["dmma", "emulated"],
-                    help="large_*: FP64 tensor products, or FP64 emulated on the BF16 tensor cores")
+                    help="large_*, serve: FP64 tensor products, or FP64 emulated on the BF16 tensor cores")
     ap.add_argument("--nb", type=int, default=0, help="large_*: force N_B (0 = planner)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

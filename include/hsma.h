@@ -242,6 +242,7 @@ HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64
 typedef struct hsma_server hsma_server_t;
 
 #define HSMA_SERVER_FAKE_DEVICE 0x1u /* no GPU: launches complete after a modelled time (tests) */
+#define HSMA_SERVER_FP64_EMULATED 0x2u /* blocked requests (m > 64) use hsma_opts_t.fp64_products = 1 */
 
 typedef struct {
   int32_t dtype;  /* HSMA_R64 or HSMA_C128                                        */
@@ -269,7 +270,7 @@ typedef struct {
   uint64_t batched_launches, blocked_launches;
 } hsma_server_stats_t;
 
-/* Create a server on the current device (flags: 0 or HSMA_SERVER_FAKE_DEVICE). */
+/* Create a server on the current device (flags: 0, HSMA_SERVER_FAKE_DEVICE, HSMA_SERVER_FP64_EMULATED). */
 HSMA_API hsma_status_t hsma_server_create(size_t budget_bytes, int n_streams, unsigned int flags,
                                           hsma_server_t **out);
 /* Enqueue a request (thread-safe, non-blocking); *ticket identifies it.  Host

@@ -197,7 +197,7 @@ hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const
       if (plan.path == HSMA_PATH_SMALL)
         return hsma_small_single(dtype, plan.groups, A, lda, B, ldb, (int)m, (int)n, al, unit, st);
       if (opts != nullptr && opts->fp64_products == 1) {
-        const int nb = opts->nb != 0 ? opts->nb : 512;
+        const int nb = opts->nb != 0 ? opts->nb : kHsmaEmulatedNb;
         if (info) info->plan.nb = nb;
         return hsma_blocked_emulated(dtype, nb, A, lda, B, ldb, m, n, al, unit, st);
       }

@@ -1,21 +1,26 @@
 // Reduced-precision modes of the blocked solve (the paper lists mixed
-// precision as future work, Section 6; the blocked algorithm is Section 4.3).
+// precision as future work, Section 6; the blocked algorithm is Section 4.3),
+// and FP64 products emulated on the BF16 tensor cores.
 //
 // FP32-result mode (HSMA_R32_BF16): phase 1 inverts the diagonal blocks in
-// FP32; phase 2 forms X_r = D_r^{-1} B_r with FP32 FMAs and applies the
-// trailing update B_{r+1:} -= A_{r+1:,r} X_r on the 5th-generation tensor
-// cores: operands in BF16, products accumulated in FP32 in tensor memory
-// (tcgen05.mma kind::f16, cta_group::1, 128 x 256 tiles, TMA loads with
-// 128-byte swizzle).  With three terms per update the operands are split,
-// a = hi(a) + lo(a), and the products hi*hi + hi*lo + lo*hi are accumulated in
-// one pass by concatenating along K: [A_hi A_hi A_lo] [X_hi; X_lo; X_hi].
+// FP32; phase 2 forms X_r = D_r^{-1} B_r and applies the trailing update
+// B_{r+1:} -= A_{r+1:,r} X_r on the 5th-generation tensor cores: operands in
+// BF16, products accumulated in FP32 in tensor memory (tcgen05.mma kind::f16,
+// 128 x 256 tiles, TMA loads with 128-byte swizzle).  The solve product cuts
+// both operands into three BF16 slices (24 significant bits, exact for FP32)
+// and sums the six slice pairs with p + q <= 2 in one accumulator (the
+// refinement's correction solves use FP32 FMAs instead).  With three
+// terms per update the operands are split, a = hi(a) + lo(a), and the products
+// hi*hi + hi*lo + lo*hi are accumulated in one pass by concatenating along K:
+// [A_hi A_hi A_lo] [X_hi; X_lo; X_hi].
 //
 // FP64-result mode (HSMA_R64_IR): X_0 from the FP32-result solve of the
-// rounded data, then iterative refinement: R = alpha B - L X in FP64 (FP64
-// tensor products), C from the FP32-result solve of L C = R, X += C in FP64,
-// until ||R||_F / (||L||_F ||X||_F + |alpha| ||B||_F) <= tol.  Every
-// refinement kernel checks a device-side "converged" flag first, so the host
-// enqueues the maximum number of steps without waiting on the device.
+// rounded data, then iterative refinement: R = alpha B - L X in FP64 (emulated
+// on the tensor cores, below, or FP64 tensor products), C from the FP32-result
+// solve of L C = R, X += C in FP64, until
+// ||R||_F / (||L||_F ||X||_F + |alpha| ||B||_F) <= tol.  Every refinement
+// kernel checks a device-side "converged" flag first, so the host enqueues the
+// maximum number of steps without waiting on the device.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
           for (int j = 0; j < CW; ++j) {
             const int col = n0 + c0 + j;
             if constexpr (MODE == TC_F32)
-              dst[j] = (row < M && col < N) ? __ldcs(p.C32 + row + (int64_t)col * p.ldc) : 0.0f;
+              dst[j] = (p.beta != 0.0f && row < M && col < N) ? __ldcs(p.C32 + row + (int64_t)col * p.ldc) : 0.0f;
             else
               dst[j] = (!fresh && row < M && col < N) ? p.C64[row + (int64_t)col * p.ldc] : 0.0;
           }
@@ -552,7 +557,7 @@ int tc_cluster_pref() {
 // CTAs sharing the B tile.
 template <int MODE>
 hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, int sb, const TcArgs &a0,
-                      const char *phase, cudaStream_t st) {
+                      const char *phase, cudaStream_t st, int64_t a_rows = 0) {
   if (a0.M <= 0 || a0.N <= 0) return HSMA_OK;
   if (a0.K % TC_BK != 0 || a0.K <= 0) return HSMA_ERR_INVALID_ARG;
   static DeviceFlags attr;
@@ -566,11 +571,11 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   const int tiles_m = (a0.M + TC_BM - 1) / TC_BM, tiles_n = (a0.N + TC_BN - 1) / TC_BN;
   const int cl = (tiles_m >= 2 && tc_cluster_pref() == 2) ? 2 : 1;
   CUtensorMap ma, mb;
-  if (!make_slice_map(&ma, Ap, (uint64_t)a0.K, (uint64_t)a0.M, (uint64_t)sa, TC_BM) ||
+  if (!make_slice_map(&ma, Ap, (uint64_t)a0.K, (uint64_t)(a_rows > 0 ? a_rows : a0.M), (uint64_t)sa, TC_BM) ||
       !make_slice_map(&mb, Bp, (uint64_t)a0.K, (uint64_t)a0.N, (uint64_t)sb, TC_BN / cl))
     return HSMA_ERR_CUDA;
   TcArgs a = a0;
-  if (MODE == TC_F32) {
+  if (MODE == TC_F32 && a.nunits == 0) {
     a.nunits = 1;
     a.ubeg[0] = 0;
     a.ubeg[1] = 1;
@@ -648,7 +653,64 @@ struct R32Plan {
   int unit = 0;
   float *Dinv = nullptr;
   __nv_bfloat16 *panels = nullptr;  // step r's panel at panel_off(r), rows x Kp; null: converted per step
+  // solve products on the tensor cores (the negated inverses cut into three
+  // BF16 slices, [block][slice][nb][Kd], row-major, Kd = nb rounded up to 64),
+  // else FP32 FMAs on the CUDA cores.  The tensor-core form is faster; its FP32
+  // accumulation inside the MMA is less accurate (about ten times the FP32
+  // rounding error here), which costs the refinement an extra step, so the
+  // FP64-result mode keeps the FP32 FMAs.
+  bool tc_solve = false;
+  __nv_bfloat16 *dslices = nullptr;
 };
+
+int r32_kd(int nb) { return round_up(nb, TC_BK); }
+
+size_t r32_dslices_elems(int nb, int64_t m) { return (size_t)((m + nb - 1) / nb) * 3 * nb * r32_kd(nb); }
+
+// x = a + b + c with a, b, c in BF16 (each remainder is exact in FP32)
+__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c) {
+  a = __float2bfloat16_rn(x);
+  float r = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r);
+  r -= __bfloat162float(b);
+  c = __float2bfloat16_rn(r);
+}
+
+// negated three-way slices of every diagonal-block inverse (column-major nb x nb
+// blocks, zeros outside the computed part) as out[blk][s][i][k]
+__global__ void r32_dslice_kernel(const float *__restrict__ Dinv, int nb, int64_t nblk, int Kd,
+                                  __nv_bfloat16 *out) {
+  const int64_t per = (int64_t)nb * Kd, total = nblk * per;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / per;
+    const int i = (int)((e % per) / Kd), k = (int)(e % Kd);
+    const float v = k < nb ? -Dinv[b * nb * nb + i + (int64_t)k * nb] : 0.0f;
+    __nv_bfloat16 x0, x1, x2;
+    split3_bf16(v, x0, x1, x2);
+    __nv_bfloat16 *o = out + b * 3 * per + (int64_t)i * Kd + k;
+    o[0] = x0;
+    o[per] = x1;
+    o[2 * per] = x2;
+  }
+}
+
+// three-way slices of scale * W (sr x n, column-major, ld ldw) as
+// out[s][j][k] (row-major n x Kd per slice, zero beyond sr)
+__global__ void r32_xslice_kernel(const float *__restrict__ W, int64_t ldw, int sr, int64_t n, int Kd, float scale,
+                                  __nv_bfloat16 *out, const int *skip) {
+  if (skip != nullptr && *(volatile const int *)skip) return;
+  const int64_t per = n * Kd;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / Kd;
+    const int k = (int)(e % Kd);
+    const float v = k < sr ? scale * W[k + j * ldw] : 0.0f;
+    __nv_bfloat16 x0, x1, x2;
+    split3_bf16(v, x0, x1, x2);
+    out[e] = x0;
+    out[per + e] = x1;
+    out[2 * per + e] = x2;
+  }
+}
 
 int64_t panel_rows(const R32Plan &P, int64_t r) {
   const int64_t r0 = r * P.nb, sr = std::min<int64_t>(P.nb, P.m - r0);
@@ -682,9 +744,15 @@ __global__ void copy_f32_kernel(const float *__restrict__ src, int64_t lds, floa
 
 hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
   hsma_status_t s = hsma_diag_inverse(HSMA_R32_BF16, P.nb, P.A, P.lda, P.m, P.unit, P.Dinv, st);
-  if (s != HSMA_OK || !keep_panels) return s;
+  if (s != HSMA_OK) return s;
   const int64_t nblk = (P.m + P.nb - 1) / P.nb;
   HsmaTraceScope ts("convert", st);
+  if (P.tc_solve) {
+    r32_dslice_kernel<<<g_launch_grid(nblk * P.nb * r32_kd(P.nb)), 256, 0, st>>>(P.Dinv, P.nb, nblk, r32_kd(P.nb),
+                                                                                 P.dslices);
+    HSMA_CUDA_TRY(cudaGetLastError());
+  }
+  if (!keep_panels) return HSMA_OK;
   for (int64_t r = 0; r + 1 < nblk; ++r) {
     const int64_t r0 = r * P.nb, sr = std::min<int64_t>(P.nb, P.m - r0);
     const int rows = (int)panel_rows(P, r);
@@ -706,14 +774,30 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
   const size_t w_b = sizeof(float) * (size_t)nb * n;
   const size_t a_b = P.panels ? 0 : sizeof(__nv_bfloat16) * (size_t)rows_max * Kp;
   const size_t x_b = sizeof(__nv_bfloat16) * (size_t)n * Kp;
+  const int Kd = r32_kd(nb);
+  const size_t x3_b = P.tc_solve ? sizeof(__nv_bfloat16) * 3 * (size_t)n * Kd : 0;
   auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
   void *ws = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&ws, al(w_b) + al(a_b) + al(x_b), st);
+  hsma_status_t s = hsma_ws_alloc(&ws, al(w_b) + al(a_b) + al(x_b) + al(x3_b), st);
   if (s != HSMA_OK) return s;
   unsigned char *base = static_cast<unsigned char *>(ws);
   float *W = reinterpret_cast<float *>(base);
   __nv_bfloat16 *Ap = reinterpret_cast<__nv_bfloat16 *>(base + al(w_b));
   __nv_bfloat16 *Xp = reinterpret_cast<__nv_bfloat16 *>(base + al(w_b) + al(a_b));
+  __nv_bfloat16 *X3 = reinterpret_cast<__nv_bfloat16 *>(base + al(w_b) + al(a_b) + al(x_b));
+  // X_r = D_r^{-1} (scale W): slice pairs (p, q) with p + q <= 2 of the three
+  // BF16 slices of each operand, summed in one FP32 accumulator
+  TcArgs sa{};
+  {
+    const uint8_t ps[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+    sa.nunits = 1;
+    sa.ubeg[0] = 0;
+    sa.ubeg[1] = 6;
+    for (int q = 0; q < 6; ++q) {
+      sa.pa[q] = ps[q][0];
+      sa.pb[q] = ps[q][1];
+    }
+  }
   for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
     const int64_t r0 = r * nb;
     const int sr = (int)std::min<int64_t>(nb, m - r0);
@@ -721,8 +805,25 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
       HsmaTraceScope ts("copy", st);
       copy_f32_kernel<<<g_launch_grid((int64_t)sr * n), 256, 0, st>>>(B + r0, ldb, W, nb, sr, n, skip);
     }
-    s = sgemm_scale(P.Dinv + (size_t)r * nb * nb, nb, W, nb, B + r0, ldb, sr, (int)n, sr, r == 0 ? alpha : 1.0f, 1,
-                    skip, st);
+    if (P.tc_solve) {
+      {
+        HsmaTraceScope ts("convert", st);
+        r32_xslice_kernel<<<g_launch_grid(n * Kd), 256, 0, st>>>(W, nb, sr, n, Kd, r == 0 ? alpha : 1.0f, X3, skip);
+        if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
+      }
+      sa.C32 = B + r0;
+      sa.ldc = ldb;
+      sa.beta = 0.0f;
+      sa.M = sr;
+      sa.N = (int)n;
+      sa.K = Kd;
+      sa.tri = 1;
+      sa.skip = skip;
+      s = tc_gemm<TC_F32>(P.dslices + (size_t)r * 3 * nb * Kd, 3, X3, 3, sa, "solve_bf16", st, nb);
+    } else {
+      s = sgemm_scale(P.Dinv + (size_t)r * nb * nb, nb, W, nb, B + r0, ldb, sr, (int)n, sr, r == 0 ? alpha : 1.0f, 1,
+                      skip, st);
+    }
     if (s != HSMA_OK || r0 + sr >= m) break;
     const int rows = (int)(m - r0 - sr);
     const __nv_bfloat16 *panel = P.panels ? P.panels + panel_off(P, r) : Ap;
@@ -767,10 +868,13 @@ hsma_status_t r32_solve(int nb, int terms, const float *A, int64_t lda, float *B
   P.lda = lda;
   P.unit = unit;
   const int64_t nblk = (m + nb - 1) / nb;
+  const size_t dinv_b = (sizeof(float) * (size_t)nblk * nb * nb + 1023) & ~(size_t)1023;
   void *ws = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&ws, sizeof(float) * (size_t)nblk * nb * nb, st);
+  hsma_status_t s = hsma_ws_alloc(&ws, dinv_b + sizeof(__nv_bfloat16) * r32_dslices_elems(nb, m), st);
   if (s != HSMA_OK) return s;
   P.Dinv = static_cast<float *>(ws);
+  P.tc_solve = true;
+  P.dslices = reinterpret_cast<__nv_bfloat16 *>(static_cast<unsigned char *>(ws) + dinv_b);
   s = r32_prepare(P, false, st);
   if (s == HSMA_OK) s = r32_apply(P, B, ldb, n, alpha, nullptr, st);
   hsma_status_t f = hsma_ws_free(ws, st);
@@ -1229,28 +1333,49 @@ __global__ void scale_kernel(double *B, int64_t ldb, int64_t rows, int64_t n, do
 // real columns): inside a panel, each solved block updates only the panel's
 // remaining rows; below the panel, one update with K = h N_B covers all h
 // blocks.  The result is the same product sum, grouped differently.
+// Workspace of blocked_emulated: the inverses, one block row of B, and the
+// slices of an update panel, of one inverse and of the right operand.
+struct EmuLayout {
+  int W = 1, h = 1, Kpb = 0, Kpp = 0;
+  int64_t P = 0;
+  size_t dinv_b = 0, w_b = 0, pa_b = 0, pd_b = 0, px_b = 0;
+  size_t total() const { return dinv_b + w_b + pa_b + pd_b + px_b; }
+};
+
+EmuLayout emu_layout(bool cplx, int nb, int64_t m, int64_t n) {
+  EmuLayout L;
+  L.W = cplx ? 2 : 1;
+  const int64_t nblk = (m + nb - 1) / nb;
+  L.h = std::max(1, 1024 / (L.W * nb));
+  L.P = (int64_t)L.h * nb;  // panel width (source columns)
+  L.Kpb = oz_kp((int64_t)L.W * nb);
+  L.Kpp = oz_kp(L.W * L.P);
+  auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+  const size_t eb = sizeof(double) * L.W;
+  L.dinv_b = al(eb * (size_t)nblk * nb * nb);
+  L.w_b = al(eb * (size_t)nb * n);
+  L.pa_b = al(oz_operand_bytes((int64_t)L.W * m, L.Kpp));
+  L.pd_b = al(oz_operand_bytes((int64_t)L.W * nb, L.Kpb));
+  L.px_b = al(oz_operand_bytes(n, L.Kpp));
+  return L;
+}
+
 hsma_status_t blocked_emulated(bool cplx, int nb, const double *A, int64_t lda, double *B, int64_t ldb, int64_t m,
                                int64_t n, const double *alpha, int unit, cudaStream_t st) {
-  const int W = cplx ? 2 : 1;
-  const int64_t nblk = (m + nb - 1) / nb;
-  const int h = std::max(1, 1024 / (W * nb));
-  const int64_t P = (int64_t)h * nb;  // panel width (source columns)
-  const int Kpb = oz_kp((int64_t)W * nb), Kpp = oz_kp(W * P);
+  const EmuLayout E = emu_layout(cplx, nb, m, n);
+  const int W = E.W;
+  const int64_t P = E.P;
+  const int Kpb = E.Kpb, Kpp = E.Kpp;
   if (Kpp > kOzMaxK || (int64_t)W * m > INT32_MAX || n > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
-  auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
   const size_t eb = sizeof(double) * W;
-  const size_t dinv_b = al(eb * (size_t)nblk * nb * nb);
-  const size_t w_b = al(eb * (size_t)nb * n);
-  const size_t pa_b = al(oz_operand_bytes((int64_t)W * m, Kpp));
-  const size_t pd_b = al(oz_operand_bytes((int64_t)W * nb, Kpb));
-  const size_t px_b = al(oz_operand_bytes(n, Kpp));
+  const size_t dinv_b = E.dinv_b, w_b = E.w_b, pa_b = E.pa_b;
   void *ws = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&ws, dinv_b + w_b + pa_b + pd_b + px_b, st);
+  hsma_status_t s = hsma_ws_alloc(&ws, E.total(), st);
   if (s != HSMA_OK) return s;
   unsigned char *base = static_cast<unsigned char *>(ws);
   double *Dinv = reinterpret_cast<double *>(base);
   double *Wb = reinterpret_cast<double *>(base + dinv_b);
-  unsigned char *pa_mem = base + dinv_b + w_b, *px_mem = base + dinv_b + w_b + pa_b + pd_b;
+  unsigned char *pa_mem = base + dinv_b + w_b, *px_mem = base + dinv_b + w_b + pa_b + E.pd_b;
   // views of the operand buffers for a given K (the buffers hold the widest)
   auto view = [](unsigned char *mem, int64_t rows_cap, int Kp, int64_t rows) {
     OzOperand o = oz_operand(mem, rows_cap, Kp);
@@ -1457,6 +1582,10 @@ hsma_status_t hsma_blocked_emulated(int dtype, int nb, const void *A, int64_t ld
   if (dtype != HSMA_R64 && dtype != HSMA_C128) return HSMA_ERR_INVALID_ARG;
   return blocked_emulated(dtype == HSMA_C128, nb, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb,
                           m, n, alpha, unit, st);
+}
+
+size_t hsma_blocked_emulated_ws_bytes(int dtype, int nb, int64_t m, int64_t n) {
+  return emu_layout(dtype == HSMA_C128, nb, m, n).total();
 }
 
 extern "C" HSMA_API hsma_status_t hsma_gemm_f64_emulated(int64_t M, int64_t N, int64_t K, const double *A,

@@ -17,3 +17,9 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
 // products emulated in FP64 on the BF16 tensor cores (exact integer slices).
 hsma_status_t hsma_blocked_emulated(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
                                     int64_t n, const double *alpha, int unit, cudaStream_t st);
+
+// Device workspace hsma_blocked_emulated takes from the pool (bytes).
+size_t hsma_blocked_emulated_ws_bytes(int dtype, int nb, int64_t m, int64_t n);
+
+// N_B of the emulated blocked path when the caller gives none.
+constexpr int kHsmaEmulatedNb = 512;

@@ -13,6 +13,9 @@
 // request alone, because each request's arithmetic does not depend on what
 // runs beside it.
 //
+// With HSMA_SERVER_FP64_EMULATED the blocked requests use FP64 products
+// emulated on the BF16 tensor cores (the fp64_products option).
+//
 // A fake-device mode (HSMA_SERVER_FAKE_DEVICE) runs the same admission and
 // queue logic with no GPU: each "launch" completes after a modelled time.
 #include <cuda_runtime.h>
@@ -30,6 +33,7 @@
 #include "../../include/hsma.h"
 #include "common.cuh"
 #include "gen.h"
+#include "mixed.h"
 
 namespace {
 
@@ -84,9 +88,10 @@ struct hsma_server {
 
 namespace {
 
-size_t request_bytes(const hsma_request_t &r) {
+size_t request_bytes(const hsma_request_t &r, bool emulated) {
   const size_t es = esize(r.dtype);
   size_t b = es * (size_t)r.m * (size_t)r.m + es * (size_t)r.m * (size_t)r.n;
+  if (r.m > 64 && emulated) return b + hsma_blocked_emulated_ws_bytes(r.dtype, kHsmaEmulatedNb, r.m, r.n);
   if (r.m > 64) {
     hsma_plan_t p;
     hsma_plan(r.dtype, r.m, r.n, &p);
@@ -231,7 +236,11 @@ void launch(hsma_server *s, std::vector<uint64_t> &small_group, std::vector<uint
     for (uint64_t t : large) {
       Req &q = *s->all[t];
       cudaStream_t st = s->streams[q.stream];
-      hsma_status_t rc = hsma_trsm_llnn(q.r.dtype, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st);
+      hsma_opts_t o;
+      std::memset(&o, 0, sizeof o);
+      o.fp64_products = (s->flags & HSMA_SERVER_FP64_EMULATED) ? 1 : 0;
+      hsma_status_t rc = hsma_trsm_llnn_ex(q.r.dtype, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st,
+                                           &o, nullptr);
       if (rc == HSMA_OK) rc = fetch_output(s, q);
       q.status = rc;
       s->n_blocked.fetch_add(1);
@@ -365,6 +374,7 @@ extern "C" {
 HSMA_API hsma_status_t hsma_server_create(size_t budget_bytes, int n_streams, unsigned int flags,
                                           hsma_server_t **out) {
   if (out == nullptr || budget_bytes == 0 || n_streams < 1 || n_streams > 64) return HSMA_ERR_INVALID_ARG;
+  if ((flags & ~(HSMA_SERVER_FAKE_DEVICE | HSMA_SERVER_FP64_EMULATED)) != 0) return HSMA_ERR_INVALID_ARG;
   *out = nullptr;
   auto *s = new hsma_server();
   s->budget = budget_bytes;
@@ -413,7 +423,7 @@ HSMA_API hsma_status_t hsma_server_submit(hsma_server_t *s, const hsma_request_t
   auto q = std::make_unique<Req>();
   q->r = r;
   q->arrival = Clock::now();
-  q->need = request_bytes(r);
+  q->need = request_bytes(r, (s->flags & HSMA_SERVER_FP64_EMULATED) != 0);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return HSMA_ERR_BUSY;

@@ -68,6 +68,7 @@ class ServerStats(ctypes.Structure):
 
 
 SERVER_FAKE_DEVICE = 0x1
+SERVER_FP64_EMULATED = 0x2
 
 
 class Info(ctypes.Structure):

@@ -77,3 +77,36 @@ def test_served_device_generated_inputs(H):
         A, B = I.gen_A(77, m, code, inst=k), I.gen_B(77, m, n, code, inst=k)
         assert oracle.forward_error(X, oracle.solve(A, B, 1.0)) <= 1e-12
     assert H.hsma_server_destroy(s) == 0
+
+
+def test_served_emulated_results_equal_alone_and_oracle(H):
+    """HSMA_SERVER_FP64_EMULATED: blocked requests use the emulated FP64 products; each result is
+    bitwise the same request solved alone with fp64_products = 1, and within 1e-12 of the oracle."""
+    import torch
+    t, ms, ns, dts = I.serving_requests(8, 24, m_range=(65, 900), n_range=(1, 96))
+    s = H.hsma_server_create(1 << 30, 4, H.SERVER_FP64_EMULATED)
+    keep = []
+    for k in range(len(ms)):
+        code, m, n = int(dts[k]), int(ms[k]), int(ns[k])
+        A, B = I.gen_A(8, m, code, inst=k), I.gen_B(8, m, n, code, inst=k)
+        X = np.zeros_like(B, order="F")
+        alpha = 1.5 if code == I.R64 else 1.5 - 0.5j
+        r = H.Request()
+        r.dtype, r.diag, r.m, r.n = code, 0, m, n
+        r.alpha[0], r.alpha[1] = complex(alpha).real, complex(alpha).imag
+        r.A_host, r.lda, r.B_host, r.ldb = A.ctypes.data, m, B.ctypes.data, m
+        r.X_host, r.ldx = X.ctypes.data, m
+        keep.append((code, A, B, X, alpha, r, H.hsma_server_submit(s, r)))
+    assert H.hsma_server_drain(s, 120.0) == 0
+    assert H.hsma_server_stats(s).blocked_launches >= 1
+    opts = H.Opts()
+    opts.fp64_products = 1
+    for code, A, B, X, alpha, _, tk in keep:
+        assert H.hsma_server_poll(s, tk)[2] == 0
+        dA, dB = H.to_device(A), H.to_device(B)
+        m, n = B.shape
+        H.hsma_trsm_llnn_ex(code, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts)
+        torch.cuda.synchronize()
+        assert np.array_equal(X, H.from_device(dB))
+        assert oracle.forward_error(X, oracle.solve(A, B, alpha)) <= 1e-12
+    assert H.hsma_server_destroy(s) == 0

@@ -88,3 +88,26 @@ def test_invalid_requests(H):
     with pytest.raises(H.HsmaError):
         H.hsma_server_submit(s, bad)
     assert H.hsma_server_destroy(s) == 0
+
+
+def test_unknown_server_flags_rejected(H):
+    with pytest.raises(H.HsmaError):
+        H.hsma_server_create(1 << 20, 1, 0x80)
+
+
+def test_emulated_flag_accounts_for_its_workspace(H):
+    """With FP64 products emulated, a blocked request also reserves the slice buffers:
+    a budget that fits the plain request's need is too small for the emulated one."""
+    need_plain = 8 * 512 * 512 + 8 * 512 * 64 + 8 * (2 * 256 * 256 + 256 * 64)
+    flags = H.SERVER_FAKE_DEVICE | H.SERVER_FP64_EMULATED
+    s = H.hsma_server_create(need_plain + 1000, 1, flags)
+    t = H.hsma_server_submit(s, _req(H, 512, 64))
+    assert H.hsma_server_drain(s, 30.0) == 0
+    done, _, status = H.hsma_server_poll(s, t)
+    assert done and status == 3  # HSMA_ERR_NO_MEMORY: never fits
+    assert H.hsma_server_destroy(s) == 0
+    s = H.hsma_server_create(1 << 30, 2, flags)
+    ts = [H.hsma_server_submit(s, _req(H, 512, 64, 0, 3, i)) for i in range(4)]
+    assert H.hsma_server_drain(s, 30.0) == 0
+    assert all(H.hsma_server_poll(s, t)[2] == 0 for t in ts)
+    assert H.hsma_server_destroy(s) == 0

@@ -275,12 +275,14 @@ def run_batched(args, dist, device):
         clocks = sampler.stop()
     ms_max = dist.max(ms_total, device=device)
 
-    # end to end through the C ABI with host buffers: H2D of A and B, solve, D2H of X
+    # end to end through the C ABI with host buffers: the host-buffer batch entry point
+    # copies A and B in and X out, chunk by chunk, overlapped with the solves
+    hm, hn = ms.astype(np.int32), ns.astype(np.int32)
+    hoA, hoB = offA.astype(np.int64), offB.astype(np.int64)
+
     def e2e_step():
-        dA.copy_(pinA, non_blocking=True)
-        dB.copy_(pinB, non_blocking=True)
-        step()
-        outB.copy_(dB, non_blocking=True)
+        H.hsma_trsm_llnn_vbatched_host(H.C128, 0, batch, hm, hn, alpha, pinA.data_ptr(), hoA, pinB.data_ptr(), hoB,
+                                       outB.data_ptr(), chunks=args.e2e_chunks, stream=sp)
 
     e2e_steps = max(1, min(args.steps, 50))
     for _ in range(2):
@@ -725,6 +727,7 @@ def main(argv=None):
     ap.add_argument("--fp64-products", default="dmma", choices=["dmma", "emulated"],
                     help="large_*, serve: FP64 tensor products, or FP64 emulated on the BF16 tensor cores")
     ap.add_argument("--nb", type=int, default=0, help="large_*: force N_B (0 = planner)")
+    ap.add_argument("--e2e-chunks", type=int, default=0, help="batched e2e: host-buffer chunks (0 = library default)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

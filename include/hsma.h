@@ -178,6 +178,31 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batc
                                       int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream);
 
 /*
+ * The varlen batch with its matrices in HOST memory (no paper counterpart:
+ * the paper's solves are device-resident).  The batch is cut into `chunks`
+ * groups of consecutive instances (0 = 4); each group's host-to-device copy,
+ * batched solve and device-to-host copy run on one of three internal streams,
+ * so copies of some groups overlap the solves of others.
+ *
+ * h_m, h_n: HOST arrays of `batch` sizes (0 <= m_i <= 64, n_i >= 0).
+ * hA, hB: HOST buffers holding every A_i (column-major, lda = m_i, m_i^2
+ *        elements at element offset h_offA[i]) and every B_i (ldb = m_i, m_i n_i
+ *        elements at h_offB[i]); offsets increase and regions do not overlap.
+ * hX: HOST buffer receiving X_i at h_offB[i] (may equal hB).
+ * Use page-locked host memory for asynchronous copies (pageable memory works,
+ * with synchronous staging).  The call is asynchronous on `stream`: hX is
+ * valid, and hA / hB may be reused, once the stream has been synchronised.
+ * Results equal hsma_trsm_llnn_vbatched on the same data, bit for bit.
+ * Errors: INVALID_ARG for a bad size, offset order or null pointer;
+ * UNSUPPORTED for m_i > 64 or another dtype.  Concurrent calls share the
+ * internal streams (their work is serialised, not mixed).
+ */
+HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int diag, int32_t batch, const int32_t *h_m,
+                                                    const int32_t *h_n, const void *alpha, const void *hA,
+                                                    const int64_t *h_offA, const void *hB, const int64_t *h_offB,
+                                                    void *hX, int32_t chunks, void *stream);
+
+/*
  * Allocation-free form of hsma_trsm_llnn_vbatched (same arguments, same
  * results bit for bit).  It has no counterpart in the paper; it exists for
  * callers that cannot have the library allocate device memory during a

@@ -33,6 +33,7 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
+           "hsma_trsm_llnn_vbatched_host",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -96,6 +97,8 @@ def _load():
     lib.hsma_trsm_llnn_vbatched_noalloc.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p,
                                                     vp]
     lib.hsma_trsm_llnn_vbatched_noalloc.restype = c_int
+    lib.hsma_trsm_llnn_vbatched_host.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+    lib.hsma_trsm_llnn_vbatched_host.restype = c_int
     lib.hsma_plan.argtypes = [c_int, i64, i64, ctypes.POINTER(Plan)]
     lib.hsma_plan.restype = c_int
     lib.hsma_small_cost.argtypes = [c_int, i64, i64, i32]
@@ -192,6 +195,20 @@ def hsma_trsm_llnn_vbatched_noalloc(dtype, diag, batch, d_m, d_n, alpha, d_A, d_
                                              d_ldb, max_m, max_n, d_status or None, stream)
     if check:
         _check(s, "hsma_trsm_llnn_vbatched_noalloc")
+    return s
+
+
+def hsma_trsm_llnn_vbatched_host(dtype, diag, batch, h_m, h_n, alpha, hA, h_offA, hB, h_offB, hX, chunks=0,
+                                 stream=0, check=True) -> int:
+    """Varlen batch with matrices in host memory (pointers as ints; h_m, h_n int32 and h_offA,
+    h_offB int64 host arrays, numpy arrays accepted), copies overlapped with the solves."""
+    def ptr(a):
+        return a.ctypes.data if isinstance(a, np.ndarray) else a
+    s = _lib.hsma_trsm_llnn_vbatched_host(dtype, diag, batch, ptr(h_m), ptr(h_n),
+                                          ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), ptr(hA), ptr(h_offA),
+                                          ptr(hB), ptr(h_offB), ptr(hX), chunks, stream)
+    if check:
+        _check(s, "hsma_trsm_llnn_vbatched_host")
     return s
 
 

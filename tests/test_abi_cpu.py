@@ -113,3 +113,27 @@ def test_small_cost_model(H):
     assert H.hsma_small_cost(H.C128, 32, 32, 1) == 4 * H.hsma_small_cost(H.R64, 32, 32, 1)
     assert H.hsma_small_cost(H.C128, 33, 8, 1) == -1.0   # complex G=1 holds 32 rows at most
     assert H.hsma_small_cost(H.R64, 65, 8, 2) == -1.0
+
+
+def test_vbatched_host_argument_checks(H):
+    """The host-buffer batch validates sizes and offsets on the host, before any device call."""
+    import numpy as np
+    m = np.array([4, 8], dtype=np.int32)
+    n = np.array([2, 3], dtype=np.int32)
+    offA = np.array([0, 16], dtype=np.int64)
+    offB = np.array([0, 8], dtype=np.int64)
+    buf = np.zeros(256)
+    p = buf.ctypes.data
+    f = H.hsma_trsm_llnn_vbatched_host
+    assert f(0, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, 0, check=False) == 0                      # empty batch
+    assert f(2, 0, 2, m, n, 1.0, p, offA, p, offB, p, check=False) == 2                # dtype unsupported
+    assert f(9, 0, 2, m, n, 1.0, p, offA, p, offB, p, check=False) == 1                # dtype unknown
+    assert f(0, 5, 2, m, n, 1.0, p, offA, p, offB, p, check=False) == 1                # diag unknown
+    assert f(0, 0, 2, m, n, 1.0, 0, offA, p, offB, p, check=False) == 1                # NULL hA
+    big = np.array([4, 65], dtype=np.int32)
+    assert f(0, 0, 2, big, n, 1.0, p, offA, p, offB, p, check=False) == 2              # m > 64
+    neg = np.array([4, -1], dtype=np.int32)
+    assert f(0, 0, 2, neg, n, 1.0, p, offA, p, offB, p, check=False) == 1              # m < 0
+    overlap = np.array([0, 15], dtype=np.int64)                                        # A_0 holds 16 elements
+    assert f(0, 0, 2, m, n, 1.0, p, overlap, p, offB, p, check=False) == 1
+    assert f(0, 0, 2, m, n, 1.0, p, offA, p, offB, p, chunks=-1, check=False) == 1

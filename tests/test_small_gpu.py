@@ -193,3 +193,34 @@ def test_device_generator_matches_host(H, code):
         ref = I.gen_A(42, m, code, inst=inst) if kind == 0 else I.gen_B(42, m, cols, code, inst=inst)
         assert np.array_equal(got[:m], ref)
         assert np.all(got[m:] == 7.0)
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+@pytest.mark.parametrize("chunks,pinned", [(0, True), (1, True), (3, False), (7, True)])
+def test_batched_host_buffers_equal_device_batch(H, code, chunks, pinned):
+    """The host-buffer entry point (chunked copies overlapped with the solves) gives the
+    device-resident batch's results bit for bit, pinned or pageable host memory."""
+    import torch
+    alpha = 1.5 if code == I.R64 else 1.5 - 0.5j
+    As, Bs = _config1(code, batch=1000, seed=11)
+    dev = _run_batch(H, code, As, Bs, alpha).results()
+    ms = np.array([a.shape[1] for a in As], dtype=np.int32)
+    ns = np.array([b.shape[1] for b in Bs], dtype=np.int32)
+    offA = np.concatenate([[0], np.cumsum(ms.astype(np.int64) ** 2)[:-1]]).astype(np.int64)
+    offB = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns)[:-1]]).astype(np.int64)
+    hA = np.concatenate([a.ravel(order="F") for a in As])
+    hB = np.concatenate([b.ravel(order="F") for b in Bs])
+    if pinned:
+        tA, tB = torch.from_numpy(hA).pin_memory(), torch.from_numpy(hB).pin_memory()
+        tX = torch.empty_like(tB).pin_memory()
+        pA, pB, pX, X = tA.data_ptr(), tB.data_ptr(), tX.data_ptr(), tX
+    else:
+        hX = np.empty_like(hB)
+        pA, pB, pX, X = hA.ctypes.data, hB.ctypes.data, hX.ctypes.data, hX
+    H.hsma_trsm_llnn_vbatched_host(code, 0, len(As), ms, ns, alpha, pA, offA, pB, offB, pX, chunks=chunks,
+                                   stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    out = X.numpy() if pinned else X
+    for b in range(len(As)):
+        got = out[offB[b]:offB[b] + ms[b] * ns[b]].reshape((ms[b], ns[b]), order="F")
+        assert np.array_equal(got, dev[b]), b

@@ -267,7 +267,7 @@ HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64
 typedef struct hsma_server hsma_server_t;
 
 #define HSMA_SERVER_FAKE_DEVICE 0x1u /* no GPU: launches complete after a modelled time (tests) */
-#define HSMA_SERVER_FP64_EMULATED 0x2u /* blocked requests (m > 64) use hsma_opts_t.fp64_products = 1 */
+#define HSMA_SERVER_FP64_EMULATED 0x2u /* requests with m >= 384 use hsma_opts_t.fp64_products = 1 */
 
 typedef struct {
   int32_t dtype;  /* HSMA_R64 or HSMA_C128                                        */

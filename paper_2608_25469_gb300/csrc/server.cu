@@ -13,8 +13,10 @@
 // request alone, because each request's arithmetic does not depend on what
 // runs beside it.
 //
-// With HSMA_SERVER_FP64_EMULATED the blocked requests use FP64 products
-// emulated on the BF16 tensor cores (the fp64_products option).
+// With HSMA_SERVER_FP64_EMULATED the blocked requests with m >= 384 use FP64
+// products emulated on the BF16 tensor cores (the fp64_products option); below
+// that the FP64 tensor products of a few block steps take no longer than the
+// emulated path's extra slicing launches.
 //
 // A fake-device mode (HSMA_SERVER_FAKE_DEVICE) runs the same admission and
 // queue logic with no GPU: each "launch" completes after a modelled time.
@@ -88,10 +90,16 @@ struct hsma_server {
 
 namespace {
 
-size_t request_bytes(const hsma_request_t &r, bool emulated) {
+constexpr int64_t kEmulatedMinM = 384;  // smallest m served with emulated products
+
+bool use_emulated(const hsma_request_t &r, unsigned flags) {
+  return (flags & HSMA_SERVER_FP64_EMULATED) != 0 && r.m >= kEmulatedMinM;
+}
+
+size_t request_bytes(const hsma_request_t &r, unsigned flags) {
   const size_t es = esize(r.dtype);
   size_t b = es * (size_t)r.m * (size_t)r.m + es * (size_t)r.m * (size_t)r.n;
-  if (r.m > 64 && emulated) return b + hsma_blocked_emulated_ws_bytes(r.dtype, kHsmaEmulatedNb, r.m, r.n);
+  if (use_emulated(r, flags)) return b + hsma_blocked_emulated_ws_bytes(r.dtype, kHsmaEmulatedNb, r.m, r.n);
   if (r.m > 64) {
     hsma_plan_t p;
     hsma_plan(r.dtype, r.m, r.n, &p);
@@ -238,7 +246,7 @@ void launch(hsma_server *s, std::vector<uint64_t> &small_group, std::vector<uint
       cudaStream_t st = s->streams[q.stream];
       hsma_opts_t o;
       std::memset(&o, 0, sizeof o);
-      o.fp64_products = (s->flags & HSMA_SERVER_FP64_EMULATED) ? 1 : 0;
+      o.fp64_products = use_emulated(q.r, s->flags) ? 1 : 0;
       hsma_status_t rc = hsma_trsm_llnn_ex(q.r.dtype, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st,
                                            &o, nullptr);
       if (rc == HSMA_OK) rc = fetch_output(s, q);
@@ -423,7 +431,7 @@ HSMA_API hsma_status_t hsma_server_submit(hsma_server_t *s, const hsma_request_t
   auto q = std::make_unique<Req>();
   q->r = r;
   q->arrival = Clock::now();
-  q->need = request_bytes(r, (s->flags & HSMA_SERVER_FP64_EMULATED) != 0);
+  q->need = request_bytes(r, s->flags);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return HSMA_ERR_BUSY;

@@ -80,8 +80,8 @@ def test_served_device_generated_inputs(H):
 
 
 def test_served_emulated_results_equal_alone_and_oracle(H):
-    """HSMA_SERVER_FP64_EMULATED: blocked requests use the emulated FP64 products; each result is
-    bitwise the same request solved alone with fp64_products = 1, and within 1e-12 of the oracle."""
+    """HSMA_SERVER_FP64_EMULATED: requests with m >= 384 use the emulated FP64 products; each result
+    is bitwise the same request solved alone with the same products, and within 1e-12 of the oracle."""
     import torch
     t, ms, ns, dts = I.serving_requests(8, 24, m_range=(65, 900), n_range=(1, 96))
     s = H.hsma_server_create(1 << 30, 4, H.SERVER_FP64_EMULATED)
@@ -99,12 +99,12 @@ def test_served_emulated_results_equal_alone_and_oracle(H):
         keep.append((code, A, B, X, alpha, r, H.hsma_server_submit(s, r)))
     assert H.hsma_server_drain(s, 120.0) == 0
     assert H.hsma_server_stats(s).blocked_launches >= 1
-    opts = H.Opts()
-    opts.fp64_products = 1
     for code, A, B, X, alpha, _, tk in keep:
         assert H.hsma_server_poll(s, tk)[2] == 0
         dA, dB = H.to_device(A), H.to_device(B)
         m, n = B.shape
+        opts = H.Opts()
+        opts.fp64_products = 1 if m >= 384 else 0  # the server's rule
         H.hsma_trsm_llnn_ex(code, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts)
         torch.cuda.synchronize()
         assert np.array_equal(X, H.from_device(dB))

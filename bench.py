@@ -192,14 +192,20 @@ def profile_traffic(name: str, files, work=None):
 SMALL_SOURCES = ["paper_2608_25469_gb300/csrc/small.cu", "paper_2608_25469_gb300/csrc/common.cuh"]
 
 
-def batched_inputs(seed, batch=8192):
+def batched_inputs(seed, batch=8192, c64=False):
+    """The config-1 batch (complex128; complex64 = the same values rounded)."""
     from paper_2608_25469_gb300 import inputs as I
     ms, ns = I.batched_sizes(seed, batch)
     As = [I.gen_A(seed, int(m), I.C128, inst=b) for b, m in enumerate(ms)]
     Bs = [I.gen_B(seed, int(m), int(n), I.C128, inst=b) for b, (m, n) in enumerate(zip(ms, ns))]
+    es = 16
+    if c64:
+        As = [np.asfortranarray(a.astype(np.complex64)) for a in As]
+        Bs = [np.asfortranarray(b.astype(np.complex64)) for b in Bs]
+        es = 8
     flops = float(sum(4.0 * float(m) * m * n for m, n in zip(ms, ns)))
     # algorithmic bytes: lower triangle of A read, B read, X written
-    abytes = float(sum(16 * (m * (m + 1) // 2) + 2 * 16 * m * n for m, n in zip(ms, ns)))
+    abytes = float(sum(es * (m * (m + 1) // 2) + 2 * es * m * n for m, n in zip(ms, ns)))
     return As, Bs, ms, ns, flops, abytes
 
 
@@ -215,14 +221,15 @@ def cpu_baseline_batched(As, Bs, alpha, min_seconds=3.0):
     return reps, el, oracle.num_threads()
 
 
-def run_batched(args, dist, device):
+def run_batched(args, dist, device, c64=False):
     import torch
     from paper_2608_25469_gb300 import hsma as H
     alpha = 1.5 - 0.5j
     seed = shard_seed(args.seed, dist.rank)
-    As, Bs, ms, ns, flops, abytes = batched_inputs(seed)
+    As, Bs, ms, ns, flops, abytes = batched_inputs(seed, c64=c64)
     batch = len(As)
-    es = 16
+    es = 8 if c64 else 16
+    code = H.C64 if c64 else H.C128
     # pack: one buffer for all A (lda = m), one for all B (ldb = m)
     offA = np.concatenate([[0], np.cumsum(ms.astype(np.int64) ** 2)[:-1]])
     offB = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns)[:-1]])
@@ -242,7 +249,7 @@ def run_batched(args, dist, device):
     sp = int(st.cuda_stream)
 
     def step():
-        H.hsma_trsm_llnn_vbatched(H.C128, 0, batch, dm.data_ptr(), dn.data_ptr(), alpha, pa.data_ptr(),
+        H.hsma_trsm_llnn_vbatched(code, 0, batch, dm.data_ptr(), dn.data_ptr(), alpha, pa.data_ptr(),
                                   dld.data_ptr(), pb.data_ptr(), dld.data_ptr(), 64, 64, 0, sp)
 
     for _ in range(args.warmup):
@@ -281,7 +288,7 @@ def run_batched(args, dist, device):
     hoA, hoB = offA.astype(np.int64), offB.astype(np.int64)
 
     def e2e_step():
-        H.hsma_trsm_llnn_vbatched_host(H.C128, 0, batch, hm, hn, alpha, pinA.data_ptr(), hoA, pinB.data_ptr(), hoB,
+        H.hsma_trsm_llnn_vbatched_host(code, 0, batch, hm, hn, alpha, pinA.data_ptr(), hoA, pinB.data_ptr(), hoB,
                                        outB.data_ptr(), chunks=args.e2e_chunks, stream=sp)
 
     e2e_steps = max(1, min(args.steps, 50))
@@ -301,38 +308,49 @@ def run_batched(args, dist, device):
 
     kernel_ms = solve_ms / max(solve_cnt, 1)
     achieved = flops / (kernel_ms * 1e-3) / 1e9
-    traffic = profile_traffic("vbatched_solve_c128_8192.txt", SMALL_SOURCES)
+    name = "c64" if c64 else "c128"
+    traffic = profile_traffic(f"vbatched_solve_{name}_8192.txt", SMALL_SOURCES)
+    if c64:
+        # FP32 work is cheap here: the algorithmic bytes bind (HBM roofline, measured copy bandwidth)
+        peaks, src = load_peaks()
+        gbs = abytes / (kernel_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(gbs, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": "vbatched_solve_kernel<cplxf>",
+                "kernel_ms": round(kernel_ms, 5), "kernel_gflops": round(achieved, 2),
+                "peak_source": f"HBM copy bandwidth, {src}"}
+    else:
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
+                "kernel": "vbatched_solve_kernel<cplx>", "kernel_ms": round(kernel_ms, 5),
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "hbm_frac": round(abytes / (kernel_ms * 1e-3) / 1e9 / load_peaks()[0]["hbm_gbs"], 4)}
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": "batched_small_c128: 8192 complex128 solves per GPU, m,n ~ U{8..64}, "
-                               "alpha=(1.5,-0.5), non-unit, one varlen batched call per step",
+        "scaling": "weak", "vs_baseline": None, "dtype": name, "data": "synthetic",
+        "config": {"workload": f"batched_small_{name}: 8192 {'complex64' if c64 else 'complex128'} solves per "
+                               "GPU, m,n ~ U{8..64}, alpha=(1.5,-0.5), non-unit, one varlen batched call per step",
                    "batch_per_gpu": batch, "seed": args.seed, "global_batch": batch * dist.world,
                    "l2": f"inputs larger than L2 ({abytes / 1e6:.0f} MB algorithmic per step)",
                    "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
-                     "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
-                     "kernel": "vbatched_solve_kernel<cplx>", "kernel_ms": round(kernel_ms, 5),
-                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
-                     "hbm_frac": round(abytes / (kernel_ms * 1e-3) / 1e9 / load_peaks()[0]["hbm_gbs"], 4)},
+        "roofline": roof,
         "e2e": {"value": round(e2e_value, 3), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(hostA.nbytes + hostB.nbytes), "d2h_bytes_per_step": int(hostB.nbytes)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        reps, el, cores = cpu_baseline_batched(As, Bs, alpha, args.cpu_seconds)
+        wide = (lambda L: [np.asfortranarray(x.astype(np.complex128)) for x in L]) if c64 else (lambda L: L)
+        reps, el, cores = cpu_baseline_batched(wide(As), wide(Bs), alpha, args.cpu_seconds)
         out["cpu_baseline"] = {"value": round(flops * reps / el / 1e9, 4), "unit": "GFLOP/s", "cores": cores,
                                "kind": "oracle",
                                "sample": f"the full 8192-instance batch, {reps} pass(es) in {el:.2f} s"}
     return out
 
 
-LARGE_SOURCES = ["paper_2608_25469_gb300/csrc/blocked.cu", "paper_2608_25469_gb300/csrc/tma.cuh",
-                 "paper_2608_25469_gb300/csrc/common.cuh"]
-EMU_SOURCES = ["paper_2608_25469_gb300/csrc/mixed.cu", "paper_2608_25469_gb300/csrc/tma.cuh",
-               "paper_2608_25469_gb300/csrc/common.cuh"]
+# the files that hold each profiled kernel (a summary's traffic is used only while they are unchanged)
+LARGE_SOURCES = ["paper_2608_25469_gb300/csrc/blocked.cu", "paper_2608_25469_gb300/csrc/tma.cuh"]
+EMU_SOURCES = ["paper_2608_25469_gb300/csrc/tc_gemm.cuh", "paper_2608_25469_gb300/csrc/tma.cuh"]
 
 
 def run_large(args, dist, device, code, m):
@@ -746,6 +764,8 @@ def main(argv=None):
     from paper_2608_25469_gb300 import hsma as H
     if args.workload == "batched_c128":
         out = run_batched(args, dist, device)
+    elif args.workload == "batched_c64":
+        out = run_batched(args, dist, device, c64=True)
     elif args.workload == "large_fp64":
         out = run_large(args, dist, device, H.R64, args.m or 16384)
     elif args.workload == "large_c128":

@@ -61,8 +61,13 @@ typedef enum {
   HSMA_C128 = 1,     /* double complex                                        */
   HSMA_R32_BF16 = 2, /* float result; trailing updates in BF16 on tensor cores
                         with FP32 accumulation                                */
-  HSMA_R64_IR = 3    /* double result from FP32-result solves plus FP64
+  HSMA_R64_IR = 3,   /* double result from FP32-result solves plus FP64
                         iterative refinement                                  */
+  HSMA_R32 = 4,      /* float: m <= 64 in FP32 on the CUDA cores; larger m as
+                        HSMA_R32_BF16 (FP32 result)                           */
+  HSMA_C64 = 5       /* float complex: m <= 64 in FP32 on the CUDA cores;
+                        larger m solved in complex FP64 (emulated products)
+                        and rounded back                                      */
 } hsma_dtype_t;
 
 typedef enum { HSMA_NON_UNIT = 0, HSMA_UNIT = 1 } hsma_diag_t;
@@ -158,7 +163,8 @@ HSMA_API hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t
  * TRSM is the paper's future work, Section 6; each instance is the Section 2.1
  * solve done by the small kernel of Section 4.2).
  *
- * dtype  HSMA_R64 or HSMA_C128 (one dtype and one alpha for the whole batch).
+ * dtype  HSMA_R64, HSMA_C128, HSMA_R32 or HSMA_C64 (one dtype and one alpha for
+ *        the whole batch; FP32 dtypes compute in FP32).
  * batch  number of instances (>= 0).
  * d_m, d_n, d_lda, d_ldb: DEVICE arrays of `batch` int32 sizes.
  * d_A, d_B: DEVICE arrays of `batch` device pointers.
@@ -180,7 +186,7 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batc
 /*
  * The varlen batch with its matrices in HOST memory (no paper counterpart:
  * the paper's solves are device-resident).  The batch is cut into `chunks`
- * groups of consecutive instances (0 = 4); each group's host-to-device copy,
+ * groups of consecutive instances (0 = 8); each group's host-to-device copy,
  * batched solve and device-to-host copy run on one of three internal streams,
  * so copies of some groups overlap the solves of others.
  *

@@ -22,7 +22,8 @@
 
 namespace {
 
-bool valid_dtype(int d) { return d >= HSMA_R64 && d <= HSMA_R64_IR; }
+bool valid_dtype(int d) { return d >= HSMA_R64 && d <= HSMA_C64; }
+bool is_complex(int d) { return d == HSMA_C128 || d == HSMA_C64; }
 bool valid_diag(int d) { return d == HSMA_NON_UNIT || d == HSMA_UNIT; }
 
 // ---------------------------------------------------------------------------
@@ -46,8 +47,11 @@ int lookup_nb(int dtype, int64_t m, int64_t n) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const TuneEntry *tab = g_tune.empty() ? kCompiledTable : g_tune.data();
   const size_t cnt = g_tune.empty() ? sizeof(kCompiledTable) / sizeof(kCompiledTable[0]) : g_tune.size();
-  // R64_IR tunes as R32 (its solves run in FP32); fall back to R64 entries if a dtype has none
-  const int want = dtype == HSMA_R64_IR ? HSMA_R32_BF16 : dtype;
+  // R64_IR and R32 tune as R32_BF16 (their blocked solves run that path), C64 as C128;
+  // fall back to R64 entries if a dtype has none
+  const int want = (dtype == HSMA_R64_IR || dtype == HSMA_R32) ? HSMA_R32_BF16
+                   : dtype == HSMA_C64                         ? HSMA_C128
+                                                               : dtype;
   for (int pass = 0; pass < 2; ++pass) {
     const int d = pass == 0 ? want : HSMA_R64;
     double best = 1e300;
@@ -72,12 +76,12 @@ hsma_status_t make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts
   int path = opts ? opts->path : HSMA_PATH_AUTO;
   if (path < HSMA_PATH_AUTO || path > HSMA_PATH_BLOCKED) return HSMA_ERR_INVALID_ARG;
   if (opts && (opts->fp64_products < 0 || opts->fp64_products > 1)) return HSMA_ERR_INVALID_ARG;
-  const bool small_ok = m <= 64 && (dtype == HSMA_R64 || dtype == HSMA_C128);
+  const bool small_ok = m <= 64 && hsma_small_dtype(dtype);
   if (path == HSMA_PATH_AUTO) path = small_ok ? HSMA_PATH_SMALL : HSMA_PATH_BLOCKED;
   if (path == HSMA_PATH_SMALL && !small_ok) return HSMA_ERR_UNSUPPORTED;
   p->path = path;
   if (path == HSMA_PATH_SMALL) {
-    const bool cplx_ = dtype == HSMA_C128;
+    const bool cplx_ = is_complex(dtype);
     int g = opts ? opts->groups : 0;
     if (g != 0) {
       if (g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return HSMA_ERR_INVALID_ARG;
@@ -98,14 +102,15 @@ hsma_status_t make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts
 size_t elem_bytes(int dtype) {
   switch (dtype) {
     case HSMA_C128: return 16;
-    case HSMA_R32_BF16: return 4;
+    case HSMA_R32_BF16:
+    case HSMA_R32: return 4;
     default: return 8;
   }
 }
 
 bool alpha_is_zero(int dtype, const void *alpha) {
   const double *a = static_cast<const double *>(alpha);
-  if (dtype == HSMA_C128) return a[0] == 0.0 && a[1] == 0.0;
+  if (is_complex(dtype)) return a[0] == 0.0 && a[1] == 0.0;
   return a[0] == 0.0;
 }
 
@@ -135,10 +140,10 @@ hsma_status_t hsma_plan(int dtype, int64_t m, int64_t n, hsma_plan_t *out) {
 }
 
 double hsma_small_cost(int dtype, int64_t m, int64_t n, int32_t groups) {
-  if (m < 1 || m > 64 || n < 0 || (dtype != HSMA_R64 && dtype != HSMA_C128)) return -1.0;
+  if (m < 1 || m > 64 || n < 0 || !hsma_small_dtype(dtype)) return -1.0;
   if (groups != 1 && groups != 2 && groups != 4 && groups != 8 && groups != 16 && groups != 32) return -1.0;
-  if (!hsma_small_g_ok(groups, (int)m, dtype == HSMA_C128)) return -1.0;
-  return hsma_small_total_instr((int)m, (int)n, groups, dtype == HSMA_C128);
+  if (!hsma_small_g_ok(groups, (int)m, is_complex(dtype))) return -1.0;
+  return hsma_small_total_instr((int)m, (int)n, groups, is_complex(dtype));
 }
 
 hsma_status_t hsma_tuning_load(const char *path) {
@@ -208,6 +213,15 @@ hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const
     case HSMA_R64_IR:
       return hsma_mixed_ir(plan.nb, opts, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb, m,
                            n, al[0], unit, st, info);
+    case HSMA_R32:
+      if (plan.path == HSMA_PATH_SMALL)
+        return hsma_small_single(dtype, plan.groups, A, lda, B, ldb, (int)m, (int)n, al, unit, st);
+      return hsma_mixed_r32(plan.nb, opts ? opts->bf16_terms : 0, static_cast<const float *>(A), lda,
+                            static_cast<float *>(B), ldb, m, n, al[0], unit, st);
+    case HSMA_C64:
+      if (plan.path == HSMA_PATH_SMALL)
+        return hsma_small_single(dtype, plan.groups, A, lda, B, ldb, (int)m, (int)n, al, unit, st);
+      return hsma_c64_blocked(opts && opts->nb ? opts->nb : kHsmaEmulatedNb, A, lda, B, ldb, m, n, al, unit, st);
     default:
       return HSMA_ERR_INVALID_ARG;
   }
@@ -222,7 +236,7 @@ hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const 
                                       const void *alpha, const void *const *d_A, const int32_t *d_lda,
                                       void *const *d_B, const int32_t *d_ldb, int32_t max_m, int32_t max_n,
                                       uint32_t *d_status, void *stream) {
-  if (dtype != HSMA_R64 && dtype != HSMA_C128) {
+  if (!hsma_small_dtype(dtype)) {
     return valid_dtype(dtype) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
   }
   if (!valid_diag(diag) || batch < 0 || max_m < 0 || max_n < 0) return HSMA_ERR_INVALID_ARG;

@@ -19,10 +19,15 @@ static inline hsma_status_t hsma_from_cuda(cudaError_t e) {
 }
 
 // ---------------------------------------------------------------------------
-// Element types.  `cplx` is the interleaved (re, im) layout of complex128.
+// Element types.  `cplx` is the interleaved (re, im) layout of complex128,
+// `cplxf` that of complex64.
 // ---------------------------------------------------------------------------
 struct cplx {
   double re, im;
+};
+
+struct __align__(8) cplxf {
+  float re, im;
 };
 
 template <class T>
@@ -30,6 +35,7 @@ struct Elem;
 
 template <>
 struct Elem<double> {
+  static constexpr bool kComplex = false;
   static constexpr int kFlopsPerFma = 1;  // DFMA instructions per multiply-add
   __device__ __forceinline__ static double zero() { return 0.0; }
   __device__ __forceinline__ static double one() { return 1.0; }
@@ -45,6 +51,7 @@ struct Elem<double> {
 
 template <>
 struct Elem<float> {
+  static constexpr bool kComplex = false;
   static constexpr int kFlopsPerFma = 1;
   __device__ __forceinline__ static float zero() { return 0.0f; }
   __device__ __forceinline__ static float one() { return 1.0f; }
@@ -59,6 +66,7 @@ struct Elem<float> {
 
 template <>
 struct Elem<cplx> {
+  static constexpr bool kComplex = true;
   static constexpr int kFlopsPerFma = 4;
   __device__ __forceinline__ static cplx zero() { return cplx{0.0, 0.0}; }
   __device__ __forceinline__ static cplx one() { return cplx{1.0, 0.0}; }
@@ -109,6 +117,64 @@ struct Elem<cplx> {
   }
   __device__ __forceinline__ static bool is_zero(cplx a) { return a.re == 0.0 && a.im == 0.0; }
 };
+
+template <>
+struct Elem<cplxf> {
+  static constexpr bool kComplex = true;
+  static constexpr int kFlopsPerFma = 4;
+  __device__ __forceinline__ static cplxf zero() { return cplxf{0.0f, 0.0f}; }
+  __device__ __forceinline__ static cplxf one() { return cplxf{1.0f, 0.0f}; }
+  __device__ __forceinline__ static cplxf mul(cplxf a, cplxf b) {
+    cplxf r;
+    r.re = fmaf(a.re, b.re, -(a.im * b.im));
+    r.im = fmaf(a.re, b.im, a.im * b.re);
+    return r;
+  }
+  __device__ __forceinline__ static cplxf fms(cplxf a, cplxf x, cplxf s) {
+    s.re = fmaf(-a.re, x.re, s.re);
+    s.re = fmaf(a.im, x.im, s.re);
+    s.im = fmaf(-a.re, x.im, s.im);
+    s.im = fmaf(-a.im, x.re, s.im);
+    return s;
+  }
+  // Smith's division with numerator 1
+  __device__ __forceinline__ static cplxf recip(cplxf a) {
+    cplxf r;
+    if (fabsf(a.re) >= fabsf(a.im)) {
+      const float t = a.im / a.re, d = a.re + a.im * t;
+      r.re = 1.0f / d;
+      r.im = -t / d;
+    } else {
+      const float t = a.re / a.im, d = a.re * t + a.im;
+      r.re = t / d;
+      r.im = -1.0f / d;
+    }
+    return r;
+  }
+  __device__ __forceinline__ static cplxf shfl(cplxf v, int src) {
+    return cplxf{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+  }
+  __device__ __forceinline__ static cplxf ld(const cplxf *p) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return cplxf{v.x, v.y};
+  }
+  __device__ __forceinline__ static void st(cplxf *p, cplxf v) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v.re, v.im);
+  }
+  __device__ __forceinline__ static bool is_zero(cplxf a) { return a.re == 0.0f && a.im == 0.0f; }
+};
+
+// alpha (host double, or double[2] for complex) in the element type
+template <class T>
+inline T hsma_alpha_as(const double *a);
+template <>
+inline double hsma_alpha_as<double>(const double *a) { return a[0]; }
+template <>
+inline float hsma_alpha_as<float>(const double *a) { return (float)a[0]; }
+template <>
+inline cplx hsma_alpha_as<cplx>(const double *a) { return cplx{a[0], a[1]}; }
+template <>
+inline cplxf hsma_alpha_as<cplxf>(const double *a) { return cplxf{(float)a[0], (float)a[1]}; }
 
 // ---------------------------------------------------------------------------
 // Small-path cost model (Section 4.2 kernel as laid out on this GPU).

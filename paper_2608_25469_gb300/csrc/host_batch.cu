@@ -60,7 +60,7 @@ extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int di
                                                                 const int64_t *h_offA, const void *hB,
                                                                 const int64_t *h_offB, void *hX, int32_t chunks,
                                                                 void *stream) {
-  if (dtype != HSMA_R64 && dtype != HSMA_C128) {
+  if (!hsma_small_dtype(dtype)) {
     return (dtype == HSMA_R32_BF16 || dtype == HSMA_R64_IR) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
   }
   if ((diag != HSMA_NON_UNIT && diag != HSMA_UNIT) || batch < 0 || chunks < 0) return HSMA_ERR_INVALID_ARG;
@@ -75,8 +75,8 @@ extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int di
                   h_offB[i] < h_offB[i - 1] + (int64_t)h_m[i - 1] * h_n[i - 1]))
       return HSMA_ERR_INVALID_ARG;
   }
-  const int es = dtype == HSMA_C128 ? 16 : 8;
-  const int nch = std::min<int32_t>(batch, chunks > 0 ? chunks : 4);
+  const int es = hsma_small_esize(dtype);
+  const int nch = std::min<int32_t>(batch, chunks > 0 ? chunks : 8);
   const int32_t per = (batch + nch - 1) / nch;
   // element extents of each chunk in the packed buffers
   auto extA = [&](int32_t b, int32_t e) { return h_offA[e - 1] + (int64_t)h_m[e - 1] * h_m[e - 1] - h_offA[b]; };

@@ -23,3 +23,8 @@ size_t hsma_blocked_emulated_ws_bytes(int dtype, int nb, int64_t m, int64_t n);
 
 // N_B of the emulated blocked path when the caller gives none.
 constexpr int kHsmaEmulatedNb = 512;
+
+// complex64 blocked solve (m > 64): widened to complex128, solved with emulated
+// FP64 products, rounded back into B.
+hsma_status_t hsma_c64_blocked(int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m, int64_t n,
+                               const double *alpha, int unit, cudaStream_t st);

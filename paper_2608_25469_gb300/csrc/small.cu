@@ -164,7 +164,7 @@ __device__ __forceinline__ void zero_tiles(T *B, int64_t ldb, int m, int n) {
 // Dispatch over the row-group variants compiled into the batched kernel.
 template <class T>
 struct Variants {
-  static constexpr bool kCplx = sizeof(T) == sizeof(cplx);
+  static constexpr bool kCplx = Elem<T>::kComplex;
   __device__ __forceinline__ static void run(int g, const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n,
                                              int tile0, int step) {
     if constexpr ((kBatchedGMask & 1u) != 0) {
@@ -198,7 +198,7 @@ struct Variants {
 // complex G = 1 one (MMAX = 32); stage with the variant's MMAX.
 template <class T>
 __device__ __forceinline__ int variant_mmax(int g) {
-  return (sizeof(T) == sizeof(cplx) && g == 1) ? 32 : 64;
+  return (Elem<T>::kComplex && g == 1) ? 32 : 64;
 }
 
 template <class T, int W>
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
                                                                  uint32_t *status) {
   __shared__ int hist[kBuckets];
   __shared__ int offs[kBuckets];
-  const bool cplx_ = sizeof(T) == sizeof(cplx);
+  const bool cplx_ = Elem<T>::kComplex;
   for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) hist[k] = 0;
   __syncthreads();
   uint32_t err = 0;
@@ -391,18 +391,13 @@ static hsma_status_t small_single_impl(int g, const void *A, int64_t lda, void *
   int dev = 0, nsm = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const bool cplx_ = sizeof(T) == sizeof(cplx);
+  const bool cplx_ = Elem<T>::kComplex;
   if (g == 0) g = hsma_small_pick_g_single(m, n, cplx_, nsm);
   if (!hsma_small_g_ok(g, m, cplx_)) return HSMA_ERR_INVALID_ARG;
-  T al;
-  if constexpr (sizeof(T) == sizeof(cplx)) {
-    al = T{alpha[0], alpha[1]};
-  } else {
-    al = alpha[0];
-  }
+  const T al = hsma_alpha_as<T>(alpha);
   const T *a = static_cast<const T *>(A);
   T *b = static_cast<T *>(B);
-  if constexpr (sizeof(T) == sizeof(cplx)) {
+  if constexpr (Elem<T>::kComplex) {
     switch (g) {
       case 1: return launch_single_g<T, 1, 32>(a, lda, b, ldb, m, n, al, unit, nsm, st);
       case 2: return launch_single_g<T, 2, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
@@ -427,8 +422,12 @@ static hsma_status_t small_single_impl(int g, const void *A, int64_t lda, void *
 
 hsma_status_t hsma_small_single(int dtype, int g, const void *A, int64_t lda, void *B, int64_t ldb, int m, int n,
                                 const double *alpha, int unit, cudaStream_t st) {
-  if (dtype == HSMA_C128) return small_single_impl<cplx>(g, A, lda, B, ldb, m, n, alpha, unit, st);
-  return small_single_impl<double>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+  switch (dtype) {
+    case HSMA_C128: return small_single_impl<cplx>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+    case HSMA_R32: return small_single_impl<float>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+    case HSMA_C64: return small_single_impl<cplxf>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+    default: return small_single_impl<double>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+  }
 }
 
 template <class T>
@@ -444,12 +443,7 @@ static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32
     if (s != HSMA_OK) return s;
     attr_done.set();
   }
-  T al;
-  if constexpr (sizeof(T) == sizeof(cplx)) {
-    al = T{alpha[0], alpha[1]};
-  } else {
-    al = alpha[0];
-  }
+  const T al = hsma_alpha_as<T>(alpha);
   {
     HsmaTraceScope ts("vbatched_schedule", st);
     vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status);
@@ -472,9 +466,12 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
                                   void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
                                   int32_t *scratch, cudaStream_t st) {
-  if (dtype == HSMA_C128)
-    return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
-  return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+  switch (dtype) {
+    case HSMA_C128: return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+    case HSMA_R32: return vbatched_impl<float>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+    case HSMA_C64: return vbatched_impl<cplxf>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+    default: return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -519,7 +516,7 @@ extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_noalloc(int dtype, int
                                                                   const int32_t *d_ldb, int32_t max_m,
                                                                   int32_t max_n, uint32_t *d_status,
                                                                   void *stream) {
-  if (dtype != HSMA_R64 && dtype != HSMA_C128) {
+  if (!hsma_small_dtype(dtype)) {
     return (dtype == HSMA_R32_BF16 || dtype == HSMA_R64_IR) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
   }
   if ((diag != HSMA_NON_UNIT && diag != HSMA_UNIT) || batch < 0 || max_m < 0 || max_n < 0)

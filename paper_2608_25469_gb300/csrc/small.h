@@ -19,3 +19,11 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
                                   void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
                                   int32_t *scratch, cudaStream_t st);
+
+// dtypes the small kernels and the varlen batch handle
+inline bool hsma_small_dtype(int dtype) {
+  return dtype == HSMA_R64 || dtype == HSMA_C128 || dtype == HSMA_R32 || dtype == HSMA_C64;
+}
+
+// element size in bytes of a small-path dtype
+inline int hsma_small_esize(int dtype) { return (dtype == HSMA_C128) ? 16 : (dtype == HSMA_R32 ? 4 : 8); }

@@ -19,7 +19,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libhsma.so")
 
-R64, C128, R32_BF16, R64_IR = 0, 1, 2, 3
+R64, C128, R32_BF16, R64_IR, R32, C64 = 0, 1, 2, 3, 4, 5
 NON_UNIT, UNIT = 0, 1
 PATH_AUTO, PATH_SMALL, PATH_BLOCKED = 0, 1, 2
 OK = 0

@@ -14,7 +14,8 @@ def lib():
 
 def torch_dtype(np_dtype):
     import torch
-    return {np.float64: torch.float64, np.complex128: torch.complex128, np.float32: torch.float32}[np.dtype(np_dtype).type]
+    return {np.float64: torch.float64, np.complex128: torch.complex128, np.float32: torch.float32,
+            np.complex64: torch.complex64}[np.dtype(np_dtype).type]
 
 
 class Batch:

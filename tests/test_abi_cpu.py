@@ -137,3 +137,15 @@ def test_vbatched_host_argument_checks(H):
     overlap = np.array([0, 15], dtype=np.int64)                                        # A_0 holds 16 elements
     assert f(0, 0, 2, m, n, 1.0, p, overlap, p, offB, p, check=False) == 1
     assert f(0, 0, 2, m, n, 1.0, p, offA, p, offB, p, chunks=-1, check=False) == 1
+
+
+def test_fp32_dtypes_plan_and_cost(H):
+    """HSMA_R32 and HSMA_C64 use the small direct solve up to m = 64, the blocked path above."""
+    for code in (H.R32, H.C64):
+        assert H.hsma_plan(code, 64, 100).path == H.PATH_SMALL
+        assert H.hsma_plan(code, 65, 1).path == H.PATH_BLOCKED
+        assert H.hsma_small_cost(code, 40, 40, 2) > 0
+    # the complex dtypes share the complex cost (four FMAs per multiply-add)
+    assert H.hsma_small_cost(H.C64, 40, 40, 2) == H.hsma_small_cost(H.C128, 40, 40, 2)
+    assert H.hsma_small_cost(H.R32, 40, 40, 2) == H.hsma_small_cost(H.R64, 40, 40, 2)
+    assert H.hsma_trsm_llnn(6, 0, 4, 4, 1.0, 1, 4, 1, 4, check=False) == 1  # unknown dtype

@@ -87,6 +87,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_backward_error_d.restype = dbl
     lib.oracle_backward_error_z.argtypes = [c_int, i64, i64, ptr, ptr, i64, ptr, i64, ptr, i64]
     lib.oracle_backward_error_z.restype = dbl
+    lib.oracle_trsm_general.argtypes = [c_int, c_int, c_int, c_int, c_int, i64, i64, ptr, ptr, i64, ptr, i64]
+    lib.oracle_trsm_general.restype = c_int
     lib.oracle_num_threads.restype = c_int
     lib.oracle_set_num_threads.argtypes = [c_int]
     return lib
@@ -134,6 +136,28 @@ def solve(A: np.ndarray, B: np.ndarray, alpha, unit: bool = False, m: int | None
     else:
         al = _alpha_arr(alpha)
         rc = L.oracle_trsm_llnn_z(int(unit), m, n, _ptr(al), _ptr(A), A.shape[0], _ptr(X), X.shape[0])
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return X
+
+
+def solve_general(A: np.ndarray, B: np.ndarray, alpha, side: int = 0, uplo: int = 0, trans: int = 0,
+                  unit: bool = False, _lib=None) -> np.ndarray:
+    """The BLAS triangular-solve variants by definition (the paper's case is side = uplo =
+    trans = 0): side 0 solves op(A) X = alpha B (A is m x m), side 1 solves X op(A) = alpha B
+    (A is n x n); uplo 0/1 picks the lower/upper triangle of A; trans 0/1/2 is op(A) = A, A^T,
+    A^H.  Returns a copy of B with the solution in rows [0, m)."""
+    L = _lib or lib()
+    _check_fortran(A, "A")
+    _check_fortran(B, "B")
+    X = np.array(B, order="F", copy=True)
+    m, n = (X.shape[0], X.shape[1])
+    cx = 1 if np.iscomplexobj(X) else 0
+    if np.iscomplexobj(A) != bool(cx) or X.dtype not in (np.float64, np.complex128):
+        raise ValueError("A and B must both be float64 or both complex128")
+    al = _alpha_arr(alpha)
+    rc = L.oracle_trsm_general(cx, side, uplo, trans, int(unit), m, n, _ptr(al), _ptr(A), A.shape[0], _ptr(X),
+                               X.shape[0])
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return X

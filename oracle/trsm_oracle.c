@@ -135,6 +135,96 @@ int oracle_trsm_llnn_z(int unit, int64_t m, int64_t n, const double *alpha,
   return 0;
 }
 
+/* ---------------------------------------------------------------------------
+ * The other BLAS triangular-solve variants, by their definition (the paper
+ * studies the left / lower / no-transpose case only; these extend it):
+ *
+ *   side 0 (left):   op(A) X = alpha B,  A is m x m
+ *   side 1 (right):  X op(A) = alpha B,  A is n x n
+ *   uplo 0 / 1:      the lower / upper triangle of A is referenced
+ *   trans 0 / 1 / 2: op(A) = A, A^T, or A^H (conjugate transpose)
+ *   unit:            the diagonal of A is taken as 1 and never read
+ *
+ * T(p, q) denotes op(A)'s entry.  Left: each column x of X solves T x = alpha b
+ * by forward substitution when T is lower triangular and backward when it is
+ * upper, x_i = (alpha b_i - sum_k T(i,k) x_k) / T(i,i) over the already solved
+ * k, summed in ascending k.  Right: each row y of X solves y T = alpha b, i.e.
+ * y_k = (alpha b_k - sum_l y_l T(l,k)) / T(k,k) over the solved l (ascending),
+ * forward in k when T is upper, backward when lower.  Real data runs through
+ * the same complex operations with zero imaginary parts, which round exactly
+ * as the real ones.
+ * ------------------------------------------------------------------------- */
+static zv g_get(int cx, const double *A, int64_t lda, int64_t i, int64_t k) {
+  zv v;
+  if (cx) {
+    v.re = A[2 * (i + k * lda)];
+    v.im = A[2 * (i + k * lda) + 1];
+  } else {
+    v.re = A[i + k * lda];
+    v.im = 0.0;
+  }
+  return v;
+}
+
+static zv g_op(int cx, int trans, const double *A, int64_t lda, int64_t p, int64_t q) {
+  if (trans == 0) return g_get(cx, A, lda, p, q);
+  zv v = g_get(cx, A, lda, q, p);
+  if (trans == 2) v.im = -v.im;
+  return v;
+}
+
+static void g_put(int cx, double *B, int64_t ldb, int64_t i, int64_t j, zv v) {
+  if (cx) {
+    B[2 * (i + j * ldb)] = v.re;
+    B[2 * (i + j * ldb) + 1] = v.im;
+  } else {
+    B[i + j * ldb] = v.re;
+  }
+}
+
+int oracle_trsm_general(int cx, int side, int uplo, int trans, int unit, int64_t m, int64_t n,
+                        const double *alpha, const double *A, int64_t lda, double *B, int64_t ldb) {
+  const int64_t na = side == 0 ? m : n; /* order of A */
+  if (m < 0 || n < 0 || side < 0 || side > 1 || uplo < 0 || uplo > 1 || trans < 0 || trans > 2) return 1;
+  if (lda < (na > 1 ? na : 1) || ldb < (m > 1 ? m : 1)) return 1;
+  if (!cx && trans == 2) trans = 1; /* A^H = A^T for real A */
+  if (m == 0 || n == 0) return 0;
+  const zv al = {alpha[0], cx ? alpha[1] : 0.0};
+  const int t_lower = (uplo == 0) != (trans != 0);
+  if (al.re == 0.0 && al.im == 0.0) {
+    const zv z = {0.0, 0.0};
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t i = 0; i < m; i++) g_put(cx, B, ldb, i, j, z);
+    return 0;
+  }
+  if (side == 0) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < n; j++) {
+      for (int64_t t = 0; t < m; t++) {
+        const int64_t i = t_lower ? t : m - 1 - t;
+        zv s = z_mul(al, g_get(cx, B, ldb, i, j));
+        const int64_t k0 = t_lower ? 0 : i + 1, k1 = t_lower ? i : m;
+        for (int64_t k = k0; k < k1; k++) s = z_sub(s, z_mul(g_op(cx, trans, A, lda, i, k), g_get(cx, B, ldb, k, j)));
+        if (!unit) s = z_div(s, g_op(cx, trans, A, lda, i, i));
+        g_put(cx, B, ldb, i, j, s);
+      }
+    }
+  } else {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < m; i++) {
+      for (int64_t t = 0; t < n; t++) {
+        const int64_t k = t_lower ? n - 1 - t : t;
+        zv s = z_mul(al, g_get(cx, B, ldb, i, k));
+        const int64_t l0 = t_lower ? k + 1 : 0, l1 = t_lower ? n : k;
+        for (int64_t l = l0; l < l1; l++) s = z_sub(s, z_mul(g_get(cx, B, ldb, i, l), g_op(cx, trans, A, lda, l, k)));
+        if (!unit) s = z_div(s, g_op(cx, trans, A, lda, k, k));
+        g_put(cx, B, ldb, i, k, s);
+      }
+    }
+  }
+  return 0;
+}
+
 /* Only the listed columns of B (column indices cols[0..ncols-1]) are solved;
  * the others are left untouched.  Columns are independent, so each listed
  * column equals the corresponding column of a full solve. */

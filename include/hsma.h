@@ -71,6 +71,9 @@ typedef enum {
 } hsma_dtype_t;
 
 typedef enum { HSMA_NON_UNIT = 0, HSMA_UNIT = 1 } hsma_diag_t;
+typedef enum { HSMA_LEFT = 0, HSMA_RIGHT = 1 } hsma_side_t;
+typedef enum { HSMA_LOWER = 0, HSMA_UPPER = 1 } hsma_uplo_t;
+typedef enum { HSMA_NO_TRANS = 0, HSMA_TRANS = 1, HSMA_CONJ_TRANS = 2 } hsma_trans_t;
 
 typedef enum {
   HSMA_OK = 0,
@@ -157,6 +160,24 @@ HSMA_API hsma_status_t hsma_trsm_llnn(int dtype, int diag, int64_t m, int64_t n,
 HSMA_API hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const void *alpha,
                                 const void *A, int64_t lda, void *B, int64_t ldb, void *stream,
                                 const hsma_opts_t *opts, hsma_info_t *info);
+
+/*
+ * The other BLAS triangular-solve variants (no paper counterpart: the paper
+ * studies the left / lower / no-transpose case):
+ *   side HSMA_LEFT:  op(A) X = alpha B, A is m x m (lda >= max(1, m));
+ *   side HSMA_RIGHT: X op(A) = alpha B, A is n x n (lda >= max(1, n));
+ *   uplo: the triangle of A that is referenced; trans: op(A) = A, A^T or A^H
+ *   (A^H = A^T for real dtypes); diag as for hsma_trsm_llnn.
+ * B is m x n (ldb >= max(1, m)), overwritten with X.  Every dtype.  The left /
+ * lower / no-transpose case is hsma_trsm_llnn_ex itself; the others gather
+ * the triangle into lower form (rows reversed when op(A) would be upper) and
+ * B (transposed for the right side) into workspace of (order of A)^2 + m n
+ * elements, solve, and scatter X back.  opts and info as for
+ * hsma_trsm_llnn_ex (they apply to that inner solve).
+ */
+HSMA_API hsma_status_t hsma_trsm(int dtype, int side, int uplo, int trans, int diag, int64_t m, int64_t n,
+                                 const void *alpha, const void *A, int64_t lda, void *B, int64_t ldb, void *stream,
+                                 const hsma_opts_t *opts, hsma_info_t *info);
 
 /*
  * Varlen batch of independent small solves in one persistent launch (batched

@@ -21,6 +21,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libhsma.so")
 
 R64, C128, R32_BF16, R64_IR, R32, C64 = 0, 1, 2, 3, 4, 5
 NON_UNIT, UNIT = 0, 1
+LEFT, RIGHT = 0, 1
+LOWER, UPPER = 0, 1
+NO_TRANS, TRANS, CONJ_TRANS = 0, 1, 2
 PATH_AUTO, PATH_SMALL, PATH_BLOCKED = 0, 1, 2
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_BUSY = range(1, 8)
@@ -33,7 +36,7 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
-           "hsma_trsm_llnn_vbatched_host",
+           "hsma_trsm_llnn_vbatched_host", "hsma_trsm",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -99,6 +102,8 @@ def _load():
     lib.hsma_trsm_llnn_vbatched_noalloc.restype = c_int
     lib.hsma_trsm_llnn_vbatched_host.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     lib.hsma_trsm_llnn_vbatched_host.restype = c_int
+    lib.hsma_trsm.argtypes = [c_int, c_int, c_int, c_int, c_int, i64, i64, vp, vp, i64, vp, i64, vp, vp, vp]
+    lib.hsma_trsm.restype = c_int
     lib.hsma_plan.argtypes = [c_int, i64, i64, ctypes.POINTER(Plan)]
     lib.hsma_plan.restype = c_int
     lib.hsma_small_cost.argtypes = [c_int, i64, i64, i32]
@@ -175,6 +180,17 @@ def hsma_trsm_llnn_ex(dtype, diag, m, n, alpha, A, lda, B, ldb, stream=0, opts: 
                                ctypes.byref(info) if info is not None else None)
     if check:
         _check(s, "hsma_trsm_llnn_ex")
+    return s
+
+
+def hsma_trsm(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream=0, opts: Opts | None = None,
+              info: Info | None = None, check=True) -> int:
+    """BLAS triangular-solve variants: side LEFT/RIGHT, uplo LOWER/UPPER, trans NO_TRANS/TRANS/CONJ_TRANS."""
+    s = _lib.hsma_trsm(dtype, side, uplo, trans, diag, m, n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), A,
+                       lda, B, ldb, stream, ctypes.byref(opts) if opts is not None else None,
+                       ctypes.byref(info) if info is not None else None)
+    if check:
+        _check(s, "hsma_trsm")
     return s
 
 

@@ -149,3 +149,17 @@ def test_fp32_dtypes_plan_and_cost(H):
     assert H.hsma_small_cost(H.C64, 40, 40, 2) == H.hsma_small_cost(H.C128, 40, 40, 2)
     assert H.hsma_small_cost(H.R32, 40, 40, 2) == H.hsma_small_cost(H.R64, 40, 40, 2)
     assert H.hsma_trsm_llnn(6, 0, 4, 4, 1.0, 1, 4, 1, 4, check=False) == 1  # unknown dtype
+
+
+def test_variant_argument_checks(H):
+    """hsma_trsm validates side / uplo / trans / diag and the leading dimension of A by side."""
+    f = H.hsma_trsm
+    assert f(0, 2, 0, 0, 0, 4, 4, 1.0, 1, 4, 1, 4, check=False) == 1   # side
+    assert f(0, 0, 2, 0, 0, 4, 4, 1.0, 1, 4, 1, 4, check=False) == 1   # uplo
+    assert f(0, 0, 0, 3, 0, 4, 4, 1.0, 1, 4, 1, 4, check=False) == 1   # trans
+    assert f(0, 0, 0, 1, 2, 4, 4, 1.0, 1, 4, 1, 4, check=False) == 1   # diag
+    assert f(9, 0, 0, 1, 0, 4, 4, 1.0, 1, 4, 1, 4, check=False) == 1   # dtype
+    assert f(0, 1, 0, 0, 0, 4, 9, 1.0, 1, 8, 1, 4, check=False) == 1   # right side: lda < n
+    assert f(0, 0, 1, 0, 0, 4, 9, 1.0, 1, 3, 1, 4, check=False) == 1   # left side: lda < m
+    assert f(0, 1, 1, 2, 0, 0, 9, 1.0, 0, 9, 0, 1, check=False) == 0   # m = 0: quick return
+    assert f(0, 1, 1, 2, 0, 4, 4, 1.0, 0, 4, 1, 4, check=False) == 1   # NULL A

@@ -462,7 +462,8 @@ def run_large(args, dist, device, code, m):
                       "fp64_equivalent_gflops": round(achieved, 1)} if emulated else
                      {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
                       "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                      "traffic": profile_traffic(f"update_gemm_{name}.txt", LARGE_SOURCES),
+                      "traffic": profile_traffic(f"update_gemm_{name}.txt", LARGE_SOURCES,
+                                                 work=upd_flops / max(upd_cnt / max(args.steps, 1), 1)),
                       "kernel": "gemm_kernel (update_gemm, DMMA m8n8k4)",
                       "peak_source": "derived FP64 (DMMA shares the FP64 budget): 2 FMA/clk/SM x 152 x 2070 MHz"}),
         "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phases.items()},

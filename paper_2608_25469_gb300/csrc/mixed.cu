@@ -393,7 +393,9 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
       sa.K = Kd;
       sa.tri = 1;
       sa.skip = skip;
-      s = tc_gemm<TC_F32>(P.dslices + (size_t)r * 3 * nb * Kd, 3, X3, 3, sa, "solve_bf16", st, nb);
+      SliceLayout dl;
+      dl.rows = nb;  // the inverse's slices are stored nb rows high
+      s = tc_gemm<TC_F32>(P.dslices + (size_t)r * 3 * nb * Kd, 3, X3, 3, sa, "solve_bf16", st, dl);
     } else {
       s = sgemm_scale(P.Dinv + (size_t)r * nb * nb, nb, W, nb, B + r0, ldb, sr, (int)n, sr, r == 0 ? alpha : 1.0f, 1,
                       skip, st);
@@ -867,7 +869,13 @@ hsma_status_t oz_product(const OzOperand &L, const OzOperand &X, double *C, int6
   return tc_gemm<TC_OZ>(L.slices, kOzS, X.slices, kOzS, a, phase, st);
 }
 
-// R -= L X in emulated FP64 (R holds alpha B on entry); skip: device flag
+// R -= L X in emulated FP64 (R holds alpha B on entry); skip: device flag.
+// K runs in chunks of kOzResidualChunk columns of L: chunk c touches only rows
+// below its start (L is lower triangular) and each launch re-reads a chunk's
+// slices, which stay in L2, for all its slice pairs; one launch over the whole
+// K would stream every row tile's full slices from memory once per pair.
+constexpr int kOzResidualChunk = 1024;
+
 hsma_status_t oz_residual(const OzOperand &L, const double *X, int64_t ldx, double *R, int64_t ldr, OzOperand &Xo,
                           const int *skip, cudaStream_t st) {
   {
@@ -875,7 +883,35 @@ hsma_status_t oz_residual(const OzOperand &L, const double *X, int64_t ldx, doub
     hsma_status_t s = oz_slice_x(X, ldx, L.rows, L.kexp, Xo, skip, st);
     if (s != HSMA_OK) return s;
   }
-  return oz_product(L, Xo, R, ldr, 1, 0, 1, skip, "residual", st);
+  const int64_t m = L.rows, Kp = L.Kp;
+  for (int64_t c0 = 0; c0 < m; c0 += kOzResidualChunk) {
+    const int kc = (int)std::min<int64_t>(kOzResidualChunk, m - c0);
+    TcArgs a{};
+    a.C64 = R + c0;
+    a.ldc = ldr;
+    a.beta0 = 1;
+    a.negate = 0;
+    a.rexp = L.exps + c0;
+    a.cexp = Xo.exps;
+    a.M = (int)(m - c0);
+    a.N = Xo.rows;
+    a.K = oz_kp(kc);
+    a.tri = 1;  // rows c0 + i need chunk columns <= i only
+    a.skip = skip;
+    oz_units(a.K, a);
+    SliceLayout la, lb;  // views into the full slice stacks at row / K offset c0
+    la.rows = m - c0;
+    la.kext = Kp - c0;
+    la.ld = Kp;
+    la.sst = m * Kp;
+    lb.rows = Xo.rows;
+    lb.kext = Kp - c0;
+    lb.ld = Kp;
+    lb.sst = (int64_t)Xo.rows * Kp;
+    hsma_status_t s = tc_gemm<TC_OZ>(L.slices + c0 * Kp + c0, kOzS, Xo.slices + c0, kOzS, a, "residual", st, la, lb);
+    if (s != HSMA_OK) return s;
+  }
+  return HSMA_OK;
 }
 
 __global__ void scale_kernel(double *B, int64_t ldb, int64_t rows, int64_t n, double ar, double ai, int cplx) {

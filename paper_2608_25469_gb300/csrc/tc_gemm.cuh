@@ -359,11 +359,11 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
 // 3-D tensor map over BF16 operand slices (K contiguous, rows, slice), one
 // box = 64 K-values x box_rows rows of one slice, 128-byte swizzle.
 bool make_slice_map(CUtensorMap *map, const void *base, uint64_t K, uint64_t rows, uint64_t slices,
-                    uint32_t box_rows) {
+                    uint32_t box_rows, uint64_t ld, uint64_t sst) {
   PFN_encodeTiled enc = hsma_encode_fn();
-  if (enc == nullptr || (uintptr_t)base % 16 != 0 || (K * 2) % 16 != 0) return false;
+  if (enc == nullptr || (uintptr_t)base % 16 != 0 || (ld * 2) % 16 != 0 || (sst * 2) % 16 != 0 || K > ld) return false;
   const cuuint64_t dims[3] = {K, rows, slices};
-  const cuuint64_t strides[2] = {K * 2, K * rows * 2};
+  const cuuint64_t strides[2] = {ld * 2, sst * 2};
   const cuuint32_t box[3] = {(cuuint32_t)TC_BK, box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
@@ -380,13 +380,21 @@ int tc_cluster_pref() {
   return v;
 }
 
+// Layout of an operand's slice stack in memory: rows, K extent addressable
+// from the base (0: the product's K), row stride and slice stride in elements
+// (0: dense, ld = K extent, sst = rows * ld).  A view into a larger stack (a
+// row and K offset) keeps the stack's strides.
+struct SliceLayout {
+  int64_t rows = 0, kext = 0, ld = 0, sst = 0;
+};
+
 // Launch the persistent product.  A: sa slices of M x K (row-major), B: sb
 // slices of N x K; the unit table of a0 names the slice pairs (TC_F32: one
-// unit, one pair, filled in here).  Pairs of row tiles run as clusters of two
-// CTAs sharing the B tile.
+// unit, one pair, filled in here unless given).  Pairs of row tiles run as
+// clusters of two CTAs sharing the B tile.
 template <int MODE>
 hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, int sb, const TcArgs &a0,
-                      const char *phase, cudaStream_t st, int64_t a_rows = 0) {
+                      const char *phase, cudaStream_t st, SliceLayout la = {}, SliceLayout lb = {}) {
   if (a0.M <= 0 || a0.N <= 0) return HSMA_OK;
   if (a0.K % TC_BK != 0 || a0.K <= 0) return HSMA_ERR_INVALID_ARG;
   static DeviceFlags attr;
@@ -400,8 +408,20 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   const int tiles_m = (a0.M + TC_BM - 1) / TC_BM, tiles_n = (a0.N + TC_BN - 1) / TC_BN;
   const int cl = (tiles_m >= 2 && tc_cluster_pref() == 2) ? 2 : 1;
   CUtensorMap ma, mb;
-  if (!make_slice_map(&ma, Ap, (uint64_t)a0.K, (uint64_t)(a_rows > 0 ? a_rows : a0.M), (uint64_t)sa, TC_BM) ||
-      !make_slice_map(&mb, Bp, (uint64_t)a0.K, (uint64_t)a0.N, (uint64_t)sb, TC_BN / cl))
+  auto dense = [&](SliceLayout l, int64_t rows) {
+    if (l.rows == 0) l.rows = rows;
+    if (l.kext == 0) l.kext = a0.K;
+    if (l.ld == 0) l.ld = l.kext;
+    if (l.sst == 0) l.sst = l.rows * l.ld;
+    return l;
+  };
+  la = dense(la, a0.M);
+  lb = dense(lb, a0.N);
+  if (la.kext < a0.K || lb.kext < a0.K) return HSMA_ERR_INVALID_ARG;
+  if (!make_slice_map(&ma, Ap, (uint64_t)la.kext, (uint64_t)la.rows, (uint64_t)sa, TC_BM, (uint64_t)la.ld,
+                      (uint64_t)la.sst) ||
+      !make_slice_map(&mb, Bp, (uint64_t)lb.kext, (uint64_t)lb.rows, (uint64_t)sb, TC_BN / cl, (uint64_t)lb.ld,
+                      (uint64_t)lb.sst))
     return HSMA_ERR_CUDA;
   TcArgs a = a0;
   if (MODE == TC_F32 && a.nunits == 0) {

@@ -205,6 +205,21 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batc
                                       int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream);
 
 /*
+ * The varlen batch for the other left-side variants (no paper counterpart):
+ * op(A_i) X_i = alpha B_i with uplo / trans as for hsma_trsm; the kernel reads
+ * A_i and B_i through an index map (row reversal for upper op(A), transposed
+ * and conjugated reads), so there are no copies.  side must be HSMA_LEFT
+ * (HSMA_RIGHT returns HSMA_ERR_UNSUPPORTED; use hsma_trsm per instance).
+ * Other arguments and errors as hsma_trsm_llnn_vbatched, which is this call
+ * with HSMA_LEFT, HSMA_LOWER, HSMA_NO_TRANS.
+ */
+HSMA_API hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int diag, int32_t batch,
+                                          const int32_t *d_m, const int32_t *d_n, const void *alpha,
+                                          const void *const *d_A, const int32_t *d_lda, void *const *d_B,
+                                          const int32_t *d_ldb, int32_t max_m, int32_t max_n, uint32_t *d_status,
+                                          void *stream);
+
+/*
  * The varlen batch with its matrices in HOST memory (no paper counterpart:
  * the paper's solves are device-resident).  The batch is cut into `chunks`
  * groups of consecutive instances (0 = 8); each group's host-to-device copy,
@@ -242,9 +257,11 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int diag, int32_t
  * that array (about 256 KB) until the process exits.  Limit: batch <= 65536
  * instances; a larger batch returns HSMA_ERR_UNSUPPORTED without launching.
  * The first call on a device looks up the array's device address (one
- * cudaGetSymbolAddress per device, made with that device current); make that
- * first call before any stream capture.  The call itself allocates and frees
- * nothing.  All calls share the one array: each call resets the counters it
+ * cudaGetSymbolAddress per device, made with that device current) and, like
+ * the first varlen batch of any kind, copies a 32 KB table of per-size
+ * schedule entries into a second static array; make that first call before
+ * any stream capture (a capturing first call computes the entries in the
+ * kernel instead).  The call itself allocates and frees nothing.  All calls share the one array: each call resets the counters it
  * needs, but calls whose work overlaps on the GPU (on different streams, or
  * from different threads, without ordering between them) race on the array
  * and must be serialised by the caller.

@@ -236,9 +236,21 @@ hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const 
                                       const void *alpha, const void *const *d_A, const int32_t *d_lda,
                                       void *const *d_B, const int32_t *d_ldb, int32_t max_m, int32_t max_n,
                                       uint32_t *d_status, void *stream) {
+  return hsma_trsm_vbatched(dtype, HSMA_LEFT, HSMA_LOWER, HSMA_NO_TRANS, diag, batch, d_m, d_n, alpha, d_A, d_lda,
+                            d_B, d_ldb, max_m, max_n, d_status, stream);
+}
+
+hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int diag, int32_t batch,
+                                 const int32_t *d_m, const int32_t *d_n, const void *alpha, const void *const *d_A,
+                                 const int32_t *d_lda, void *const *d_B, const int32_t *d_ldb, int32_t max_m,
+                                 int32_t max_n, uint32_t *d_status, void *stream) {
   if (!hsma_small_dtype(dtype)) {
     return valid_dtype(dtype) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
   }
+  if ((side != HSMA_LEFT && side != HSMA_RIGHT) || (uplo != HSMA_LOWER && uplo != HSMA_UPPER) ||
+      trans < HSMA_NO_TRANS || trans > HSMA_CONJ_TRANS)
+    return HSMA_ERR_INVALID_ARG;
+  if (side == HSMA_RIGHT) return HSMA_ERR_UNSUPPORTED;
   if (!valid_diag(diag) || batch < 0 || max_m < 0 || max_n < 0) return HSMA_ERR_INVALID_ARG;
   if (max_m > 64) return HSMA_ERR_UNSUPPORTED;
   if (batch > (1 << 24) - 1) return HSMA_ERR_UNSUPPORTED;
@@ -251,7 +263,7 @@ hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const 
   hsma_status_t s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
   if (s != HSMA_OK) return s;
   s = hsma_small_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda, d_B, d_ldb,
-                          diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st);
+                          diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st, uplo, trans);
   hsma_status_t f = hsma_ws_free(scratch, st);
   return s != HSMA_OK ? s : f;
 }

@@ -177,6 +177,26 @@ template <>
 inline cplxf hsma_alpha_as<cplxf>(const double *a) { return cplxf{(float)a[0], (float)a[1]}; }
 
 // ---------------------------------------------------------------------------
+// Element loops over a rows x cols column-major block without integer
+// division: blockIdx.y strides the columns, blockIdx.x and the threads the
+// rows.  hsma_grid_rc gives the matching launch grid (256 threads).
+// ---------------------------------------------------------------------------
+#define HSMA_FOR_RC(i, j, rows, cols)                                                       \
+  for (int64_t j = blockIdx.y; j < (int64_t)(cols); j += gridDim.y)                         \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)(rows); \
+         i += (int64_t)gridDim.x * blockDim.x)
+
+inline dim3 hsma_grid_rc(int64_t rows, int64_t cols) {
+  // about 16 CTAs of 256 threads per SM in total; the loops stride the rest
+  int64_t bx = (rows + 255) / 256;
+  bx = bx < 1 ? 1 : (bx > 64 ? 64 : bx);
+  const int64_t cap = 2432 / bx;
+  int64_t by = cols < cap ? cols : cap;
+  by = by < 1 ? 1 : by;
+  return dim3((unsigned)bx, (unsigned)by);
+}
+
+// ---------------------------------------------------------------------------
 // Small-path cost model (Section 4.2 kernel as laid out on this GPU).
 //
 // A warp holds C = 32/G columns of X; each column's rows are spread over G

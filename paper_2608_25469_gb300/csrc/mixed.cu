@@ -170,20 +170,20 @@ __global__ void __launch_bounds__(256) convert_panel_kernel(const float *__restr
 __global__ void __launch_bounds__(256) convert_x_kernel(const float *__restrict__ X, int64_t ldx, int nb, int n,
                                                         int terms, int Kp, __nv_bfloat16 *out, const int *skip) {
   if (skip != nullptr && *(volatile const int *)skip) return;
-  const int64_t total = (int64_t)n * Kp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / Kp), kp = (int)(e % Kp);
-    const int part = kp / nb, k = kp % nb;
-    float v = 0.0f;
-    if (part < terms) {
-      const float x = X[k + (int64_t)j * ldx];
-      __nv_bfloat16 hi, lo;
-      split_bf16(x, hi, lo);
-      out[e] = (terms == 3 && part == 1) ? lo : hi;
-      continue;
+  // rows: k within one part (plus the zero tail), columns: j
+  HSMA_FOR_RC(k, j, nb, n) {
+    const float x = X[k + j * ldx];
+    __nv_bfloat16 hi, lo;
+    split_bf16(x, hi, lo);
+    __nv_bfloat16 *o = out + j * Kp + k;
+    o[0] = hi;
+    if (terms == 3) {
+      o[nb] = lo;
+      o[2 * nb] = hi;
     }
-    out[e] = __float2bfloat16_rn(v);
   }
+  const int tail0 = terms * nb;
+  HSMA_FOR_RC(k, j, Kp - tail0, n) out[j * Kp + tail0 + k] = __float2bfloat16_rn(0.0f);
 }
 
 int g_launch_grid(int64_t total) {
@@ -254,14 +254,13 @@ __device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16 &a, __nv_bflo
 // blocks, zeros outside the computed part) as out[blk][s][i][k]
 __global__ void r32_dslice_kernel(const float *__restrict__ Dinv, int nb, int64_t nblk, int Kd,
                                   __nv_bfloat16 *out) {
-  const int64_t per = (int64_t)nb * Kd, total = nblk * per;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / per;
-    const int i = (int)((e % per) / Kd), k = (int)(e % Kd);
-    const float v = k < nb ? -Dinv[b * nb * nb + i + (int64_t)k * nb] : 0.0f;
+  const int64_t per = (int64_t)nb * Kd;
+  HSMA_FOR_RC(k, c, Kd, nblk * nb) {
+    const int64_t b = c / nb, i = c - b * nb;  // one division per column
+    const float v = k < nb ? -Dinv[b * nb * nb + i + k * nb] : 0.0f;
     __nv_bfloat16 x0, x1, x2;
     split3_bf16(v, x0, x1, x2);
-    __nv_bfloat16 *o = out + b * 3 * per + (int64_t)i * Kd + k;
+    __nv_bfloat16 *o = out + b * 3 * per + i * Kd + k;
     o[0] = x0;
     o[per] = x1;
     o[2 * per] = x2;
@@ -274,9 +273,8 @@ __global__ void r32_xslice_kernel(const float *__restrict__ W, int64_t ldw, int 
                                   __nv_bfloat16 *out, const int *skip) {
   if (skip != nullptr && *(volatile const int *)skip) return;
   const int64_t per = n * Kd;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / Kd;
-    const int k = (int)(e % Kd);
+  HSMA_FOR_RC(k, j, Kd, n) {
+    const int64_t e = j * Kd + k;
     const float v = k < sr ? scale * W[k + j * ldw] : 0.0f;
     __nv_bfloat16 x0, x1, x2;
     split3_bf16(v, x0, x1, x2);
@@ -309,11 +307,7 @@ size_t r32_panels_elems(int nb, int terms, int64_t m) {
 __global__ void copy_f32_kernel(const float *__restrict__ src, int64_t lds, float *dst, int64_t ldd, int rows,
                                 int64_t cols, const int *skip) {
   if (skip != nullptr && *(volatile const int *)skip) return;
-  const int64_t total = (int64_t)rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
-    dst[i + j * ldd] = src[i + j * lds];
-  }
+  HSMA_FOR_RC(i, j, rows, cols) dst[i + j * ldd] = src[i + j * lds];
 }
 
 hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
@@ -322,7 +316,7 @@ hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
   const int64_t nblk = (P.m + P.nb - 1) / P.nb;
   HsmaTraceScope ts("convert", st);
   if (P.tc_solve) {
-    r32_dslice_kernel<<<g_launch_grid(nblk * P.nb * r32_kd(P.nb)), 256, 0, st>>>(P.Dinv, P.nb, nblk, r32_kd(P.nb),
+    r32_dslice_kernel<<<hsma_grid_rc(r32_kd(P.nb), nblk * P.nb), 256, 0, st>>>(P.Dinv, P.nb, nblk, r32_kd(P.nb),
                                                                                  P.dslices);
     HSMA_CUDA_TRY(cudaGetLastError());
   }
@@ -377,12 +371,12 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
     const int sr = (int)std::min<int64_t>(nb, m - r0);
     {
       HsmaTraceScope ts("copy", st);
-      copy_f32_kernel<<<g_launch_grid((int64_t)sr * n), 256, 0, st>>>(B + r0, ldb, W, nb, sr, n, skip);
+      copy_f32_kernel<<<hsma_grid_rc(sr, n), 256, 0, st>>>(B + r0, ldb, W, nb, sr, n, skip);
     }
     if (P.tc_solve) {
       {
         HsmaTraceScope ts("convert", st);
-        r32_xslice_kernel<<<g_launch_grid(n * Kd), 256, 0, st>>>(W, nb, sr, n, Kd, r == 0 ? alpha : 1.0f, X3, skip);
+        r32_xslice_kernel<<<hsma_grid_rc(Kd, n), 256, 0, st>>>(W, nb, sr, n, Kd, r == 0 ? alpha : 1.0f, X3, skip);
         if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
       }
       sa.C32 = B + r0;
@@ -409,7 +403,7 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
         dim3 g1((rows + 31) / 32, (nb + 31) / 32);
         convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, nb, P.terms, Kp, Ap);
       }
-      convert_x_kernel<<<g_launch_grid((int64_t)n * Kp), 256, 0, st>>>(B + r0, ldb, nb, (int)n, P.terms, Kp, Xp,
+      convert_x_kernel<<<hsma_grid_rc(nb, n), 256, 0, st>>>(B + r0, ldb, nb, (int)n, P.terms, Kp, Xp,
                                                                        skip);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
@@ -463,9 +457,7 @@ hsma_status_t r32_solve(int nb, int terms, const float *A, int64_t lda, float *B
 __global__ void f64_to_f32_kernel(const double *__restrict__ src, int64_t lds, float *dst, int64_t ldd, int64_t rows,
                                   int64_t cols, int lower, const int *flag) {
   if (flag != nullptr && *(volatile const int *)flag) return;
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
+  HSMA_FOR_RC(i, j, rows, cols) {
     if (lower && i < j) continue;
     dst[i + j * ldd] = (float)src[i + j * lds];
   }
@@ -483,9 +475,7 @@ __global__ void scale_copy_kernel(const double *__restrict__ src, double *dst, i
 __global__ void accumulate_kernel(double *X, int64_t ldx, const float *__restrict__ Cc, int64_t ldc, int64_t rows,
                                   int64_t cols, int assign, const int *flag) {
   if (flag != nullptr && *(volatile const int *)flag) return;
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
+  HSMA_FOR_RC(i, j, rows, cols) {
     const double c = (double)Cc[i + j * ldc];
     X[i + j * ldx] = assign ? c : X[i + j * ldx] + c;
   }
@@ -496,9 +486,7 @@ __global__ void sumsq_kernel(const double *__restrict__ M_, int64_t ld, int64_t 
                              int unit, double *sums, int slot, const int *flag) {
   if (flag != nullptr && *(volatile const int *)flag) return;
   double acc = 0.0;
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
+  HSMA_FOR_RC(i, j, rows, cols) {
     if (lower && i < j) continue;
     const double v = (lower && unit && i == j) ? 1.0 : M_[i + j * ld];
     acc = fma(v, v, acc);
@@ -915,9 +903,7 @@ hsma_status_t oz_residual(const OzOperand &L, const double *X, int64_t ldx, doub
 }
 
 __global__ void scale_kernel(double *B, int64_t ldb, int64_t rows, int64_t n, double ar, double ai, int cplx) {
-  const int64_t total = rows * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
+  HSMA_FOR_RC(i, j, rows, n) {
     if (cplx) {
       double *p = B + 2 * (i + j * ldb);
       const double re = p[0], im = p[1];
@@ -1010,7 +996,7 @@ hsma_status_t blocked_emulated(bool cplx, int nb, const double *A, int64_t lda, 
     if ((s = hsma_diag_inverse(cplx ? HSMA_C128 : HSMA_R64, nb, A, lda, m, unit, Dinv, st)) != HSMA_OK) break;
     if (alpha[0] != 1.0 || (cplx && alpha[1] != 0.0)) {
       HsmaTraceScope ts("copy", st);
-      scale_kernel<<<g_launch_grid(m * n), 256, 0, st>>>(B, ldb, m, n, alpha[0], cplx ? alpha[1] : 0.0, cplx);
+      scale_kernel<<<hsma_grid_rc(m, n), 256, 0, st>>>(B, ldb, m, n, alpha[0], cplx ? alpha[1] : 0.0, cplx);
       if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
     }
     for (int64_t R0 = 0; R0 < m && s == HSMA_OK; R0 += P) {
@@ -1105,7 +1091,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
   P.A = A32;
   P.Dinv = reinterpret_cast<float *>(static_cast<unsigned char *>(ozx_ws) + ozx_b);
   P.panels = reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(P.Dinv) + dinv_b);
-  const int grid = g_launch_grid(m * n);
+  const dim3 grid = hsma_grid_rc(m, n);
   auto fail = [&](cudaError_t e) { return e == cudaSuccess ? HSMA_OK : hsma_from_cuda(e); };
   do {
     if ((s = fail(cudaMemsetAsync(sums, 0, st_b, st))) != HSMA_OK) break;
@@ -1114,9 +1100,9 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
       break;
     {
       HsmaTraceScope ts("convert", st);
-      f64_to_f32_kernel<<<g_launch_grid(m * m), 256, 0, st>>>(A, lda, A32, m, m, m, 1, nullptr);
+      f64_to_f32_kernel<<<hsma_grid_rc(m, m), 256, 0, st>>>(A, lda, A32, m, m, m, 1, nullptr);
       f64_to_f32_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 0, nullptr);
-      sumsq_kernel<<<g_launch_grid(m * m), 256, 0, st>>>(A, lda, m, m, 1, unit, sums, 0, nullptr);
+      sumsq_kernel<<<hsma_grid_rc(m, m), 256, 0, st>>>(A, lda, m, m, 1, unit, sums, 0, nullptr);
       sumsq_kernel<<<grid, 256, 0, st>>>(B0, m, m, n, 0, 0, sums, 1, nullptr);
       if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     }
@@ -1136,7 +1122,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
       if (emulated) {
         {
           HsmaTraceScope ts("refine", st);
-          scale_copy_kernel<<<grid, 256, 0, st>>>(B0, R64, m * n, alpha, state);
+          scale_copy_kernel<<<g_launch_grid(m * n), 256, 0, st>>>(B0, R64, m * n, alpha, state);
         }
         if ((s = oz_residual(Lsl, B, ldb, R64, m, Xsl, state, st)) != HSMA_OK) break;
       } else {
@@ -1226,9 +1212,7 @@ namespace {
 // complex64 lower triangle (zeros above) or block -> complex128, column-major
 __global__ void c64_to_c128_kernel(const cplxf *__restrict__ src, int64_t lds, cplx *dst, int64_t ldd, int64_t rows,
                                    int64_t cols, int lower) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
+  HSMA_FOR_RC(i, j, rows, cols) {
     cplx v{0.0, 0.0};
     if (!lower || i >= j) {
       const cplxf x = src[i + j * lds];
@@ -1240,9 +1224,7 @@ __global__ void c64_to_c128_kernel(const cplxf *__restrict__ src, int64_t lds, c
 
 __global__ void c128_to_c64_kernel(const cplx *__restrict__ src, int64_t lds, cplxf *dst, int64_t ldd, int64_t rows,
                                    int64_t cols) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
+  HSMA_FOR_RC(i, j, rows, cols) {
     const cplx v = src[i + j * lds];
     dst[i + j * ldd] = cplxf{(float)v.re, (float)v.im};
   }
@@ -1261,15 +1243,15 @@ hsma_status_t hsma_c64_blocked(int nb, const void *A, int64_t lda, void *B, int6
   cplx *B2 = reinterpret_cast<cplx *>(static_cast<unsigned char *>(ws) + a_b);
   {
     HsmaTraceScope ts("copy", st);
-    c64_to_c128_kernel<<<g_launch_grid(m * m), 256, 0, st>>>(static_cast<const cplxf *>(A), lda, A2, m, m, m, 1);
-    c64_to_c128_kernel<<<g_launch_grid(m * n), 256, 0, st>>>(static_cast<const cplxf *>(B), ldb, B2, m, m, n, 0);
+    c64_to_c128_kernel<<<hsma_grid_rc(m, m), 256, 0, st>>>(static_cast<const cplxf *>(A), lda, A2, m, m, m, 1);
+    c64_to_c128_kernel<<<hsma_grid_rc(m, n), 256, 0, st>>>(static_cast<const cplxf *>(B), ldb, B2, m, m, n, 0);
     s = hsma_from_cuda(cudaGetLastError());
   }
   if (s == HSMA_OK) s = blocked_emulated(true, nb, reinterpret_cast<const double *>(A2), m,
                                          reinterpret_cast<double *>(B2), m, m, n, alpha, unit, st);
   if (s == HSMA_OK) {
     HsmaTraceScope ts("copy", st);
-    c128_to_c64_kernel<<<g_launch_grid(m * n), 256, 0, st>>>(B2, m, static_cast<cplxf *>(B), ldb, m, n);
+    c128_to_c64_kernel<<<hsma_grid_rc(m, n), 256, 0, st>>>(B2, m, static_cast<cplxf *>(B), ldb, m, n);
     s = hsma_from_cuda(cudaGetLastError());
   }
   hsma_status_t f = hsma_ws_free(ws, st);

@@ -17,10 +17,14 @@
 //  * the substitution is fully unrolled so X stays in registers; steps past
 //    m and slots past ceil(m/G) are skipped with warp-uniform branches.
 //
-// The per-instance arithmetic is independent of the batch it sits in.
+// The per-instance arithmetic is independent of the batch it sits in.  The
+// kernels can read A and B through an index map (row reversal, transposed or
+// conjugated reads), which gives the other left-side variants without copies;
+// the paper's case runs a kernel without the map.
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "small.h"
@@ -37,6 +41,11 @@ namespace {
 #ifndef HSMA_VB_MINB
 #define HSMA_VB_MINB 3
 #endif
+// FP32 element types: the FP32 pipe leaves the kernel bound by load and
+// barrier latency, so more CTAs per SM pay off (and fit: half the registers).
+#ifndef HSMA_VB_MINB_F32
+#define HSMA_VB_MINB_F32 6
+#endif
 #ifndef HSMA_VB_GMASK
 #define HSMA_VB_GMASK 0xFu
 #endif
@@ -48,6 +57,30 @@ constexpr unsigned kBatchedGMask = HSMA_VB_GMASK;
 __host__ __device__ constexpr int col_off(int i, int mmax) { return i * (mmax - 1) - (i * (i - 1)) / 2; }
 __host__ __device__ constexpr int tri_elems(int mmax) { return col_off(mmax, mmax); }
 
+// Index map from the solved lower-triangular form onto the caller's operand
+// (the other left-side variants): with rev, row r of the form is row m-1-r of
+// the operand (and of B); with tr, A is read transposed; with cj, conjugated.
+// The identity map is the paper's left / lower / no-transpose case.
+struct SmallMap {
+  int rev, tr, cj;
+};
+
+template <class T, bool MAP>
+__device__ __forceinline__ T map_ld(const T *A, int64_t lda, int m, int r, int i, SmallMap mp) {
+  if constexpr (!MAP) return Elem<T>::ld(A + r + (int64_t)i * lda);
+  int p = mp.rev ? m - 1 - r : r, q = mp.rev ? m - 1 - i : i;
+  if (mp.tr) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+  T v = Elem<T>::ld(A + p + (int64_t)q * lda);
+  if constexpr (Elem<T>::kComplex) {
+    if (mp.cj) v.im = -v.im;
+  }
+  return v;
+}
+
 template <class T>
 struct SmemLayout {
   // triangle, then c_r = alpha/a_rr, then 1/a_rr
@@ -57,14 +90,14 @@ struct SmemLayout {
 // Stage one instance: 1/a_rr and alpha/a_rr for r < m, then the scaled strict
 // lower triangle for rows < rows_used (rows >= m are zero).  All threads of
 // the CTA take part; ends with a CTA barrier.
-template <class T, int MMAX, int W>
+template <class T, int MMAX, int W, bool MAP>
 __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict__ A, int64_t lda, int m,
-                                      int rows_used, T alpha, bool unit) {
+                                      int rows_used, T alpha, bool unit, SmallMap mp) {
   using E = Elem<T>;
   const int tid = threadIdx.x;
   for (int r = tid; r < MMAX; r += 32 * W) {
     T rv = E::one();
-    if (r < m && !unit) rv = E::recip(E::ld(A + r + (int64_t)r * lda));
+    if (r < m && !unit) rv = E::recip(map_ld<T, MAP>(A, lda, m, r, r, mp));
     sR[r] = rv;
     sC[r] = (r < m) ? E::mul(alpha, rv) : E::zero();
   }
@@ -80,7 +113,7 @@ __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const int i = i0 + u * W, r = lane + 32 * p;
-        v[u][p] = (i < m && r > i && r < m) ? E::ld(A + r + (int64_t)i * lda) : E::zero();
+        v[u][p] = (i < m && r > i && r < m) ? map_ld<T, MAP>(A, lda, m, r, i, mp) : E::zero();
       }
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -94,8 +127,9 @@ __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict
 }
 
 // One warp solves one column tile (up to 32/G columns starting at Bt).
-template <class T, int G, int MMAX>
-__device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, int64_t ldb, int m, int ncols) {
+template <class T, int G, int MMAX, bool MAP>
+__device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, int64_t ldb, int m, int ncols,
+                                           int rev) {
   using E = Elem<T>;
   constexpr int R = MMAX / G;
   const int lane = threadIdx.x & 31;
@@ -109,7 +143,7 @@ __device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, in
     const int r = g + t * G;
     s[t] = E::zero();
     if (t * G < m) {
-      if (colok && r < m) s[t] = E::mul(sC[r], E::ld(Bp + r));
+      if (colok && r < m) s[t] = E::mul(sC[r], E::ld(Bp + (MAP && rev ? m - 1 - r : r)));
     }
   }
 
@@ -137,21 +171,21 @@ __device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, in
   for (int t = 0; t < R; ++t) {
     const int r = g + t * G;
     if (t * G < m) {
-      if (colok && r < m) E::st(Bp + r, s[t]);
+      if (colok && r < m) E::st(Bp + (MAP && rev ? m - 1 - r : r), s[t]);
     }
   }
 }
 
-template <class T, int G, int MMAX>
+template <class T, int G, int MMAX, bool MAP>
 __device__ __forceinline__ void solve_tiles(const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n, int tile0,
-                                            int tile_step) {
+                                            int tile_step, int rev) {
   constexpr int C = 32 / G;
   const int warp = threadIdx.x >> 5;
   const int ntiles = (n + C - 1) / C;
   for (int t = tile0 + warp; t < ntiles; t += tile_step) {
     const int col0 = t * C;
     const int nc = (n - col0) < C ? (n - col0) : C;
-    warp_solve<T, G, MMAX>(sTri, sC, B + (int64_t)col0 * ldb, ldb, m, nc);
+    warp_solve<T, G, MMAX, MAP>(sTri, sC, B + (int64_t)col0 * ldb, ldb, m, nc, rev);
   }
 }
 
@@ -162,32 +196,32 @@ __device__ __forceinline__ void zero_tiles(T *B, int64_t ldb, int m, int n) {
 }
 
 // Dispatch over the row-group variants compiled into the batched kernel.
-template <class T>
+template <class T, bool MAP>
 struct Variants {
   static constexpr bool kCplx = Elem<T>::kComplex;
   __device__ __forceinline__ static void run(int g, const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n,
-                                             int tile0, int step) {
+                                             int tile0, int step, int rev) {
     if constexpr ((kBatchedGMask & 1u) != 0) {
       if (g == 1) {
-        solve_tiles<T, 1, kCplx ? 32 : 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        solve_tiles<T, 1, kCplx ? 32 : 64, MAP>(sTri, sC, B, ldb, m, n, tile0, step, rev);
         return;
       }
     }
     if constexpr ((kBatchedGMask & 2u) != 0) {
       if (g == 2) {
-        solve_tiles<T, 2, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        solve_tiles<T, 2, 64, MAP>(sTri, sC, B, ldb, m, n, tile0, step, rev);
         return;
       }
     }
     if constexpr ((kBatchedGMask & 4u) != 0) {
       if (g == 4) {
-        solve_tiles<T, 4, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        solve_tiles<T, 4, 64, MAP>(sTri, sC, B, ldb, m, n, tile0, step, rev);
         return;
       }
     }
     if constexpr ((kBatchedGMask & 8u) != 0) {
       if (g == 8) {
-        solve_tiles<T, 8, 64>(sTri, sC, B, ldb, m, n, tile0, step);
+        solve_tiles<T, 8, 64, MAP>(sTri, sC, B, ldb, m, n, tile0, step, rev);
         return;
       }
     }
@@ -201,14 +235,14 @@ __device__ __forceinline__ int variant_mmax(int g) {
   return (Elem<T>::kComplex && g == 1) ? 32 : 64;
 }
 
-template <class T, int W>
+template <class T, int W, bool MAP>
 __device__ __forceinline__ void stage_any(int g, T *sTri, T *sC, T *sR, const T *A, int64_t lda, int m, T alpha,
-                                          bool unit) {
+                                          bool unit, SmallMap mp) {
   const int rows_used = ((m + g - 1) / g) * g;
   if (variant_mmax<T>(g) == 32)
-    stage<T, 32, W>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
+    stage<T, 32, W, MAP>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit, mp);
   else
-    stage<T, 64, W>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit);
+    stage<T, 64, W, MAP>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit, mp);
 }
 
 template <class T>
@@ -224,13 +258,14 @@ __device__ __forceinline__ void smem_parts(unsigned char *smem, T *&sTri, T *&sC
 // ---------------------------------------------------------------------------
 template <class T, int G, int MMAX>
 __global__ void __launch_bounds__(32 * kWarpsSingle) small_single_kernel(const T *__restrict__ A, int64_t lda, T *B,
-                                                                 int64_t ldb, int m, int n, T alpha, int unit) {
+                                                                 int64_t ldb, int m, int n, T alpha, int unit,
+                                                                 SmallMap mp) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *sTri, *sC, *sR;
   smem_parts<T>(smem, sTri, sC, sR);
   const int rows_used = ((m + G - 1) / G) * G;
-  stage<T, MMAX, kWarpsSingle>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0);
-  solve_tiles<T, G, MMAX>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsSingle, gridDim.x * kWarpsSingle);
+  stage<T, MMAX, kWarpsSingle, true>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0, mp);
+  solve_tiles<T, G, MMAX, true>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsSingle, gridDim.x * kWarpsSingle, mp.rev);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,12 +278,55 @@ __global__ void __launch_bounds__(32 * kWarpsSingle) small_single_kernel(const T
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 256;
 
-__device__ __forceinline__ int cost_bucket(long long cost) {
+__host__ __device__ inline int cost_bucket(long long cost) {
   // 8 buckets per octave: the octave and the three bits below the leading one
   if (cost < 16) return 0;
+#ifdef __CUDA_ARCH__
   const int lead = 63 - __clzll(cost);
+#else
+  int lead = 0;
+  while ((cost >> (lead + 1)) != 0) ++lead;
+#endif
   const int b = lead * 8 + (int)((cost >> (lead - 3)) & 7);
   return b < kBuckets ? b : kBuckets - 1;
+}
+
+// The schedule entry of every (m, n) with m, n <= 64, real and complex:
+// G | bucket << 8.  Computed on the host from the same closed-form cost model
+// and copied to the device once per device, so the schedule pass does one
+// lookup per instance instead of evaluating the model (64-bit divisions).
+__device__ int32_t g_sched_tab[2 * 64 * 64];
+
+int32_t sched_entry(int m, int n, bool cplx_) {
+  const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
+  return g | (cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched)) << 8);
+}
+
+// Device address of the table, filled on first use on this device; null when
+// it is not yet filled and the stream is capturing (the pass then evaluates
+// the model itself).
+const int32_t *sched_table(cudaStream_t st) {
+  static const int32_t *addr[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (addr[dev] != nullptr) return addr[dev];
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+  static int32_t host[2 * 64 * 64];
+  static bool host_ready = false;
+  if (!host_ready) {
+    for (int c = 0; c < 2; ++c)
+      for (int m = 1; m <= 64; ++m)
+        for (int n = 1; n <= 64; ++n) host[c * 4096 + (m - 1) * 64 + (n - 1)] = sched_entry(m, n, c == 1);
+    host_ready = true;
+  }
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_sched_tab) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(p, host, sizeof host, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+  addr[dev] = static_cast<const int32_t *>(p);
+  return addr[dev];
 }
 
 template <class T>
@@ -258,7 +336,7 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
                                                                  const int32_t *__restrict__ dldb,
                                                                  const void *const *__restrict__ dA,
                                                                  void *const *__restrict__ dB, int32_t *scratch,
-                                                                 uint32_t *status) {
+                                                                 uint32_t *status, const int32_t *__restrict__ tab) {
   __shared__ int hist[kBuckets];
   __shared__ int offs[kBuckets];
   const bool cplx_ = Elem<T>::kComplex;
@@ -277,8 +355,14 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
       err |= HSMA_DEVERR_NULL_PTR;
       continue;
     }
-    const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
-    atomicAdd(&hist[cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched))], 1);
+    int e;
+    if (tab != nullptr && n <= 64) {
+      e = tab[(cplx_ ? 4096 : 0) + (m - 1) * 64 + (n - 1)];
+    } else {
+      const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
+      e = g | (cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched)) << 8);
+    }
+    atomicAdd(&hist[e >> 8], 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -296,21 +380,30 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
     const int lo = m > 1 ? m : 1;
     if (m <= 0 || n <= 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) continue;
     if (dA[b] == nullptr || dB[b] == nullptr) continue;
-    const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
-    const int pos = atomicAdd(&offs[cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched))], 1);
-    scratch[2 + pos] = b | (g << 24);
+    int e;
+    if (tab != nullptr && n <= 64) {
+      e = tab[(cplx_ ? 4096 : 0) + (m - 1) * 64 + (n - 1)];
+    } else {
+      const int g = hsma_small_pick_g_batched(m, n, cplx_, kWarpsBatched, kBatchedGMask);
+      e = g | (cost_bucket(hsma_small_cta_instr(m, n, g, cplx_, kWarpsBatched)) << 8);
+    }
+    const int pos = atomicAdd(&offs[e >> 8], 1);
+    scratch[2 + pos] = b | ((e & 0xff) << 24);
   }
   if (err != 0 && status != nullptr) atomicOr(status, err);
 }
 
-template <class T>
-__global__ void __launch_bounds__(32 * kWarpsBatched, HSMA_VB_MINB) vbatched_solve_kernel(const int32_t *__restrict__ dm,
+template <class T, bool MAP>
+__global__ void __launch_bounds__(32 * kWarpsBatched,
+                                  (sizeof(T) == sizeof(float) || sizeof(T) == sizeof(cplxf)) && !std::is_same<T, double>::value
+                                      ? HSMA_VB_MINB_F32
+                                      : HSMA_VB_MINB) vbatched_solve_kernel(const int32_t *__restrict__ dm,
                                                                   const int32_t *__restrict__ dn,
                                                                   const int32_t *__restrict__ dlda,
                                                                   const int32_t *__restrict__ dldb,
                                                                   const void *const *__restrict__ dA,
                                                                   void *const *__restrict__ dB, T alpha, int unit,
-                                                                  int32_t *scratch) {
+                                                                  int32_t *scratch, SmallMap mp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   T *sTri, *sC, *sR;
@@ -333,19 +426,19 @@ __global__ void __launch_bounds__(32 * kWarpsBatched, HSMA_VB_MINB) vbatched_sol
       zero_tiles<T, kWarpsBatched>(B, ldb, m, n);
       continue;
     }
-    stage_any<T, kWarpsBatched>(g, sTri, sC, sR, A, lda, m, alpha, unit != 0);
-    Variants<T>::run(g, sTri, sC, B, ldb, m, n, 0, kWarpsBatched);
+    stage_any<T, kWarpsBatched, MAP>(g, sTri, sC, sR, A, lda, m, alpha, unit != 0, mp);
+    Variants<T, MAP>::run(g, sTri, sC, B, ldb, m, n, 0, kWarpsBatched, mp.rev);
     __syncthreads();  // the next item restages shared memory
   }
 }
 
-template <class T>
+template <class T, bool MAP>
 int persistent_grid(int dev) {
   static int cached[64] = {0};
   if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
   int nsm = 0, per_sm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_solve_kernel<T>, 32 * kWarpsBatched,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_solve_kernel<T, MAP>, 32 * kWarpsBatched,
                                                 SmemLayout<T>::bytes(64));
   int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (dev >= 0 && dev < 64) cached[dev] = grid;
@@ -355,13 +448,16 @@ int persistent_grid(int dev) {
 template <class T>
 hsma_status_t set_smem_attrs() {
   const int bytes = (int)SmemLayout<T>::bytes(64);
-  HSMA_CUDA_TRY(cudaFuncSetAttribute(vbatched_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  HSMA_CUDA_TRY(
+      cudaFuncSetAttribute(vbatched_solve_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  HSMA_CUDA_TRY(
+      cudaFuncSetAttribute(vbatched_solve_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return HSMA_OK;
 }
 
 template <class T, int G, int MMAX>
 hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m, int n, T alpha, int unit,
-                              int nsm, cudaStream_t st) {
+                              int nsm, cudaStream_t st, SmallMap mp) {
   constexpr int C = 32 / G;
   const int tiles = (n + C - 1) / C;
   int grid = (tiles + kWarpsSingle - 1) / kWarpsSingle;
@@ -375,7 +471,7 @@ hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m,
     attr_done.set();
   }
   HsmaTraceScope ts("small_single", st);
-  small_single_kernel<T, G, MMAX><<<grid, 32 * kWarpsSingle, bytes, st>>>(A, lda, B, ldb, m, n, alpha, unit);
+  small_single_kernel<T, G, MMAX><<<grid, 32 * kWarpsSingle, bytes, st>>>(A, lda, B, ldb, m, n, alpha, unit, mp);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
@@ -385,9 +481,14 @@ hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m,
 // ---------------------------------------------------------------------------
 // Host entry points (internal; the C ABI validates arguments first).
 // ---------------------------------------------------------------------------
+static SmallMap make_map(int uplo, int trans) {
+  const bool op_lower = (uplo == HSMA_LOWER) != (trans != HSMA_NO_TRANS);
+  return SmallMap{op_lower ? 0 : 1, trans != HSMA_NO_TRANS ? 1 : 0, trans == HSMA_CONJ_TRANS ? 1 : 0};
+}
+
 template <class T>
 static hsma_status_t small_single_impl(int g, const void *A, int64_t lda, void *B, int64_t ldb, int m, int n,
-                                       const double *alpha, int unit, cudaStream_t st) {
+                                       const double *alpha, int unit, cudaStream_t st, SmallMap mp) {
   int dev = 0, nsm = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -399,34 +500,35 @@ static hsma_status_t small_single_impl(int g, const void *A, int64_t lda, void *
   T *b = static_cast<T *>(B);
   if constexpr (Elem<T>::kComplex) {
     switch (g) {
-      case 1: return launch_single_g<T, 1, 32>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 2: return launch_single_g<T, 2, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 4: return launch_single_g<T, 4, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 8: return launch_single_g<T, 8, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 16: return launch_single_g<T, 16, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 32: return launch_single_g<T, 32, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 1: return launch_single_g<T, 1, 32>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 2: return launch_single_g<T, 2, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 4: return launch_single_g<T, 4, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 8: return launch_single_g<T, 8, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 16: return launch_single_g<T, 16, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 32: return launch_single_g<T, 32, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
       default: return HSMA_ERR_INVALID_ARG;
     }
   } else {
     switch (g) {
-      case 1: return launch_single_g<T, 1, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 2: return launch_single_g<T, 2, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 4: return launch_single_g<T, 4, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 8: return launch_single_g<T, 8, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 16: return launch_single_g<T, 16, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
-      case 32: return launch_single_g<T, 32, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st);
+      case 1: return launch_single_g<T, 1, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 2: return launch_single_g<T, 2, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 4: return launch_single_g<T, 4, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 8: return launch_single_g<T, 8, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 16: return launch_single_g<T, 16, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
+      case 32: return launch_single_g<T, 32, 64>(a, lda, b, ldb, m, n, al, unit, nsm, st, mp);
       default: return HSMA_ERR_INVALID_ARG;
     }
   }
 }
 
 hsma_status_t hsma_small_single(int dtype, int g, const void *A, int64_t lda, void *B, int64_t ldb, int m, int n,
-                                const double *alpha, int unit, cudaStream_t st) {
+                                const double *alpha, int unit, cudaStream_t st, int uplo, int trans) {
+  const SmallMap mp = make_map(uplo, trans);
   switch (dtype) {
-    case HSMA_C128: return small_single_impl<cplx>(g, A, lda, B, ldb, m, n, alpha, unit, st);
-    case HSMA_R32: return small_single_impl<float>(g, A, lda, B, ldb, m, n, alpha, unit, st);
-    case HSMA_C64: return small_single_impl<cplxf>(g, A, lda, B, ldb, m, n, alpha, unit, st);
-    default: return small_single_impl<double>(g, A, lda, B, ldb, m, n, alpha, unit, st);
+    case HSMA_C128: return small_single_impl<cplx>(g, A, lda, B, ldb, m, n, alpha, unit, st, mp);
+    case HSMA_R32: return small_single_impl<float>(g, A, lda, B, ldb, m, n, alpha, unit, st, mp);
+    case HSMA_C64: return small_single_impl<cplxf>(g, A, lda, B, ldb, m, n, alpha, unit, st, mp);
+    default: return small_single_impl<double>(g, A, lda, B, ldb, m, n, alpha, unit, st, mp);
   }
 }
 
@@ -434,7 +536,7 @@ template <class T>
 static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32_t *dn, const double *alpha,
                                    const void *const *dA, const int32_t *dlda, void *const *dB,
                                    const int32_t *dldb, int unit, uint32_t *status, int32_t *scratch,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, SmallMap mp) {
   int dev = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   static DeviceFlags attr_done;
@@ -446,15 +548,22 @@ static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32
   const T al = hsma_alpha_as<T>(alpha);
   {
     HsmaTraceScope ts("vbatched_schedule", st);
-    vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status);
+    vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status,
+                                                    sched_table(st));
   }
   HSMA_CUDA_TRY(cudaGetLastError());
-  int grid = persistent_grid<T>(dev);
+  // the identity map (the paper's case) runs a kernel without the remapping arithmetic
+  const bool mapped = mp.rev != 0 || mp.tr != 0 || mp.cj != 0;
+  int grid = mapped ? persistent_grid<T, true>(dev) : persistent_grid<T, false>(dev);
   if (grid > batch) grid = batch;
   {
     HsmaTraceScope ts("vbatched_solve", st);
-    vbatched_solve_kernel<T><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dA,
-                                                                                          dB, al, unit, scratch);
+    if (mapped)
+      vbatched_solve_kernel<T, true><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(
+          dm, dn, dlda, dldb, dA, dB, al, unit, scratch, mp);
+    else
+      vbatched_solve_kernel<T, false><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(
+          dm, dn, dlda, dldb, dA, dB, al, unit, scratch, mp);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
@@ -465,12 +574,13 @@ size_t hsma_vbatched_scratch_bytes(int32_t batch) { return sizeof(int32_t) * (2 
 hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
                                   void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
-                                  int32_t *scratch, cudaStream_t st) {
+                                  int32_t *scratch, cudaStream_t st, int uplo, int trans) {
+  const SmallMap mp = make_map(uplo, trans);
   switch (dtype) {
-    case HSMA_C128: return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
-    case HSMA_R32: return vbatched_impl<float>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
-    case HSMA_C64: return vbatched_impl<cplxf>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
-    default: return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+    case HSMA_C128: return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
+    case HSMA_R32: return vbatched_impl<float>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
+    case HSMA_C64: return vbatched_impl<cplxf>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
+    default: return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
   }
 }
 

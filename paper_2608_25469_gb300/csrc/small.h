@@ -7,8 +7,11 @@
 #include "../../include/hsma.h"
 
 // One solve with m <= 64 (g = 0: planner choice).  Arguments already validated.
+// uplo / trans select the left-side variant (the kernel remaps indices; the
+// default is the paper's left / lower / no-transpose case).
 hsma_status_t hsma_small_single(int dtype, int g, const void *A, int64_t lda, void *B, int64_t ldb, int m, int n,
-                                const double *alpha, int unit, cudaStream_t st);
+                                const double *alpha, int unit, cudaStream_t st, int uplo = HSMA_LOWER,
+                                int trans = HSMA_NO_TRANS);
 
 // Bytes of device scratch the varlen batch needs for `batch` instances.
 size_t hsma_vbatched_scratch_bytes(int32_t batch);
@@ -18,7 +21,8 @@ size_t hsma_vbatched_scratch_bytes(int32_t batch);
 hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
                                   void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
-                                  int32_t *scratch, cudaStream_t st);
+                                  int32_t *scratch, cudaStream_t st, int uplo = HSMA_LOWER,
+                                  int trans = HSMA_NO_TRANS);
 
 // dtypes the small kernels and the varlen batch handle
 inline bool hsma_small_dtype(int dtype) {

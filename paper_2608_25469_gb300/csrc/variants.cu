@@ -12,9 +12,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "../../include/hsma.h"
 #include "common.cuh"
+#include "small.h"
 #include "trace.h"
 #include "workspace.h"
 
@@ -30,9 +32,8 @@ __device__ __forceinline__ T conj_of(T v) {
 // T(p,q) = A(p,q) or, with tsrc, A(q,p); conjugated with cj.
 template <class T>
 __global__ void remap_a_kernel(const T *__restrict__ A, int64_t lda, int64_t mE, int rev, int tsrc, int cj, T *L) {
-  const int64_t total = mE * mE;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % mE, k = e / mE;
+  HSMA_FOR_RC(i, k, mE, mE) {
+    const int64_t e = i + k * mE;
     if (i < k) {
       L[e] = Elem<T>::zero();
       continue;
@@ -47,9 +48,8 @@ __global__ void remap_a_kernel(const T *__restrict__ A, int64_t lda, int64_t mE,
 // scatter writes B from B'.
 template <class T>
 __global__ void remap_b_kernel(T *B, int64_t ldb, T *Bp, int64_t mE, int64_t nE, int rev, int right, int scatter) {
-  const int64_t total = mE * nE;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % mE, j = e / mE;
+  HSMA_FOR_RC(i, j, mE, nE) {
+    const int64_t e = i + j * mE;
     const int64_t p = rev ? mE - 1 - i : i;
     T *b = right ? B + j + p * ldb : B + p + j * ldb;
     if (scatter)
@@ -58,8 +58,6 @@ __global__ void remap_b_kernel(T *B, int64_t ldb, T *Bp, int64_t mE, int64_t nE,
       Bp[e] = *b;
   }
 }
-
-int grid_for(int64_t total) { return (int)std::min<int64_t>(std::max<int64_t>((total + 255) / 256, 1), 152 * 32); }
 
 template <class T>
 hsma_status_t variant_impl(int dtype, int side, int uplo, int trans, int diag, int64_t m, int64_t n,
@@ -83,14 +81,14 @@ hsma_status_t variant_impl(int dtype, int side, int uplo, int trans, int diag, i
   T *Bp = reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + l_b);
   {
     HsmaTraceScope ts("remap", st);
-    remap_a_kernel<T><<<grid_for(mE * mE), 256, 0, st>>>(A, lda, mE, rev, tsrc, cj, L);
-    remap_b_kernel<T><<<grid_for(mE * nE), 256, 0, st>>>(B, ldb, Bp, mE, nE, rev, right ? 1 : 0, 0);
+    remap_a_kernel<T><<<hsma_grid_rc(mE, mE), 256, 0, st>>>(A, lda, mE, rev, tsrc, cj, L);
+    remap_b_kernel<T><<<hsma_grid_rc(mE, nE), 256, 0, st>>>(B, ldb, Bp, mE, nE, rev, right ? 1 : 0, 0);
     s = hsma_from_cuda(cudaGetLastError());
   }
   if (s == HSMA_OK) s = hsma_trsm_llnn_ex(dtype, diag, mE, nE, alpha, L, mE, Bp, mE, st, opts, info);
   if (s == HSMA_OK) {
     HsmaTraceScope ts("remap", st);
-    remap_b_kernel<T><<<grid_for(mE * nE), 256, 0, st>>>(B, ldb, Bp, mE, nE, rev, right ? 1 : 0, 1);
+    remap_b_kernel<T><<<hsma_grid_rc(mE, nE), 256, 0, st>>>(B, ldb, Bp, mE, nE, rev, right ? 1 : 0, 1);
     s = hsma_from_cuda(cudaGetLastError());
   }
   hsma_status_t f = hsma_ws_free(ws, st);
@@ -119,6 +117,16 @@ extern "C" HSMA_API hsma_status_t hsma_trsm(int dtype, int side, int uplo, int t
     const size_t eb = dtype == HSMA_C128 ? 16 : ((dtype == HSMA_R32 || dtype == HSMA_R32_BF16) ? 4 : 8);
     HSMA_CUDA_TRY(cudaMemset2DAsync(B, (size_t)ldb * eb, 0, (size_t)m * eb, (size_t)n, st));
     return HSMA_OK;
+  }
+  // left side, m <= 64: the small kernels remap indices themselves (no copies)
+  const bool small_path = side == HSMA_LEFT && m <= 64 && hsma_small_dtype(dtype) &&
+                          (opts == nullptr || opts->path != HSMA_PATH_BLOCKED);
+  if (small_path) {
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->plan.path = HSMA_PATH_SMALL;
+    }
+    return hsma_small_single(dtype, 0, A, lda, B, ldb, (int)m, (int)n, a, diag == HSMA_UNIT, st, uplo, trans);
   }
   switch (dtype) {
     case HSMA_C128:

@@ -36,7 +36,7 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
-           "hsma_trsm_llnn_vbatched_host", "hsma_trsm",
+           "hsma_trsm_llnn_vbatched_host", "hsma_trsm", "hsma_trsm_vbatched",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -104,6 +104,9 @@ def _load():
     lib.hsma_trsm_llnn_vbatched_host.restype = c_int
     lib.hsma_trsm.argtypes = [c_int, c_int, c_int, c_int, c_int, i64, i64, vp, vp, i64, vp, i64, vp, vp, vp]
     lib.hsma_trsm.restype = c_int
+    lib.hsma_trsm_vbatched.argtypes = [c_int, c_int, c_int, c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32,
+                                       u32p, vp]
+    lib.hsma_trsm_vbatched.restype = c_int
     lib.hsma_plan.argtypes = [c_int, i64, i64, ctypes.POINTER(Plan)]
     lib.hsma_plan.restype = c_int
     lib.hsma_small_cost.argtypes = [c_int, i64, i64, i32]
@@ -191,6 +194,17 @@ def hsma_trsm(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, strea
                        ctypes.byref(info) if info is not None else None)
     if check:
         _check(s, "hsma_trsm")
+    return s
+
+
+def hsma_trsm_vbatched(dtype, side, uplo, trans, diag, batch, d_m, d_n, alpha, d_A, d_lda, d_B, d_ldb, max_m=0,
+                       max_n=0, d_status=0, stream=0, check=True) -> int:
+    """Varlen batch of left-side variants (uplo, trans) with in-kernel index remapping."""
+    s = _lib.hsma_trsm_vbatched(dtype, side, uplo, trans, diag, batch, d_m, d_n,
+                                ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), d_A, d_lda, d_B, d_ldb, max_m, max_n,
+                                d_status or None, stream)
+    if check:
+        _check(s, "hsma_trsm_vbatched")
     return s
 
 

@@ -163,3 +163,12 @@ def test_variant_argument_checks(H):
     assert f(0, 0, 1, 0, 0, 4, 9, 1.0, 1, 3, 1, 4, check=False) == 1   # left side: lda < m
     assert f(0, 1, 1, 2, 0, 0, 9, 1.0, 0, 9, 0, 1, check=False) == 0   # m = 0: quick return
     assert f(0, 1, 1, 2, 0, 4, 4, 1.0, 0, 4, 1, 4, check=False) == 1   # NULL A
+
+
+def test_batched_variant_argument_checks(H):
+    f = H.hsma_trsm_vbatched
+    assert f(0, 1, 0, 0, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 2   # right side: not batched
+    assert f(0, 0, 3, 0, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 1   # uplo
+    assert f(0, 0, 1, 5, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 1   # trans
+    assert f(2, 0, 1, 1, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 2   # dtype without a small path
+    assert f(0, 0, 1, 1, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, check=False) == 0   # empty batch

@@ -208,10 +208,15 @@ inline dim3 hsma_grid_rc(int64_t rows, int64_t cols) {
 //   (1 real, 4 complex); the first R term is the alpha*diag^{-1} scaling.
 // Staging the scaled triangle costs K * sum_i ceil((R*G - 1 - i)/32) per CTA.
 // ---------------------------------------------------------------------------
+// Rows a complex warp holds with G = 1 (two registers per value): 32 keeps the
+// batched kernel at three CTAs per SM.
+#ifndef HSMA_CPLX_G1_MMAX
+#define HSMA_CPLX_G1_MMAX 32
+#endif
 __host__ __device__ inline int hsma_small_rmax(int g, bool cplx_) {
   // register slots available per lane: 64 rows for any G, except complex G=1
   // which is limited to 32 rows (128 registers of X per lane)
-  return (cplx_ && g == 1) ? 32 : 64 / g;
+  return (cplx_ && g == 1) ? HSMA_CPLX_G1_MMAX : 64 / g;
 }
 
 __host__ __device__ inline bool hsma_small_g_ok(int g, int m, bool cplx_) {

@@ -203,7 +203,7 @@ struct Variants {
                                              int tile0, int step, int rev) {
     if constexpr ((kBatchedGMask & 1u) != 0) {
       if (g == 1) {
-        solve_tiles<T, 1, kCplx ? 32 : 64, MAP>(sTri, sC, B, ldb, m, n, tile0, step, rev);
+        solve_tiles<T, 1, kCplx ? HSMA_CPLX_G1_MMAX : 64, MAP>(sTri, sC, B, ldb, m, n, tile0, step, rev);
         return;
       }
     }
@@ -232,7 +232,7 @@ struct Variants {
 // complex G = 1 one (MMAX = 32); stage with the variant's MMAX.
 template <class T>
 __device__ __forceinline__ int variant_mmax(int g) {
-  return (Elem<T>::kComplex && g == 1) ? 32 : 64;
+  return (Elem<T>::kComplex && g == 1) ? HSMA_CPLX_G1_MMAX : 64;
 }
 
 template <class T, int W, bool MAP>

@@ -439,7 +439,8 @@ def run_batched_lu(args, dist, device):
                                "two varlen launches), m,n ~ U{8..64}, alpha=(1.5,-0.5)",
                    "l2": f"inputs larger than L2 ({abytes / 1e6:.0f} MB algorithmic per step)"},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP64_PEAK_GFLOPS, 1),
-                     "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                     "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                     "traffic": profile_traffic("vbatched_solve_lu_c128_8192.txt", SMALL_SOURCES),
                      "kernel": "vbatched_solve_kernel<cplx> (lower and upper maps)",
                      "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)"},
         "e2e": {"value": round(total * e2e_steps / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",

@@ -929,6 +929,13 @@ __global__ void scale_kernel(double *B, int64_t ldb, int64_t rows, int64_t n, do
 // real columns): inside a panel, each solved block updates only the panel's
 // remaining rows; below the panel, one update with K = h N_B covers all h
 // blocks.  The result is the same product sum, grouped differently.
+// Real columns per update panel of the emulated blocked solve (the panel's
+// trailing update runs with K = this many real columns).
+#ifndef HSMA_EMU_PANEL_COLS
+#define HSMA_EMU_PANEL_COLS 1024
+#endif
+constexpr int kEmuPanelCols = HSMA_EMU_PANEL_COLS;
+
 // Workspace of blocked_emulated: the inverses, one block row of B, and the
 // slices of an update panel, of one inverse and of the right operand.
 struct EmuLayout {
@@ -942,7 +949,7 @@ EmuLayout emu_layout(bool cplx, int nb, int64_t m, int64_t n) {
   EmuLayout L;
   L.W = cplx ? 2 : 1;
   const int64_t nblk = (m + nb - 1) / nb;
-  L.h = std::max(1, 1024 / (L.W * nb));
+  L.h = std::max(1, kEmuPanelCols / (L.W * nb));
   L.P = (int64_t)L.h * nb;  // panel width (source columns)
   L.Kpb = oz_kp((int64_t)L.W * nb);
   L.Kpp = oz_kp(L.W * L.P);

@@ -392,6 +392,17 @@ HSMA_API hsma_status_t hsma_gemm_f64_emulated(int64_t M, int64_t N, int64_t K, c
 HSMA_API hsma_status_t hsma_device_status(unsigned int *out);
 
 /*
+ * Self-check of the failure-detection path: one thread waits, with the same
+ * bounded mbarrier wait the tensor-core kernels use, on a barrier that nothing
+ * arrives on.  The wait gives up after limit_ns nanoseconds of wall time
+ * (1 ms .. 2 s), ORs HSMA_DEVERR_TIMEOUT into the device error word and the
+ * kernel writes 2 to the DEVICE int *d_returned (1 would mean the wait
+ * completed).  The context stays usable.  Asynchronous on `stream`.  Errors:
+ * INVALID_ARG for a null d_returned or a limit out of range.
+ */
+HSMA_API hsma_status_t hsma_check_wait_timeout(uint64_t limit_ns, int *d_returned, void *stream);
+
+/*
  * Phase tracing (off by default; also switched on by HSMA_PHASE_TIMING=1 in
  * the environment).  When on, the library records a pair of CUDA events
  * around every kernel it launches, named by phase: "small_single",

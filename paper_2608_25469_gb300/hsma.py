@@ -36,7 +36,7 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
-           "hsma_trsm_llnn_vbatched_host", "hsma_trsm", "hsma_trsm_vbatched",
+           "hsma_trsm_llnn_vbatched_host", "hsma_trsm", "hsma_trsm_vbatched", "hsma_check_wait_timeout",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -139,6 +139,8 @@ def _load():
     lib.hsma_server_destroy.restype = c_int
     lib.hsma_device_status.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.hsma_device_status.restype = c_int
+    lib.hsma_check_wait_timeout.argtypes = [ctypes.c_uint64, vp, vp]
+    lib.hsma_check_wait_timeout.restype = c_int
     return lib
 
 
@@ -317,6 +319,14 @@ def hsma_device_status() -> int:
     v = ctypes.c_uint()
     _check(_lib.hsma_device_status(ctypes.byref(v)), "hsma_device_status")
     return v.value
+
+
+def hsma_check_wait_timeout(limit_ns: int, d_returned: int, stream: int = 0, check: bool = True) -> int:
+    """Launch the self-check whose bounded wait runs out after limit_ns (device int at d_returned)."""
+    s = _lib.hsma_check_wait_timeout(int(limit_ns), d_returned or None, stream or None)
+    if check:
+        _check(s, "hsma_check_wait_timeout")
+    return s
 
 
 def hsma_trace_enable(on: bool) -> int:

@@ -172,3 +172,10 @@ def test_batched_variant_argument_checks(H):
     assert f(0, 0, 1, 5, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 1   # trans
     assert f(2, 0, 1, 1, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 2   # dtype without a small path
     assert f(0, 0, 1, 1, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, check=False) == 0   # empty batch
+
+
+def test_wait_check_argument_checks(H):
+    f = H.hsma_check_wait_timeout
+    assert f(10_000_000, 0, check=False) == 1          # NULL result pointer
+    assert f(999_999, 0x1000, check=False) == 1        # limit below 1 ms
+    assert f(2_000_000_001, 0x1000, check=False) == 1  # limit above 2 s

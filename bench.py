@@ -453,6 +453,8 @@ def run_batched_lu(args, dist, device):
 # the files that hold each profiled kernel (a summary's traffic is used only while they are unchanged)
 LARGE_SOURCES = ["paper_2608_25469_gb300/csrc/blocked.cu", "paper_2608_25469_gb300/csrc/tma.cuh"]
 EMU_SOURCES = ["paper_2608_25469_gb300/csrc/tc_gemm.cuh", "paper_2608_25469_gb300/csrc/tma.cuh"]
+# real columns per update panel of the emulated blocked solve (the library's HSMA_EMU_PANEL_COLS)
+EMU_PANEL_COLS = 2048
 
 
 def run_large(args, dist, device, code, m):
@@ -519,7 +521,7 @@ def run_large(args, dist, device, code, m):
         # blocks: per block an update of the panel's remaining rows (K = N_B),
         # per panel one update of the rows below it (K = h N_B)
         w = 2 if cplx_ else 1
-        h = max(1, 1024 // (w * nb))
+        h = max(1, EMU_PANEL_COLS // (w * nb))
         kp = lambda k: -(-(w * k) // 64) * 64  # noqa: E731
         bf16_flops = 0.0
         for R0 in range(0, m, h * nb):

@@ -53,3 +53,13 @@ def test_reference_arm_rank0_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "GFLOP/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_bench_emulated_panel_width_matches_library():
+    """bench.py counts the emulated update work with the library's panel width."""
+    import re
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_2608_25469_gb300", "csrc", "mixed.cu")).read()
+    lib = int(re.search(r"#define HSMA_EMU_PANEL_COLS (\d+)", src).group(1))
+    assert bench.EMU_PANEL_COLS == lib

@@ -222,18 +222,26 @@ HSMA_API hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int tra
 /*
  * The varlen batch with its matrices in HOST memory (no paper counterpart:
  * the paper's solves are device-resident).  The batch is cut into `chunks`
- * groups of consecutive instances (0 = 8); each group's host-to-device copy,
- * batched solve and device-to-host copy run on one of three internal streams,
- * so copies of some groups overlap the solves of others.
+ * groups of consecutive instances (0 = 8, at most 256).  The sizes and
+ * offsets are copied once; then the groups' host-to-device copies run in
+ * order on an internal copy-in stream, each group's batched solve starts (on
+ * one of two internal compute streams) as soon as its copy has landed, and
+ * its X goes back on an internal copy-out stream as soon as it is solved, so
+ * the copies overlap the solves.  Device workspace: the whole batch's A and B
+ * plus the per-instance tables (stream-ordered pool, released at the end).
  *
  * h_m, h_n: HOST arrays of `batch` sizes (0 <= m_i <= 64, n_i >= 0).
  * hA, hB: HOST buffers holding every A_i (column-major, lda = m_i, m_i^2
  *        elements at element offset h_offA[i]) and every B_i (ldb = m_i, m_i n_i
  *        elements at h_offB[i]); offsets increase and regions do not overlap.
- * hX: HOST buffer receiving X_i at h_offB[i] (may equal hB).
+ * hX: HOST buffer receiving X_i at h_offB[i] (may equal hB).  Each group is
+ *        copied as one range, so elements of hX lying between two instances
+ *        of a group receive the same elements of hB; nothing outside the
+ *        groups' ranges is written.
  * Use page-locked host memory for asynchronous copies (pageable memory works,
  * with synchronous staging).  The call is asynchronous on `stream`: hX is
- * valid, and hA / hB may be reused, once the stream has been synchronised.
+ * valid, and hA, hB, h_m, h_n, h_offA, h_offB may be reused, once the stream
+ * has been synchronised.
  * Results equal hsma_trsm_llnn_vbatched on the same data, bit for bit.
  * Errors: INVALID_ARG for a bad size, offset order or null pointer;
  * UNSUPPORTED for m_i > 64 or another dtype.  Concurrent calls share the

@@ -1,13 +1,15 @@
 // Varlen batch of small solves whose matrices live in host memory: the batch
-// is cut into chunks of consecutive instances, and each chunk's host-to-device
-// copy, solve (the persistent batched kernel) and device-to-host copy run on
-// one of three internal streams, so the copies of some chunks overlap the
-// solves of others (the copy engines and the SMs work at the same time).
+// is cut into chunks of consecutive instances; chunk copies to the device,
+// solves (the persistent batched kernel) and copies back run on separate
+// internal streams, so the copies of some chunks overlap the solves of others
+// (the copy engines and the SMs work at the same time).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <new>
 
 #include "../../include/hsma.h"
 #include "common.cuh"
@@ -17,31 +19,33 @@
 
 namespace {
 
-constexpr int kSlots = 3;
+constexpr int kStreams = 4;
+constexpr int32_t kMaxChunks = 256;
 
-struct SlotStreams {
-  cudaStream_t s[kSlots] = {};
+struct PipeStreams {
+  cudaStream_t s[kStreams] = {};
   bool ok = false;
 };
 
-// internal non-blocking streams, created once per device
-hsma_status_t slot_streams(cudaStream_t out[kSlots]) {
-  static SlotStreams per_dev[64];
+// internal non-blocking streams (copy-in, two compute, copy-out), created
+// once per device
+hsma_status_t pipe_streams(cudaStream_t out[kStreams]) {
+  static PipeStreams per_dev[64];
   static std::mutex mu;
   int d = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&d));
   if (d < 0 || d >= 64) return HSMA_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(mu);
-  SlotStreams &S = per_dev[d];
+  PipeStreams &S = per_dev[d];
   if (!S.ok) {
-    for (int k = 0; k < kSlots; ++k) HSMA_CUDA_TRY(cudaStreamCreateWithFlags(&S.s[k], cudaStreamNonBlocking));
+    for (int k = 0; k < kStreams; ++k) HSMA_CUDA_TRY(cudaStreamCreateWithFlags(&S.s[k], cudaStreamNonBlocking));
     S.ok = true;
   }
-  for (int k = 0; k < kSlots; ++k) out[k] = S.s[k];
+  for (int k = 0; k < kStreams; ++k) out[k] = S.s[k];
   return HSMA_OK;
 }
 
-// device pointers and leading dimensions of one chunk from its offsets
+// device pointers and leading dimensions of the instances from their offsets
 __global__ void chunk_meta_kernel(int count, const int32_t *__restrict__ m, const int64_t *__restrict__ offA,
                                   const int64_t *__restrict__ offB, int64_t baseA, int64_t baseB, char *dA, char *dB,
                                   int es, const void **pA, void **pB, int32_t *ld) {
@@ -50,6 +54,119 @@ __global__ void chunk_meta_kernel(int count, const int32_t *__restrict__ m, cons
   pA[i] = dA + (offA[i] - baseA) * es;
   pB[i] = dB + (offB[i] - baseB) * es;
   ld[i] = m[i] > 1 ? m[i] : 1;
+}
+
+// The whole batch's A and B get device buffers: the copy-in stream copies the
+// sizes and offsets, fills every instance's pointers, then copies A and B
+// chunk by chunk; each chunk's solve runs on one of two compute streams (so a
+// solve's tail overlaps the next one's start) once its copy has landed; the
+// copy-out stream returns each chunk's X as soon as it is solved.
+hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h_m, const int32_t *h_n,
+                            const void *alpha, const void *hA, const int64_t *h_offA, const void *hB,
+                            const int64_t *h_offB, void *hX, int nch, int32_t per, int es, cudaStream_t caller,
+                            const cudaStream_t ss[kStreams]) {
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const int64_t extA = h_offA[batch - 1] + (int64_t)h_m[batch - 1] * h_m[batch - 1] - h_offA[0];
+  const int64_t extB = h_offB[batch - 1] + (int64_t)h_m[batch - 1] * h_n[batch - 1] - h_offB[0];
+  const size_t mi_b = al(sizeof(int32_t) * batch), oi_b = al(sizeof(int64_t) * batch);
+  const size_t p_b = al(sizeof(void *) * batch);
+  const size_t a_b = al((size_t)extA * es), b_b = al((size_t)extB * es);
+  const size_t scr_b = al(hsma_vbatched_scratch_bytes(per));
+  const size_t total = a_b + b_b + 3 * mi_b + 2 * oi_b + 2 * p_b + scr_b * nch;
+  std::unique_ptr<cudaEvent_t[]> evs(new (std::nothrow) cudaEvent_t[2 * nch]());  // copied-in, solved
+  if (!evs) return HSMA_ERR_NO_MEMORY;
+  cudaEvent_t *ev = evs.get();
+  void *ws = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&ws, total, caller);
+  if (s != HSMA_OK) return s;
+  char *q = static_cast<char *>(ws);
+  char *dA = q, *dB = q + a_b;
+  q += a_b + b_b;
+  int32_t *gm = reinterpret_cast<int32_t *>(q), *gn = reinterpret_cast<int32_t *>(q + mi_b);
+  int32_t *gld = reinterpret_cast<int32_t *>(q + 2 * mi_b);
+  q += 3 * mi_b;
+  int64_t *goA = reinterpret_cast<int64_t *>(q), *goB = reinterpret_cast<int64_t *>(q + oi_b);
+  q += 2 * oi_b;
+  const void **pA = reinterpret_cast<const void **>(q);
+  void **pB = reinterpret_cast<void **>(q + p_b);
+  q += 2 * p_b;
+  int32_t *scr0 = reinterpret_cast<int32_t *>(q);
+  cudaStream_t s_in = ss[0], s_out = ss[3];
+  const cudaStream_t s_k[2] = {ss[1], ss[2]};
+  auto fail = [](cudaError_t e) { return e == cudaSuccess ? HSMA_OK : hsma_from_cuda(e); };
+  cudaEvent_t start = nullptr, fin = nullptr;
+  do {
+    if ((s = fail(cudaEventCreateWithFlags(&start, cudaEventDisableTiming))) != HSMA_OK) break;
+    if ((s = fail(cudaEventCreateWithFlags(&fin, cudaEventDisableTiming))) != HSMA_OK) break;
+    for (int k = 0; k < 2 * nch && s == HSMA_OK; ++k) s = fail(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
+    if (s != HSMA_OK) break;
+    if ((s = fail(cudaEventRecord(start, caller))) != HSMA_OK) break;
+    for (int k = 0; k < kStreams && s == HSMA_OK; ++k) s = fail(cudaStreamWaitEvent(ss[k], start, 0));
+    if (s != HSMA_OK) break;
+    {
+      HsmaTraceScope ts("host_h2d", s_in);
+      if ((s = fail(cudaMemcpyAsync(gm, h_m, sizeof(int32_t) * batch, cudaMemcpyHostToDevice, s_in))) != HSMA_OK)
+        break;
+      if ((s = fail(cudaMemcpyAsync(gn, h_n, sizeof(int32_t) * batch, cudaMemcpyHostToDevice, s_in))) != HSMA_OK)
+        break;
+      if ((s = fail(cudaMemcpyAsync(goA, h_offA, sizeof(int64_t) * batch, cudaMemcpyHostToDevice, s_in))) !=
+          HSMA_OK)
+        break;
+      if ((s = fail(cudaMemcpyAsync(goB, h_offB, sizeof(int64_t) * batch, cudaMemcpyHostToDevice, s_in))) !=
+          HSMA_OK)
+        break;
+    }
+    chunk_meta_kernel<<<(batch + 255) / 256, 256, 0, s_in>>>(batch, gm, goA, goB, h_offA[0], h_offB[0], dA, dB, es,
+                                                             pA, pB, gld);
+    if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
+    for (int c = 0; c < nch && s == HSMA_OK; ++c) {
+      const int32_t b = c * per, e = std::min(batch, b + per), cnt = e - b;
+      if (cnt <= 0) {
+        s = fail(cudaEventRecord(ev[2 * c], s_in));
+        if (s == HSMA_OK) s = fail(cudaEventRecord(ev[2 * c + 1], s_in));
+        continue;
+      }
+      const int64_t a0 = h_offA[b] - h_offA[0], b0 = h_offB[b] - h_offB[0];
+      const int64_t na = h_offA[e - 1] + (int64_t)h_m[e - 1] * h_m[e - 1] - h_offA[b];
+      const int64_t nbx = h_offB[e - 1] + (int64_t)h_m[e - 1] * h_n[e - 1] - h_offB[b];
+      {
+        HsmaTraceScope ts("host_h2d", s_in);
+        if ((s = fail(cudaMemcpyAsync(dA + a0 * es, static_cast<const char *>(hA) + h_offA[b] * es, (size_t)na * es,
+                                      cudaMemcpyHostToDevice, s_in))) != HSMA_OK)
+          break;
+        if ((s = fail(cudaMemcpyAsync(dB + b0 * es, static_cast<const char *>(hB) + h_offB[b] * es,
+                                      (size_t)nbx * es, cudaMemcpyHostToDevice, s_in))) != HSMA_OK)
+          break;
+      }
+      if ((s = fail(cudaEventRecord(ev[2 * c], s_in))) != HSMA_OK) break;
+      cudaStream_t sk = s_k[c & 1];
+      if ((s = fail(cudaStreamWaitEvent(sk, ev[2 * c], 0))) != HSMA_OK) break;
+      int32_t *scr = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scr0) + scr_b * c);
+      s = hsma_small_vbatched(dtype, cnt, gm + b, gn + b, static_cast<const double *>(alpha), pA + b, gld + b, pB + b,
+                              gld + b, diag == HSMA_UNIT, nullptr, scr, sk);
+      if (s != HSMA_OK) break;
+      if ((s = fail(cudaEventRecord(ev[2 * c + 1], sk))) != HSMA_OK) break;
+      if ((s = fail(cudaStreamWaitEvent(s_out, ev[2 * c + 1], 0))) != HSMA_OK) break;
+      {
+        HsmaTraceScope ts("host_d2h", s_out);
+        if ((s = fail(cudaMemcpyAsync(static_cast<char *>(hX) + h_offB[b] * es, dB + b0 * es, (size_t)nbx * es,
+                                      cudaMemcpyDeviceToHost, s_out))) != HSMA_OK)
+          break;
+      }
+    }
+    // the caller's stream resumes when every internal stream is done
+    for (int k = 0; k < kStreams; ++k) {
+      hsma_status_t r = fail(cudaEventRecord(fin, ss[k]));
+      if (r == HSMA_OK) r = fail(cudaStreamWaitEvent(caller, fin, 0));
+      if (s == HSMA_OK) s = r;
+    }
+  } while (0);
+  if (start) cudaEventDestroy(start);
+  if (fin) cudaEventDestroy(fin);
+  for (int k = 0; k < 2 * nch; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  hsma_status_t f = hsma_ws_free(ws, caller);
+  return s != HSMA_OK ? s : f;
 }
 
 }  // namespace
@@ -76,95 +193,11 @@ extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int di
       return HSMA_ERR_INVALID_ARG;
   }
   const int es = hsma_small_esize(dtype);
-  const int nch = std::min<int32_t>(batch, chunks > 0 ? chunks : 8);
+  const int nch = std::min<int32_t>(batch, chunks > 0 ? std::min<int32_t>(chunks, kMaxChunks) : 8);
   const int32_t per = (batch + nch - 1) / nch;
-  // element extents of each chunk in the packed buffers
-  auto extA = [&](int32_t b, int32_t e) { return h_offA[e - 1] + (int64_t)h_m[e - 1] * h_m[e - 1] - h_offA[b]; };
-  auto extB = [&](int32_t b, int32_t e) { return h_offB[e - 1] + (int64_t)h_m[e - 1] * h_n[e - 1] - h_offB[b]; };
-  int64_t maxA = 0, maxB = 0;
-  for (int c = 0; c < nch; ++c) {
-    const int32_t b = c * per, e = std::min(batch, b + per);
-    if (b >= e) continue;
-    maxA = std::max(maxA, extA(b, e));
-    maxB = std::max(maxB, extB(b, e));
-  }
-  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t a_b = al((size_t)maxA * es), b_b = al((size_t)maxB * es);
-  const size_t meta_b = al(sizeof(int32_t) * per) * 3 + al(sizeof(int64_t) * per) * 2 + al(sizeof(void *) * per) * 2;
-  const size_t scr_b = al(hsma_vbatched_scratch_bytes(per));
-  const size_t slot_b = a_b + b_b + meta_b + scr_b;
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
-  cudaStream_t ss[kSlots];
-  hsma_status_t s = slot_streams(ss);
+  cudaStream_t ss[kStreams];
+  hsma_status_t s = pipe_streams(ss);
   if (s != HSMA_OK) return s;
-  void *ws = nullptr;
-  if ((s = hsma_ws_alloc(&ws, slot_b * kSlots, caller)) != HSMA_OK) return s;
-  cudaEvent_t start = nullptr, done[kSlots] = {};
-  auto fail = [](cudaError_t e) { return e == cudaSuccess ? HSMA_OK : hsma_from_cuda(e); };
-  do {
-    if ((s = fail(cudaEventCreateWithFlags(&start, cudaEventDisableTiming))) != HSMA_OK) break;
-    if ((s = fail(cudaEventRecord(start, caller))) != HSMA_OK) break;
-    for (int k = 0; k < kSlots && s == HSMA_OK; ++k) {
-      s = fail(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming));
-      if (s == HSMA_OK) s = fail(cudaStreamWaitEvent(ss[k], start, 0));
-    }
-    for (int c = 0; c < nch && s == HSMA_OK; ++c) {
-      const int32_t b = c * per, e = std::min(batch, b + per), cnt = e - b;
-      if (cnt <= 0) continue;
-      cudaStream_t st = ss[c % kSlots];
-      char *slot = static_cast<char *>(ws) + slot_b * (c % kSlots);
-      char *dA = slot, *dB = slot + a_b;
-      char *meta = slot + a_b + b_b;
-      int32_t *dm = reinterpret_cast<int32_t *>(meta);
-      int32_t *dn = reinterpret_cast<int32_t *>(meta + al(sizeof(int32_t) * per));
-      int32_t *dld = reinterpret_cast<int32_t *>(meta + 2 * al(sizeof(int32_t) * per));
-      int64_t *doA = reinterpret_cast<int64_t *>(meta + 3 * al(sizeof(int32_t) * per));
-      int64_t *doB = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(doA) + al(sizeof(int64_t) * per));
-      const void **pA = reinterpret_cast<const void **>(reinterpret_cast<char *>(doB) + al(sizeof(int64_t) * per));
-      void **pB = reinterpret_cast<void **>(reinterpret_cast<char *>(pA) + al(sizeof(void *) * per));
-      int32_t *scr = reinterpret_cast<int32_t *>(meta + meta_b);
-      {
-        HsmaTraceScope ts("host_h2d", st);
-        const char *srcA = static_cast<const char *>(hA) + h_offA[b] * es;
-        const char *srcB = static_cast<const char *>(hB) + h_offB[b] * es;
-        if ((s = fail(cudaMemcpyAsync(dA, srcA, (size_t)extA(b, e) * es, cudaMemcpyHostToDevice, st))) != HSMA_OK)
-          break;
-        if ((s = fail(cudaMemcpyAsync(dB, srcB, (size_t)extB(b, e) * es, cudaMemcpyHostToDevice, st))) != HSMA_OK)
-          break;
-        if ((s = fail(cudaMemcpyAsync(dm, h_m + b, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st))) != HSMA_OK)
-          break;
-        if ((s = fail(cudaMemcpyAsync(dn, h_n + b, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st))) != HSMA_OK)
-          break;
-        if ((s = fail(cudaMemcpyAsync(doA, h_offA + b, sizeof(int64_t) * cnt, cudaMemcpyHostToDevice, st))) !=
-            HSMA_OK)
-          break;
-        if ((s = fail(cudaMemcpyAsync(doB, h_offB + b, sizeof(int64_t) * cnt, cudaMemcpyHostToDevice, st))) !=
-            HSMA_OK)
-          break;
-      }
-      chunk_meta_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(cnt, dm, doA, doB, h_offA[b], h_offB[b], dA, dB, es, pA,
-                                                           pB, dld);
-      if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
-      s = hsma_small_vbatched(dtype, cnt, dm, dn, static_cast<const double *>(alpha), pA, dld, pB, dld,
-                              diag == HSMA_UNIT, nullptr, scr, st);
-      if (s != HSMA_OK) break;
-      {
-        HsmaTraceScope ts("host_d2h", st);
-        char *dst = static_cast<char *>(hX) + h_offB[b] * es;
-        if ((s = fail(cudaMemcpyAsync(dst, dB, (size_t)extB(b, e) * es, cudaMemcpyDeviceToHost, st))) != HSMA_OK)
-          break;
-      }
-    }
-    for (int k = 0; k < kSlots; ++k) {
-      if (done[k] == nullptr) continue;
-      hsma_status_t r = fail(cudaEventRecord(done[k], ss[k]));
-      if (r == HSMA_OK) r = fail(cudaStreamWaitEvent(caller, done[k], 0));
-      if (s == HSMA_OK) s = r;
-    }
-  } while (0);
-  if (start) cudaEventDestroy(start);
-  for (int k = 0; k < kSlots; ++k)
-    if (done[k]) cudaEventDestroy(done[k]);
-  hsma_status_t f = hsma_ws_free(ws, caller);
-  return s != HSMA_OK ? s : f;
+  return full_pipeline(dtype, diag, batch, h_m, h_n, alpha, hA, h_offA, hB, h_offB, hX, nch, per, es, caller, ss);
 }

@@ -196,7 +196,7 @@ def test_device_generator_matches_host(H, code):
 
 
 @pytest.mark.parametrize("code", [I.R64, I.C128])
-@pytest.mark.parametrize("chunks,pinned", [(0, True), (1, True), (3, False), (7, True)])
+@pytest.mark.parametrize("chunks,pinned", [(0, True), (1, True), (3, False), (7, True), (1000, True)])
 def test_batched_host_buffers_equal_device_batch(H, code, chunks, pinned):
     """The host-buffer entry point (chunked copies overlapped with the solves) gives the
     device-resident batch's results bit for bit, pinned or pageable host memory."""
@@ -224,3 +224,35 @@ def test_batched_host_buffers_equal_device_batch(H, code, chunks, pinned):
     for b in range(len(As)):
         got = out[offB[b]:offB[b] + ms[b] * ns[b]].reshape((ms[b], ns[b]), order="F")
         assert np.array_equal(got, dev[b]), b
+
+
+def test_host_buffers_with_gaps_and_empty_instances(H):
+    """Offsets with gaps between instances (never read nor written) and instances with
+    m = 0 or n = 0 (skipped): the solved instances equal the device batch's results."""
+    import torch
+    alpha = 0.5 - 1.5j
+    As, Bs = _config1(I.C128, batch=300, seed=12)
+    for b in range(0, 300, 37):  # empty instances
+        As[b] = np.zeros((0, 0), np.complex128) if b % 2 else As[b]
+        Bs[b] = np.zeros((As[b].shape[0], 0), np.complex128) if b % 2 == 0 else np.zeros((0, 0), np.complex128)
+    dev = _run_batch(H, I.C128, As, Bs, alpha).results()
+    ms = np.array([a.shape[1] for a in As], dtype=np.int32)
+    ns = np.array([b.shape[1] for b in Bs], dtype=np.int32)
+    gap = 5
+    offA = np.concatenate([[3], 3 + np.cumsum(ms.astype(np.int64) ** 2 + gap)[:-1]]).astype(np.int64)
+    offB = np.concatenate([[2], 2 + np.cumsum(ms.astype(np.int64) * ns + gap)[:-1]]).astype(np.int64)
+    hA = np.full(int(offA[-1] + ms[-1] ** 2 + gap), np.nan, np.complex128)
+    hB = np.full(int(offB[-1] + ms[-1] * ns[-1] + gap), np.nan, np.complex128)
+    for b in range(len(As)):
+        hA[offA[b]:offA[b] + ms[b] ** 2] = As[b].ravel(order="F")
+        hB[offB[b]:offB[b] + ms[b] * ns[b]] = Bs[b].ravel(order="F")
+    hX = np.full_like(hB, 7.0)
+    H.hsma_trsm_llnn_vbatched_host(I.C128, 0, len(As), ms, ns, alpha, hA.ctypes.data, offA, hB.ctypes.data, offB,
+                                   hX.ctypes.data, chunks=5, stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    touched = np.zeros(hX.size, bool)
+    for b in range(len(As)):
+        sl = slice(offB[b], offB[b] + ms[b] * ns[b])
+        touched[sl] = True
+        assert np.array_equal(hX[sl].reshape((ms[b], ns[b]), order="F"), dev[b]), b
+    assert np.all(hX[:2] == 7.0) and np.all(hX[-gap:] == 7.0)

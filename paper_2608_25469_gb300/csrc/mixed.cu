@@ -137,10 +137,10 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
 
 // A panel (rows x nb, column-major fp32, lda) -> A' rows x Kp row-major BF16:
 // terms 1: [hi], terms 3: [hi | hi | lo]; columns past terms*nb are zero.
-__global__ void __launch_bounds__(256) convert_panel_kernel(const float *__restrict__ A, int64_t lda, int rows,
-                                                            int nb, int terms, int Kp, __nv_bfloat16 *out) {
+// One 32 x 32 tile (rows i0.., columns k0..) per CTA of 256 threads.
+__device__ __forceinline__ void convert_panel_tile(const float *__restrict__ A, int64_t lda, int rows, int nb,
+                                                   int terms, int Kp, __nv_bfloat16 *out, int i0, int k0) {
   __shared__ float tile[32][33];
-  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int kk = ty; kk < 32; kk += 8) {
     const int i = i0 + tx, k = k0 + kk;
@@ -161,8 +161,26 @@ __global__ void __launch_bounds__(256) convert_panel_kernel(const float *__restr
       }
     }
     // zero padding columns [terms*nb, Kp)
-    for (int kp = terms * nb + k0 + tx; kp < Kp && blockIdx.y == 0; kp += 32) o[kp] = __float2bfloat16_rn(0.0f);
+    for (int kp = terms * nb + k0 + tx; kp < Kp && k0 == 0; kp += 32) o[kp] = __float2bfloat16_rn(0.0f);
   }
+}
+
+__global__ void __launch_bounds__(256) convert_panel_kernel(const float *__restrict__ A, int64_t lda, int rows,
+                                                            int nb, int terms, int Kp, __nv_bfloat16 *out) {
+  convert_panel_tile(A, lda, rows, nb, terms, Kp, out, blockIdx.x * 32, blockIdx.y * 32);
+}
+
+// Every step's panel in one launch (blockIdx.z = step r < nblk - 1, whose
+// diagonal block is full): rows m - (r+1) nb below the block, stored at
+// element offset (r m - nb r (r+1) / 2) Kp, the sum of the earlier panels.
+__global__ void __launch_bounds__(256) convert_panels_kernel(const float *__restrict__ A, int64_t lda, int64_t m,
+                                                             int nb, int terms, int Kp, __nv_bfloat16 *panels) {
+  const int64_t r = blockIdx.z, r0 = r * nb;
+  const int rows = (int)(m - r0 - nb);
+  const int i0 = blockIdx.x * 32;
+  if (i0 >= rows) return;  // uniform over the CTA
+  const int64_t off = (r * m - (int64_t)nb * r * (r + 1) / 2) * Kp;
+  convert_panel_tile(A + (r0 + nb) + r0 * lda, lda, rows, nb, terms, Kp, panels + off, i0, blockIdx.y * 32);
 }
 
 // X_r (nb x n, column-major fp32, ldx) -> X' n x Kp row-major BF16:
@@ -320,14 +338,10 @@ hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
                                                                                  P.dslices);
     HSMA_CUDA_TRY(cudaGetLastError());
   }
-  if (!keep_panels) return HSMA_OK;
-  for (int64_t r = 0; r + 1 < nblk; ++r) {
-    const int64_t r0 = r * P.nb, sr = std::min<int64_t>(P.nb, P.m - r0);
-    const int rows = (int)panel_rows(P, r);
-    dim3 g1((rows + 31) / 32, (P.nb + 31) / 32);
-    convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, P.nb, P.terms, P.Kp,
-                                             P.panels + panel_off(P, r));
-  }
+  if (!keep_panels || nblk < 2) return HSMA_OK;
+  if (nblk - 1 > 65535) return HSMA_ERR_UNSUPPORTED;
+  const dim3 g((unsigned)((P.m - P.nb + 31) / 32), (unsigned)((P.nb + 31) / 32), (unsigned)(nblk - 1));
+  convert_panels_kernel<<<g, 256, 0, st>>>(P.A, P.lda, P.m, P.nb, P.terms, P.Kp, P.panels);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }
@@ -339,7 +353,7 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
   const int nb = P.nb, Kp = P.Kp;
   const int64_t m = P.m, nblk = (m + nb - 1) / nb;
   const int64_t rows_max = std::max<int64_t>(m - nb, 1);
-  const size_t w_b = sizeof(float) * (size_t)nb * n;
+  const size_t w_b = P.tc_solve ? 0 : sizeof(float) * (size_t)nb * n;
   const size_t a_b = P.panels ? 0 : sizeof(__nv_bfloat16) * (size_t)rows_max * Kp;
   const size_t x_b = sizeof(__nv_bfloat16) * (size_t)n * Kp;
   const int Kd = r32_kd(nb);
@@ -369,14 +383,17 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
   for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
     const int64_t r0 = r * nb;
     const int sr = (int)std::min<int64_t>(nb, m - r0);
-    {
+    if (!P.tc_solve) {
       HsmaTraceScope ts("copy", st);
       copy_f32_kernel<<<hsma_grid_rc(sr, n), 256, 0, st>>>(B + r0, ldb, W, nb, sr, n, skip);
     }
     if (P.tc_solve) {
+      // the product reads only the slices, so they are cut from B_r itself
+      // and X_r is written straight back into B_r
       {
         HsmaTraceScope ts("convert", st);
-        r32_xslice_kernel<<<hsma_grid_rc(Kd, n), 256, 0, st>>>(W, nb, sr, n, Kd, r == 0 ? alpha : 1.0f, X3, skip);
+        r32_xslice_kernel<<<hsma_grid_rc(Kd, n), 256, 0, st>>>(B + r0, ldb, sr, n, Kd, r == 0 ? alpha : 1.0f, X3,
+                                                                skip);
         if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
       }
       sa.C32 = B + r0;
@@ -438,14 +455,19 @@ hsma_status_t r32_solve(int nb, int terms, const float *A, int64_t lda, float *B
   P.lda = lda;
   P.unit = unit;
   const int64_t nblk = (m + nb - 1) / nb;
-  const size_t dinv_b = (sizeof(float) * (size_t)nblk * nb * nb + 1023) & ~(size_t)1023;
+  auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+  const size_t dinv_b = al(sizeof(float) * (size_t)nblk * nb * nb);
+  const size_t ds_b = al(sizeof(__nv_bfloat16) * r32_dslices_elems(nb, m));
+  // every step's A panel is converted up front, in one launch
+  const size_t pan_b = al(sizeof(__nv_bfloat16) * r32_panels_elems(nb, terms, m));
   void *ws = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&ws, dinv_b + sizeof(__nv_bfloat16) * r32_dslices_elems(nb, m), st);
+  hsma_status_t s = hsma_ws_alloc(&ws, dinv_b + ds_b + pan_b, st);
   if (s != HSMA_OK) return s;
   P.Dinv = static_cast<float *>(ws);
   P.tc_solve = true;
   P.dslices = reinterpret_cast<__nv_bfloat16 *>(static_cast<unsigned char *>(ws) + dinv_b);
-  s = r32_prepare(P, false, st);
+  P.panels = reinterpret_cast<__nv_bfloat16 *>(static_cast<unsigned char *>(ws) + dinv_b + ds_b);
+  s = r32_prepare(P, true, st);
   if (s == HSMA_OK) s = r32_apply(P, B, ldb, n, alpha, nullptr, st);
   hsma_status_t f = hsma_ws_free(ws, st);
   return s != HSMA_OK ? s : f;

@@ -91,6 +91,7 @@ typedef enum { HSMA_PATH_AUTO = 0, HSMA_PATH_SMALL = 1, HSMA_PATH_BLOCKED = 2 } 
 /* Bits OR-ed into a caller-provided device status word by the batched kernel. */
 #define HSMA_DEVERR_BAD_SIZE 0x1u  /* an instance had m<0, n<0, m>64 or ld < max(1,m) */
 #define HSMA_DEVERR_NULL_PTR 0x2u  /* an instance with m*n > 0 had a NULL A or B      */
+#define HSMA_DEVERR_BAD_PIVOT 0x8u /* hsma_getrs_vbatched: a pivot outside [k+1, m]   */
 
 /* Plan chosen for one solve (Section 4.1's dispatcher and Section 4.3.2's
  * configuration lookup). */
@@ -218,6 +219,35 @@ HSMA_API hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int tra
                                           const void *const *d_A, const int32_t *d_lda, void *const *d_B,
                                           const int32_t *d_ldb, int32_t max_m, int32_t max_n, uint32_t *d_status,
                                           void *stream);
+
+/*
+ * Varlen batch of LU-factor solves in ONE launch: the small solve fused with
+ * its consumer, for the LU factorisations that motivate the paper (Section 1;
+ * fusion at small scales is its future work, Section 6).  Instance i holds
+ * A_i = P_i L_i U_i as LAPACK getrf leaves it: one m_i x m_i column-major
+ * array (ld d_lda[i]) with L_i's multipliers below the diagonal (unit
+ * diagonal, not stored) and U_i on and above it.  Then
+ *     X_i = U_i^{-1} L_i^{-1} P_i^T (alpha B_i)   overwrites B_i,
+ * i.e. A_i X_i = alpha B_i.  Per instance one CTA applies the row
+ * interchanges, solves with L_i and then with U_i (the upper solve through
+ * the left / upper index map); the intermediate stays in that CTA's cache.
+ *
+ * d_ipiv: NULL (no interchanges) or a DEVICE array of `batch` DEVICE pointers,
+ *        each to instance i's m_i int32 pivots in LAPACK's convention
+ *        (1-based; row k was interchanged with row ipiv[k] >= k, in order
+ *        k = 1..m_i); a NULL entry means no interchanges for that instance.
+ * dtype, batch, d_m, d_n, alpha, d_lda, d_B, d_ldb, max_m, max_n: as for
+ *        hsma_trsm_llnn_vbatched (alpha = 0 gives X_i = 0).
+ * d_status: as for hsma_trsm_llnn_vbatched, plus HSMA_DEVERR_BAD_PIVOT for an
+ *        instance with a pivot outside [k, m_i] (that instance's B_i is left
+ *        untouched).
+ * Results equal two hsma_trsm_vbatched calls (unit lower, then upper) on the
+ * interchanged B, bit for bit.  Errors as hsma_trsm_llnn_vbatched.
+ */
+HSMA_API hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
+                                           const void *alpha, const void *const *d_LU, const int32_t *d_lda,
+                                           const int32_t *const *d_ipiv, void *const *d_B, const int32_t *d_ldb,
+                                           int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream);
 
 /*
  * The varlen batch with its matrices in HOST memory (no paper counterpart:

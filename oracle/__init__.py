@@ -15,12 +15,18 @@ Every function cites the passage it follows:
   acceptance measure for the solve; Frobenius norms as in Table 2's metric).
 * ``forward_error``: normwise relative forward error ||X - X_ref||_F / ||X_ref||_F,
   the measure of Table 2.
+* ``solve_general``: the BLAS variants (side, uplo, trans, diag) by definition.
+* ``getrs``: the solve from LU factors (Section 1's motivating use): row
+  interchanges in order, then the unit-lower and the upper solve.
 
 Pins (see ``tests/test_oracle_pins.py``): identity and diagonal A, the unit
 lower-bidiagonal closed form, exact rational elimination on small dyadic inputs,
 LAPACK's triangular solve, the backward-error bound, and invariants (upper
 triangle never read, unit diagonal never read, columns independent, complex with
-zero imaginary part equals real).
+zero imaginary part equals real).  ``getrs`` is pinned in
+``tests/test_oracle_getrs.py``: LAPACK's getrs (scipy's lu_solve) as a black box,
+the residual of P L U X = alpha B, the exact permutation-only case, and the
+same interchanges written as a permutation matrix.
 """
 from __future__ import annotations
 
@@ -161,6 +167,23 @@ def solve_general(A: np.ndarray, B: np.ndarray, alpha, side: int = 0, uplo: int 
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return X
+
+
+def getrs(LU: np.ndarray, ipiv, B: np.ndarray, alpha, _lib=None) -> np.ndarray:
+    """Solve A X = alpha B from A's LU factors as LAPACK getrf packs them (A = P L U: L unit
+    lower below the diagonal of LU, U on and above it; ipiv 1-based, row k interchanged with
+    row ipiv[k] in order k = 1..m, or None for no interchanges), by the definition
+    X = U^{-1} L^{-1} P^T (alpha B): the interchanges applied to B in order, then the two
+    triangular solves (Section 1's motivating use of the solve)."""
+    Y = np.array(B, order="F", copy=True)
+    if ipiv is not None:
+        for k, p in enumerate(np.asarray(ipiv, dtype=np.int64)):
+            p = int(p) - 1
+            if not k <= p < Y.shape[0]:
+                raise ValueError("pivot out of range")
+            Y[[k, p], :] = Y[[p, k], :]
+    Y = solve_general(LU, Y, alpha, 0, 0, 0, True, _lib=_lib)
+    return solve_general(LU, Y, 1.0, 0, 1, 0, False, _lib=_lib)
 
 
 def solve_cols(A: np.ndarray, B: np.ndarray, alpha, cols, unit: bool = False) -> np.ndarray:

@@ -21,6 +21,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhsma.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The small-case kernels instantiate many fully unrolled variants (row groups,
+# index maps, element types); their device code is compiled in parallel pieces.
+PER_FILE_FLAGS = {"small.cu": ["-split-compile=0"]}
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden"]
 
@@ -63,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
-        cmd = [nvcc, *flags, "-c", src, "-o", obj]
+        cmd = [nvcc, *flags, *PER_FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -73,7 +76,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     try:
         with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-            objs = list(ex.map(compile_one, _sources()))
+            # the slowest translation unit first
+            srcs = sorted(_sources(), key=lambda p: os.path.basename(p) not in PER_FILE_FLAGS)
+            objs = list(ex.map(compile_one, srcs))
         fd, tmp = tempfile.mkstemp(prefix="libhsma.", suffix=".so", dir=BUILD)
         os.close(fd)
         libdir = _cuda_lib_dir(nvcc)

@@ -268,6 +268,30 @@ hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int d
   return s != HSMA_OK ? s : f;
 }
 
+hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
+                                  const void *alpha, const void *const *d_LU, const int32_t *d_lda,
+                                  const int32_t *const *d_ipiv, void *const *d_B, const int32_t *d_ldb,
+                                  int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream) {
+  if (!hsma_small_dtype(dtype)) {
+    return valid_dtype(dtype) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
+  }
+  if (batch < 0 || max_m < 0 || max_n < 0) return HSMA_ERR_INVALID_ARG;
+  if (max_m > 64) return HSMA_ERR_UNSUPPORTED;
+  if (batch > (1 << 24) - 1) return HSMA_ERR_UNSUPPORTED;
+  if (batch == 0) return HSMA_OK;
+  if (alpha == nullptr || d_m == nullptr || d_n == nullptr || d_LU == nullptr || d_lda == nullptr ||
+      d_B == nullptr || d_ldb == nullptr)
+    return HSMA_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *scratch = nullptr;
+  hsma_status_t s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
+  if (s != HSMA_OK) return s;
+  s = hsma_small_getrs_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_LU, d_lda, d_ipiv,
+                                d_B, d_ldb, d_status, static_cast<int32_t *>(scratch), st);
+  hsma_status_t f = hsma_ws_free(scratch, st);
+  return s != HSMA_OK ? s : f;
+}
+
 hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64_t inst, int64_t m, int64_t cols, void *dst,
                               int64_t ld, void *stream) {
   if ((dtype != HSMA_R64 && dtype != HSMA_C128) || (kind != 0 && kind != 1)) return HSMA_ERR_INVALID_ARG;

@@ -432,6 +432,128 @@ __global__ void __launch_bounds__(32 * kWarpsBatched,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Varlen batch of LU-factor solves in one launch: the small solve fused with
+// its consumer.  Per instance the CTA applies the row interchanges to B,
+// stages the unit-lower factor and solves, then stages the upper factor in
+// row-reversed form (the left / upper index map) and solves again on the
+// intermediate result, which the same CTA has just written (cache resident).
+// ---------------------------------------------------------------------------
+
+// Row interchanges k <-> ipiv[k]-1, k = 0..m-1 in order, applied to B as one
+// gather (row r takes the old row perm[r]).  False, with B untouched, when a
+// pivot lies outside [k, m).  All threads of the CTA take part.
+template <class T>
+__device__ __forceinline__ bool lu_permute_rows(T *B, int64_t ldb, int m, int n, const int32_t *__restrict__ ipiv,
+                                                int *sPiv, int *sPerm, int *sBad) {
+  using E = Elem<T>;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) sPiv[k] = ipiv[k] - 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int bad = 0;
+    for (int r = 0; r < m; ++r) sPerm[r] = r;
+    for (int k = 0; k < m && !bad; ++k) {
+      const int p = sPiv[k];
+      if (p < k || p >= m) {
+        bad = 1;
+      } else {
+        const int t = sPerm[k];
+        sPerm[k] = sPerm[p];
+        sPerm[p] = t;
+      }
+    }
+    *sBad = bad;
+  }
+  __syncthreads();
+  if (*sBad) return false;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p0 = lane < m ? sPerm[lane] : 0, p1 = lane + 32 < m ? sPerm[lane + 32] : 0;
+  for (int j = warp; j < n; j += kWarpsBatched) {  // warp-uniform: every lane shuffles
+    T *col = B + (int64_t)j * ldb;
+    const T v0 = lane < m ? E::ld(col + lane) : E::zero();
+    const T v1 = lane + 32 < m ? E::ld(col + lane + 32) : E::zero();
+    const T a0 = E::shfl(v0, p0 & 31), b0 = E::shfl(v1, p0 & 31);
+    const T a1 = E::shfl(v0, p1 & 31), b1 = E::shfl(v1, p1 & 31);
+    if (lane < m) E::st(col + lane, p0 < 32 ? a0 : b0);
+    if (lane + 32 < m) E::st(col + lane + 32, p1 < 32 ? a1 : b1);
+  }
+  __syncthreads();
+  return true;
+}
+
+// One triangular solve of the LU pair: stage (with the map) and solve every
+// column tile.  Kept out of line so the compiler handles each of the two
+// solves once, not the fused kernel as one body.
+template <class T, bool MAP>
+__device__ __noinline__ void lu_stage_solve(int g, T *sTri, T *sC, T *sR, const T *A, int64_t lda, T *B,
+                                            int64_t ldb, int m, int n, T alpha, bool unit, SmallMap mp) {
+  stage_any<T, kWarpsBatched, MAP>(g, sTri, sC, sR, A, lda, m, alpha, unit, mp);
+  Variants<T, MAP>::run(g, sTri, sC, B, ldb, m, n, 0, kWarpsBatched, mp.rev);
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * kWarpsBatched,
+                                  (sizeof(T) == sizeof(float) || sizeof(T) == sizeof(cplxf)) && !std::is_same<T, double>::value
+                                      ? HSMA_VB_MINB_F32
+                                      : HSMA_VB_MINB) vbatched_lu_kernel(const int32_t *__restrict__ dm,
+                                                                  const int32_t *__restrict__ dn,
+                                                                  const int32_t *__restrict__ dlda,
+                                                                  const int32_t *__restrict__ dldb,
+                                                                  const void *const *__restrict__ dA,
+                                                                  const int32_t *const *__restrict__ dipiv,
+                                                                  void *const *__restrict__ dB, T alpha,
+                                                                  int32_t *scratch, uint32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item, s_bad;
+  __shared__ int s_piv[64], s_perm[64];
+  T *sTri, *sC, *sR;
+  smem_parts<T>(smem, sTri, sC, sR);
+  const int nitems = *(volatile int32_t *)(scratch + 1);
+  const bool azero = Elem<T>::is_zero(alpha);
+  const SmallMap lower{0, 0, 0}, upper{1, 0, 0};
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(scratch, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= nitems) break;
+    const int e = scratch[2 + item];
+    const int b = e & 0xffffff, g = e >> 24;
+    const int m = dm[b], n = dn[b];
+    const T *A = static_cast<const T *>(dA[b]);
+    T *B = static_cast<T *>(dB[b]);
+    const int64_t lda = dlda[b], ldb = dldb[b];
+    const int32_t *ipiv = dipiv != nullptr ? dipiv[b] : nullptr;
+    if (ipiv != nullptr && !lu_permute_rows<T>(B, ldb, m, n, ipiv, s_piv, s_perm, &s_bad)) {
+      if (threadIdx.x == 0 && status != nullptr) atomicOr(status, HSMA_DEVERR_BAD_PIVOT);
+      continue;
+    }
+    if (azero) {
+      zero_tiles<T, kWarpsBatched>(B, ldb, m, n);
+      continue;
+    }
+    // L Y = alpha P^T B (unit diagonal, not read)
+    lu_stage_solve<T, false>(g, sTri, sC, sR, A, lda, B, ldb, m, n, alpha, true, lower);
+    __syncthreads();
+    // U X = Y
+    lu_stage_solve<T, true>(g, sTri, sC, sR, A, lda, B, ldb, m, n, Elem<T>::one(), false, upper);
+    __syncthreads();  // the next item restages shared memory
+  }
+}
+
+template <class T>
+int lu_grid(int dev) {
+  static int cached[64] = {0};
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  int nsm = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vbatched_lu_kernel<T>, 32 * kWarpsBatched,
+                                                SmemLayout<T>::bytes(64));
+  int grid = nsm * (per_sm > 0 ? per_sm : 1);
+  if (dev >= 0 && dev < 64) cached[dev] = grid;
+  return grid;
+}
+
 template <class T, bool MAP>
 int persistent_grid(int dev) {
   static int cached[64] = {0};
@@ -581,6 +703,50 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
     case HSMA_R32: return vbatched_impl<float>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
     case HSMA_C64: return vbatched_impl<cplxf>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
     default: return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
+  }
+}
+
+template <class T>
+static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t *dn, const double *alpha,
+                                const void *const *dLU, const int32_t *dlda, const int32_t *const *dipiv,
+                                void *const *dB, const int32_t *dldb, uint32_t *status, int32_t *scratch,
+                                cudaStream_t st) {
+  int dev = 0;
+  HSMA_CUDA_TRY(cudaGetDevice(&dev));
+  static DeviceFlags attr_done;
+  if (!attr_done.test()) {
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(vbatched_lu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SmemLayout<T>::bytes(64)));
+    attr_done.set();
+  }
+  const T al = hsma_alpha_as<T>(alpha);
+  {
+    HsmaTraceScope ts("vbatched_schedule", st);
+    vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dLU, dB, scratch, status,
+                                                    sched_table(st));
+  }
+  HSMA_CUDA_TRY(cudaGetLastError());
+  int grid = lu_grid<T>(dev);
+  if (grid > batch) grid = batch;
+  {
+    HsmaTraceScope ts("vbatched_lu", st);
+    vbatched_lu_kernel<T><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dLU,
+                                                                                       dipiv, dB, al, scratch,
+                                                                                       status);
+  }
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
+                                        const double *alpha, const void *const *dLU, const int32_t *dlda,
+                                        const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,
+                                        uint32_t *status, int32_t *scratch, cudaStream_t st) {
+  switch (dtype) {
+    case HSMA_C128: return getrs_impl<cplx>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
+    case HSMA_R32: return getrs_impl<float>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
+    case HSMA_C64: return getrs_impl<cplxf>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
+    default: return getrs_impl<double>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
   }
 }
 

@@ -24,6 +24,13 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
                                   int32_t *scratch, cudaStream_t st, int uplo = HSMA_LOWER,
                                   int trans = HSMA_NO_TRANS);
 
+// Varlen batch of LU-factor solves in one launch (schedule pre-pass + fused
+// kernel): X = U^{-1} L^{-1} P^T (alpha B) per instance; dipiv may be NULL.
+hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
+                                        const double *alpha, const void *const *dLU, const int32_t *dlda,
+                                        const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,
+                                        uint32_t *status, int32_t *scratch, cudaStream_t st);
+
 // dtypes the small kernels and the varlen batch handle
 inline bool hsma_small_dtype(int dtype) {
   return dtype == HSMA_R64 || dtype == HSMA_C128 || dtype == HSMA_R32 || dtype == HSMA_C64;

@@ -27,7 +27,7 @@ NO_TRANS, TRANS, CONJ_TRANS = 0, 1, 2
 PATH_AUTO, PATH_SMALL, PATH_BLOCKED = 0, 1, 2
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_BUSY = range(1, 8)
-DEVERR_BAD_SIZE, DEVERR_NULL_PTR, DEVERR_TIMEOUT = 0x1, 0x2, 0x4
+DEVERR_BAD_SIZE, DEVERR_NULL_PTR, DEVERR_TIMEOUT, DEVERR_BAD_PIVOT = 0x1, 0x2, 0x4, 0x8
 STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTED", 3: "HSMA_ERR_NO_MEMORY",
                 4: "HSMA_ERR_CUDA", 5: "HSMA_ERR_TIMEOUT", 6: "HSMA_ERR_NOT_CONVERGED", 7: "HSMA_ERR_BUSY"}
 
@@ -37,6 +37,7 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
            "hsma_trsm_llnn_vbatched_host", "hsma_trsm", "hsma_trsm_vbatched", "hsma_check_wait_timeout",
+           "hsma_getrs_vbatched",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -139,6 +140,8 @@ def _load():
     lib.hsma_server_destroy.restype = c_int
     lib.hsma_device_status.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.hsma_device_status.restype = c_int
+    lib.hsma_getrs_vbatched.argtypes = [c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p, vp]
+    lib.hsma_getrs_vbatched.restype = c_int
     lib.hsma_check_wait_timeout.argtypes = [ctypes.c_uint64, vp, vp]
     lib.hsma_check_wait_timeout.restype = c_int
     return lib
@@ -207,6 +210,17 @@ def hsma_trsm_vbatched(dtype, side, uplo, trans, diag, batch, d_m, d_n, alpha, d
                                 d_status or None, stream)
     if check:
         _check(s, "hsma_trsm_vbatched")
+    return s
+
+
+def hsma_getrs_vbatched(dtype, batch, d_m, d_n, alpha, d_LU, d_lda, d_ipiv, d_B, d_ldb, max_m=0, max_n=0,
+                        d_status=0, stream=0, check=True) -> int:
+    """Varlen batch of LU-factor solves in one launch: X = U^{-1} L^{-1} P^T (alpha B) per instance
+    (packed getrf factors; d_ipiv: device array of per-instance pivot pointers, or 0 for none)."""
+    s = _lib.hsma_getrs_vbatched(dtype, batch, d_m, d_n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), d_LU,
+                                 d_lda, d_ipiv or None, d_B, d_ldb, max_m, max_n, d_status or None, stream)
+    if check:
+        _check(s, "hsma_getrs_vbatched")
     return s
 
 

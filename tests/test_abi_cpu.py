@@ -179,3 +179,13 @@ def test_wait_check_argument_checks(H):
     assert f(10_000_000, 0, check=False) == 1          # NULL result pointer
     assert f(999_999, 0x1000, check=False) == 1        # limit below 1 ms
     assert f(2_000_000_001, 0x1000, check=False) == 1  # limit above 2 s
+
+
+def test_getrs_argument_checks(H):
+    f = H.hsma_getrs_vbatched
+    assert f(2, 4, 1, 1, 1.0, 1, 1, 0, 1, 1, check=False) == 2              # dtype without a small path
+    assert f(9, 4, 1, 1, 1.0, 1, 1, 0, 1, 1, check=False) == 1              # unknown dtype
+    assert f(0, 4, 1, 1, 1.0, 1, 1, 0, 1, 1, max_m=65, check=False) == 2    # m beyond the small path
+    assert f(0, -1, 1, 1, 1.0, 1, 1, 0, 1, 1, check=False) == 1             # negative batch
+    assert f(0, 4, 1, 1, 1.0, 0, 1, 0, 1, 1, check=False) == 1              # NULL LU
+    assert f(0, 0, 0, 0, 1.0, 0, 0, 0, 0, 0, check=False) == 0              # empty batch

@@ -1,0 +1,58 @@
+"""Pins for the oracle's LU-factor solve (getrs), by means other than the oracle itself:
+LAPACK's getrs (scipy.linalg.lu_solve, a black box) on getrf factors; the residual of
+P L U X = alpha B with A rebuilt from the factors; L = U = I, where X = P^T (alpha B)
+exactly; and the interchanges written out as a permutation matrix."""
+import numpy as np
+import pytest
+
+import oracle
+
+la = pytest.importorskip("scipy.linalg")
+
+
+def _factors(seed, m, cx):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, m)) + (1j * rng.standard_normal((m, m)) if cx else 0.0)
+    lu, piv = la.lu_factor(A)
+    return np.asfortranarray(A), np.asfortranarray(lu), piv + 1  # LAPACK's 1-based pivots
+
+
+@pytest.mark.parametrize("cx", [False, True])
+@pytest.mark.parametrize("m,n", [(1, 3), (7, 5), (33, 17), (64, 64)])
+def test_getrs_matches_lapack_and_residual(cx, m, n):
+    A, LU, ipiv = _factors(m * 7 + n, m, cx)
+    rng = np.random.default_rng(m)
+    B = np.asfortranarray(rng.standard_normal((m, n)) + (1j * rng.standard_normal((m, n)) if cx else 0.0))
+    alpha = 0.75 - 1.5j if cx else -1.25
+    X = oracle.getrs(LU, ipiv, B, alpha)
+    ref = la.lu_solve((LU, ipiv - 1), alpha * B)
+    assert np.linalg.norm(X - ref) <= 1e-12 * np.linalg.norm(ref)
+    R = A @ X - alpha * B
+    assert np.linalg.norm(R) <= 1e-12 * (np.linalg.norm(A) * np.linalg.norm(X) + abs(alpha) * np.linalg.norm(B))
+
+
+def test_getrs_identity_factors_is_the_permutation():
+    m, n = 9, 4
+    ipiv = np.array([3, 2, 9, 5, 5, 8, 7, 8, 9])  # 1-based, ipiv[k] >= k + 1
+    LU = np.asfortranarray(np.eye(m))
+    B = np.asfortranarray(np.arange(m * n, dtype=np.float64).reshape(m, n, order="F"))
+    X = oracle.getrs(LU, ipiv, B, 2.0)
+    P = np.eye(m)
+    for k, p in enumerate(ipiv - 1):  # P^T as the product of the interchanges
+        P[[k, p], :] = P[[p, k], :]
+    assert np.array_equal(X, P @ (2.0 * B))
+
+
+def test_getrs_without_pivots_is_two_triangular_solves():
+    A, LU, _ = _factors(3, 20, True)
+    B = np.asfortranarray(np.ones((20, 3), dtype=np.complex128))
+    X = oracle.getrs(LU, None, B, 1.0)
+    L = np.tril(LU, -1) + np.eye(20)
+    U = np.triu(LU)
+    ref = la.solve_triangular(U, la.solve_triangular(L, B, lower=True, unit_diagonal=True), lower=False)
+    assert np.linalg.norm(X - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_getrs_rejects_pivot_out_of_range():
+    with pytest.raises(ValueError):
+        oracle.getrs(np.asfortranarray(np.eye(3)), np.array([2, 1, 3]), np.asfortranarray(np.ones((3, 1))), 1.0)

@@ -250,6 +250,21 @@ HSMA_API hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32
                                            int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream);
 
 /*
+ * Varlen batch of Cholesky-factor solves in ONE launch (the same fused
+ * kernel): instance i holds A_i = L_i L_i^H's lower factor L_i as LAPACK
+ * potrf leaves it (uplo = lower; the strict upper triangle is not read), and
+ *     X_i = L_i^{-H} L_i^{-1} (alpha B_i)   overwrites B_i
+ * (L_i^T for the real dtypes).  The second solve reads L_i through the
+ * reversed, transposed and conjugated index map.  Arguments and errors as
+ * hsma_getrs_vbatched without pivots; results equal two hsma_trsm_vbatched
+ * calls (lower, then lower with HSMA_CONJ_TRANS) bit for bit.
+ */
+HSMA_API hsma_status_t hsma_potrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
+                                           const void *alpha, const void *const *d_L, const int32_t *d_lda,
+                                           void *const *d_B, const int32_t *d_ldb, int32_t max_m, int32_t max_n,
+                                           uint32_t *d_status, void *stream);
+
+/*
  * The varlen batch with its matrices in HOST memory (no paper counterpart:
  * the paper's solves are device-resident).  The batch is cut into `chunks`
  * groups of consecutive instances (0 = 8, at most 256).  The sizes and

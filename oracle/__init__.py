@@ -18,6 +18,8 @@ Every function cites the passage it follows:
 * ``solve_general``: the BLAS variants (side, uplo, trans, diag) by definition.
 * ``getrs``: the solve from LU factors (Section 1's motivating use): row
   interchanges in order, then the unit-lower and the upper solve.
+* ``potrs``: the solve from a lower Cholesky factor: the lower solve, then
+  the conjugate-transposed one.
 
 Pins (see ``tests/test_oracle_pins.py``): identity and diagonal A, the unit
 lower-bidiagonal closed form, exact rational elimination on small dyadic inputs,
@@ -26,7 +28,8 @@ triangle never read, unit diagonal never read, columns independent, complex with
 zero imaginary part equals real).  ``getrs`` is pinned in
 ``tests/test_oracle_getrs.py``: LAPACK's getrs (scipy's lu_solve) as a black box,
 the residual of P L U X = alpha B, the exact permutation-only case, and the
-same interchanges written as a permutation matrix.
+same interchanges written as a permutation matrix; ``potrs`` against LAPACK's
+potrs (scipy's cho_solve) and the residual of L L^H X = alpha B.
 """
 from __future__ import annotations
 
@@ -184,6 +187,14 @@ def getrs(LU: np.ndarray, ipiv, B: np.ndarray, alpha, _lib=None) -> np.ndarray:
             Y[[k, p], :] = Y[[p, k], :]
     Y = solve_general(LU, Y, alpha, 0, 0, 0, True, _lib=_lib)
     return solve_general(LU, Y, 1.0, 0, 1, 0, False, _lib=_lib)
+
+
+def potrs(Lf: np.ndarray, B: np.ndarray, alpha, _lib=None) -> np.ndarray:
+    """Solve A X = alpha B from A's lower Cholesky factor (A = L L^H, L in the lower triangle of
+    Lf as LAPACK potrf leaves it), by the definition X = L^{-H} L^{-1} (alpha B): the lower solve,
+    then the conjugate-transposed one (transposed for real data)."""
+    Y = solve_general(Lf, B, alpha, 0, 0, 0, False, _lib=_lib)
+    return solve_general(Lf, Y, 1.0, 0, 0, 2 if np.iscomplexobj(Lf) else 1, False, _lib=_lib)
 
 
 def solve_cols(A: np.ndarray, B: np.ndarray, alpha, cols, unit: bool = False) -> np.ndarray:

@@ -268,10 +268,11 @@ hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int d
   return s != HSMA_OK ? s : f;
 }
 
-hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
-                                  const void *alpha, const void *const *d_LU, const int32_t *d_lda,
-                                  const int32_t *const *d_ipiv, void *const *d_B, const int32_t *d_ldb,
-                                  int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream) {
+static hsma_status_t factor_solve_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
+                                           const void *alpha, const void *const *d_LU, const int32_t *d_lda,
+                                           const int32_t *const *d_ipiv, void *const *d_B, const int32_t *d_ldb,
+                                           int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream,
+                                           int chol) {
   if (!hsma_small_dtype(dtype)) {
     return valid_dtype(dtype) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
   }
@@ -287,9 +288,25 @@ hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, 
   hsma_status_t s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
   if (s != HSMA_OK) return s;
   s = hsma_small_getrs_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_LU, d_lda, d_ipiv,
-                                d_B, d_ldb, d_status, static_cast<int32_t *>(scratch), st);
+                                d_B, d_ldb, d_status, static_cast<int32_t *>(scratch), st, chol);
   hsma_status_t f = hsma_ws_free(scratch, st);
   return s != HSMA_OK ? s : f;
+}
+
+hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
+                                  const void *alpha, const void *const *d_LU, const int32_t *d_lda,
+                                  const int32_t *const *d_ipiv, void *const *d_B, const int32_t *d_ldb,
+                                  int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream) {
+  return factor_solve_vbatched(dtype, batch, d_m, d_n, alpha, d_LU, d_lda, d_ipiv, d_B, d_ldb, max_m, max_n,
+                               d_status, stream, 0);
+}
+
+hsma_status_t hsma_potrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
+                                  const void *alpha, const void *const *d_L, const int32_t *d_lda, void *const *d_B,
+                                  const int32_t *d_ldb, int32_t max_m, int32_t max_n, uint32_t *d_status,
+                                  void *stream) {
+  return factor_solve_vbatched(dtype, batch, d_m, d_n, alpha, d_L, d_lda, nullptr, d_B, d_ldb, max_m, max_n,
+                               d_status, stream, 1);
 }
 
 hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64_t inst, int64_t m, int64_t cols, void *dst,

@@ -433,11 +433,13 @@ __global__ void __launch_bounds__(32 * kWarpsBatched,
 }
 
 // ---------------------------------------------------------------------------
-// Varlen batch of LU-factor solves in one launch: the small solve fused with
-// its consumer.  Per instance the CTA applies the row interchanges to B,
-// stages the unit-lower factor and solves, then stages the upper factor in
-// row-reversed form (the left / upper index map) and solves again on the
-// intermediate result, which the same CTA has just written (cache resident).
+// Varlen batch of factor solves in one launch: the small solve fused with
+// its consumer.  LU factors: per instance the CTA applies the row
+// interchanges to B, stages the unit-lower factor and solves, then stages the
+// upper factor in row-reversed form (the left / upper index map) and solves
+// again on the intermediate result, which the same CTA has just written
+// (cache resident).  Cholesky factors (A = L L^H): the lower factor, then its
+// conjugate transpose through the reversed, transposed, conjugated map.
 // ---------------------------------------------------------------------------
 
 // Row interchanges k <-> ipiv[k]-1, k = 0..m-1 in order, applied to B as one
@@ -481,7 +483,7 @@ __device__ __forceinline__ bool lu_permute_rows(T *B, int64_t ldb, int m, int n,
   return true;
 }
 
-// One triangular solve of the LU pair: stage (with the map) and solve every
+// One triangular solve of the pair: stage (with the map) and solve every
 // column tile.  Kept out of line so the compiler handles each of the two
 // solves once, not the fused kernel as one body.
 template <class T, bool MAP>
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(32 * kWarpsBatched,
                                                                   const void *const *__restrict__ dA,
                                                                   const int32_t *const *__restrict__ dipiv,
                                                                   void *const *__restrict__ dB, T alpha,
-                                                                  int32_t *scratch, uint32_t *status) {
+                                                                  int32_t *scratch, uint32_t *status, int chol) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item, s_bad;
   __shared__ int s_piv[64], s_perm[64];
@@ -510,7 +512,8 @@ __global__ void __launch_bounds__(32 * kWarpsBatched,
   smem_parts<T>(smem, sTri, sC, sR);
   const int nitems = *(volatile int32_t *)(scratch + 1);
   const bool azero = Elem<T>::is_zero(alpha);
-  const SmallMap lower{0, 0, 0}, upper{1, 0, 0};
+  // second factor: U (upper), or L^H (lower read transposed and conjugated)
+  const SmallMap lower{0, 0, 0}, second{1, chol, chol};
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(scratch, 1);
     __syncthreads();
@@ -532,11 +535,11 @@ __global__ void __launch_bounds__(32 * kWarpsBatched,
       zero_tiles<T, kWarpsBatched>(B, ldb, m, n);
       continue;
     }
-    // L Y = alpha P^T B (unit diagonal, not read)
-    lu_stage_solve<T, false>(g, sTri, sC, sR, A, lda, B, ldb, m, n, alpha, true, lower);
+    // L Y = alpha P^T B (LU: unit diagonal, not read)
+    lu_stage_solve<T, false>(g, sTri, sC, sR, A, lda, B, ldb, m, n, alpha, chol == 0, lower);
     __syncthreads();
-    // U X = Y
-    lu_stage_solve<T, true>(g, sTri, sC, sR, A, lda, B, ldb, m, n, Elem<T>::one(), false, upper);
+    // U X = Y, or L^H X = Y
+    lu_stage_solve<T, true>(g, sTri, sC, sR, A, lda, B, ldb, m, n, Elem<T>::one(), false, second);
     __syncthreads();  // the next item restages shared memory
   }
 }
@@ -710,7 +713,7 @@ template <class T>
 static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t *dn, const double *alpha,
                                 const void *const *dLU, const int32_t *dlda, const int32_t *const *dipiv,
                                 void *const *dB, const int32_t *dldb, uint32_t *status, int32_t *scratch,
-                                cudaStream_t st) {
+                                cudaStream_t st, int chol) {
   int dev = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   static DeviceFlags attr_done;
@@ -732,7 +735,7 @@ static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t 
     HsmaTraceScope ts("vbatched_lu", st);
     vbatched_lu_kernel<T><<<grid, 32 * kWarpsBatched, SmemLayout<T>::bytes(64), st>>>(dm, dn, dlda, dldb, dLU,
                                                                                        dipiv, dB, al, scratch,
-                                                                                       status);
+                                                                                       status, chol);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
@@ -741,12 +744,17 @@ static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t 
 hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                         const double *alpha, const void *const *dLU, const int32_t *dlda,
                                         const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,
-                                        uint32_t *status, int32_t *scratch, cudaStream_t st) {
+                                        uint32_t *status, int32_t *scratch, cudaStream_t st, int chol) {
+  if (chol) dipiv = nullptr;
   switch (dtype) {
-    case HSMA_C128: return getrs_impl<cplx>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
-    case HSMA_R32: return getrs_impl<float>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
-    case HSMA_C64: return getrs_impl<cplxf>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
-    default: return getrs_impl<double>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st);
+    case HSMA_C128:
+      return getrs_impl<cplx>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
+    case HSMA_R32:
+      return getrs_impl<float>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
+    case HSMA_C64:
+      return getrs_impl<cplxf>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
+    default:
+      return getrs_impl<double>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
   }
 }
 

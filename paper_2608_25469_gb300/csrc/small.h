@@ -24,12 +24,14 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
                                   int32_t *scratch, cudaStream_t st, int uplo = HSMA_LOWER,
                                   int trans = HSMA_NO_TRANS);
 
-// Varlen batch of LU-factor solves in one launch (schedule pre-pass + fused
-// kernel): X = U^{-1} L^{-1} P^T (alpha B) per instance; dipiv may be NULL.
+// Varlen batch of factor solves in one launch (schedule pre-pass + fused
+// kernel): chol = 0, X = U^{-1} L^{-1} P^T (alpha B) from packed LU factors
+// (dipiv may be NULL); chol = 1, X = L^{-H} L^{-1} (alpha B) from a lower
+// Cholesky factor (dipiv ignored).
 hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                         const double *alpha, const void *const *dLU, const int32_t *dlda,
                                         const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,
-                                        uint32_t *status, int32_t *scratch, cudaStream_t st);
+                                        uint32_t *status, int32_t *scratch, cudaStream_t st, int chol = 0);
 
 // dtypes the small kernels and the varlen batch handle
 inline bool hsma_small_dtype(int dtype) {

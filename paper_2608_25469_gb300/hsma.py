@@ -37,7 +37,7 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
            "hsma_trsm_llnn_vbatched_host", "hsma_trsm", "hsma_trsm_vbatched", "hsma_check_wait_timeout",
-           "hsma_getrs_vbatched",
+           "hsma_getrs_vbatched", "hsma_potrs_vbatched",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -142,6 +142,8 @@ def _load():
     lib.hsma_device_status.restype = c_int
     lib.hsma_getrs_vbatched.argtypes = [c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p, vp]
     lib.hsma_getrs_vbatched.restype = c_int
+    lib.hsma_potrs_vbatched.argtypes = [c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p, vp]
+    lib.hsma_potrs_vbatched.restype = c_int
     lib.hsma_check_wait_timeout.argtypes = [ctypes.c_uint64, vp, vp]
     lib.hsma_check_wait_timeout.restype = c_int
     return lib
@@ -221,6 +223,16 @@ def hsma_getrs_vbatched(dtype, batch, d_m, d_n, alpha, d_LU, d_lda, d_ipiv, d_B,
                                  d_lda, d_ipiv or None, d_B, d_ldb, max_m, max_n, d_status or None, stream)
     if check:
         _check(s, "hsma_getrs_vbatched")
+    return s
+
+
+def hsma_potrs_vbatched(dtype, batch, d_m, d_n, alpha, d_L, d_lda, d_B, d_ldb, max_m=0, max_n=0, d_status=0,
+                        stream=0, check=True) -> int:
+    """Varlen batch of Cholesky-factor solves in one launch: X = L^{-H} L^{-1} (alpha B) per instance."""
+    s = _lib.hsma_potrs_vbatched(dtype, batch, d_m, d_n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), d_L,
+                                 d_lda, d_B, d_ldb, max_m, max_n, d_status or None, stream)
+    if check:
+        _check(s, "hsma_potrs_vbatched")
     return s
 
 

@@ -189,3 +189,11 @@ def test_getrs_argument_checks(H):
     assert f(0, -1, 1, 1, 1.0, 1, 1, 0, 1, 1, check=False) == 1             # negative batch
     assert f(0, 4, 1, 1, 1.0, 0, 1, 0, 1, 1, check=False) == 1              # NULL LU
     assert f(0, 0, 0, 0, 1.0, 0, 0, 0, 0, 0, check=False) == 0              # empty batch
+
+
+def test_potrs_argument_checks(H):
+    f = H.hsma_potrs_vbatched
+    assert f(3, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 2              # dtype without a small path
+    assert f(0, 4, 1, 1, 1.0, 1, 1, 1, 1, max_m=65, check=False) == 2    # m beyond the small path
+    assert f(1, 4, 1, 1, 1.0, 1, 1, 0, 1, check=False) == 1              # NULL B
+    assert f(1, 0, 0, 0, 1.0, 0, 0, 0, 0, check=False) == 0              # empty batch

@@ -142,3 +142,60 @@ def test_getrs_alpha_zero_and_empty_instances(H):
     for b in range(len(LUs)):
         assert np.all(out[b] == 0.0), b
 
+
+
+def _chol_instances(seed, batch, cx, lo=1):
+    ms, ns = I.batched_sizes(seed, batch, lo=lo)
+    rng = np.random.default_rng(seed)
+    Ls, Bs = [], []
+    for m, n in zip(ms, ns):
+        m, n = int(m), int(n)
+        G = rng.standard_normal((m, m)) + (1j * rng.standard_normal((m, m)) if cx else 0.0)
+        Lf = la.cholesky(G @ G.conj().T / m + np.eye(m), lower=True)
+        Lf[np.triu_indices(m, 1)] = np.nan  # never read
+        Ls.append(np.asfortranarray(Lf))
+        Bs.append(np.asfortranarray(rng.standard_normal((m, n)) + (1j * rng.standard_normal((m, n)) if cx else 0.0)))
+    return Ls, Bs
+
+
+def _run_potrs(H, code, Ls, Bs, alpha):
+    import torch
+    bt = U.Batch(Ls, Bs)
+    a = bt.args()
+    H.hsma_potrs_vbatched(code, bt.batch, a[0], a[1], alpha, a[2], a[3], a[4], a[5], max_m=64,
+                          d_status=bt.d_status.data_ptr(), stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    return bt
+
+
+@pytest.mark.parametrize("cx", [False, True])
+def test_potrs_batch_matches_oracle_and_two_launches(H, cx):
+    import torch
+    code = I.C128 if cx else I.R64
+    alpha = 0.5 - 1.0j if cx else 2.0
+    Ls, Bs = _chol_instances(41, 500, cx)
+    bt = _run_potrs(H, code, Ls, Bs, alpha)
+    assert bt.status() == 0
+    fused = bt.results()
+    two = U.Batch(Ls, Bs)
+    a = two.args()
+    H.hsma_trsm_vbatched(code, H.LEFT, H.LOWER, H.NO_TRANS, H.NON_UNIT, two.batch, a[0], a[1], alpha, a[2], a[3],
+                         a[4], a[5], 64, 64, 0, H.stream_ptr())
+    H.hsma_trsm_vbatched(code, H.LEFT, H.LOWER, H.CONJ_TRANS if cx else H.TRANS, H.NON_UNIT, two.batch, a[0], a[1],
+                         1.0, a[2], a[3], a[4], a[5], 64, 64, 0, H.stream_ptr())
+    torch.cuda.synchronize()
+    two = two.results()
+    for b in range(len(Ls)):
+        assert np.array_equal(fused[b], two[b]), b
+        ref = oracle.potrs(Ls[b], Bs[b], alpha)
+        assert oracle.forward_error(fused[b], ref) <= 1e-12, b
+
+
+def test_potrs_complex64(H):
+    Ls, Bs = _chol_instances(42, 200, True)
+    L32 = [np.asfortranarray(x.astype(np.complex64)) for x in Ls]
+    B32 = [np.asfortranarray(x.astype(np.complex64)) for x in Bs]
+    out = _run_potrs(H, 5, L32, B32, 1.0).results()
+    for b in range(len(Ls)):
+        ref = oracle.potrs(np.asfortranarray(L32[b].astype(np.complex128)), np.asfortranarray(B32[b].astype(np.complex128)), 1.0)
+        assert oracle.forward_error(out[b].astype(np.complex128), ref) <= 2e-5, b

@@ -56,3 +56,26 @@ def test_getrs_without_pivots_is_two_triangular_solves():
 def test_getrs_rejects_pivot_out_of_range():
     with pytest.raises(ValueError):
         oracle.getrs(np.asfortranarray(np.eye(3)), np.array([2, 1, 3]), np.asfortranarray(np.ones((3, 1))), 1.0)
+
+
+def _chol(seed, m, cx):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((m, m)) + (1j * rng.standard_normal((m, m)) if cx else 0.0)
+    A = G @ G.conj().T / m + np.eye(m)
+    return np.asfortranarray(A), np.asfortranarray(la.cholesky(A, lower=True))
+
+
+@pytest.mark.parametrize("cx", [False, True])
+@pytest.mark.parametrize("m,n", [(1, 2), (9, 4), (40, 31), (64, 64)])
+def test_potrs_matches_lapack_and_residual(cx, m, n):
+    A, Lf = _chol(m + 100 * n, m, cx)
+    P = Lf.copy(order="F")
+    P[np.triu_indices(m, 1)] = np.nan  # the strict upper triangle is never read
+    rng = np.random.default_rng(n)
+    B = np.asfortranarray(rng.standard_normal((m, n)) + (1j * rng.standard_normal((m, n)) if cx else 0.0))
+    alpha = 1.25 + 0.5j if cx else 0.5
+    X = oracle.potrs(P, B, alpha)
+    ref = la.cho_solve((Lf, True), alpha * B)
+    assert np.linalg.norm(X - ref) <= 1e-12 * np.linalg.norm(ref)
+    R = A @ X - alpha * B
+    assert np.linalg.norm(R) <= 1e-12 * (np.linalg.norm(A) * np.linalg.norm(X) + abs(alpha) * np.linalg.norm(B))

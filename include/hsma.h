@@ -350,8 +350,8 @@ HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64
                               int64_t cols, void *dst, int64_t ld, void *stream);
 
 /*
- * Serving loop (the benchmark spec's continuous-batching server; batched TRSM is
- * the paper's future work, Section 6).  A server owns a scheduler thread, a
+ * Serving loop (a continuous-batching server for streams of solves; batched
+ * TRSM is the paper's future work, Section 6).  A server owns a scheduler thread, a
  * ring of CUDA streams and a device memory pool on the current device.
  * Submitted requests are admitted in arrival order while their device memory
  * (A, B and the blocked path's workspace) fits `budget_bytes`; admitted

@@ -41,3 +41,52 @@ def test_vbatched_graph_replay_matches_eager():
     refs = oracle.solve_batch(As[:20], Bs[:20], alpha)
     for b in range(20):
         assert oracle.forward_error(got[b], refs[b]) <= 1e-12
+
+
+def test_getrs_graph_replay_matches_eager():
+    """The fused LU-factor solve (with row interchanges) captured into a CUDA graph."""
+    import torch
+    la = pytest.importorskip("scipy.linalg")
+    H = U.lib()
+    alpha = 0.5 - 1.0j
+    ms, ns = I.batched_sizes(4, 300)
+    rng = np.random.default_rng(4)
+    LUs, pivs, Bs = [], [], []
+    for m, n in zip(ms, ns):
+        m, n = int(m), int(n)
+        A = (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))) / np.sqrt(m) + 2.0 * np.eye(m)
+        lu, piv = la.lu_factor(A[rng.permutation(m)])
+        LUs.append(np.asfortranarray(lu))
+        pivs.append((piv + 1).astype(np.int32))
+        Bs.append(np.asfortranarray(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))))
+    off = np.concatenate([[0], np.cumsum([len(p) for p in pivs])[:-1]]).astype(np.int64)
+    dpiv = torch.from_numpy(np.concatenate(pivs)).cuda()
+    dptr = torch.from_numpy((dpiv.data_ptr() + 4 * off).astype(np.int64)).cuda()
+
+    def call(bt, st):
+        a = bt.args()
+        H.hsma_getrs_vbatched(I.C128, bt.batch, a[0], a[1], alpha, a[2], a[3], dptr.data_ptr(), a[4], a[5], max_m=64,
+                              stream=st)
+
+    eager = U.Batch(LUs, Bs)
+    call(eager, H.stream_ptr())
+    torch.cuda.synchronize()
+    ref = eager.results()
+    bt = U.Batch(LUs, Bs)
+    B0 = bt.dB.clone()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            call(bt, int(s.cuda_stream))
+    torch.cuda.synchronize()
+    for _ in range(2):
+        bt.dB.copy_(B0)
+        g.replay()
+        torch.cuda.synchronize()
+        got = bt.results()
+        for b in range(bt.batch):
+            assert np.array_equal(got[b], ref[b]), b
+    for b in range(0, bt.batch, 29):
+        assert oracle.forward_error(got[b], oracle.getrs(LUs[b], pivs[b], Bs[b], alpha)) <= 1e-12, b

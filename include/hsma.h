@@ -250,6 +250,23 @@ HSMA_API hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32
                                            int32_t max_m, int32_t max_n, uint32_t *d_status, void *stream);
 
 /*
+ * One solve with LU or Cholesky factors, any m (the factorisations that
+ * motivate the paper, Section 1).  hsma_getrs: A = P L U packed as for
+ * hsma_getrs_vbatched (DEVICE LU, lda >= max(1,m)); ipiv: NULL or a DEVICE
+ * array of m int32 pivots in LAPACK's convention; X = U^{-1} L^{-1} P^T
+ * (alpha B) overwrites B (DEVICE, ldb >= max(1,m)).  The interchanges are
+ * applied as one gather through a workspace copy of B (pivots read by one
+ * CTA: shared memory up to m = 28000, global memory beyond), then the
+ * unit-lower and the upper solve run through hsma_trsm with `opts` (small
+ * kernel or blocked path, FP64 products emulated on request).  A pivot outside
+ * [k, m] sets HSMA_DEVERR_BAD_PIVOT in the device error word
+ * (hsma_device_status) and the interchanges are skipped (X is then not the
+ * solution).  hsma_potrs: A = L L^H with L in the lower triangle of L (the
+ * strict upper triangle is not read); X = L^{-H} L^{-1} (alpha B) (L^T for
+ * real dtypes).  Both: dtype any hsma_dtype_t; m = 0 or n = 0 is a no-op;
+ * asynchronous on `stream`; errors as hsma_trsm.
+ */
+/*
  * Varlen batch of Cholesky-factor solves in ONE launch (the same fused
  * kernel): instance i holds A_i = L_i L_i^H's lower factor L_i as LAPACK
  * potrf leaves it (uplo = lower; the strict upper triangle is not read), and
@@ -259,6 +276,11 @@ HSMA_API hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32
  * hsma_getrs_vbatched without pivots; results equal two hsma_trsm_vbatched
  * calls (lower, then lower with HSMA_CONJ_TRANS) bit for bit.
  */
+HSMA_API hsma_status_t hsma_getrs(int dtype, int64_t m, int64_t n, const void *alpha, const void *LU, int64_t lda,
+                                  const int32_t *ipiv, void *B, int64_t ldb, void *stream, const hsma_opts_t *opts);
+HSMA_API hsma_status_t hsma_potrs(int dtype, int64_t m, int64_t n, const void *alpha, const void *L, int64_t lda,
+                                  void *B, int64_t ldb, void *stream, const hsma_opts_t *opts);
+
 HSMA_API hsma_status_t hsma_potrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
                                            const void *alpha, const void *const *d_L, const int32_t *d_lda,
                                            void *const *d_B, const int32_t *d_ldb, int32_t max_m, int32_t max_n,

@@ -37,7 +37,7 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
            "hsma_trsm_llnn_vbatched_host", "hsma_trsm", "hsma_trsm_vbatched", "hsma_check_wait_timeout",
-           "hsma_getrs_vbatched", "hsma_potrs_vbatched",
+           "hsma_getrs_vbatched", "hsma_potrs_vbatched", "hsma_getrs", "hsma_potrs",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
 
@@ -144,6 +144,10 @@ def _load():
     lib.hsma_getrs_vbatched.restype = c_int
     lib.hsma_potrs_vbatched.argtypes = [c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32p, vp]
     lib.hsma_potrs_vbatched.restype = c_int
+    lib.hsma_getrs.argtypes = [c_int, i64, i64, vp, vp, i64, vp, vp, i64, vp, ctypes.POINTER(Opts)]
+    lib.hsma_getrs.restype = c_int
+    lib.hsma_potrs.argtypes = [c_int, i64, i64, vp, vp, i64, vp, i64, vp, ctypes.POINTER(Opts)]
+    lib.hsma_potrs.restype = c_int
     lib.hsma_check_wait_timeout.argtypes = [ctypes.c_uint64, vp, vp]
     lib.hsma_check_wait_timeout.restype = c_int
     return lib
@@ -223,6 +227,24 @@ def hsma_getrs_vbatched(dtype, batch, d_m, d_n, alpha, d_LU, d_lda, d_ipiv, d_B,
                                  d_lda, d_ipiv or None, d_B, d_ldb, max_m, max_n, d_status or None, stream)
     if check:
         _check(s, "hsma_getrs_vbatched")
+    return s
+
+
+def hsma_getrs(dtype, m, n, alpha, LU, lda, ipiv, B, ldb, stream=0, opts: Opts | None = None, check=True) -> int:
+    """One solve from LU factors (device pointers; ipiv: device int32 pivots or 0)."""
+    s = _lib.hsma_getrs(dtype, m, n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), LU, lda, ipiv or None, B, ldb,
+                        stream or None, ctypes.byref(opts) if opts is not None else None)
+    if check:
+        _check(s, "hsma_getrs")
+    return s
+
+
+def hsma_potrs(dtype, m, n, alpha, L, lda, B, ldb, stream=0, opts: Opts | None = None, check=True) -> int:
+    """One solve from a lower Cholesky factor (device pointers)."""
+    s = _lib.hsma_potrs(dtype, m, n, ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), L, lda, B, ldb,
+                        stream or None, ctypes.byref(opts) if opts is not None else None)
+    if check:
+        _check(s, "hsma_potrs")
     return s
 
 

@@ -197,3 +197,13 @@ def test_potrs_argument_checks(H):
     assert f(0, 4, 1, 1, 1.0, 1, 1, 1, 1, max_m=65, check=False) == 2    # m beyond the small path
     assert f(1, 4, 1, 1, 1.0, 1, 1, 0, 1, check=False) == 1              # NULL B
     assert f(1, 0, 0, 0, 1.0, 0, 0, 0, 0, check=False) == 0              # empty batch
+
+
+def test_single_factor_solve_argument_checks(H):
+    assert H.hsma_getrs(9, 4, 4, 1.0, 1, 4, 0, 1, 4, check=False) == 1     # unknown dtype
+    assert H.hsma_getrs(0, 4, 4, 1.0, 1, 3, 0, 1, 4, check=False) == 1     # lda < m
+    assert H.hsma_getrs(0, 4, 4, 1.0, 0, 4, 0, 1, 4, check=False) == 1     # NULL LU
+    assert H.hsma_getrs(0, 0, 4, 1.0, 0, 1, 0, 0, 1, check=False) == 0     # m = 0: no-op
+    assert H.hsma_potrs(1, 4, -1, 1.0, 1, 4, 1, 4, check=False) == 1       # n < 0
+    assert H.hsma_potrs(1, 4, 4, 1.0, 1, 4, 1, 2, check=False) == 1        # ldb < m
+    assert H.hsma_potrs(1, 5, 0, 1.0, 0, 5, 0, 5, check=False) == 0        # n = 0: no-op

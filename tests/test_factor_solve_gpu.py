@@ -77,3 +77,33 @@ def test_potrs_single(H, cx, m, n):
     torch.cuda.synchronize()
     assert H.hsma_device_status() == 0
     assert oracle.forward_error(H.from_device(dB), oracle.potrs(Lf, B, alpha)) <= 1e-12
+
+
+@pytest.mark.parametrize("code,m,n", [(0, 64, 1), (1, 200, 3), (3, 300, 20)])
+def test_getrs_single_without_pivots(H, code, m, n):
+    """ipiv = NULL: no interchanges; dtype 3 runs each triangular solve in the FP64-result
+    refinement mode."""
+    import torch
+    cx = code == 1
+    LU, _, B = _lu(m + 7 * n, m, n, cx)
+    dLU, dB = H.to_device(LU), H.to_device(B)
+    H.hsma_getrs(code, m, n, 1.25, dLU.data_ptr(), m, 0, dB.data_ptr(), m, H.stream_ptr())
+    torch.cuda.synchronize()
+    assert H.hsma_device_status() == 0
+    assert oracle.forward_error(H.from_device(dB), oracle.getrs(LU, None, B, 1.25)) <= 1e-12
+
+
+def test_potrs_single_emulated_products(H):
+    import torch
+    m, n = 700, 30
+    rng = np.random.default_rng(7)
+    G = _mat(rng, m, m, False)
+    Lf = np.asfortranarray(la.cholesky(G @ G.T / m + np.eye(m), lower=True))
+    B = np.asfortranarray(_mat(rng, m, n, False))
+    dL, dB = H.to_device(Lf), H.to_device(B)
+    opts = H.Opts()
+    opts.fp64_products = 1
+    H.hsma_potrs(0, m, n, 1.0, dL.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts)
+    torch.cuda.synchronize()
+    assert H.hsma_device_status() == 0
+    assert oracle.forward_error(H.from_device(dB), oracle.potrs(Lf, B, 1.0)) <= 1e-12

@@ -256,3 +256,17 @@ def test_host_buffers_with_gaps_and_empty_instances(H):
         touched[sl] = True
         assert np.array_equal(hX[sl].reshape((ms[b], ns[b]), order="F"), dev[b]), b
     assert np.all(hX[:2] == 7.0) and np.all(hX[-gap:] == 7.0)
+
+
+def test_golden_integer_solves_bitwise(H):
+    """The integer-valued golden solves (small kernel for m <= 64, blocked path above):
+    every intermediate is an integer below 2^53, so the GPU result equals X bit for bit."""
+    import torch
+    from tests import golden_cases
+    for dtype, A, B, alpha, X in golden_cases.load():
+        code = I.C128 if dtype == "c128" else I.R64
+        m, n = B.shape
+        dA, dB = H.to_device(A), H.to_device(B)
+        H.hsma_trsm_llnn(code, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr())
+        torch.cuda.synchronize()
+        assert np.array_equal(H.from_device(dB), X), (dtype, m, n)

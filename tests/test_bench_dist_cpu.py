@@ -63,3 +63,45 @@ def test_bench_emulated_panel_width_matches_library():
     src = open(os.path.join(ROOT, "paper_2608_25469_gb300", "csrc", "mixed.cu")).read()
     lib = int(re.search(r"#define HSMA_EMU_PANEL_COLS (\d+)", src).group(1))
     assert bench.EMU_PANEL_COLS == lib
+
+
+def test_profile_traffic_follows_source_hash_and_scales_by_work(tmp_path, monkeypatch):
+    """A committed ncu summary's DRAM bytes are used only while the hash of the kernel's
+    sources matches, and are scaled by the bench launch's work when the capture was smaller."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.source_sha(["k.cu"])
+    (tmp_path / "profiles" / "p.txt").write_text(
+        f"# title\nsource_sha256_16: {sha}\ndram_bytes_per_launch: 1000\nwork_per_launch: 10\n")
+    assert bench.profile_traffic("p.txt", ["k.cu"]) == 1000.0
+    assert bench.profile_traffic("p.txt", ["k.cu"], work=25) == 2500.0
+    src.write_text("kernel v2\n")  # the kernel changed since the capture
+    assert bench.profile_traffic("p.txt", ["k.cu"]) is None
+    assert bench.profile_traffic("missing.txt", ["k.cu"]) is None
+
+
+def test_committed_profiles_are_well_formed():
+    """Every summary under profiles/ gives the ncu command that made it, the sources it was
+    taken on (which exist) and their hash; a hash that no longer matches (the kernel changed
+    since the capture, so the bench reports no traffic figure) is reported as a warning."""
+    import warnings
+    sys.path.insert(0, ROOT)
+    import bench
+    names = sorted(os.listdir(os.path.join(ROOT, "profiles")))
+    assert names
+    for name in names:
+        kv = {}
+        for line in open(os.path.join(ROOT, "profiles", name)):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv.setdefault(k.strip(), v.strip())
+        assert kv["command"].startswith("ncu ") and "--clock-control none" in kv["command"], name
+        files = [x.strip() for x in kv["sources"].split(",")]
+        assert all(os.path.exists(os.path.join(ROOT, f)) for f in files), name
+        float(kv["dram_bytes_per_launch"])
+        if kv["source_sha256_16"] != bench.source_sha(files):
+            warnings.warn(f"profiles/{name} was captured on older sources")

@@ -207,3 +207,23 @@ def test_single_factor_solve_argument_checks(H):
     assert H.hsma_potrs(1, 4, -1, 1.0, 1, 4, 1, 4, check=False) == 1       # n < 0
     assert H.hsma_potrs(1, 4, 4, 1.0, 1, 4, 1, 2, check=False) == 1        # ldb < m
     assert H.hsma_potrs(1, 5, 0, 1.0, 0, 5, 0, 5, check=False) == 0        # n = 0: no-op
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/hsma.h is a C ABI: it compiles as strict C99 (and as C++), with no torch or
+    CUDA types in any signature."""
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = os.path.join(root, "include", "hsma.h")
+    code = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)  # declarations only
+    assert "torch" not in code and "cudaStream_t" not in code and "at::" not in code
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "c.c"
+    src.write_text('#include "hsma.h"\nint main(void) { return (int)(sizeof(hsma_opts_t) == 0); }\n')
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([gcc, "-x", lang, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                            "-I", os.path.dirname(hdr), str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr

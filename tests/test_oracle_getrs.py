@@ -79,3 +79,53 @@ def test_potrs_matches_lapack_and_residual(cx, m, n):
     assert np.linalg.norm(X - ref) <= 1e-12 * np.linalg.norm(ref)
     R = A @ X - alpha * B
     assert np.linalg.norm(R) <= 1e-12 * (np.linalg.norm(A) * np.linalg.norm(X) + abs(alpha) * np.linalg.norm(B))
+
+
+GETRS_MUTANTS = {
+    "interchanges applied in reverse order": (
+        "for k, p in enumerate(np.asarray(ipiv, dtype=np.int64)):",
+        "for k, p in reversed(list(enumerate(np.asarray(ipiv, dtype=np.int64)))):"),
+    "unit diagonal of L ignored": ("Y = solve_general(LU, Y, alpha, 0, 0, 0, True, _lib=_lib)",
+                                   "Y = solve_general(LU, Y, alpha, 0, 0, 0, False, _lib=_lib)"),
+    "upper factor read as lower": ("return solve_general(LU, Y, 1.0, 0, 1, 0, False, _lib=_lib)",
+                                   "return solve_general(LU, Y, 1.0, 0, 0, 0, False, _lib=_lib)"),
+}
+POTRS_MUTANTS = {
+    "second solve not transposed": ("return solve_general(Lf, Y, 1.0, 0, 0, 2 if np.iscomplexobj(Lf) else 1, False,",
+                                    "return solve_general(Lf, Y, 1.0, 0, 0, 0, False,"),
+    "transposed without conjugation": ("0, 0, 2 if np.iscomplexobj(Lf) else 1, False,", "0, 0, 1, False,"),
+}
+
+
+def _mutant(fn, old, new):
+    import inspect
+    src = inspect.getsource(fn)
+    assert src.count(old) == 1, f"mutation site not found: {old}"
+    ns = dict(vars(oracle))
+    exec(src.replace(old, new, 1), ns)
+    return ns[fn.__name__]
+
+
+@pytest.mark.parametrize("name", list(GETRS_MUTANTS))
+def test_getrs_pins_catch_mutant(name):
+    bad = _mutant(oracle.getrs, *GETRS_MUTANTS[name])
+    caught = False
+    for cx in (False, True):
+        A, LU, ipiv = _factors(17, 33, cx)
+        B = np.asfortranarray(np.arange(33 * 4, dtype=np.float64).reshape(33, 4) - 50.0)
+        if cx:
+            B = np.asfortranarray(B + 0.5j * B[::-1])
+        X = bad(LU, ipiv, B, 1.0)
+        ref = la.lu_solve((LU, ipiv - 1), B)
+        caught |= not np.linalg.norm(X - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert caught, name
+
+
+@pytest.mark.parametrize("name", list(POTRS_MUTANTS))
+def test_potrs_pins_catch_mutant(name):
+    bad = _mutant(oracle.potrs, *POTRS_MUTANTS[name])
+    A, Lf = _chol(5, 20, True)
+    B = np.asfortranarray(np.arange(60, dtype=np.float64).reshape(20, 3) * (1 - 0.5j))
+    X = bad(Lf, B, 1.0)
+    ref = la.cho_solve((Lf, True), B)
+    assert not np.linalg.norm(X - ref) <= 1e-12 * np.linalg.norm(ref), name

@@ -858,7 +858,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched_c128")
+    ap.add_argument("--workload", default="batched_c128",
+                    choices=["batched_c128", "batched_c64", "batched_lu_c128", "large_fp64", "large_c128",
+                             "single_fp64_64", "serve", "mixed_r32", "mixed_ir"],
+                    help="default: 8192 complex128 varlen solves per GPU")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -460,10 +460,15 @@ HSMA_API hsma_status_t hsma_gemm_f64_emulated(int64_t M, int64_t N, int64_t K, c
 
 /*
  * Device-side error bits the library's kernels raise (a bounded wait that ran
- * out: HSMA_DEVERR_TIMEOUT).  Synchronises the device, returns the bits
+ * out: HSMA_DEVERR_TIMEOUT; a refinement that did not converge:
+ * HSMA_DEVERR_NOT_CONVERGED).  Synchronises the device, returns the bits
  * accumulated since the last call in *out, and clears them.
  */
 #define HSMA_DEVERR_TIMEOUT 0x4u
+/* R64_IR: the refinement took ir_max_iter steps without reaching ir_tol.  The
+ * same solve called with a non-NULL hsma_info_t also returns
+ * HSMA_ERR_NOT_CONVERGED; without one this bit is the only report. */
+#define HSMA_DEVERR_NOT_CONVERGED 0x10u
 HSMA_API hsma_status_t hsma_device_status(unsigned int *out);
 
 /*

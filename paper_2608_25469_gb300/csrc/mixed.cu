@@ -518,14 +518,19 @@ __global__ void sumsq_kernel(const double *__restrict__ M_, int64_t ld, int64_t 
   if ((threadIdx.x & 31) == 0) atomicAdd(&sums[slot], acc);
 }
 
-// sums: [0] ||L||^2, [1] ||B||^2, [2] ||R||^2, [3] ||X||^2; state: [0] converged, [1] steps, [2..3] eta (double)
-__global__ void check_kernel(double *sums, int *state, double alpha_abs, double tol, int step) {
+// sums: [0] ||L||^2, [1] ||B||^2, [2] ||R||^2, [3] ||X||^2; state: [0] converged, [1] steps, [2..3] eta (double).
+// At the last allowed check (last != 0) a refinement that has not reached the
+// tolerance raises HSMA_DEVERR_NOT_CONVERGED in the device error word, so the
+// failure is visible to callers that do not ask for the info block.
+__global__ void check_kernel(double *sums, int *state, double alpha_abs, double tol, int step, int last,
+                             unsigned int *err) {
   if (state[0]) return;
   const double nr = sqrt(sums[2]), den = sqrt(sums[0]) * sqrt(sums[3]) + alpha_abs * sqrt(sums[1]);
   const double eta = den > 0.0 ? nr / den : nr;
   *reinterpret_cast<double *>(state + 2) = eta;
   state[1] = step;
   if (eta <= tol) state[0] = 1;
+  else if (last && err != nullptr) atomicOr(err, HSMA_DEVERR_NOT_CONVERGED);
   sums[2] = 0.0;
   sums[3] = 0.0;
 }
@@ -1166,7 +1171,8 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
         HsmaTraceScope ts("refine", st);
         sumsq_kernel<<<grid, 256, 0, st>>>(R64, m, m, n, 0, 0, sums, 2, state);
         sumsq_kernel<<<grid, 256, 0, st>>>(B, ldb, m, n, 0, 0, sums, 3, state);
-        check_kernel<<<1, 1, 0, st>>>(sums, state, std::fabs(alpha), tol, it);
+        check_kernel<<<1, 1, 0, st>>>(sums, state, std::fabs(alpha), tol, it, it == itmax ? 1 : 0,
+                                      hsma_dev_error_ptr());
         if (it == itmax) break;
         f64_to_f32_kernel<<<grid, 256, 0, st>>>(R64, m, R32, m, m, n, 0, state);
         if ((s = fail(cudaGetLastError())) != HSMA_OK) break;

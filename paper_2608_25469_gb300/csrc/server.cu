@@ -53,7 +53,7 @@ struct Req {
 };
 
 struct Flight {  // one launch in flight: a batched group or one blocked solve
-  std::vector<uint64_t> tickets;
+  std::vector<Req *> reqs;  // owned by hsma_server::all; a Req never moves
   cudaEvent_t ev = nullptr;
   void *meta = nullptr;  // device arrays of a batched group
   Clock::time_point fake_done;
@@ -74,9 +74,12 @@ struct hsma_server {
 
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<std::unique_ptr<Req>> all;  // indexed by ticket
-  std::deque<uint64_t> inbox;            // submitted, not yet seen by the scheduler
-  std::deque<uint64_t> pending;          // waiting for admission
+  // Every request, indexed by ticket.  The deque is only touched under `mu`;
+  // the scheduler works on the Req objects themselves (which never move) so
+  // it never indexes the deque while a submit may be growing it.
+  std::deque<std::unique_ptr<Req>> all;
+  std::deque<Req *> inbox;    // submitted, not yet seen by the scheduler
+  std::deque<Req *> pending;  // waiting for admission
   std::vector<Flight> flights;
   bool stop = false;
   std::thread worker;
@@ -161,31 +164,31 @@ void finish(hsma_server *s, Req &q, Clock::time_point now) {
 }
 
 // Launch what was admitted in this tick.  Called with the lock NOT held.
-void launch(hsma_server *s, std::vector<uint64_t> &small_group, std::vector<uint64_t> &large) {
+void launch(hsma_server *s, std::vector<Req *> &small_group, std::vector<Req *> &large) {
   std::vector<Flight> out;
   if (s->fake) {
     auto now = Clock::now();
     double tsum = 0.0;
     Flight f;
-    for (uint64_t t : small_group) tsum += fake_seconds(s->all[t]->r);
+    for (Req *q : small_group) tsum += fake_seconds(q->r);
     if (!small_group.empty()) {
-      f.tickets = small_group;
+      f.reqs = small_group;
       f.fake_done = now + std::chrono::microseconds((long)(tsum * 1e6));
       out.push_back(f);
     }
-    for (uint64_t t : large) {
+    for (Req *q : large) {
       Flight g;
-      g.tickets = {t};
-      g.fake_done = now + std::chrono::microseconds((long)(fake_seconds(s->all[t]->r) * 1e6));
+      g.reqs = {q};
+      g.fake_done = now + std::chrono::microseconds((long)(fake_seconds(q->r) * 1e6));
       out.push_back(g);
     }
   } else {
     cudaSetDevice(s->device);
     // one batched launch per dtype for the small requests, on stream 0
     for (int dt = HSMA_R64; dt <= HSMA_C128; ++dt) {
-      std::vector<uint64_t> g;
-      for (uint64_t t : small_group)
-        if (s->all[t]->r.dtype == dt) g.push_back(t);
+      std::vector<Req *> g;
+      for (Req *q : small_group)
+        if (q->r.dtype == dt) g.push_back(q);
       if (g.empty()) continue;
       cudaStream_t st = s->streams[0];
       const int nb = (int)g.size();
@@ -193,14 +196,14 @@ void launch(hsma_server *s, std::vector<uint64_t> &small_group, std::vector<uint
       std::vector<int32_t> hm(nb), hn(nb);
       std::vector<void *> ha(nb), hb(nb);
       for (int k = 0; k < nb; ++k) {
-        Req &q = *s->all[g[k]];
+        Req &q = *g[k];
         hm[k] = (int32_t)q.r.m;
         hn[k] = (int32_t)q.r.n;
         ha[k] = q.dA;
         hb[k] = q.dB;
       }
       Flight f;
-      f.tickets = g;
+      f.reqs = g;
       const size_t bytes = (size_t)nb * (3 * sizeof(int32_t) + 2 * sizeof(void *)) + 64;
       hsma_status_t rc = dev_alloc(s, &f.meta, bytes, st);
       hsma_status_t rc2 = HSMA_OK;
@@ -216,33 +219,33 @@ void launch(hsma_server *s, std::vector<uint64_t> &small_group, std::vector<uint
         cudaMemcpyAsync(dn, hn.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st);
         // alpha and diag per group: requests with different alpha/diag go one launch each
         // (grouped by the first request's values; others fall back to single launches)
-        const hsma_request_t &r0 = s->all[g[0]]->r;
+        const hsma_request_t &r0 = g[0]->r;
         bool uniform = true;
-        for (uint64_t t : g) {
-          const hsma_request_t &r = s->all[t]->r;
+        for (Req *q : g) {
+          const hsma_request_t &r = q->r;
           uniform &= r.alpha[0] == r0.alpha[0] && r.alpha[1] == r0.alpha[1] && r.diag == r0.diag;
         }
         if (uniform) {
           rc2 = hsma_trsm_llnn_vbatched(dt, r0.diag, nb, dm, dn, r0.alpha, (const void *const *)dpa, dm,
                                         (void *const *)dpb, dm, 64, 0, nullptr, st);
         } else {
-          for (uint64_t t : g) {
-            Req &q = *s->all[t];
+          for (Req *qp : g) {
+            Req &q = *qp;
             hsma_status_t r1 = hsma_trsm_llnn(dt, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st);
             if (r1 != HSMA_OK) rc2 = r1;
           }
         }
-        for (uint64_t t : g) fetch_output(s, *s->all[t]);
+        for (Req *q : g) fetch_output(s, *q);
         s->n_batched.fetch_add(1);
       }
       if (rc != HSMA_OK || rc2 != HSMA_OK)
-        for (uint64_t t : g) s->all[t]->status = rc != HSMA_OK ? rc : rc2;
+        for (Req *q : g) q->status = rc != HSMA_OK ? rc : rc2;
       cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
       cudaEventRecord(f.ev, st);
       out.push_back(f);
     }
-    for (uint64_t t : large) {
-      Req &q = *s->all[t];
+    for (Req *qp : large) {
+      Req &q = *qp;
       cudaStream_t st = s->streams[q.stream];
       hsma_opts_t o;
       std::memset(&o, 0, sizeof o);
@@ -253,7 +256,7 @@ void launch(hsma_server *s, std::vector<uint64_t> &small_group, std::vector<uint
       q.status = rc;
       s->n_blocked.fetch_add(1);
       Flight f;
-      f.tickets = {t};
+      f.reqs = {qp};
       cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
       cudaEventRecord(f.ev, st);
       out.push_back(f);
@@ -266,7 +269,7 @@ void launch(hsma_server *s, std::vector<uint64_t> &small_group, std::vector<uint
 void worker_loop(hsma_server *s) {
   if (!s->fake) cudaSetDevice(s->device);
   for (;;) {
-    std::vector<uint64_t> small_group, large;
+    std::vector<Req *> small_group, large;
     bool idle = true;
     {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -278,7 +281,7 @@ void worker_loop(hsma_server *s) {
       // admission in arrival order: a request that does not fit waits; later
       // ones that fit may go first (the budget is much larger than one request)
       for (auto it = s->pending.begin(); it != s->pending.end();) {
-        Req &q = *s->all[*it];
+        Req &q = **it;
         if (q.need > s->budget) {  // can never fit
           q.status = HSMA_ERR_NO_MEMORY;
           finish(s, q, Clock::now());
@@ -306,13 +309,13 @@ void worker_loop(hsma_server *s) {
     if (!small_group.empty() || !large.empty()) {
       idle = false;
       if (!s->fake) {
-        for (uint64_t t : small_group) {
-          hsma_status_t rc = stage_inputs(s, *s->all[t]);
-          if (rc != HSMA_OK) s->all[t]->status = rc;
+        for (Req *q : small_group) {
+          hsma_status_t rc = stage_inputs(s, *q);
+          if (rc != HSMA_OK) q->status = rc;
         }
-        for (uint64_t t : large) {
-          hsma_status_t rc = stage_inputs(s, *s->all[t]);
-          if (rc != HSMA_OK) s->all[t]->status = rc;
+        for (Req *q : large) {
+          hsma_status_t rc = stage_inputs(s, *q);
+          if (rc != HSMA_OK) q->status = rc;
         }
       }
       launch(s, small_group, large);
@@ -331,7 +334,7 @@ void worker_loop(hsma_server *s) {
             cudaError_t e = cudaEventQuery(it->ev);
             ready = e != cudaErrorNotReady;
             if (e != cudaSuccess && e != cudaErrorNotReady) {
-              for (uint64_t t : it->tickets) s->all[t]->status = HSMA_ERR_CUDA;
+              for (Req *q : it->reqs) q->status = HSMA_ERR_CUDA;
               (void)cudaGetLastError();
             }
           }
@@ -348,8 +351,8 @@ void worker_loop(hsma_server *s) {
         auto now = Clock::now();
         for (auto &f : done) {
           if (!s->fake) {
-            for (uint64_t t : f.tickets) {
-              Req &q = *s->all[t];
+            for (Req *qp : f.reqs) {
+              Req &q = *qp;
               cudaFreeAsync(q.dA, s->streams[q.stream]);
               cudaFreeAsync(q.dB, s->streams[q.stream]);
               q.dA = q.dB = nullptr;
@@ -358,8 +361,8 @@ void worker_loop(hsma_server *s) {
             cudaEventDestroy(f.ev);
           }
           std::lock_guard<std::mutex> lk(s->mu);
-          for (uint64_t t : f.tickets) {
-            Req &q = *s->all[t];
+          for (Req *qp : f.reqs) {
+            Req &q = *qp;
             s->in_use -= q.need;
             finish(s, q, now);
           }
@@ -436,8 +439,8 @@ HSMA_API hsma_status_t hsma_server_submit(hsma_server_t *s, const hsma_request_t
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return HSMA_ERR_BUSY;
     *ticket = s->all.size();
+    s->inbox.push_back(q.get());
     s->all.push_back(std::move(q));
-    s->inbox.push_back(*ticket);
   }
   s->n_sub.fetch_add(1);
   s->cv.notify_all();

@@ -74,7 +74,7 @@ struct TcArgs {
   int M, N, K;
   int tri;          // row tile i0 needs k < i0 + TC_BM only
   int nunits;       // accumulation units per tile (TC_F32: 1)
-  int band;         // cluster-tile rows per band of the tile order (set by the launcher)
+  int band;         // tile rows per band of the tile order (set by the launcher)
   uint8_t ubeg[kOzMaxUnits + 1];  // unit u accumulates pairs ubeg[u] .. ubeg[u+1]-1
   int8_t uexp[kOzMaxUnits];       // TC_OZ: weight exponent of unit u
   uint8_t pa[kOzPairs], pb[kOzPairs];  // slice of A and of B for each pair
@@ -110,16 +110,12 @@ __device__ __forceinline__ double oz_scale(uint32_t f, int shift) {
 // alternate between items, so the epilogue of one item runs while the next
 // item's products accumulate.  Tiles are dealt round-robin to the CTAs (one
 // per SM).  Operands are 3-D: (K, rows, slice); a unit sums the products of
-// its slice pairs over the whole K range in one accumulator.
-// CL = 2: clusters of two CTAs own vertically adjacent tiles (m0, m0 + 128)
-// with the same columns; each CTA loads its own A tile and one half of the
-// shared B tile, multicast into both CTAs' shared memory, which cuts the
-// operand traffic from L2 per product by a third.  A stage is refilled only
-// after both CTAs' MMAs released it (commits multicast to both CTAs).
+// its slice pairs over the whole K range in one accumulator.  Every CTA loads
+// its own A and B tiles with plain (single-CTA) TMA.
 constexpr int TC_WARPS = 10;
 constexpr int TC_EPI_WARPS = 8;
 
-template <int MODE, int CL>
+template <int MODE>
 __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                    const __grid_constant__ CUtensorMap mapB,
                                                                    const __grid_constant__ TcArgs p) {
@@ -134,34 +130,31 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = p.M, N = p.N, nunits = p.nunits;
-  uint32_t rank = 0;
-  if constexpr (CL > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+  const int cid = blockIdx.x, ncl = gridDim.x;
   const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TC_BN - 1) / TC_BN;
-  const int tiles_mc = (tiles_m + CL - 1) / CL;
-  const int ntiles = tiles_mc * tiles_n;  // cluster tiles
-  // Cluster tiles run in bands of p.band cluster-tile rows, column by column
-  // inside a band.  For short K the host picks 16 tile rows, so the tiles in
-  // flight at once (one per SM) cover about 16 row tiles x 10 column tiles and
-  // their operand slices stay in L2 while every slice pair re-reads them; for
+  const int ntiles = tiles_m * tiles_n;
+  // Tiles run in bands of p.band tile rows, column by column inside a band.
+  // For short K the host picks 16 tile rows, so the tiles in flight at once
+  // (one per SM) cover about 16 row tiles x 10 column tiles and their operand
+  // slices stay in L2 while every slice pair re-reads them; for
   // long K one band spans all rows (column-major order), so the right operand's
   // slices are shared by every row tile in flight.
   const int G = max(1, p.band);
-  auto tile_k = [&](int t, int &m0, int &n0) {  // cluster tile -> this CTA's origin and K-block count
+  auto tile_k = [&](int t, int &m0, int &n0) {  // tile -> its origin and K-block count
     const int band = t / (G * tiles_n);
-    const int gb = min(G, tiles_mc - band * G);
+    const int gb = min(G, tiles_m - band * G);
     const int idx = t - band * G * tiles_n;
     const int pm = band * G + idx % gb;
-    m0 = (pm * CL + (int)rank) * TC_BM;
+    m0 = pm * TC_BM;
     n0 = (idx / gb) * TC_BN;
-    const int kall = p.tri ? min(p.K, (pm + 1) * CL * TC_BM) : p.K;  // the same in every CTA of a cluster
+    const int kall = p.tri ? min(p.K, (pm + 1) * TC_BM) : p.K;
     return (kall + TC_BK - 1) / TC_BK;
   };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -178,7 +171,6 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL > 1) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
@@ -201,11 +193,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
             unsigned char *st = smem + s * TC_STAGE_BYTES;
             mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
             tma_load_3d(st, &mapA, &full[s], kb * TC_BK, m0, sa);
-            if constexpr (CL == 1)
-              tma_load_3d(st + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0, sb);
-            else
-              tma_load_3d_multicast(st + TC_A_BYTES + rank * (TC_B_BYTES / CL), &mapB, &full[s], kb * TC_BK,
-                                    n0 + (int)rank * (TC_BN / CL), sb, (uint16_t)((1u << CL) - 1));
+            tma_load_3d(st + TC_A_BYTES, &mapB, &full[s], kb * TC_BK, n0, sb);
           }
         }
       }
@@ -248,16 +236,9 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
                     : "memory");
                 accum = 1u;
               }
-              if constexpr (CL == 1)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&empty[s]))
-                             : "memory");
-              else
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], "
-                    "%1;" ::"r"(smem_u32(&empty[s])),
-                    "h"((uint16_t)((1u << CL) - 1))
-                    : "memory");
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                               smem_u32(&empty[s]))
+                           : "memory");
             }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -352,8 +333,6 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_TMEM_COLS)
                  : "memory");
   }
-  // no CTA leaves while its peer may still signal its barriers
-  if constexpr (CL > 1) cluster_sync();
 }
 
 // 3-D tensor map over BF16 operand slices (K contiguous, rows, slice), one
@@ -371,15 +350,6 @@ bool make_slice_map(CUtensorMap *map, const void *base, uint64_t K, uint64_t row
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Clusters of two CTAs unless HSMA_TC_CLUSTER=1 (a tuning knob, read once).
-int tc_cluster_pref() {
-  static const int v = [] {
-    const char *e = std::getenv("HSMA_TC_CLUSTER");
-    return (e != nullptr && std::atoi(e) == 1) ? 1 : 2;
-  }();
-  return v;
-}
-
 // Layout of an operand's slice stack in memory: rows, K extent addressable
 // from the base (0: the product's K), row stride and slice stride in elements
 // (0: dense, ld = K extent, sst = rows * ld).  A view into a larger stack (a
@@ -390,8 +360,7 @@ struct SliceLayout {
 
 // Launch the persistent product.  A: sa slices of M x K (row-major), B: sb
 // slices of N x K; the unit table of a0 names the slice pairs (TC_F32: one
-// unit, one pair, filled in here unless given).  Pairs of row tiles run as
-// clusters of two CTAs sharing the B tile.
+// unit, one pair, filled in here unless given).  One CTA per SM.
 template <int MODE>
 hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, int sb, const TcArgs &a0,
                       const char *phase, cudaStream_t st, SliceLayout la = {}, SliceLayout lb = {}) {
@@ -400,13 +369,10 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   static DeviceFlags attr;
   if (!attr.test()) {
     HSMA_CUDA_TRY(
-        cudaFuncSetAttribute(tc_gemm_kernel<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    HSMA_CUDA_TRY(
-        cudaFuncSetAttribute(tc_gemm_kernel<MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     attr.set();
   }
   const int tiles_m = (a0.M + TC_BM - 1) / TC_BM, tiles_n = (a0.N + TC_BN - 1) / TC_BN;
-  const int cl = (tiles_m >= 2 && tc_cluster_pref() == 2) ? 2 : 1;
   CUtensorMap ma, mb;
   auto dense = [&](SliceLayout l, int64_t rows) {
     if (l.rows == 0) l.rows = rows;
@@ -420,7 +386,7 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   if (la.kext < a0.K || lb.kext < a0.K) return HSMA_ERR_INVALID_ARG;
   if (!make_slice_map(&ma, Ap, (uint64_t)la.kext, (uint64_t)la.rows, (uint64_t)sa, TC_BM, (uint64_t)la.ld,
                       (uint64_t)la.sst) ||
-      !make_slice_map(&mb, Bp, (uint64_t)lb.kext, (uint64_t)lb.rows, (uint64_t)sb, TC_BN / cl, (uint64_t)lb.ld,
+      !make_slice_map(&mb, Bp, (uint64_t)lb.kext, (uint64_t)lb.rows, (uint64_t)sb, TC_BN, (uint64_t)lb.ld,
                       (uint64_t)lb.sst))
     return HSMA_ERR_CUDA;
   TcArgs a = a0;
@@ -441,27 +407,11 @@ hsma_status_t tc_gemm(const __nv_bfloat16 *Ap, int sa, const __nv_bfloat16 *Bp, 
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return HSMA_ERR_UNSUPPORTED;
   if (nsm[dev] == 0) HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
-  const int ctiles = ((tiles_m + cl - 1) / cl) * tiles_n;
-  a.band = a.K <= 2048 ? 16 / cl : (tiles_m + cl - 1) / cl;
-  const int clusters = std::max(1, std::min(ctiles, nsm[dev] / cl));
+  const int ntiles = tiles_m * tiles_n;
+  a.band = a.K <= 2048 ? 16 : tiles_m;
+  const int grid = std::max(1, std::min(ntiles, nsm[dev]));
   HsmaTraceScope ts(phase, st);
-  if (cl == 1) {
-    tc_gemm_kernel<MODE, 1><<<clusters, 32 * TC_WARPS, TC_SMEM, st>>>(ma, mb, a);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(clusters * cl));
-    cfg.blockDim = dim3(32 * TC_WARPS);
-    cfg.dynamicSmemBytes = TC_SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cl;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    HSMA_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE, 2>, ma, mb, a));
-  }
+  tc_gemm_kernel<MODE><<<grid, 32 * TC_WARPS, TC_SMEM, st>>>(ma, mb, a);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }

@@ -79,23 +79,6 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
-// 3-D tiled TMA load multicast to the CTAs of this cluster in cta_mask: the
-// box lands at the same shared-memory offset in each, and each CTA's mbarrier
-// at the offset of `bar` receives the completed bytes.
-__device__ __forceinline__ void tma_load_3d_multicast(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
-                                                      int z, uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
-      "%4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "h"(cta_mask)
-      : "memory");
-}
-
-// All threads of all CTAs of the cluster (release / acquire).
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // ---------------------------------------------------------------------------
 // Host: encode a 2-D tensor map over a column-major matrix of 8-byte words
 // (rows x cols, leading dimension ld words), box box_rows x box_cols.

@@ -28,6 +28,7 @@ PATH_AUTO, PATH_SMALL, PATH_BLOCKED = 0, 1, 2
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_BUSY = range(1, 8)
 DEVERR_BAD_SIZE, DEVERR_NULL_PTR, DEVERR_TIMEOUT, DEVERR_BAD_PIVOT = 0x1, 0x2, 0x4, 0x8
+DEVERR_NOT_CONVERGED = 0x10
 STATUS_NAMES = {0: "HSMA_OK", 1: "HSMA_ERR_INVALID_ARG", 2: "HSMA_ERR_UNSUPPORTED", 3: "HSMA_ERR_NO_MEMORY",
                 4: "HSMA_ERR_CUDA", 5: "HSMA_ERR_TIMEOUT", 6: "HSMA_ERR_NOT_CONVERGED", 7: "HSMA_ERR_BUSY"}
 

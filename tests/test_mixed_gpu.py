@@ -134,3 +134,53 @@ def test_ir_mode_unit_diagonal_emulated(H):
     X = H.from_device(dB)
     assert info.converged == 1
     assert oracle.forward_error(X, oracle.solve(A1, B, -0.5)) <= 1e-12
+
+
+def test_ir_not_converged_reported_without_info(H):
+    """A refinement that cannot reach its tolerance within ir_max_iter steps is not
+    silent: called with no info block the solve returns OK (asynchronous) but the
+    device error word carries HSMA_DEVERR_NOT_CONVERGED; with an info block the
+    call returns HSMA_ERR_NOT_CONVERGED."""
+    import torch
+    m, n = 600, 40
+    A, B = I.gen_A(21, m, I.R64), I.gen_B(21, m, n, I.R64)
+    assert H.hsma_device_status() == 0
+    opts = H.Opts()
+    opts.ir_max_iter = 1
+    opts.ir_tol = 1e-300  # unreachable
+    dA, dB = H.to_device(A), H.to_device(B)
+    s = H.hsma_trsm_llnn_ex(H.R64_IR, 0, m, n, 1.0, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts)
+    assert s == 0
+    torch.cuda.synchronize()
+    assert H.hsma_device_status() == H.DEVERR_NOT_CONVERGED
+    assert H.hsma_device_status() == 0  # cleared by the read
+    # the result is still the refined one (one step), within the FP64 tolerance
+    assert oracle.forward_error(H.from_device(dB), oracle.solve(A, B, 1.0)) <= 1e-12
+    dB = H.to_device(B)
+    info = H.Info()
+    s = H.hsma_trsm_llnn_ex(H.R64_IR, 0, m, n, 1.0, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr(), opts=opts,
+                            info=info, check=False)
+    torch.cuda.synchronize()
+    assert s == 6 and info.converged == 0 and info.ir_iters == 1
+    H.hsma_device_status()
+    # a reachable tolerance raises nothing
+    dB = H.to_device(B)
+    H.hsma_trsm_llnn_ex(H.R64_IR, 0, m, n, 1.0, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr())
+    torch.cuda.synchronize()
+    assert H.hsma_device_status() == 0
+
+
+def test_ir_mode_config3_sampled(H):
+    """FP64-result mode at the m = 8192, n = 4096 workload size: forward error on 64
+    sampled columns against the FP64 oracle (exact per column) <= 1e-12, and the
+    normwise residual ratio reported by the refinement <= 1e-15."""
+    m, n = 8192, 4096
+    A = I.gen_A(0, m, I.R64)
+    B = I.gen_B(0, m, n, I.R64)
+    X, info = _ir(H, A, B, 1.0)
+    assert info.converged == 1 and info.ir_residual <= 1e-15
+    cols = np.arange(0, n, 64)
+    ref = oracle.solve_cols(A, B, 1.0, cols)
+    err = oracle.forward_error(X[:, cols], ref)
+    assert err <= 1e-12, err
+    assert H.hsma_device_status() == 0

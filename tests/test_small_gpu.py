@@ -227,8 +227,11 @@ def test_batched_host_buffers_equal_device_batch(H, code, chunks, pinned):
 
 
 def test_host_buffers_with_gaps_and_empty_instances(H):
-    """Offsets with gaps between instances (never read nor written) and instances with
-    m = 0 or n = 0 (skipped): the solved instances equal the device batch's results."""
+    """Offsets with gaps between instances and instances with m = 0 or n = 0 (skipped):
+    the solved instances equal the device batch's results.  Each group of consecutive
+    instances is copied as one range, so a gap inside a group receives hB's gap
+    elements and a gap between groups (or before the first / after the last
+    instance) keeps hX's old contents."""
     import torch
     alpha = 0.5 - 1.5j
     As, Bs = _config1(I.C128, batch=300, seed=12)
@@ -250,12 +253,18 @@ def test_host_buffers_with_gaps_and_empty_instances(H):
     H.hsma_trsm_llnn_vbatched_host(I.C128, 0, len(As), ms, ns, alpha, hA.ctypes.data, offA, hB.ctypes.data, offB,
                                    hX.ctypes.data, chunks=5, stream=H.stream_ptr())
     torch.cuda.synchronize()
-    touched = np.zeros(hX.size, bool)
     for b in range(len(As)):
         sl = slice(offB[b], offB[b] + ms[b] * ns[b])
-        touched[sl] = True
         assert np.array_equal(hX[sl].reshape((ms[b], ns[b]), order="F"), dev[b]), b
     assert np.all(hX[:2] == 7.0) and np.all(hX[-gap:] == 7.0)
+    per = -(-len(As) // 5)  # instances per group for chunks = 5
+    for b in range(len(As) - 1):
+        g = hX[offB[b] + ms[b] * ns[b]:offB[b + 1]]
+        assert g.size == gap
+        if b // per == (b + 1) // per:  # inside one group: hB's gap elements (NaN)
+            assert np.all(np.isnan(g)), b
+        else:  # between groups: untouched
+            assert np.all(g == 7.0), b
 
 
 def test_golden_integer_solves_bitwise(H):

@@ -190,6 +190,7 @@ def profile_traffic(name: str, files, work=None):
 
 
 SMALL_SOURCES = ["paper_2608_25469_gb300/csrc/small.cu", "paper_2608_25469_gb300/csrc/common.cuh"]
+PACKED_SOURCES = ["paper_2608_25469_gb300/csrc/packed.cu", "paper_2608_25469_gb300/csrc/common.cuh"]
 
 
 def batched_inputs(seed, batch=8192, c64=False):
@@ -275,6 +276,7 @@ def run_batched(args, dist, device, c64=False):
     H.hsma_trace_enable(False)
     ms_total = e0.elapsed_time(e1)
     solve_ms, solve_cnt = H.hsma_trace_read("vbatched_solve")
+    phases = {ph: H.hsma_trace_read(ph) for ph in ("vbatched_schedule", "vbatched_prep", "vbatched_solve")}
     launches = H.hsma_trace_launches()
     clocks = None
     if sampler:
@@ -336,6 +338,7 @@ def run_batched(args, dist, device, c64=False):
         "roofline": roof,
         "e2e": {"value": round(e2e_value, 3), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(hostA.nbytes + hostB.nbytes), "d2h_bytes_per_step": int(hostB.nbytes)},
+        "phases_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in phases.items() if v[1]},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

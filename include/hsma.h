@@ -191,14 +191,20 @@ HSMA_API hsma_status_t hsma_trsm(int dtype, int side, int uplo, int trans, int d
  * d_m, d_n, d_lda, d_ldb: DEVICE arrays of `batch` int32 sizes.
  * d_A, d_B: DEVICE arrays of `batch` device pointers.
  * max_m  host upper bound on every m_i: 1..64, or 0 for "unknown" (taken as
- *        64); a larger value returns HSMA_ERR_UNSUPPORTED (use hsma_trsm_llnn
- *        per instance for m > 64).
+ *        64); it sizes the workspace, and an instance with m_i > max_m is
+ *        skipped and flagged HSMA_DEVERR_BAD_SIZE; a larger value returns
+ *        HSMA_ERR_UNSUPPORTED (use hsma_trsm_llnn per instance for m > 64).
  * max_n  host upper bound on every n_i, or 0 if unknown (only a hint).
  * d_status: optional DEVICE uint32 word; the kernel ORs HSMA_DEVERR_* bits into
  *        it for instances it skips as invalid.  May be NULL.
- * Instances are scheduled longest first; each instance's arithmetic does not
- * depend on the others, so results are bit-identical to solving it alone
- * through this entry point with batch = 1.
+ * The columns of all instances with the same m are dealt to warps 32 (or,
+ * for complex128 with m > 32, 16) at a time, so a warp may serve several
+ * instances; an instance's arithmetic never depends on the others, so results
+ * are bit-identical to solving it alone through this entry point with
+ * batch = 1.  Workspace (stream-ordered pool): room for the pre-scaled
+ * triangle and diagonal of every instance, batch x r (r + 1) / 2 elements
+ * with r = max_m (rounded up to even for complex128), plus 20 bytes per
+ * instance.
  */
 HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const int32_t *d_m,
                                       const int32_t *d_n, const void *alpha, const void *const *d_A,

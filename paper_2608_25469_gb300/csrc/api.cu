@@ -23,6 +23,15 @@
 namespace {
 
 bool valid_dtype(int d) { return d >= HSMA_R64 && d <= HSMA_C64; }
+
+// Column-packed varlen batch unless HSMA_VB_PACKED=0 (read once).
+bool packed_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("HSMA_VB_PACKED");
+    return !(e != nullptr && std::atoi(e) == 0);
+  }();
+  return on;
+}
 bool is_complex(int d) { return d == HSMA_C128 || d == HSMA_C64; }
 bool valid_diag(int d) { return d == HSMA_NON_UNIT || d == HSMA_UNIT; }
 
@@ -260,10 +269,21 @@ hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int d
     return HSMA_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void *scratch = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
+  // the paper's case in FP64 runs the column-packed batch (the FP64 pipe
+  // binds, so full warp tiles pay); FP32 types and the other variants the
+  // per-instance kernel (with its index map)
+  const bool packed = uplo == HSMA_LOWER && trans == HSMA_NO_TRANS && (dtype == HSMA_R64 || dtype == HSMA_C128) &&
+                      packed_enabled();
+  hsma_status_t s = hsma_ws_alloc(
+      &scratch, packed ? hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m) : hsma_vbatched_scratch_bytes(batch),
+      st);
   if (s != HSMA_OK) return s;
-  s = hsma_small_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda, d_B, d_ldb,
-                          diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st, uplo, trans);
+  if (packed)
+    s = hsma_small_vbatched_packed(dtype, batch, max_m, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda,
+                                   d_B, d_ldb, diag == HSMA_UNIT, d_status, scratch, st);
+  else
+    s = hsma_small_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda, d_B, d_ldb,
+                            diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st, uplo, trans);
   hsma_status_t f = hsma_ws_free(scratch, st);
   return s != HSMA_OK ? s : f;
 }

@@ -1,0 +1,497 @@
+// Column-packed varlen batch of small solves (m <= 64), the paper's
+// left / lower / no-transpose case (Section 4.2.1's direct solve, batched).
+//
+// The FP64 pipe bounds this work, and a warp-wide FP64 instruction costs the
+// same whether 1 or 32 of its lanes do useful work.  Solving instance by
+// instance leaves lanes idle whenever n is not a multiple of a warp's column
+// count, and warps of a CTA idle while the busiest one finishes the instance.
+// Here the columns of ALL instances with the same m form one stream: a warp
+// takes 32/G consecutive columns of that stream, which may belong to several
+// instances, so every warp tile is full except the last one of each m.
+//
+//  1. schedule (one CTA): validates the instances, groups them by m, orders
+//     the groups by the cost of one warp tile (longest first), and writes
+//     per position in that order the instance and its first column in the
+//     stream (staged triangles lie position by position);
+//  2. prep (all SMs, one warp per instance): 1/a_rr, alpha/a_rr and the
+//     strict lower triangle with row r pre-multiplied by 1/a_rr, packed by
+//     columns into a workspace (the same products the shared-memory staging
+//     of the per-instance kernel computes, so results agree bit for bit);
+//  3. solve (persistent, independent warps): each warp pulls a tile, finds
+//     the instance and column of each of its lanes, keeps its columns of X in
+//     registers (lane group g of G lanes holds rows g, g+G, ...) and runs the
+//     forward substitution, reading the staged triangles through the L1/L2
+//     caches: at this GPU's FP64 rate one 16-byte operand per 64-cycle warp
+//     instruction is far below what the caches deliver.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "small.h"
+#include "trace.h"
+
+namespace {
+
+constexpr int kPkWarps = 4;     // warps per CTA of the solve kernel (independent)
+constexpr int kPkMinBlocks = 3;  // resident CTAs per SM (register cap of the solve kernel)
+constexpr int kPkSchedThreads = 1024;
+constexpr int kPkHeaderWords = 8;
+
+// Rows per lane group G of the packed solve: FP64 complex values take four
+// registers each, so m > 32 spreads a column over two lanes; every other
+// element type keeps whole columns of up to 64 rows in one lane.
+template <class T>
+__host__ __device__ constexpr bool pk_two_lanes() {
+  return sizeof(T) == 16;
+}
+__host__ __device__ inline int pk_groups(int m, bool two_lanes) { return (two_lanes && m > 32) ? 2 : 1; }
+// rows stored per column of a staged triangle: m rounded up to the lane groups
+__host__ __device__ inline int pk_rows(int m, int g) { return ((m + g - 1) / g) * g; }
+// packed strict-lower triangle of `rows` rows: column i holds rows i+1 .. rows-1
+__host__ __device__ inline int64_t pk_col_off(int i, int rows) {
+  return (int64_t)i * (rows - 1) - ((int64_t)i * (i - 1)) / 2;
+}
+__host__ __device__ inline int64_t pk_tri_elems(int rows) { return pk_col_off(rows, rows); }
+// staged elements per instance: the triangle, then alpha/a_rr for every row
+__host__ __device__ inline int64_t pk_stage_elems(int m, bool two_lanes) {
+  const int rows = pk_rows(m, pk_groups(m, two_lanes));
+  return pk_tri_elems(rows) + rows;
+}
+
+// Scratch layout (bytes, each part 256-aligned):
+//   header  int32[8]       [0] next tile, [1] tiles, [2] groups, [3] positions
+//   groups  int32[64][16]  per group of equal m, in schedule order: m, G,
+//                          first tile, first position, end position, staged
+//                          elements per instance, first stream column
+//                          (int64, words 6..7), first staged element (int64,
+//                          words 8..9)
+//   inst    int32[batch]   instance at each position
+//   colpref int64[batch+1] first stream column of each position
+//   stage   T[...]         staged triangles, position by position
+struct PkLayout {
+  size_t groups, inst, colpref, stage, total;
+};
+
+constexpr int kPkGroupWords = 16;
+
+// Groups in schedule order: m values by decreasing FP64 instructions of one
+// warp tile (longest first), computed on the host.
+struct PkOrder {
+  uint8_t m[64];
+};
+
+inline size_t pk_align(size_t v) { return (v + 255) & ~(size_t)255; }
+
+PkLayout pk_layout(int32_t batch, int max_m, int esize, bool two_lanes) {
+  PkLayout L;
+  const size_t b = (size_t)(batch > 0 ? batch : 0);
+  const int mm = (max_m <= 0 || max_m > 64) ? 64 : max_m;
+  L.groups = pk_align(sizeof(int32_t) * kPkHeaderWords);
+  L.inst = L.groups + pk_align(sizeof(int32_t) * 64 * kPkGroupWords);
+  L.colpref = L.inst + pk_align(sizeof(int32_t) * b);
+  L.stage = L.colpref + pk_align(sizeof(int64_t) * (b + 1));
+  // every instance's staged size is at most that of an m = max_m instance
+  int64_t per = 0;
+  for (int m = 1; m <= mm; ++m) per = per > pk_stage_elems(m, two_lanes) ? per : pk_stage_elems(m, two_lanes);
+  L.total = L.stage + pk_align((size_t)per * b * (size_t)esize);
+  return L;
+}
+
+PkOrder pk_order(bool two_lanes, bool cplx_) {
+  PkOrder o;
+  long long cost[64];
+  int n = 0;
+  for (int m = 64; m >= 1; --m) {
+    const long long c = hsma_small_tile_instr(m, pk_groups(m, two_lanes), cplx_);
+    int k = n++;
+    while (k > 0 && cost[k - 1] < c) {
+      o.m[k] = o.m[k - 1];
+      cost[k] = cost[k - 1];
+      --k;
+    }
+    o.m[k] = (uint8_t)m;
+    cost[k] = c;
+  }
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// 1. Schedule.  One CTA, two passes over the instances.  Instances with m = 0
+// or n = 0 are valid and need no work; invalid ones set a status bit and are
+// skipped (as the per-instance kernel does).  An instance above mmax (the
+// caller's bound, which sized the staging workspace) counts as invalid.  One
+// 64-bit atomic per instance hands out its position within the group (high
+// bits) and its first column within the group's stream (low bits) together,
+// so stream columns increase with the position.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kPkSchedThreads) packed_schedule_kernel(
+    int batch, const int32_t *__restrict__ dm, const int32_t *__restrict__ dn, const int32_t *__restrict__ dlda,
+    const int32_t *__restrict__ dldb, const void *const *__restrict__ dA, void *const *__restrict__ dB,
+    unsigned char *scratch, PkLayout L, int mmax, PkOrder order, uint32_t *status) {
+  constexpr bool two = pk_two_lanes<T>();
+  constexpr int kColBits = 40;
+  __shared__ int cnt[65], gpos0[65];
+  __shared__ unsigned long long csum[65], cur[65];
+  __shared__ long long gcol0[65];
+  __shared__ int s_over;
+  int32_t *hdr = reinterpret_cast<int32_t *>(scratch);
+  int32_t *grp = reinterpret_cast<int32_t *>(scratch + L.groups);
+  int32_t *inst = reinterpret_cast<int32_t *>(scratch + L.inst);
+  int64_t *colpref = reinterpret_cast<int64_t *>(scratch + L.colpref);
+  const int tid = threadIdx.x;
+  for (int k = tid; k < 65; k += blockDim.x) {
+    cnt[k] = 0;
+    csum[k] = 0;
+    cur[k] = 0;
+  }
+  __syncthreads();
+  uint32_t err = 0;
+  auto valid = [&](int b, int &m, int &n) {
+    m = dm[b];
+    n = dn[b];
+    const int lo = m > 1 ? m : 1;
+    if (m < 0 || n < 0 || m > mmax || dlda[b] < lo || dldb[b] < lo) {
+      err |= HSMA_DEVERR_BAD_SIZE;
+      return false;
+    }
+    if (m == 0 || n == 0) return false;
+    if (dA[b] == nullptr || dB[b] == nullptr) {
+      err |= HSMA_DEVERR_NULL_PTR;
+      return false;
+    }
+    return true;
+  };
+  for (int b = tid; b < batch; b += blockDim.x) {
+    int m, n;
+    if (!valid(b, m, n)) continue;
+    atomicAdd(&cnt[m], 1);
+    atomicAdd(&csum[m], (unsigned long long)n);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // a group's column count must fit the low bits of the cursor
+    s_over = 0;
+    for (int m = 1; m <= 64; ++m) s_over |= csum[m] >= (1ull << kColBits) ? 1 : 0;
+    int ng = 0, pos = 0, tile = 0;
+    long long col = 0, stg = 0;
+    for (int k = 0; k < 64; ++k) {
+      const int m = order.m[k];
+      if (cnt[m] == 0) continue;
+      const int g = pk_groups(m, two);
+      const long long tiles = g == 1 ? ((long long)csum[m] + 31) >> 5 : ((long long)csum[m] + 15) >> 4;
+      const int se = (int)pk_stage_elems(m, two);
+      int32_t *e = grp + ng * kPkGroupWords;
+      e[0] = m;
+      e[1] = g;
+      e[2] = tile;
+      e[3] = pos;
+      e[4] = pos + cnt[m];
+      e[5] = se;
+      *reinterpret_cast<long long *>(e + 6) = col;
+      *reinterpret_cast<long long *>(e + 8) = stg;
+      gpos0[m] = pos;
+      gcol0[m] = col;
+      ++ng;
+      pos += cnt[m];
+      tile += (int)tiles;
+      col += (long long)csum[m];
+      stg += (long long)cnt[m] * se;
+    }
+    if (s_over) {  // nothing is solved; the caller sees BAD_SIZE
+      ng = pos = tile = 0;
+      col = 0;
+      err |= HSMA_DEVERR_BAD_SIZE;
+    }
+    hdr[0] = 0;
+    hdr[1] = tile;
+    hdr[2] = ng;
+    hdr[3] = pos;
+    colpref[pos] = col;
+  }
+  __syncthreads();
+  for (int b = tid; b < batch && !s_over; b += blockDim.x) {
+    int m, n;
+    if (!valid(b, m, n)) continue;
+    const unsigned long long old = atomicAdd(&cur[m], (1ull << kColBits) + (unsigned long long)n);
+    const int p = gpos0[m] + (int)(old >> kColBits);
+    inst[p] = b;
+    colpref[p] = gcol0[m] + (long long)(old & ((1ull << kColBits) - 1));
+  }
+  if (err != 0 && status != nullptr) atomicOr(status, err);
+}
+
+// Copy the group table into shared memory (every thread of the CTA).
+__device__ __forceinline__ int pk_load_groups(const unsigned char *scratch, const PkLayout &L, int32_t *sgrp) {
+  const int32_t *hdr = reinterpret_cast<const int32_t *>(scratch);
+  const int32_t *grp = reinterpret_cast<const int32_t *>(scratch + L.groups);
+  const int ng = hdr[2];
+  for (int k = threadIdx.x; k < ng * kPkGroupWords; k += blockDim.x) sgrp[k] = grp[k];
+  __syncthreads();
+  return ng;
+}
+
+// ---------------------------------------------------------------------------
+// 2. Prep: one warp per position.  The reciprocals of the diagonal go to a
+// per-warp shared row table; then the lanes walk the packed triangle element
+// by element (consecutive elements in consecutive lanes), so every lane of
+// every FP64 instruction produces a staged value.
+// ---------------------------------------------------------------------------
+constexpr int kPkPrepWarps = 8;
+
+template <class T>
+__global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const int32_t *__restrict__ dm,
+                                                                       const void *const *__restrict__ dA,
+                                                                       const int32_t *__restrict__ dlda,
+                                                                       const unsigned char *__restrict__ scratch,
+                                                                       PkLayout L, T *stage, T alpha, int unit) {
+  using E = Elem<T>;
+  __shared__ __align__(16) int32_t sgrp[64 * kPkGroupWords];
+  __shared__ T sR[kPkPrepWarps][64];
+  const int ng = pk_load_groups(scratch, L, sgrp);
+  const int32_t *hdr = reinterpret_cast<const int32_t *>(scratch);
+  const int32_t *inst = reinterpret_cast<const int32_t *>(scratch + L.inst);
+  const int np = hdr[3];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int wid = blockIdx.x * kPkPrepWarps + w, nw = gridDim.x * kPkPrepWarps;
+  T *rinv = sR[w];
+  int k = 0;
+  for (int p = wid; p < np; p += nw) {
+    while (k + 1 < ng && sgrp[(k + 1) * kPkGroupWords + 3] <= p) ++k;  // positions only grow
+    const int32_t *e = sgrp + k * kPkGroupWords;
+    const int m = e[0], rows = pk_rows(m, e[1]);
+    const int64_t off = *reinterpret_cast<const long long *>(e + 8) + (int64_t)(p - e[3]) * e[5];
+    const int b = inst[p];
+    const T *A = static_cast<const T *>(dA[b]);
+    const int64_t lda = dlda[b];
+    T *tri = stage + off;
+    T *sc = tri + pk_tri_elems(rows);
+    __syncwarp();
+    for (int r = lane; r < rows; r += 32) {  // warp-uniform trip count per 32 rows
+      T rv = E::one();
+      if (r < m && !unit) rv = E::recip(E::ld(A + r + (int64_t)r * lda));
+      rinv[r] = rv;
+      sc[r] = r < m ? E::mul(alpha, rv) : E::zero();
+    }
+    __syncwarp();
+    // element q of the packed triangle: column i, row i + 1 + local index
+    const int total = (int)pk_tri_elems(rows);
+    int i = 0, loc = lane;
+    while (i < rows - 1 && loc >= rows - 1 - i) {
+      loc -= rows - 1 - i;
+      ++i;
+    }
+    for (int q = lane; q < total; q += 32) {
+      const int r = i + 1 + loc;
+      const T v = r < m ? E::ld(A + r + (int64_t)i * lda) : E::zero();
+      tri[q] = E::mul(rinv[r], v);
+      loc += 32;
+      while (i < rows - 1 && loc >= rows - 1 - i) {
+        loc -= rows - 1 - i;
+        ++i;
+      }
+    }
+  }
+}
+
+// Staged values are 16-byte aligned: complex128 is read as one vector.
+template <class T>
+__device__ __forceinline__ T pk_ld(const T *p) {
+  return Elem<T>::ld(p);
+}
+template <>
+__device__ __forceinline__ cplx pk_ld<cplx>(const cplx *p) {
+  const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+  return cplx{v.x, v.y};
+}
+
+// ---------------------------------------------------------------------------
+// 3. Solve.  A warp tile: C = 32/G columns of one m's stream; lane l holds
+// column c = l / G of the tile, rows g + t*G (g = l % G) in register slot t.
+// ---------------------------------------------------------------------------
+template <class T, int G, int MMAX>
+__device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bool active, int m, int rows,
+                                            bool azero) {
+  using E = Elem<T>;
+  constexpr int R = MMAX / G;
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G, c = lane / G;
+  if (azero) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int r = g + t * G;
+      if (t * G < m && active && r < m) E::st(Bp + r, E::zero());
+    }
+    return;
+  }
+  T s[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int r = g + t * G;
+    s[t] = E::zero();
+    if (t * G < m) {
+      if (active && r < m) s[t] = E::mul(pk_ld(sc + r), E::ld(Bp + r));
+    }
+  }
+  int64_t base = -1;  // column i of the staged triangle starts at tri + base + i + 1
+#pragma unroll
+  for (int i = 0; i < MMAX - 1; ++i) {
+    if (i >= m - 1) break;  // warp-uniform: the last row updates nothing
+    const int tb = i / G, gi = i % G;
+    const T x = (G == 1) ? s[tb] : E::shfl(s[tb], c * G + gi);
+    const T *col = tri + base;
+    if (G > 1 && gi < G - 1) {
+      // boundary slot: only rows strictly below i update
+      const int r = g + tb * G;
+      const int ra = r > i ? r : i + 1;
+      const T ns = E::fms(pk_ld(col + ra), x, s[tb]);
+      if (r > i) s[tb] = ns;
+    }
+#pragma unroll
+    for (int t = tb + 1; t < R; ++t) {
+      if (t * G >= m) break;  // warp-uniform
+      s[t] = E::fms(pk_ld(col + g + t * G), x, s[t]);
+    }
+    base += rows - 2 - i;
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int r = g + t * G;
+    if (t * G < m) {
+      if (active && r < m) E::st(Bp + r, s[t]);
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * kPkWarps, kPkMinBlocks) packed_solve_kernel(
+    void *const *__restrict__ dB, const int32_t *__restrict__ dldb, unsigned char *scratch, PkLayout L,
+    const T *__restrict__ stage, int azero) {
+  constexpr bool two = pk_two_lanes<T>();
+  __shared__ __align__(16) int32_t sgrp[64 * kPkGroupWords];
+  int32_t *hdr = reinterpret_cast<int32_t *>(scratch);
+  const int32_t *inst = reinterpret_cast<const int32_t *>(scratch + L.inst);
+  const int64_t *colpref = reinterpret_cast<const int64_t *>(scratch + L.colpref);
+  const int ng = pk_load_groups(scratch, L, sgrp);
+  const int ntiles = *(volatile const int32_t *)(hdr + 1);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(hdr, 1);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= ntiles) break;
+    int k = 0;
+    while (k + 1 < ng && sgrp[(k + 1) * kPkGroupWords + 2] <= tile) ++k;  // warp-uniform
+    const int32_t *e = sgrp + k * kPkGroupWords;
+    const int m = e[0], G = e[1], pos0 = e[3], pos1 = e[4];
+    const long long col0 = *reinterpret_cast<const long long *>(e + 6);
+    const long long colend = colpref[pos1];
+    const int C = 32 / G;
+    const long long gc = col0 + (long long)(tile - e[2]) * C + lane / G;
+    const bool active = gc < colend;
+    // position of the lane's instance: last p in [pos0, pos1) with colpref[p] <= gc
+    int p = pos0;
+    if (active) {
+      int lo = pos0, hi = pos1 - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (colpref[mid] <= gc) lo = mid;
+        else hi = mid - 1;
+      }
+      p = lo;
+    }
+    const int p_lane0 = __shfl_sync(0xffffffffu, p, 0);  // lane 0 is always active
+    if (!active) p = p_lane0;
+    const int b = inst[p];
+    const long long j = active ? gc - colpref[p] : 0;
+    T *Bp = static_cast<T *>(dB[b]) + j * (int64_t)dldb[b];
+    const int rows = pk_rows(m, G);
+    const T *tri = stage + *reinterpret_cast<const long long *>(e + 8) + (int64_t)(p - pos0) * e[5];
+    const T *sc = tri + pk_tri_elems(rows);
+    if constexpr (two) {
+      if (G == 1)
+        packed_tile<T, 1, 32>(tri, sc, Bp, active, m, rows, azero != 0);
+      else
+        packed_tile<T, 2, 64>(tri, sc, Bp, active, m, rows, azero != 0);
+    } else {
+      packed_tile<T, 1, 64>(tri, sc, Bp, active, m, rows, azero != 0);
+    }
+  }
+}
+
+template <class T>
+int packed_grid(int dev) {
+  static int cached[64] = {0};
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  int nsm = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, packed_solve_kernel<T>, 32 * kPkWarps, 0);
+  const int grid = nsm * (per_sm > 0 ? per_sm : 1);
+  if (dev >= 0 && dev < 64) cached[dev] = grid;
+  return grid;
+}
+
+int sm_count(int dev) {
+  static int cached[64] = {0};
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (dev >= 0 && dev < 64) cached[dev] = nsm;
+  return nsm;
+}
+
+template <class T>
+hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int32_t *dn, const double *alpha,
+                          const void *const *dA, const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
+                          uint32_t *status, void *scratch, cudaStream_t st) {
+  int dev = 0;
+  HSMA_CUDA_TRY(cudaGetDevice(&dev));
+  const PkLayout L = pk_layout(batch, max_m, (int)sizeof(T), pk_two_lanes<T>());
+  unsigned char *scr = static_cast<unsigned char *>(scratch);
+  T *stage = reinterpret_cast<T *>(scr + L.stage);
+  const T al = hsma_alpha_as<T>(alpha);
+  const bool azero = Elem<T>::kComplex ? (alpha[0] == 0.0 && alpha[1] == 0.0) : alpha[0] == 0.0;
+  {
+    static const PkOrder order = pk_order(pk_two_lanes<T>(), Elem<T>::kComplex);
+    const int mmax = (max_m <= 0 || max_m > 64) ? 64 : max_m;
+    HsmaTraceScope ts("vbatched_schedule", st);
+    packed_schedule_kernel<T><<<1, kPkSchedThreads, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scr, L, mmax, order,
+                                                             status);
+  }
+  HSMA_CUDA_TRY(cudaGetLastError());
+  if (!azero) {
+    // one warp per instance, up to 16 warps per SM over the whole GPU
+    const int nsm = sm_count(dev);
+    int blocks = (batch + kPkPrepWarps - 1) / kPkPrepWarps;
+    if (blocks > 2 * nsm) blocks = 2 * nsm;
+    HsmaTraceScope ts("vbatched_prep", st);
+    packed_prep_kernel<T><<<blocks, 32 * kPkPrepWarps, 0, st>>>(dm, dA, dlda, scr, L, stage, al, unit);
+    HSMA_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    HsmaTraceScope ts("vbatched_solve", st);
+    packed_solve_kernel<T><<<packed_grid<T>(dev), 32 * kPkWarps, 0, st>>>(dB, dldb, scr, L, stage, azero ? 1 : 0);
+  }
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
+}  // namespace
+
+size_t hsma_vbatched_packed_scratch_bytes(int dtype, int32_t batch, int32_t max_m) {
+  const int es = hsma_small_esize(dtype);
+  return pk_layout(batch, max_m, es, es == 16).total;
+}
+
+hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m, const int32_t *dm,
+                                         const int32_t *dn, const double *alpha, const void *const *dA,
+                                         const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
+                                         uint32_t *status, void *scratch, cudaStream_t st) {
+  switch (dtype) {
+    case HSMA_C128:
+      return packed_impl<cplx>(batch, max_m, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+    case HSMA_R64:
+      return packed_impl<double>(batch, max_m, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+    default:
+      return HSMA_ERR_UNSUPPORTED;
+  }
+}

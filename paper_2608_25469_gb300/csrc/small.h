@@ -33,6 +33,17 @@ hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t 
                                         const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,
                                         uint32_t *status, int32_t *scratch, cudaStream_t st, int chol = 0);
 
+// Column-packed varlen batch for the left / lower / no-transpose solve in
+// HSMA_R64 or HSMA_C128 (packed.cu): schedule, prep and solve passes;
+// `scratch` holds hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m)
+// bytes (max_m: a bound on every m_i, 0 = 64).  Results equal
+// hsma_small_vbatched's bit for bit.
+size_t hsma_vbatched_packed_scratch_bytes(int dtype, int32_t batch, int32_t max_m);
+hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m, const int32_t *dm,
+                                         const int32_t *dn, const double *alpha, const void *const *dA,
+                                         const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
+                                         uint32_t *status, void *scratch, cudaStream_t st);
+
 // dtypes the small kernels and the varlen batch handle
 inline bool hsma_small_dtype(int dtype) {
   return dtype == HSMA_R64 || dtype == HSMA_C128 || dtype == HSMA_R32 || dtype == HSMA_C64;

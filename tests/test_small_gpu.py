@@ -9,6 +9,7 @@ from tests import gpu_util as U
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12  # relative Frobenius forward error, fp64 and complex128
+R32, C64 = 4, 5  # the C ABI's FP32 dtype codes (the generators draw FP64 values, rounded)
 
 
 @pytest.fixture(scope="module")
@@ -279,3 +280,114 @@ def test_golden_integer_solves_bitwise(H):
         H.hsma_trsm_llnn(code, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr())
         torch.cuda.synchronize()
         assert np.array_equal(H.from_device(dB), X), (dtype, m, n)
+
+
+def _noalloc(H, code, As, Bs, alpha, unit=False):
+    """The per-instance batched kernel (the allocation-free entry point runs it)."""
+    import torch
+    bt = U.Batch(As, Bs)
+    H.hsma_trsm_llnn_vbatched_noalloc(code, int(unit), bt.batch, *bt.args()[:2], alpha, *bt.args()[2:], max_m=64,
+                                      max_n=0, d_status=bt.d_status.data_ptr(), stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    return bt
+
+
+def _mix(code, sizes, seed, pad=0):
+    dt = {I.R64: np.float64, I.C128: np.complex128, C64: np.complex64, R32: np.float32}[code]
+    gcode = I.C128 if code in (I.C128, C64) else I.R64
+    As, Bs = [], []
+    for b, (m, n) in enumerate(sizes):
+        A = I.gen_A(seed, m, gcode, inst=b).astype(dt)
+        B = I.gen_B(seed, m, n, gcode, inst=b).astype(dt)
+        As.append(I.embed(A, m + pad) if pad else np.asfortranarray(A))
+        Bs.append(I.embed(B, m + pad) if pad else np.asfortranarray(B))
+    return As, Bs
+
+
+PACKED_MIXES = {
+    # the workload's size mix
+    "uniform8_64": lambda rng: [(int(m), int(n)) for m, n in rng.integers(8, 65, (1500, 2))],
+    # one column per instance: a warp tile spans 16 or 32 instances
+    "n1": lambda rng: [(int(m), 1) for m in rng.integers(1, 65, 900)],
+    # wide instances (n > 64) and every m, including 1, 32, 33 and 64
+    "wide_every_m": lambda rng: [(m, int(rng.integers(60, 200))) for m in range(1, 65)],
+    # a single instance, and groups with one instance each
+    "single": lambda rng: [(33, 7)],
+    "one_per_m": lambda rng: [(m, (m * 7) % 40 + 1) for m in range(64, 0, -1)],
+}
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128, C64, R32])
+@pytest.mark.parametrize("mix", sorted(PACKED_MIXES))
+def test_packed_batch_equals_per_instance_kernel(H, code, mix):
+    """The column-packed batch (warps serve columns of several instances of the same m)
+    gives the per-instance kernel's results bit for bit, on size mixes that put many
+    instances in one warp tile, wide instances, every m and lone instances; and the
+    oracle's within the dtype's tolerance."""
+    rng = np.random.default_rng(sum(map(ord, mix)))
+    sizes = PACKED_MIXES[mix](rng)
+    alpha = {I.R64: 1.5, R32: 1.5}.get(code, 1.5 - 0.5j)
+    As, Bs = _mix(code, sizes, seed=31)
+    got = _run_batch(H, code, As, Bs, alpha)
+    ref = _noalloc(H, code, As, Bs, alpha)
+    assert got.status() == 0 and ref.status() == 0
+    G, R = got.results(), ref.results()
+    for b in range(len(As)):
+        assert np.array_equal(G[b], R[b]), (mix, b, sizes[b])
+    tol = TOL if code in (I.R64, I.C128) else 2e-5
+    wide = lambda L: [np.asfortranarray(x.astype(np.complex128 if np.iscomplexobj(x) else np.float64)) for x in L]
+    pick = list(range(0, len(As), max(1, len(As) // 60)))
+    refs = oracle.solve_batch(wide([As[b] for b in pick]), wide([Bs[b] for b in pick]), alpha)
+    for k, b in enumerate(pick):
+        assert oracle.forward_error(G[b].astype(refs[k].dtype), refs[k]) <= tol, (mix, b)
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+def test_packed_batch_padding_unit_and_zero_alpha(H, code):
+    """lda, ldb > m: padding rows of B stay untouched and padding rows of A are never
+    read (NaN); unit diagonal (NaN on the diagonal, never read); alpha = 0 gives zeros
+    without reading A.  Bit-equal to the per-instance kernel."""
+    rng = np.random.default_rng(4)
+    sizes = [(int(m), int(n)) for m, n in rng.integers(1, 65, (400, 2))]
+    As, Bs = _mix(code, sizes, seed=8, pad=3)
+    for A in As:
+        A[np.triu_indices(A.shape[1], 1)] = np.nan
+    alpha = 0.75 if code == I.R64 else 0.25 + 1j
+    got = _run_batch(H, code, As, Bs, alpha)
+    ref = _noalloc(H, code, As, Bs, alpha)
+    for b, (X, Y) in enumerate(zip(got.results(), ref.results())):
+        m = sizes[b][0]
+        assert np.all(np.isnan(X[m:])), b
+        assert np.array_equal(X[:m], Y[:m]), b
+    Au = [np.array(A, order="F") for A in As]
+    for A in Au:
+        np.fill_diagonal(A, np.nan)
+    got = _run_batch(H, code, Au, Bs, alpha, unit=True)
+    ref = _noalloc(H, code, Au, Bs, alpha, unit=True)
+    for b, (X, Y) in enumerate(zip(got.results(), ref.results())):
+        m = sizes[b][0]
+        assert np.array_equal(X[:m], Y[:m]) and not np.isnan(X[:m]).any(), b
+        if b % 50 == 0:
+            A1 = np.array(As[b][:m], order="F")
+            np.fill_diagonal(A1, 1.0)
+            A1[np.triu_indices(m, 1)] = 0
+            assert oracle.forward_error(X[:m], oracle.solve(A1, np.asfortranarray(Bs[b][:m]), alpha)) <= TOL
+    Anan = [np.full_like(A, np.nan) for A in As]
+    got = _run_batch(H, code, Anan, Bs, 0.0)
+    for b, X in enumerate(got.results()):
+        m = sizes[b][0]
+        assert np.all(X[:m] == 0) and np.all(np.isnan(X[m:])), b
+
+
+def test_packed_batch_instance_above_max_m_is_skipped(H):
+    """max_m sizes the staging workspace: an instance with m above it is skipped and
+    flagged (HSMA_DEVERR_BAD_SIZE), its B untouched; the others are solved."""
+    code = I.C128
+    alpha = 2.0 - 1j
+    As, Bs = _mix(code, [(20, 9), (40, 5), (17, 33)], seed=3)
+    bt = _run_batch(H, code, As, Bs, alpha, max_m=24)
+    assert bt.status() & H.DEVERR_BAD_SIZE
+    X = bt.results()
+    assert np.array_equal(X[1], Bs[1])
+    for b in (0, 2):
+        assert oracle.forward_error(X[b], oracle.solve(As[b], Bs[b], alpha)) <= TOL

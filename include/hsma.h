@@ -197,14 +197,15 @@ HSMA_API hsma_status_t hsma_trsm(int dtype, int side, int uplo, int trans, int d
  * max_n  host upper bound on every n_i, or 0 if unknown (only a hint).
  * d_status: optional DEVICE uint32 word; the kernel ORs HSMA_DEVERR_* bits into
  *        it for instances it skips as invalid.  May be NULL.
- * The columns of all instances with the same m are dealt to warps 32 (or,
- * for complex128 with m > 32, 16) at a time, so a warp may serve several
- * instances; an instance's arithmetic never depends on the others, so results
- * are bit-identical to solving it alone through this entry point with
- * batch = 1.  Workspace (stream-ordered pool): room for the pre-scaled
+ * HSMA_C128: the columns of all instances with the same m are dealt to warps
+ * 32 (16 for m > 32) at a time, so a warp may serve several instances; the
+ * other dtypes deal each instance's column tiles to the warps of one CTA.  An
+ * instance's arithmetic never depends on the others, so results are
+ * bit-identical to solving it alone through this entry point with batch = 1.
+ * Workspace (stream-ordered pool): for HSMA_C128 room for the pre-scaled
  * triangle and diagonal of every instance, batch x r (r + 1) / 2 elements
- * with r = max_m (rounded up to even for complex128), plus 20 bytes per
- * instance.
+ * with r = max_m rounded up to even, plus 20 bytes per instance; otherwise
+ * 4 bytes per instance.
  */
 HSMA_API hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const int32_t *d_m,
                                       const int32_t *d_n, const void *alpha, const void *const *d_A,
@@ -300,8 +301,9 @@ HSMA_API hsma_status_t hsma_potrs_vbatched(int dtype, int32_t batch, const int32
  * order on an internal copy-in stream, each group's batched solve starts (on
  * one of two internal compute streams) as soon as its copy has landed, and
  * its X goes back on an internal copy-out stream as soon as it is solved, so
- * the copies overlap the solves.  Device workspace: the whole batch's A and B
- * plus the per-instance tables (stream-ordered pool, released at the end).
+ * the copies overlap the solves.  Device workspace: the whole batch's A and B,
+ * the per-instance tables and, for HSMA_C128, the staged triangles of two
+ * chunks (stream-ordered pool, released at the end).
  *
  * h_m, h_n: HOST arrays of `batch` sizes (0 <= m_i <= 64, n_i >= 0).
  * hA, hB: HOST buffers holding every A_i (column-major, lda = m_i, m_i^2

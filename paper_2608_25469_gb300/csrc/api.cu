@@ -269,10 +269,10 @@ hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int d
     return HSMA_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void *scratch = nullptr;
-  // the paper's case in FP64 runs the column-packed batch (the FP64 pipe
-  // binds, so full warp tiles pay); FP32 types and the other variants the
+  // the paper's case in complex128 runs the column-packed batch (the FP64
+  // pipe binds, so full warp tiles pay); the other dtypes and variants the
   // per-instance kernel (with its index map)
-  const bool packed = uplo == HSMA_LOWER && trans == HSMA_NO_TRANS && (dtype == HSMA_R64 || dtype == HSMA_C128) &&
+  const bool packed = uplo == HSMA_LOWER && trans == HSMA_NO_TRANS && hsma_vbatched_packed_dtype(dtype) &&
                       packed_enabled();
   hsma_status_t s = hsma_ws_alloc(
       &scratch, packed ? hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m) : hsma_vbatched_scratch_bytes(batch),

@@ -84,21 +84,18 @@ struct Elem<cplx> {
     s.im = fma(-a.im, x.re, s.im);
     return s;
   }
-  // 1/a, scaled by the larger component of a (Smith's division with numerator 1)
+  // 1/a, scaled by the larger component of a (Smith's division with numerator
+  // 1).  Written with selects rather than a branch: lanes of a warp that take
+  // different branches would otherwise run both branches' three divisions.
+  //   |re| >= |im|: t = im/re, d = re + im t, 1/a = (1/d, -t/d)
+  //   otherwise:    t = re/im, d = re t + im, 1/a = (t/d, -1/d)
   __device__ __forceinline__ static cplx recip(cplx a) {
-    cplx r;
-    if (fabs(a.re) >= fabs(a.im)) {
-      double t = a.im / a.re;
-      double d = a.re + a.im * t;
-      r.re = 1.0 / d;
-      r.im = -t / d;
-    } else {
-      double t = a.re / a.im;
-      double d = a.re * t + a.im;
-      r.re = t / d;
-      r.im = -1.0 / d;
-    }
-    return r;
+    const bool big = fabs(a.re) >= fabs(a.im);
+    const double p = big ? a.re : a.im, q = big ? a.im : a.re;  // larger, smaller
+    const double t = q / p;
+    const double d = fma(q, t, p);
+    const double u = 1.0 / d, v = t / d;
+    return big ? cplx{u, -v} : cplx{v, -u};
   }
   __device__ __forceinline__ static cplx shfl(cplx v, int src) {
     cplx r;
@@ -137,19 +134,14 @@ struct Elem<cplxf> {
     s.im = fmaf(-a.im, x.re, s.im);
     return s;
   }
-  // Smith's division with numerator 1
+  // Smith's division with numerator 1 (selects, as for cplx)
   __device__ __forceinline__ static cplxf recip(cplxf a) {
-    cplxf r;
-    if (fabsf(a.re) >= fabsf(a.im)) {
-      const float t = a.im / a.re, d = a.re + a.im * t;
-      r.re = 1.0f / d;
-      r.im = -t / d;
-    } else {
-      const float t = a.re / a.im, d = a.re * t + a.im;
-      r.re = t / d;
-      r.im = -1.0f / d;
-    }
-    return r;
+    const bool big = fabsf(a.re) >= fabsf(a.im);
+    const float p = big ? a.re : a.im, q = big ? a.im : a.re;
+    const float t = q / p;
+    const float d = fmaf(q, t, p);
+    const float u = 1.0f / d, v = t / d;
+    return big ? cplxf{u, -v} : cplxf{v, -u};
   }
   __device__ __forceinline__ static cplxf shfl(cplxf v, int src) {
     return cplxf{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
@@ -291,12 +283,12 @@ __host__ __device__ inline double hsma_small_time_model(int m, int n, int g, boo
   const int C = 32 / g;
   const int tiles = (n + C - 1) / C;
   const double stage = (double)hsma_small_stage_instr(m, g, cplx_);
-  // every CTA (two warps) stages the triangle once
-  const double total = tiles * tile + stage * ((tiles + 1) / 2);
+  // every CTA (four warps) stages the triangle once
+  const double total = tiles * tile + stage * ((tiles + 3) / 4);
   // whole-GPU pipe: 4 sub-partitions per SM, ~84% of nominal measured
   const double tput = total * 64.0 / (4.0 * nsm * 0.84);
-  // one warp alone on its sub-partition, with staging split over two warps
-  const double warp = (tile + 0.5 * stage) * 64.0;
+  // one warp alone on its sub-partition, with staging split over four warps
+  const double warp = (tile + 0.25 * stage) * 64.0;
   // dependent chain: per step one multiply-add latency (two for complex) plus a shuffle
   const double chain = (m - 1) * ((cplx_ ? 128.0 : 64.0) + (g > 1 ? 40.0 : 0.0));
   const double busy = tput > warp ? tput : warp;

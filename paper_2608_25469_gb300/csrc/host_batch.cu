@@ -71,8 +71,16 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
   const size_t mi_b = al(sizeof(int32_t) * batch), oi_b = al(sizeof(int64_t) * batch);
   const size_t p_b = al(sizeof(void *) * batch);
   const size_t a_b = al((size_t)extA * es), b_b = al((size_t)extB * es);
-  const size_t scr_b = al(hsma_vbatched_scratch_bytes(per));
-  const size_t total = a_b + b_b + 3 * mi_b + 2 * oi_b + 2 * p_b + scr_b * nch;
+  // complex128 runs the column-packed batch, the others the per-instance
+  // kernel; chunks on one compute stream run in order, so each stream needs
+  // one scratch
+  const bool packed = hsma_vbatched_packed_dtype(dtype);
+  int32_t max_m = 0;
+  for (int32_t i = 0; i < batch; ++i) max_m = std::max(max_m, h_m[i]);
+  const size_t scr_b = al(packed ? hsma_vbatched_packed_scratch_bytes(dtype, per, max_m)
+                                 : hsma_vbatched_scratch_bytes(per));
+  const int nscr = nch < 2 ? nch : 2;
+  const size_t total = a_b + b_b + 3 * mi_b + 2 * oi_b + 2 * p_b + scr_b * nscr;
   std::unique_ptr<cudaEvent_t[]> evs(new (std::nothrow) cudaEvent_t[2 * nch]());  // copied-in, solved
   if (!evs) return HSMA_ERR_NO_MEMORY;
   cudaEvent_t *ev = evs.get();
@@ -141,9 +149,13 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
       if ((s = fail(cudaEventRecord(ev[2 * c], s_in))) != HSMA_OK) break;
       cudaStream_t sk = s_k[c & 1];
       if ((s = fail(cudaStreamWaitEvent(sk, ev[2 * c], 0))) != HSMA_OK) break;
-      int32_t *scr = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scr0) + scr_b * c);
-      s = hsma_small_vbatched(dtype, cnt, gm + b, gn + b, static_cast<const double *>(alpha), pA + b, gld + b, pB + b,
-                              gld + b, diag == HSMA_UNIT, nullptr, scr, sk);
+      int32_t *scr = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scr0) + scr_b * (c & 1));
+      if (packed)
+        s = hsma_small_vbatched_packed(dtype, cnt, max_m, gm + b, gn + b, static_cast<const double *>(alpha), pA + b,
+                                       gld + b, pB + b, gld + b, diag == HSMA_UNIT, nullptr, scr, sk);
+      else
+        s = hsma_small_vbatched(dtype, cnt, gm + b, gn + b, static_cast<const double *>(alpha), pA + b, gld + b,
+                                pB + b, gld + b, diag == HSMA_UNIT, nullptr, scr, sk);
       if (s != HSMA_OK) break;
       if ((s = fail(cudaEventRecord(ev[2 * c + 1], sk))) != HSMA_OK) break;
       if ((s = fail(cudaStreamWaitEvent(s_out, ev[2 * c + 1], 0))) != HSMA_OK) break;

@@ -33,7 +33,6 @@ namespace {
 
 constexpr int kPkWarps = 4;     // warps per CTA of the solve kernel (independent)
 constexpr int kPkMinBlocks = 3;  // resident CTAs per SM (register cap of the solve kernel)
-constexpr int kPkSchedThreads = 1024;
 constexpr int kPkHeaderWords = 8;
 
 // Rows per lane group G of the packed solve: FP64 complex values take four
@@ -59,6 +58,9 @@ __host__ __device__ inline int64_t pk_stage_elems(int m, bool two_lanes) {
 
 // Scratch layout (bytes, each part 256-aligned):
 //   header  int32[8]       [0] next tile, [1] tiles, [2] groups, [3] positions
+//   counts  per m (1..64): instances (int32), columns (uint64), and the
+//           placement cursor (uint64: instances << 40 | columns); zeroed
+//           before every call
 //   groups  int32[64][16]  per group of equal m, in schedule order: m, G,
 //                          first tile, first position, end position, staged
 //                          elements per instance, first stream column
@@ -68,7 +70,12 @@ __host__ __device__ inline int64_t pk_stage_elems(int m, bool two_lanes) {
 //   colpref int64[batch+1] first stream column of each position
 //   stage   T[...]         staged triangles, position by position
 struct PkLayout {
-  size_t groups, inst, colpref, stage, total;
+  size_t counts, groups, inst, colpref, stage, total;
+};
+
+struct PkCounts {
+  unsigned long long csum[65], cur[65];
+  int cnt[65];
 };
 
 constexpr int kPkGroupWords = 16;
@@ -85,7 +92,8 @@ PkLayout pk_layout(int32_t batch, int max_m, int esize, bool two_lanes) {
   PkLayout L;
   const size_t b = (size_t)(batch > 0 ? batch : 0);
   const int mm = (max_m <= 0 || max_m > 64) ? 64 : max_m;
-  L.groups = pk_align(sizeof(int32_t) * kPkHeaderWords);
+  L.counts = pk_align(sizeof(int32_t) * kPkHeaderWords);
+  L.groups = L.counts + pk_align(sizeof(PkCounts));
   L.inst = L.groups + pk_align(sizeof(int32_t) * 64 * kPkGroupWords);
   L.colpref = L.inst + pk_align(sizeof(int32_t) * b);
   L.stage = L.colpref + pk_align(sizeof(int64_t) * (b + 1));
@@ -115,109 +123,159 @@ PkOrder pk_order(bool two_lanes, bool cplx_) {
 }
 
 // ---------------------------------------------------------------------------
-// 1. Schedule.  One CTA, two passes over the instances.  Instances with m = 0
-// or n = 0 are valid and need no work; invalid ones set a status bit and are
-// skipped (as the per-instance kernel does).  An instance above mmax (the
-// caller's bound, which sized the staging workspace) counts as invalid.  One
-// 64-bit atomic per instance hands out its position within the group (high
-// bits) and its first column within the group's stream (low bits) together,
-// so stream columns increase with the position.
+// 1. Schedule, in two grid-wide passes over the instances (one instance per
+// thread).  Instances with m = 0 or n = 0 are valid and need no work; invalid
+// ones set a status bit and are skipped (as the per-instance kernel does).
+// An instance above mmax (the caller's bound, which sized the staging
+// workspace) counts as invalid.
+//   count: per m, the instances and their columns (CTA totals in shared
+//          memory, then one global atomic per m and CTA);
+//   place: every CTA derives the group table from the totals (CTA 0 writes
+//          it), gives its instances of each m consecutive slots with one
+//          shared 64-bit atomic each (slot in the high bits, first column in
+//          the low bits, so stream columns increase with the position), and
+//          reserves the CTA's range of each m with one global atomic.
 // ---------------------------------------------------------------------------
+constexpr int kPkSchedThreads2 = 512;
+constexpr int kPkColBits = 40;
+
+__device__ __forceinline__ bool pk_valid(int b, const int32_t *__restrict__ dm, const int32_t *__restrict__ dn,
+                                         const int32_t *__restrict__ dlda, const int32_t *__restrict__ dldb,
+                                         const void *const *__restrict__ dA, void *const *__restrict__ dB, int mmax,
+                                         int &m, int &n, uint32_t &err) {
+  m = dm[b];
+  n = dn[b];
+  const int lda = dlda[b], ldb = dldb[b];
+  const bool nul = dA[b] == nullptr || dB[b] == nullptr;
+  const int lo = m > 1 ? m : 1;
+  if (m < 0 || n < 0 || m > mmax || lda < lo || ldb < lo) {
+    err |= HSMA_DEVERR_BAD_SIZE;
+    return false;
+  }
+  if (m == 0 || n == 0) return false;
+  if (nul) {
+    err |= HSMA_DEVERR_NULL_PTR;
+    return false;
+  }
+  return true;
+}
+
 template <class T>
-__global__ void __launch_bounds__(kPkSchedThreads) packed_schedule_kernel(
+__global__ void __launch_bounds__(kPkSchedThreads2) packed_count_kernel(
     int batch, const int32_t *__restrict__ dm, const int32_t *__restrict__ dn, const int32_t *__restrict__ dlda,
     const int32_t *__restrict__ dldb, const void *const *__restrict__ dA, void *const *__restrict__ dB,
-    unsigned char *scratch, PkLayout L, int mmax, PkOrder order, uint32_t *status) {
-  constexpr bool two = pk_two_lanes<T>();
-  constexpr int kColBits = 40;
-  __shared__ int cnt[65], gpos0[65];
-  __shared__ unsigned long long csum[65], cur[65];
-  __shared__ long long gcol0[65];
-  __shared__ int s_over;
-  int32_t *hdr = reinterpret_cast<int32_t *>(scratch);
-  int32_t *grp = reinterpret_cast<int32_t *>(scratch + L.groups);
-  int32_t *inst = reinterpret_cast<int32_t *>(scratch + L.inst);
-  int64_t *colpref = reinterpret_cast<int64_t *>(scratch + L.colpref);
-  const int tid = threadIdx.x;
-  for (int k = tid; k < 65; k += blockDim.x) {
+    unsigned char *scratch, PkLayout L, int mmax, uint32_t *status) {
+  __shared__ int cnt[65];
+  __shared__ unsigned long long csum[65];
+  PkCounts *g = reinterpret_cast<PkCounts *>(scratch + L.counts);
+  for (int k = threadIdx.x; k < 65; k += blockDim.x) {
     cnt[k] = 0;
     csum[k] = 0;
-    cur[k] = 0;
   }
   __syncthreads();
   uint32_t err = 0;
-  auto valid = [&](int b, int &m, int &n) {
-    m = dm[b];
-    n = dn[b];
-    const int lo = m > 1 ? m : 1;
-    if (m < 0 || n < 0 || m > mmax || dlda[b] < lo || dldb[b] < lo) {
-      err |= HSMA_DEVERR_BAD_SIZE;
-      return false;
-    }
-    if (m == 0 || n == 0) return false;
-    if (dA[b] == nullptr || dB[b] == nullptr) {
-      err |= HSMA_DEVERR_NULL_PTR;
-      return false;
-    }
-    return true;
-  };
-  for (int b = tid; b < batch; b += blockDim.x) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x) {
     int m, n;
-    if (!valid(b, m, n)) continue;
+    if (!pk_valid(b, dm, dn, dlda, dldb, dA, dB, mmax, m, n, err)) continue;
     atomicAdd(&cnt[m], 1);
     atomicAdd(&csum[m], (unsigned long long)n);
   }
   __syncthreads();
-  if (tid == 0) {
-    // a group's column count must fit the low bits of the cursor
-    s_over = 0;
-    for (int m = 1; m <= 64; ++m) s_over |= csum[m] >= (1ull << kColBits) ? 1 : 0;
+  for (int m = threadIdx.x; m <= 64; m += blockDim.x) {
+    if (cnt[m] == 0) continue;
+    atomicAdd(&g->cnt[m], cnt[m]);
+    atomicAdd(&g->csum[m], csum[m]);
+  }
+  if (err != 0 && status != nullptr) atomicOr(status, err);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPkSchedThreads2) packed_place_kernel(
+    int batch, const int32_t *__restrict__ dm, const int32_t *__restrict__ dn, const int32_t *__restrict__ dlda,
+    const int32_t *__restrict__ dldb, const void *const *__restrict__ dA, void *const *__restrict__ dB,
+    unsigned char *scratch, PkLayout L, int mmax, PkOrder order) {
+  constexpr bool two = pk_two_lanes<T>();
+  __shared__ int gpos0[65];
+  __shared__ long long gcol0[65];
+  __shared__ unsigned long long ccur[65], cbase[65], tcsum[65];
+  __shared__ int tcnt[65];
+  __shared__ int s_over;
+  PkCounts *g = reinterpret_cast<PkCounts *>(scratch + L.counts);
+  int32_t *hdr = reinterpret_cast<int32_t *>(scratch);
+  int32_t *grp = reinterpret_cast<int32_t *>(scratch + L.groups);
+  int32_t *inst = reinterpret_cast<int32_t *>(scratch + L.inst);
+  int64_t *colpref = reinterpret_cast<int64_t *>(scratch + L.colpref);
+  for (int k = threadIdx.x; k < 65; k += blockDim.x) {
+    tcnt[k] = g->cnt[k];
+    tcsum[k] = g->csum[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the group table, in schedule order (every CTA derives the same one)
+    int over = 0;
+    for (int m = 1; m <= 64; ++m) over |= tcsum[m] >= (1ull << kPkColBits) ? 1 : 0;
     int ng = 0, pos = 0, tile = 0;
     long long col = 0, stg = 0;
-    for (int k = 0; k < 64; ++k) {
+    for (int k = 0; k < 64 && !over; ++k) {
       const int m = order.m[k];
-      if (cnt[m] == 0) continue;
-      const int g = pk_groups(m, two);
-      const long long tiles = g == 1 ? ((long long)csum[m] + 31) >> 5 : ((long long)csum[m] + 15) >> 4;
+      const int c = tcnt[m];
+      if (c == 0) continue;
+      const unsigned long long cs = tcsum[m];
+      const int gg = pk_groups(m, two);
+      const long long tiles = gg == 1 ? ((long long)cs + 31) >> 5 : ((long long)cs + 15) >> 4;
       const int se = (int)pk_stage_elems(m, two);
-      int32_t *e = grp + ng * kPkGroupWords;
-      e[0] = m;
-      e[1] = g;
-      e[2] = tile;
-      e[3] = pos;
-      e[4] = pos + cnt[m];
-      e[5] = se;
-      *reinterpret_cast<long long *>(e + 6) = col;
-      *reinterpret_cast<long long *>(e + 8) = stg;
+      if (blockIdx.x == 0) {
+        int32_t *e = grp + ng * kPkGroupWords;
+        e[0] = m;
+        e[1] = gg;
+        e[2] = tile;
+        e[3] = pos;
+        e[4] = pos + c;
+        e[5] = se;
+        *reinterpret_cast<long long *>(e + 6) = col;
+        *reinterpret_cast<long long *>(e + 8) = stg;
+      }
       gpos0[m] = pos;
       gcol0[m] = col;
       ++ng;
-      pos += cnt[m];
+      pos += c;
       tile += (int)tiles;
-      col += (long long)csum[m];
-      stg += (long long)cnt[m] * se;
+      col += (long long)cs;
+      stg += (long long)c * se;
     }
-    if (s_over) {  // nothing is solved; the caller sees BAD_SIZE
-      ng = pos = tile = 0;
-      col = 0;
-      err |= HSMA_DEVERR_BAD_SIZE;
+    if (blockIdx.x == 0) {  // a column count beyond the cursor's low bits: nothing is solved
+      hdr[0] = 0;
+      hdr[1] = over ? 0 : tile;
+      hdr[2] = over ? 0 : ng;
+      hdr[3] = over ? 0 : pos;
+      colpref[over ? 0 : pos] = over ? 0 : col;
     }
-    hdr[0] = 0;
-    hdr[1] = tile;
-    hdr[2] = ng;
-    hdr[3] = pos;
-    colpref[pos] = col;
+    s_over = over;
   }
   __syncthreads();
-  for (int b = tid; b < batch && !s_over; b += blockDim.x) {
-    int m, n;
-    if (!valid(b, m, n)) continue;
-    const unsigned long long old = atomicAdd(&cur[m], (1ull << kColBits) + (unsigned long long)n);
-    const int p = gpos0[m] + (int)(old >> kColBits);
-    inst[p] = b;
-    colpref[p] = gcol0[m] + (long long)(old & ((1ull << kColBits) - 1));
+  if (s_over) return;
+  uint32_t err = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int b0 = blockIdx.x * blockDim.x; b0 < batch; b0 += stride) {
+    for (int k = threadIdx.x; k < 65; k += blockDim.x) ccur[k] = 0;
+    __syncthreads();
+    const int b = b0 + threadIdx.x;
+    int m = 0, n = 0;
+    const bool ok = b < batch && pk_valid(b, dm, dn, dlda, dldb, dA, dB, mmax, m, n, err);
+    unsigned long long mine = 0;
+    if (ok) mine = atomicAdd(&ccur[m], (1ull << kPkColBits) + (unsigned long long)n);
+    __syncthreads();
+    for (int k = threadIdx.x; k <= 64; k += blockDim.x)
+      if (ccur[k] != 0) cbase[k] = atomicAdd(&g->cur[k], ccur[k]);
+    __syncthreads();
+    if (ok) {
+      const unsigned long long at = cbase[m] + mine;
+      const int p = gpos0[m] + (int)(at >> kPkColBits);
+      inst[p] = b;
+      colpref[p] = gcol0[m] + (long long)(at & ((1ull << kPkColBits) - 1));
+    }
+    __syncthreads();  // ccur and cbase are reused by the next chunk
   }
-  if (err != 0 && status != nullptr) atomicOr(status, err);
 }
 
 // Copy the group table into shared memory (every thread of the CTA).
@@ -273,21 +331,32 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
       sc[r] = r < m ? E::mul(alpha, rv) : E::zero();
     }
     __syncwarp();
-    // element q of the packed triangle: column i, row i + 1 + local index
+    // element q of the packed triangle: column i, row i + 1 + local index;
+    // four elements per lane in flight (loads first)
     const int total = (int)pk_tri_elems(rows);
     int i = 0, loc = lane;
-    while (i < rows - 1 && loc >= rows - 1 - i) {
-      loc -= rows - 1 - i;
-      ++i;
-    }
-    for (int q = lane; q < total; q += 32) {
-      const int r = i + 1 + loc;
-      const T v = r < m ? E::ld(A + r + (int64_t)i * lda) : E::zero();
-      tri[q] = E::mul(rinv[r], v);
-      loc += 32;
+    auto advance = [&](int by) {
+      loc += by;
       while (i < rows - 1 && loc >= rows - 1 - i) {
         loc -= rows - 1 - i;
         ++i;
+      }
+    };
+    advance(0);
+    for (int q0 = 0; q0 < total; q0 += 4 * 32) {
+      int rr[4];
+      T vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * 32 + lane;
+        rr[u] = i + 1 + loc;
+        vv[u] = (q < total && rr[u] < m) ? E::ld(A + rr[u] + (int64_t)i * lda) : E::zero();
+        advance(32);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * 32 + lane;
+        if (q < total) tri[q] = E::mul(rinv[rr[u]], vv[u]);
       }
     }
   }
@@ -453,16 +522,22 @@ hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int
   {
     static const PkOrder order = pk_order(pk_two_lanes<T>(), Elem<T>::kComplex);
     const int mmax = (max_m <= 0 || max_m > 64) ? 64 : max_m;
+    const int nsm = sm_count(dev);
+    int blocks = (batch + kPkSchedThreads2 - 1) / kPkSchedThreads2;
+    if (blocks > 4 * nsm) blocks = 4 * nsm;
     HsmaTraceScope ts("vbatched_schedule", st);
-    packed_schedule_kernel<T><<<1, kPkSchedThreads, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scr, L, mmax, order,
-                                                             status);
+    HSMA_CUDA_TRY(cudaMemsetAsync(scr + L.counts, 0, sizeof(PkCounts), st));
+    packed_count_kernel<T><<<blocks, kPkSchedThreads2, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scr, L, mmax,
+                                                                status);
+    packed_place_kernel<T><<<blocks, kPkSchedThreads2, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scr, L, mmax,
+                                                                order);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   if (!azero) {
-    // one warp per instance, up to 16 warps per SM over the whole GPU
+    // one warp per instance, up to 32 warps per SM over the whole GPU
     const int nsm = sm_count(dev);
     int blocks = (batch + kPkPrepWarps - 1) / kPkPrepWarps;
-    if (blocks > 2 * nsm) blocks = 2 * nsm;
+    if (blocks > 4 * nsm) blocks = 4 * nsm;
     HsmaTraceScope ts("vbatched_prep", st);
     packed_prep_kernel<T><<<blocks, 32 * kPkPrepWarps, 0, st>>>(dm, dA, dlda, scr, L, stage, al, unit);
     HSMA_CUDA_TRY(cudaGetLastError());
@@ -489,8 +564,6 @@ hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m
   switch (dtype) {
     case HSMA_C128:
       return packed_impl<cplx>(batch, max_m, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
-    case HSMA_R64:
-      return packed_impl<double>(batch, max_m, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
     default:
       return HSMA_ERR_UNSUPPORTED;
   }

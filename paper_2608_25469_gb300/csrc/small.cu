@@ -49,7 +49,10 @@ namespace {
 #ifndef HSMA_VB_GMASK
 #define HSMA_VB_GMASK 0xFu
 #endif
-constexpr int kWarpsSingle = 2;
+// Single solve: four warps per CTA, one per SM sub-partition (each
+// sub-partition has its own FP64 pipe, which bounds a warp's substitution
+// steps), sharing one staged triangle.
+constexpr int kWarpsSingle = 4;
 constexpr int kWarpsBatched = HSMA_VB_WARPS;
 constexpr unsigned kBatchedGMask = HSMA_VB_GMASK;
 
@@ -87,12 +90,16 @@ struct SmemLayout {
   __host__ __device__ static constexpr size_t bytes(int mmax) { return sizeof(T) * (tri_elems(mmax) + 2 * mmax); }
 };
 
-// Stage one instance: 1/a_rr and alpha/a_rr for r < m, then the scaled strict
-// lower triangle for rows < rows_used (rows >= m are zero).  All threads of
-// the CTA take part; ends with a CTA barrier.
+// Stage one instance: 1/a_rr and alpha/a_rr for every row r < MMAX (1 and 0
+// past m), then the strict lower triangle with row r pre-multiplied by 1/a_rr,
+// for the columns the substitution reads (i < m - 1) and rows i + 1 ..
+// rows_used - 1 (zeros past m).  The threads walk those elements in packed
+// order (consecutive elements in consecutive threads, four in flight), so
+// every thread does useful work on every pass and the index arithmetic stays
+// small.  All threads of the CTA take part; ends with a CTA barrier.
 template <class T, int MMAX, int W, bool MAP>
 __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict__ A, int64_t lda, int m,
-                                      int rows_used, T alpha, bool unit, SmallMap mp) {
+                                            int rows_used, T alpha, bool unit, SmallMap mp) {
   using E = Elem<T>;
   const int tid = threadIdx.x;
   for (int r = tid; r < MMAX; r += 32 * W) {
@@ -102,26 +109,28 @@ __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict
     sC[r] = (r < m) ? E::mul(alpha, rv) : E::zero();
   }
   __syncthreads();
-  // U columns per warp in flight, P row chunks of 32 per column: the loads of
-  // a batch are issued before any of them is used
-  const int warp = tid >> 5, lane = tid & 31;
-  constexpr int U = 4, P = (MMAX + 31) / 32;
-  for (int i0 = warp; i0 < m; i0 += W * U) {
-    T v[U][P];
+  int i = 0, loc = tid;
+  auto advance = [&](int by) {
+    loc += by;
+    while (i < m - 1 && loc >= rows_used - 1 - i) {
+      loc -= rows_used - 1 - i;
+      ++i;
+    }
+  };
+  advance(0);
+  while (i < m - 1) {
+    int rr[4], ii[4];
+    T vv[4];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < 4; ++u) {  // four elements in flight: loads first
+      ii[u] = i;
+      rr[u] = i + 1 + loc;
+      vv[u] = (i < m - 1 && rr[u] < m) ? map_ld<T, MAP>(A, lda, m, rr[u], i, mp) : E::zero();
+      advance(32 * W);
+    }
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const int i = i0 + u * W, r = lane + 32 * p;
-        v[u][p] = (i < m && r > i && r < m) ? map_ld<T, MAP>(A, lda, m, r, i, mp) : E::zero();
-      }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const int i = i0 + u * W, r = lane + 32 * p;
-        if (i < m && r > i && r < rows_used) sTri[col_off(i, MMAX) - i - 1 + r] = E::mul(sR[r], v[u][p]);
-      }
+    for (int u = 0; u < 4; ++u)
+      if (ii[u] < m - 1) sTri[col_off(ii[u], MMAX) - ii[u] - 1 + rr[u]] = E::mul(sR[rr[u]], vv[u]);
   }
   __syncthreads();
 }

@@ -34,11 +34,15 @@ hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t 
                                         uint32_t *status, int32_t *scratch, cudaStream_t st, int chol = 0);
 
 // Column-packed varlen batch for the left / lower / no-transpose solve in
-// HSMA_R64 or HSMA_C128 (packed.cu): schedule, prep and solve passes;
+// HSMA_C128 (packed.cu): schedule, prep and solve passes;
 // `scratch` holds hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m)
 // bytes (max_m: a bound on every m_i, 0 = 64).  Results equal
 // hsma_small_vbatched's bit for bit.
 size_t hsma_vbatched_packed_scratch_bytes(int dtype, int32_t batch, int32_t max_m);
+// dtypes whose varlen batch runs the column-packed kernels (measured faster
+// than the per-instance kernel: complex128; real FP64 keeps the per-instance
+// kernel, whose G choice already fills its lanes at 4x less work per element)
+inline bool hsma_vbatched_packed_dtype(int dtype) { return dtype == HSMA_C128; }
 hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m, const int32_t *dm,
                                          const int32_t *dn, const double *alpha, const void *const *dA,
                                          const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,

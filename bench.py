@@ -1181,9 +1181,9 @@ def run_mixed(args, dist, device, mode):
                 "kernel": "tc_gemm_kernel<TC_F32> (update_bf16: split-BF16 trailing update, FP32 accumulate)",
                 "kernel_ms": round(kernel_ms, 5), "peak_source": f"bf16 tensor (measured burst), {src}"}
     else:
-        evals = counts.get("residual", 0) / max(1, -(-m // 1024))  # one launch per K chunk
+        evals = int(info.ir_iters) + 1  # residual evaluations that did work (one per check)
         res_fl = ir_residual_bf16_flops(m, n)
-        rcnt = counts.get("residual", 1)
+        rcnt = counts.get("residual", 1)  # launches per step (one per K chunk and evaluation)
         kernel_ms = phases.get("residual", 0.0) / max(rcnt, 1)
         ach = res_fl * evals / max(rcnt, 1) / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else 0.0
         pk = peaks["bf16_tflops_sustained"] * 1e3

@@ -146,6 +146,11 @@ HSMA_API const char *hsma_version(void);
  * dtype  HSMA_R64 / HSMA_C128: A, B are double / interleaved complex double.
  *        HSMA_R32_BF16: A, B are float; the result is FP32.
  *        HSMA_R64_IR: A, B are double; FP32-result solves refined in FP64.
+ *        The host reads the stopping test after each refinement step (the
+ *        call then waits for the stream once per step, and returns once the
+ *        refinement has stopped); on a capturing stream every allowed step
+ *        is recorded instead and the device skips the steps after
+ *        convergence.
  * diag   HSMA_NON_UNIT or HSMA_UNIT.
  * Paths: m <= 64 runs the small direct solve (Section 4.2; triangle in shared
  * memory, columns of X in registers, warp-shuffle forward substitution);
@@ -371,7 +376,10 @@ HSMA_API hsma_status_t hsma_tuning_load(const char *path);
 /*
  * Fill a device matrix with the seeded synthetic workload (not part of the
  * solve; used to build inputs on the device).  kind 0 = A (lower triangular:
- * off-diagonal (2u-1)/m, diagonal 1+u, zeros above), kind 1 = B (2u-1), drawn
+ * off-diagonal (2u-1)/m, diagonal 1+u, zeros above), kind 1 = B (2u-1),
+ * kind 2 = packed LU factors as getrf leaves them without interchanges (A's
+ * entries below the diagonal; on and above it the transpose of a second
+ * triangle drawn like A from the streams U_RE = 4, U_IM = 5), drawn
  * from the counter-based SplitMix64 streams described in inputs.py.  `inst` is
  * the instance id (-1 for a single solve).  rows x cols written at `dst` with
  * leading dimension ld (>= rows); dtype HSMA_R64 or HSMA_C128.
@@ -384,10 +392,12 @@ HSMA_API hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64
  * TRSM is the paper's future work, Section 6).  A server owns a scheduler thread, a
  * ring of CUDA streams and a device memory pool on the current device.
  * Submitted requests are admitted in arrival order while their device memory
- * (A, B and the blocked path's workspace) fits `budget_bytes`; admitted
- * requests with m <= 64 that are ready together run as one varlen batched
- * launch, larger ones run the blocked path on the streams, overlapping on the
- * device.  Memory is freed when a request's completion event fires; latency is
+ * (A, B, pivots and the blocked path's workspace) fits `budget_bytes`;
+ * admitted requests with m <= 64 that are ready together run as one varlen
+ * batched launch per dtype and kind (triangular solves; LU- and
+ * Cholesky-factor solves through the fused factor-solve batch), larger ones
+ * run the blocked path on the streams (hsma_trsm_llnn_ex, hsma_getrs,
+ * hsma_potrs), overlapping on the device.  Memory is freed when a request's completion event fires; latency is
  * measured from submission to that event.  Each result equals the request
  * solved alone (up to the rounding of the path chosen for its size).
  */
@@ -414,7 +424,23 @@ typedef struct {
      discarded when X_host == NULL                                            */
   void *X_host;
   int64_t ldx;
+  /* what to solve with A (HSMA_REQ_*; 0 = the triangular solve)              */
+  int32_t kind;
+  int32_t reserved;
+  /* HSMA_REQ_GETRS: m pivots (LAPACK's 1-based sequential interchanges) in
+     host memory, or NULL for none; must be NULL for the other kinds        */
+  const int32_t *ipiv_host;
 } hsma_request_t;
+
+/* Request kinds.  TRSM: X = alpha L^{-1} B (L the lower triangle of A, diag as
+ * given).  GETRS: A holds packed LU factors (hsma_getrs), X = U^{-1} L^{-1}
+ * P^T (alpha B); generated inputs use hsma_gen_matrix kind 2 (no
+ * interchanges).  POTRS: A holds a lower Cholesky factor L (hsma_potrs),
+ * X = L^{-H} L^{-1} (alpha B); generated inputs draw L as kind 0.  diag is
+ * ignored by GETRS and POTRS. */
+#define HSMA_REQ_TRSM 0
+#define HSMA_REQ_GETRS 1
+#define HSMA_REQ_POTRS 2
 
 typedef struct {
   uint64_t submitted, admitted, completed;

@@ -96,7 +96,8 @@ hsma_status_t make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts
       if (g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return HSMA_ERR_INVALID_ARG;
       if (!hsma_small_g_ok(g, (int)m, cplx_)) return HSMA_ERR_INVALID_ARG;
     } else {
-      g = hsma_small_pick_g_single((int)std::max<int64_t>(m, 1), (int)std::min<int64_t>(n, 1 << 30), cplx_, 152);
+      g = hsma_small_pick_g_single((int)std::max<int64_t>(m, 1), (int)std::min<int64_t>(n, 1 << 30), cplx_,
+                                   hsma_sm_count());
     }
     p->groups = g;
   } else {
@@ -331,9 +332,9 @@ hsma_status_t hsma_potrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, 
 
 hsma_status_t hsma_gen_matrix(int dtype, int kind, uint64_t seed, int64_t inst, int64_t m, int64_t cols, void *dst,
                               int64_t ld, void *stream) {
-  if ((dtype != HSMA_R64 && dtype != HSMA_C128) || (kind != 0 && kind != 1)) return HSMA_ERR_INVALID_ARG;
+  if ((dtype != HSMA_R64 && dtype != HSMA_C128) || kind < 0 || kind > 2) return HSMA_ERR_INVALID_ARG;
   if (m < 0 || cols < 0 || ld < std::max<int64_t>(1, m) || inst < -1) return HSMA_ERR_INVALID_ARG;
-  if (kind == 0 && cols != m) return HSMA_ERR_INVALID_ARG;
+  if (kind != 1 && cols != m) return HSMA_ERR_INVALID_ARG;
   if (m * cols > 0 && dst == nullptr) return HSMA_ERR_INVALID_ARG;
   return hsma_gen_launch(dtype, kind, seed, inst, m, cols, dst, ld, static_cast<cudaStream_t>(stream));
 }

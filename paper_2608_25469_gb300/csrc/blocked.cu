@@ -455,16 +455,15 @@ bool tma_ok(const void *p, int64_t ld) {
   return ((uintptr_t)p % 16 == 0) && ((ld * (int64_t)sizeof(T)) % 16 == 0);
 }
 
-int sm_count() {
-  static int n[64] = {0};
-  int d = 0;
-  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 152;
-  if (n[d] == 0) cudaDeviceGetAttribute(&n[d], cudaDevAttrMultiProcessorCount, d);
-  return n[d] > 0 ? n[d] : 152;
-}
+int sm_count() { return hsma_sm_count(); }
 
-// Elements of partial-product workspace the split products of one solve may need.
-size_t partial_elems_max() { return (size_t)2 * 152 * 64 * 64 + (size_t)2 * 152 * 128 * 16; }
+// Elements of partial-product workspace the split products of one solve may
+// need: a product is split only while its tiles number fewer than two per SM,
+// so S x M x N stays below 2 x SMs x (one tile) for either tile shape.
+size_t partial_elems_max() {
+  const size_t sms = (size_t)sm_count();
+  return 2 * sms * 64 * 64 + 2 * sms * 128 * 16;
+}
 
 template <class T, class TL>
 hsma_status_t gemm_tiled(const GemmArgs<T> &p0, const char *phase, cudaStream_t st, T *P, size_t P_elems) {
@@ -581,7 +580,7 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
   const size_t dinv_bytes = sizeof(T) * (size_t)nblk * nb * nb;
   const size_t w_bytes = sizeof(T) * (size_t)nb * n;
   // partial products of split-K launches (only when n is small)
-  const size_t p_elems = (size_t)n * 64 < (size_t)2 * 152 * 64 * 64 ? partial_elems_max() : 0;
+  const size_t p_elems = (size_t)n * 64 < (size_t)2 * sm_count() * 64 * 64 ? partial_elems_max() : 0;
   hsma_status_t s = hsma_ws_alloc(&ws, dinv_bytes + w_bytes + sizeof(T) * p_elems, st);
   if (s != HSMA_OK) return s;
   T *Dinv = static_cast<T *>(ws);
@@ -641,6 +640,14 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
 }
 
 }  // namespace
+
+int hsma_sm_count() {
+  static int n[64] = {0};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return kHsmaDefaultSms;
+  if (n[d] == 0) cudaDeviceGetAttribute(&n[d], cudaDevAttrMultiProcessorCount, d);
+  return n[d] > 0 ? n[d] : kHsmaDefaultSms;
+}
 
 unsigned int *hsma_dev_error_ptr() {
   static unsigned int *ptr[64] = {nullptr};

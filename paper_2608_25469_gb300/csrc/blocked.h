@@ -27,3 +27,8 @@ hsma_status_t hsma_residual_f64(const double *A, int64_t lda, int unit, const do
 // Device address (current device) of the library's device error word, whose
 // HSMA_DEVERR_* bits kernels raise; NULL on a CUDA error.
 unsigned int *hsma_dev_error_ptr();
+
+// SMs of the current device (cached per device); kHsmaDefaultSms (a GB300's
+// 152) when no device can be queried, e.g. for host-only plan queries.
+constexpr int kHsmaDefaultSms = 152;
+int hsma_sm_count();

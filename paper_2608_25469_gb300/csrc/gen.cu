@@ -6,6 +6,8 @@
 //   u64(seed, s, i) = mix64(key + (i+1)*G),   u01 = (u64 >> 11) * 2^-53,
 // streams A_RE=0, B_RE=1, A_IM=2, B_IM=3 offset by (inst+1) << 8.
 // A (m x m): (2u-1)/m below the diagonal, 1+u on it, 0 above.  B: 2u-1.
+// Packed LU factors (kind 2): A's entries below the diagonal; on and above
+// it U(i, j) = T(j, i), T drawn like A from streams U_RE=4, U_IM=5.
 // Element index is i + j*m (the logical, unpadded column-major index).
 #include <cuda_runtime.h>
 
@@ -38,13 +40,16 @@ __device__ __forceinline__ double a_entry(uint64_t key, int64_t i, int64_t j, in
   return __ddiv_rn(2.0 * u - 1.0, (double)m);
 }
 
-__global__ void gen_kernel(int cplx_, int kind, uint64_t key_re, uint64_t key_im, int64_t m, int64_t cols,
-                           double *dst, int64_t ld) {
+__global__ void gen_kernel(int cplx_, int kind, uint64_t key_re, uint64_t key_im, uint64_t ukey_re,
+                           uint64_t ukey_im, int64_t m, int64_t cols, double *dst, int64_t ld) {
   const int64_t total = m * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % m, j = e / m;
     double re, im = 0.0;
-    if (kind == 0) {
+    if (kind == 2 && i <= j) {
+      re = a_entry(ukey_re, j, i, m);
+      if (cplx_) im = a_entry(ukey_im, j, i, m);
+    } else if (kind != 1) {
       re = a_entry(key_re, i, j, m);
       if (cplx_) im = a_entry(key_im, i, j, m);
     } else {
@@ -64,14 +69,20 @@ __global__ void gen_kernel(int cplx_, int kind, uint64_t key_re, uint64_t key_im
 
 hsma_status_t hsma_gen_launch(int dtype, int kind, uint64_t seed, int64_t inst, int64_t m, int64_t cols, void *dst,
                               int64_t ld, cudaStream_t st) {
-  const uint64_t base_re = kind == 0 ? 0 : 1, base_im = kind == 0 ? 2 : 3;
+  const uint64_t base_re = kind == 1 ? 1 : 0, base_im = kind == 1 ? 3 : 2;
   const uint64_t hi = (uint64_t)(inst + 1) << 8;
   const uint64_t kre = stream_key(seed, base_re + hi), kim = stream_key(seed, base_im + hi);
+  const uint64_t ukre = stream_key(seed, 4 + hi), ukim = stream_key(seed, 5 + hi);
   const int64_t total = m * cols;
   if (total == 0) return HSMA_OK;
+  static int nsm[64] = {0};
+  int dev = 0;
+  HSMA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return HSMA_ERR_UNSUPPORTED;
+  if (nsm[dev] == 0) HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  gen_kernel<<<(unsigned)blocks, 256, 0, st>>>(dtype == HSMA_C128, kind, kre, kim, m, cols,
+  if (blocks > (int64_t)nsm[dev] * 64) blocks = (int64_t)nsm[dev] * 64;
+  gen_kernel<<<(unsigned)blocks, 256, 0, st>>>(dtype == HSMA_C128, kind, kre, kim, ukre, ukim, m, cols,
                                                static_cast<double *>(dst), ld);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;

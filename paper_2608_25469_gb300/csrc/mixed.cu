@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) convert_x_kernel(const float *__restrict_
 
 int g_launch_grid(int64_t total) {
   int64_t b = (total + 255) / 256;
-  return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32);
+  return (int)std::min<int64_t>(std::max<int64_t>(b, 1), (int64_t)hsma_sm_count() * 32);
 }
 
 hsma_status_t bf16_update(const __nv_bfloat16 *Ap, const __nv_bfloat16 *Bp, int M, int N, int Kp, float beta, float *C,
@@ -833,7 +833,7 @@ hsma_status_t oz_slice_a(bool cplx, const double *A, int64_t lda, int rows, int 
 hsma_status_t oz_slice_x(const double *X, int64_t ldx, int K, const int *kexp, OzOperand &o, const int *skip,
                          cudaStream_t st) {
   if (o.rows <= 0) return HSMA_OK;
-  const int grid = std::min((o.rows + 7) / 8, 152 * 16);
+  const int grid = std::min((o.rows + 7) / 8, hsma_sm_count() * 16);
   oz_slice_x_kernel<<<grid, 256, 0, st>>>(X, ldx, K, o.rows, o.Kp, kexp, o.exps, o.slices, (size_t)o.rows * o.Kp,
                                           skip);
   HSMA_CUDA_TRY(cudaGetLastError());
@@ -1153,6 +1153,12 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
       HsmaTraceScope ts("refine", st);
       accumulate_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 1, nullptr);
     }
+    // Outside stream capture the host reads the stopping test after every
+    // step and launches nothing more once it holds; under capture every step
+    // is recorded and the device skips the ones after convergence.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((s = fail(cudaStreamIsCapturing(st, &cap))) != HSMA_OK) break;
+    const bool host_test = cap == cudaStreamCaptureStatusNone;
     for (int it = 0; it <= itmax && s == HSMA_OK; ++it) {
       // R = alpha B - L X in FP64, then the stopping test
       if (emulated) {
@@ -1174,6 +1180,12 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
         check_kernel<<<1, 1, 0, st>>>(sums, state, std::fabs(alpha), tol, it, it == itmax ? 1 : 0,
                                       hsma_dev_error_ptr());
         if (it == itmax) break;
+        if (host_test) {
+          int conv = 0;
+          if ((s = fail(cudaMemcpyAsync(&conv, state, sizeof conv, cudaMemcpyDeviceToHost, st))) != HSMA_OK) break;
+          if ((s = fail(cudaStreamSynchronize(st))) != HSMA_OK) break;
+          if (conv) break;
+        }
         f64_to_f32_kernel<<<grid, 256, 0, st>>>(R64, m, R32, m, m, n, 0, state);
         if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
       }

@@ -1,14 +1,15 @@
 // Serving loop: continuous batching of triangular solves on one GPU.
 //
-// Requests (fp64 or complex128, any m, n) are submitted from any host thread
-// and stamped with their arrival time.  A scheduler thread admits pending
-// requests in arrival order while their device memory (A, B and the blocked
-// path's workspace) fits the budget, brings their data onto the device
-// (generated there from a seed, or copied from host memory), and launches
-// them without waiting for earlier work: requests with m <= 64 that are
-// ready together are grouped into one varlen batched launch; larger requests
-// run the blocked path on a ring of streams, so their work overlaps on the
-// device.  A completion event per launch frees the memory and records the
+// Requests (fp64 or complex128, any m, n; a triangular solve, or a solve with
+// LU or Cholesky factors) are submitted from any host thread and stamped with
+// their arrival time.  A scheduler thread admits pending requests in arrival
+// order while their device memory (A, B, pivots and the blocked path's
+// workspace) fits the budget, brings their data onto the device (generated
+// there from a seed, or copied from host memory), and launches them without
+// waiting for earlier work: requests with m <= 64 that are ready together are
+// grouped into one varlen batched launch per dtype and kind (the factor
+// solves through the fused factor-solve batch); larger requests run the
+// blocked path on a ring of streams, so their work overlaps on the device.  A completion event per launch frees the memory and records the
 // latency (arrival to completion).  Results are the same as solving each
 // request alone, because each request's arithmetic does not depend on what
 // runs beside it.
@@ -45,7 +46,7 @@ struct Req {
   hsma_request_t r;
   Clock::time_point arrival;
   size_t need = 0;
-  void *dA = nullptr, *dB = nullptr;
+  void *dA = nullptr, *dB = nullptr, *dPiv = nullptr;
   int stream = 0;
   std::atomic<int> done{0};
   double latency = 0.0;
@@ -102,6 +103,12 @@ bool use_emulated(const hsma_request_t &r, unsigned flags) {
 size_t request_bytes(const hsma_request_t &r, unsigned flags) {
   const size_t es = esize(r.dtype);
   size_t b = es * (size_t)r.m * (size_t)r.m + es * (size_t)r.m * (size_t)r.n;
+  if (r.ipiv_host != nullptr) b += sizeof(int32_t) * (size_t)r.m;
+  if (r.m > 64 && r.kind != HSMA_REQ_TRSM) {
+    // the factor solves: permutation and a gathered copy of B, then two
+    // triangular solves one after the other (their workspaces never coexist)
+    b += sizeof(int32_t) * (size_t)r.m + es * (size_t)r.m * (size_t)r.n;
+  }
   if (use_emulated(r, flags)) return b + hsma_blocked_emulated_ws_bytes(r.dtype, kHsmaEmulatedNb, r.m, r.n);
   if (r.m > 64) {
     hsma_plan_t p;
@@ -131,13 +138,16 @@ hsma_status_t stage_inputs(hsma_server *s, Req &q) {
   const size_t es = esize(r.dtype);
   hsma_status_t rc = dev_alloc(s, &q.dA, es * r.m * r.m, st);
   if (rc == HSMA_OK) rc = dev_alloc(s, &q.dB, es * r.m * r.n, st);
+  if (rc == HSMA_OK && r.ipiv_host != nullptr) rc = dev_alloc(s, &q.dPiv, sizeof(int32_t) * r.m, st);
   if (rc != HSMA_OK) return rc;
+  if (r.ipiv_host != nullptr)
+    HSMA_CUDA_TRY(cudaMemcpyAsync(q.dPiv, r.ipiv_host, sizeof(int32_t) * r.m, cudaMemcpyHostToDevice, st));
   if (r.A_host != nullptr) {
     HSMA_CUDA_TRY(cudaMemcpy2DAsync(q.dA, es * r.m, r.A_host, es * r.lda, es * r.m, r.m, cudaMemcpyHostToDevice, st));
     HSMA_CUDA_TRY(cudaMemcpy2DAsync(q.dB, es * r.m, r.B_host, es * r.ldb, es * r.m, r.n, cudaMemcpyHostToDevice, st));
     return HSMA_OK;
   }
-  rc = hsma_gen_launch(r.dtype, 0, r.gen_seed, r.gen_inst, r.m, r.m, q.dA, r.m, st);
+  rc = hsma_gen_launch(r.dtype, r.kind == HSMA_REQ_GETRS ? 2 : 0, r.gen_seed, r.gen_inst, r.m, r.m, q.dA, r.m, st);
   if (rc == HSMA_OK) rc = hsma_gen_launch(r.dtype, 1, r.gen_seed, r.gen_inst, r.m, r.n, q.dB, r.m, st);
   return rc;
 }
@@ -163,6 +173,81 @@ void finish(hsma_server *s, Req &q, Clock::time_point now) {
   s->n_done.fetch_add(1);
 }
 
+// One varlen batched launch for the requests of group g (one dtype and kind,
+// all with m <= 64) on stream 0: the triangular-solve batch, or the fused
+// factor-solve batch.  Requests whose alpha (or, for triangular solves, diag)
+// differs from the first one's run as single solves of the same kind.
+Flight launch_group(hsma_server *s, int dt, int kind, const std::vector<Req *> &g) {
+  cudaStream_t st = s->streams[0];
+  const int nb = (int)g.size();
+  // host staging of the group's size and pointer arrays (pageable copies are fine: small)
+  std::vector<int32_t> hm(nb), hn(nb);
+  std::vector<void *> ha(nb), hb(nb), hp(nb);
+  for (int k = 0; k < nb; ++k) {
+    hm[k] = (int32_t)g[k]->r.m;
+    hn[k] = (int32_t)g[k]->r.n;
+    ha[k] = g[k]->dA;
+    hb[k] = g[k]->dB;
+    hp[k] = g[k]->dPiv;
+  }
+  Flight f;
+  f.reqs = g;
+  const size_t bytes = (size_t)nb * (3 * sizeof(int32_t) + 3 * sizeof(void *)) + 64;
+  hsma_status_t rc = dev_alloc(s, &f.meta, bytes, st);
+  hsma_status_t rc2 = HSMA_OK;
+  if (rc == HSMA_OK) {
+    unsigned char *base = static_cast<unsigned char *>(f.meta);
+    void **dpa = reinterpret_cast<void **>(base);
+    void **dpb = dpa + nb;
+    void **dpp = dpb + nb;
+    int32_t *dm = reinterpret_cast<int32_t *>(dpp + nb);
+    int32_t *dn = dm + nb;
+    cudaMemcpyAsync(dpa, ha.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dpb, hb.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dpp, hp.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dm, hm.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dn, hn.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st);
+    const hsma_request_t &r0 = g[0]->r;
+    bool uniform = true;
+    for (Req *q : g) {
+      const hsma_request_t &r = q->r;
+      uniform &= r.alpha[0] == r0.alpha[0] && r.alpha[1] == r0.alpha[1] &&
+                 (kind != HSMA_REQ_TRSM || r.diag == r0.diag);
+    }
+    if (uniform) {
+      if (kind == HSMA_REQ_GETRS)
+        rc2 = hsma_getrs_vbatched(dt, nb, dm, dn, r0.alpha, (const void *const *)dpa, dm,
+                                  (const int32_t *const *)dpp, (void *const *)dpb, dm, 64, 0, nullptr, st);
+      else if (kind == HSMA_REQ_POTRS)
+        rc2 = hsma_potrs_vbatched(dt, nb, dm, dn, r0.alpha, (const void *const *)dpa, dm, (void *const *)dpb, dm, 64,
+                                  0, nullptr, st);
+      else
+        rc2 = hsma_trsm_llnn_vbatched(dt, r0.diag, nb, dm, dn, r0.alpha, (const void *const *)dpa, dm,
+                                      (void *const *)dpb, dm, 64, 0, nullptr, st);
+    } else {
+      for (Req *qp : g) {
+        Req &q = *qp;
+        hsma_status_t r1;
+        if (kind == HSMA_REQ_GETRS)
+          r1 = hsma_getrs(dt, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, static_cast<const int32_t *>(q.dPiv), q.dB,
+                          q.r.m, st, nullptr);
+        else if (kind == HSMA_REQ_POTRS)
+          r1 = hsma_potrs(dt, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st, nullptr);
+        else
+          r1 = hsma_trsm_llnn(dt, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st);
+        if (r1 != HSMA_OK) rc2 = r1;
+      }
+    }
+    for (Req *q : g) fetch_output(s, *q);
+    s->n_batched.fetch_add(1);
+  }
+  if (rc != HSMA_OK || rc2 != HSMA_OK)
+    for (Req *q : g) q->status = rc != HSMA_OK ? rc : rc2;
+  cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
+  cudaEventRecord(f.ev, st);
+  return f;
+}
+
 // Launch what was admitted in this tick.  Called with the lock NOT held.
 void launch(hsma_server *s, std::vector<Req *> &small_group, std::vector<Req *> &large) {
   std::vector<Flight> out;
@@ -184,65 +269,14 @@ void launch(hsma_server *s, std::vector<Req *> &small_group, std::vector<Req *> 
     }
   } else {
     cudaSetDevice(s->device);
-    // one batched launch per dtype for the small requests, on stream 0
+    // one batched launch per dtype and kind for the small requests, on stream 0
     for (int dt = HSMA_R64; dt <= HSMA_C128; ++dt) {
-      std::vector<Req *> g;
-      for (Req *q : small_group)
-        if (q->r.dtype == dt) g.push_back(q);
-      if (g.empty()) continue;
-      cudaStream_t st = s->streams[0];
-      const int nb = (int)g.size();
-      // host staging of the group's size and pointer arrays (pageable copies are fine: small)
-      std::vector<int32_t> hm(nb), hn(nb);
-      std::vector<void *> ha(nb), hb(nb);
-      for (int k = 0; k < nb; ++k) {
-        Req &q = *g[k];
-        hm[k] = (int32_t)q.r.m;
-        hn[k] = (int32_t)q.r.n;
-        ha[k] = q.dA;
-        hb[k] = q.dB;
+      for (int kind = HSMA_REQ_TRSM; kind <= HSMA_REQ_POTRS; ++kind) {
+        std::vector<Req *> g;
+        for (Req *q : small_group)
+          if (q->r.dtype == dt && q->r.kind == kind) g.push_back(q);
+        if (!g.empty()) out.push_back(launch_group(s, dt, kind, g));
       }
-      Flight f;
-      f.reqs = g;
-      const size_t bytes = (size_t)nb * (3 * sizeof(int32_t) + 2 * sizeof(void *)) + 64;
-      hsma_status_t rc = dev_alloc(s, &f.meta, bytes, st);
-      hsma_status_t rc2 = HSMA_OK;
-      if (rc == HSMA_OK) {
-        unsigned char *base = static_cast<unsigned char *>(f.meta);
-        void **dpa = reinterpret_cast<void **>(base);
-        void **dpb = dpa + nb;
-        int32_t *dm = reinterpret_cast<int32_t *>(dpb + nb);
-        int32_t *dn = dm + nb;
-        cudaMemcpyAsync(dpa, ha.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(dpb, hb.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(dm, hm.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(dn, hn.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st);
-        // alpha and diag per group: requests with different alpha/diag go one launch each
-        // (grouped by the first request's values; others fall back to single launches)
-        const hsma_request_t &r0 = g[0]->r;
-        bool uniform = true;
-        for (Req *q : g) {
-          const hsma_request_t &r = q->r;
-          uniform &= r.alpha[0] == r0.alpha[0] && r.alpha[1] == r0.alpha[1] && r.diag == r0.diag;
-        }
-        if (uniform) {
-          rc2 = hsma_trsm_llnn_vbatched(dt, r0.diag, nb, dm, dn, r0.alpha, (const void *const *)dpa, dm,
-                                        (void *const *)dpb, dm, 64, 0, nullptr, st);
-        } else {
-          for (Req *qp : g) {
-            Req &q = *qp;
-            hsma_status_t r1 = hsma_trsm_llnn(dt, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st);
-            if (r1 != HSMA_OK) rc2 = r1;
-          }
-        }
-        for (Req *q : g) fetch_output(s, *q);
-        s->n_batched.fetch_add(1);
-      }
-      if (rc != HSMA_OK || rc2 != HSMA_OK)
-        for (Req *q : g) q->status = rc != HSMA_OK ? rc : rc2;
-      cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
-      cudaEventRecord(f.ev, st);
-      out.push_back(f);
     }
     for (Req *qp : large) {
       Req &q = *qp;
@@ -250,8 +284,15 @@ void launch(hsma_server *s, std::vector<Req *> &small_group, std::vector<Req *> 
       hsma_opts_t o;
       std::memset(&o, 0, sizeof o);
       o.fp64_products = use_emulated(q.r, s->flags) ? 1 : 0;
-      hsma_status_t rc = hsma_trsm_llnn_ex(q.r.dtype, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st,
-                                           &o, nullptr);
+      hsma_status_t rc;
+      if (q.r.kind == HSMA_REQ_GETRS)
+        rc = hsma_getrs(q.r.dtype, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, static_cast<const int32_t *>(q.dPiv), q.dB,
+                        q.r.m, st, &o);
+      else if (q.r.kind == HSMA_REQ_POTRS)
+        rc = hsma_potrs(q.r.dtype, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st, &o);
+      else
+        rc = hsma_trsm_llnn_ex(q.r.dtype, q.r.diag, q.r.m, q.r.n, q.r.alpha, q.dA, q.r.m, q.dB, q.r.m, st, &o,
+                               nullptr);
       if (rc == HSMA_OK) rc = fetch_output(s, q);
       q.status = rc;
       s->n_blocked.fetch_add(1);
@@ -355,7 +396,8 @@ void worker_loop(hsma_server *s) {
               Req &q = *qp;
               cudaFreeAsync(q.dA, s->streams[q.stream]);
               cudaFreeAsync(q.dB, s->streams[q.stream]);
-              q.dA = q.dB = nullptr;
+              if (q.dPiv) cudaFreeAsync(q.dPiv, s->streams[q.stream]);
+              q.dA = q.dB = q.dPiv = nullptr;
             }
             if (f.meta) cudaFreeAsync(f.meta, s->streams[0]);
             cudaEventDestroy(f.ev);
@@ -431,6 +473,8 @@ HSMA_API hsma_status_t hsma_server_submit(hsma_server_t *s, const hsma_request_t
   if (r.A_host != nullptr && (r.B_host == nullptr || r.lda < r.m || r.ldb < r.m)) return HSMA_ERR_INVALID_ARG;
   if (r.X_host != nullptr && r.ldx < r.m) return HSMA_ERR_INVALID_ARG;
   if (r.A_host == nullptr && r.gen_inst < -1) return HSMA_ERR_INVALID_ARG;
+  if (r.kind < HSMA_REQ_TRSM || r.kind > HSMA_REQ_POTRS) return HSMA_ERR_INVALID_ARG;
+  if (r.ipiv_host != nullptr && r.kind != HSMA_REQ_GETRS) return HSMA_ERR_INVALID_ARG;
   auto q = std::make_unique<Req>();
   q->r = r;
   q->arrival = Clock::now();

@@ -64,7 +64,11 @@ class Request(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("diag", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("alpha", ctypes.c_double * 2), ("A_host", ctypes.c_void_p), ("lda", ctypes.c_int64),
                 ("B_host", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("gen_seed", ctypes.c_uint64),
-                ("gen_inst", ctypes.c_int64), ("X_host", ctypes.c_void_p), ("ldx", ctypes.c_int64)]
+                ("gen_inst", ctypes.c_int64), ("X_host", ctypes.c_void_p), ("ldx", ctypes.c_int64),
+                ("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ipiv_host", ctypes.c_void_p)]
+
+
+REQ_TRSM, REQ_GETRS, REQ_POTRS = 0, 1, 2
 
 
 class ServerStats(ctypes.Structure):

@@ -30,6 +30,8 @@ random square matrices; the distributions below are this library's reading)
   A_ii = 1 + u, A_ij = 0 for i < j.  Complex: real and imaginary parts drawn
   independently in the same way (streams A_RE and A_IM).
 * B (m x n, column-major, index i + j*m): B_ij = 2u - 1 (streams B_RE, B_IM).
+* Packed LU factors (kind 2): below the diagonal A's multipliers; on and above
+  it the transpose of a second triangle drawn like A from streams U_RE, U_IM.
 * Batched small sizes: m, n uniform on {8, ..., 64}.
 * Serving stream: m = floor(exp(U(ln 16, ln 4097))) clamped to [16, 4096],
   n = floor(exp(U(0, ln 513))) clamped to [1, 512], fp64 with probability 0.7
@@ -46,6 +48,7 @@ M2 = 0x94D049BB133111EB
 MASK = (1 << 64) - 1
 
 A_RE, B_RE, A_IM, B_IM = 0, 1, 2, 3
+U_RE, U_IM = 4, 5  # the upper factor of generated packed LU factors
 SIZE_M, SIZE_N, DTYPE_SEL, ARRIVAL = 16, 17, 18, 19
 
 R64, C128 = 0, 1  # dtype codes, identical to the C-ABI's
@@ -107,6 +110,22 @@ def gen_A(seed: int, m: int, dtype: int = R64, inst: int = -1) -> np.ndarray:
         return np.asfortranarray(re)
     im = _tri_from_uniform(m, u01(seed, stream_id(A_IM, inst), idx))
     return np.asfortranarray(re + 1j * im)
+
+
+def gen_LU(seed: int, m: int, dtype: int = R64, inst: int = -1) -> np.ndarray:
+    """Packed LU factors (LAPACK getrf layout, no interchanges), shape (m, m), Fortran
+    order: below the diagonal the multipliers of gen_A's lower triangle (streams A_RE,
+    A_IM); on and above it U = T^T, T drawn as gen_A draws A but from streams U_RE, U_IM
+    (so U_ii = 1 + u and U_ij = (2u - 1)/m, element (i, j) of U taking T's index j + i m)."""
+    idx = np.arange(m * m, dtype=np.uint64)
+    parts = []
+    for sa, su in ((A_RE, U_RE), (A_IM, U_IM))[:1 if dtype == R64 else 2]:
+        L = _tri_from_uniform(m, u01(seed, stream_id(sa, inst), idx))
+        T = _tri_from_uniform(m, u01(seed, stream_id(su, inst), idx))
+        parts.append(np.tril(L, -1) + T.T)
+    if dtype == R64:
+        return np.asfortranarray(parts[0])
+    return np.asfortranarray(parts[0] + 1j * parts[1])
 
 
 def gen_B(seed: int, m: int, n: int, dtype: int = R64, inst: int = -1) -> np.ndarray:
@@ -176,6 +195,6 @@ def flops_trsm(m, n, complex_: bool) -> float:
 
 __all__ = [
     "u64", "u01", "key", "stream_id", "gen_A", "gen_B", "gen_B_cols", "batched_sizes",
-    "serving_requests", "embed", "flops_trsm", "R64", "C128",
-    "A_RE", "B_RE", "A_IM", "B_IM",
+    "serving_requests", "embed", "flops_trsm", "R64", "C128", "gen_LU",
+    "A_RE", "B_RE", "A_IM", "B_IM", "U_RE", "U_IM",
 ]

@@ -65,3 +65,21 @@ def test_gen_B_cols_matches_gen_B():
     B = I.gen_B(4, 29, 13, I.C128, inst=2)
     cols = [0, 12, 5]
     assert np.array_equal(I.gen_B_cols(4, 29, cols, I.C128, inst=2), B[:, cols])
+
+
+def test_gen_lu_packs_two_triangles():
+    """Packed LU factors: below the diagonal gen_A's multipliers (same streams), on and
+    above it the transpose of a triangle drawn from the U streams (diagonal in [1, 2),
+    off-diagonal entries (2u - 1)/m)."""
+    for code in (I.R64, I.C128):
+        m = 23
+        F = I.gen_LU(5, m, code, inst=2)
+        A = I.gen_A(5, m, code, inst=2)
+        low = np.tril_indices(m, -1)
+        assert np.array_equal(F[low], A[low])
+        U = np.triu(F)
+        d = np.diag(U)
+        assert np.all((d.real >= 1) & (d.real < 2))
+        up = np.triu_indices(m, 1)
+        assert np.all(np.abs(U[up].real) <= 1.0 / m)
+        assert not np.array_equal(np.triu(F, 1).T[low], A[low])  # a different draw

@@ -185,13 +185,14 @@ def test_batched_edge_instances(H):
 def test_device_generator_matches_host(H, code):
     import torch
     dt = U.torch_dtype(_np_dt(code))
-    for kind, (m, cols), inst in [(0, (37, 37), -1), (1, (37, 11), 4), (0, (64, 64), 12)]:
+    for kind, (m, cols), inst in [(0, (37, 37), -1), (1, (37, 11), 4), (0, (64, 64), 12), (2, (45, 45), 3)]:
         ld = m + 3
         t = torch.full((cols, ld), 7.0, dtype=dt, device="cuda")
         H.hsma_gen_matrix(code, kind, 42, inst, m, cols, t.data_ptr(), ld, H.stream_ptr())
         torch.cuda.synchronize()
         got = H.from_device(t)
-        ref = I.gen_A(42, m, code, inst=inst) if kind == 0 else I.gen_B(42, m, cols, code, inst=inst)
+        ref = {0: lambda: I.gen_A(42, m, code, inst=inst), 1: lambda: I.gen_B(42, m, cols, code, inst=inst),
+               2: lambda: I.gen_LU(42, m, code, inst=inst)}[kind]()
         assert np.array_equal(got[:m], ref)
         assert np.all(got[m:] == 7.0)
 

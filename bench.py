@@ -511,7 +511,7 @@ def run_batched_lu(args, dist, device):
 # the files that hold each profiled kernel (a summary's traffic is used only while they are unchanged)
 LARGE_SOURCES = ["paper_2608_25469_gb300/csrc/blocked.cu", "paper_2608_25469_gb300/csrc/tma.cuh"]
 EMU_SOURCES = ["paper_2608_25469_gb300/csrc/tc_gemm.cuh", "paper_2608_25469_gb300/csrc/tma.cuh"]
-# real columns per update panel of the emulated blocked solve (the library's HSMA_EMU_PANEL_COLS)
+# real columns per update panel of the emulated blocked solve when the plan reports none
 EMU_PANEL_COLS = 2048
 
 
@@ -648,7 +648,7 @@ def run_large(args, dist, device, code, m):
         # blocks: per block an update of the panel's remaining rows (K = N_B),
         # per panel one update of the rows below it (K = h N_B)
         w = 2 if cplx_ else 1
-        h = max(1, EMU_PANEL_COLS // (w * nb))
+        h = max(1, (info.plan.panel_cols or EMU_PANEL_COLS) // (w * nb))
         kp = lambda k: -(-(w * k) // 64) * 64  # noqa: E731
         bf16_flops = 0.0
         for R0 in range(0, m, h * nb):
@@ -688,8 +688,10 @@ def run_large(args, dist, device, code, m):
         "data": "synthetic",
         "config": {"workload": f"{name}: one blocked solve m=n={m}, alpha=1, non-unit, N_B={nb}"
                                + (", FP64 products emulated on the BF16 tensor cores" if emulated else ""),
-                   "m": m, "n": n,
-                   "nb": nb, "l2": f"inputs larger than L2 ({abytes / 1e9:.2f} GB)"},
+                   "m": m, "n": n, "nb": nb,
+                   "plan": {"tile": info.plan.tile, "split_k": info.plan.split_k, "looking": info.plan.looking,
+                            "panel_cols": info.plan.panel_cols},
+                   "l2": f"inputs larger than L2 ({abytes / 1e9:.2f} GB)"},
         "roofline": ({"bound": "tensor", "achieved": round(bf16_rate, 1), "peak": round(bf16_peak, 1),
                       "unit": "GFLOP/s", "frac": round(bf16_rate / bf16_peak, 4),
                       "traffic": profile_traffic(f"update_emulated_{name}.txt", EMU_SOURCES,

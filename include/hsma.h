@@ -93,12 +93,26 @@ typedef enum { HSMA_PATH_AUTO = 0, HSMA_PATH_SMALL = 1, HSMA_PATH_BLOCKED = 2 } 
 #define HSMA_DEVERR_NULL_PTR 0x2u  /* an instance with m*n > 0 had a NULL A or B      */
 #define HSMA_DEVERR_BAD_PIVOT 0x8u /* hsma_getrs_vbatched: a pivot outside [k+1, m]   */
 
+/* Blocked-path configuration values (hsma_opts_t / hsma_plan_t). */
+#define HSMA_TILE_64x64 1   /* FP64 tensor-product CTA tile, rows x columns of B */
+#define HSMA_TILE_128x16 2
+#define HSMA_TILE_128x8 3
+#define HSMA_SPLITK_AUTO 1  /* split K across CTAs when the tiles leave SMs idle */
+#define HSMA_SPLITK_OFF 2
+#define HSMA_LOOK_RIGHT 1   /* after X_r: B_{r+1:} -= A_{r+1:,r} X_r              */
+#define HSMA_LOOK_LEFT 2    /* before X_r: B_r -= A_{r,0:r} X_{0:r} (Section 4.3)  */
+
 /* Plan chosen for one solve (Section 4.1's dispatcher and Section 4.3.2's
- * configuration lookup). */
+ * configuration lookup: the nearest profiled (m, n) of the autotuned table). */
 typedef struct {
-  int32_t path;      /* hsma_path_t: SMALL (m <= 64) or BLOCKED                     */
-  int32_t nb;        /* BLOCKED: diagonal block size (the paper's N_B)              */
-  int32_t groups;    /* SMALL: row groups per warp G; a warp holds 32/G columns    */
+  int32_t path;       /* hsma_path_t: SMALL (m <= 64) or BLOCKED                    */
+  int32_t nb;         /* BLOCKED: diagonal block size (the paper's N_B)             */
+  int32_t groups;     /* SMALL: row groups per warp G; a warp holds 32/G columns   */
+  int32_t tile;       /* BLOCKED FP64 products: HSMA_TILE_*, 0 = by n (128x8 for
+                         n <= 8, 128x16 for n <= 48, else 64x64)                  */
+  int32_t split_k;    /* BLOCKED: HSMA_SPLITK_*                                     */
+  int32_t looking;    /* BLOCKED: HSMA_LOOK_*                                       */
+  int32_t panel_cols; /* emulated FP64 products: real columns per update panel     */
   int32_t reserved;
 } hsma_plan_t;
 
@@ -122,7 +136,11 @@ typedef struct {
                           products summed exactly in FP32 and folded into the
                           FP64 result (error below 2^-59 of row max x column
                           max per product term; N_B <= 512, default 512)      */
-  int32_t reserved;
+  int32_t tile;        /* BLOCKED FP64 products: HSMA_TILE_*; 0 = table         */
+  int32_t split_k;     /* BLOCKED: HSMA_SPLITK_*; 0 = table                     */
+  int32_t looking;     /* BLOCKED: HSMA_LOOK_*; 0 = table                       */
+  int32_t panel_cols;  /* fp64_products = 1: real columns per update panel
+                          (a multiple of 64, 512 .. 8192); 0 = table          */
 } hsma_opts_t;
 
 /* Filled by hsma_trsm_llnn_ex (host memory).  Fields describing the device
@@ -368,9 +386,10 @@ HSMA_API hsma_status_t hsma_plan(int dtype, int64_t m, int64_t n, hsma_plan_t *o
  * with G row groups (the cost model the planner minimises); host only. */
 HSMA_API double hsma_small_cost(int dtype, int64_t m, int64_t n, int32_t groups);
 
-/* Replace the compiled block-size table with the one in `path` (a text file of
- * lines "dtype m n nb"; see Section 4.3.2: nearest tested scale wins).  NULL
- * restores the compiled table. */
+/* Replace the compiled configuration table with the one in `path` (a text
+ * file of lines "dtype m n nb" or "dtype m n nb tile split_k looking
+ * panel_cols", the autotuner's output; see Section 4.3.2: the nearest tested
+ * scale in (log m, log n) wins).  NULL restores the compiled table. */
 HSMA_API hsma_status_t hsma_tuning_load(const char *path);
 
 /*

@@ -45,6 +45,10 @@ struct TuneEntry {
   int dtype;
   int64_t m, n;
   int nb;
+  int tile = 0;                     // HSMA_TILE_*, 0 = by n
+  int split_k = HSMA_SPLITK_AUTO;
+  int looking = HSMA_LOOK_RIGHT;
+  int panel_cols = kEmuPanelColsDefault;  // emulated products
 };
 
 #include "tuning_table.inc"
@@ -52,19 +56,20 @@ struct TuneEntry {
 std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune;  // empty = compiled table
 
-int lookup_nb(int dtype, int64_t m, int64_t n) {
+TuneEntry lookup(int dtype, int64_t m, int64_t n) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const TuneEntry *tab = g_tune.empty() ? kCompiledTable : g_tune.data();
   const size_t cnt = g_tune.empty() ? sizeof(kCompiledTable) / sizeof(kCompiledTable[0]) : g_tune.size();
   // R64_IR and R32 tune as R32_BF16 (their blocked solves run that path), C64 as C128;
-  // fall back to R64 entries if a dtype has none
+  // fall back to R64 entries if a dtype has none (emulated-products keys to their defaults)
+  const bool emu_key = dtype == kEmulatedTableDtype(HSMA_R64) || dtype == kEmulatedTableDtype(HSMA_C128);
   const int want = (dtype == HSMA_R64_IR || dtype == HSMA_R32) ? HSMA_R32_BF16
                    : dtype == HSMA_C64                         ? HSMA_C128
                                                                : dtype;
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < (emu_key ? 1 : 2); ++pass) {
     const int d = pass == 0 ? want : HSMA_R64;
     double best = 1e300;
-    int nb = 0;
+    const TuneEntry *pick = nullptr;
     for (size_t k = 0; k < cnt; ++k) {
       if (tab[k].dtype != d) continue;
       const double dm = std::log((double)std::max<int64_t>(m, 1)) - std::log((double)tab[k].m);
@@ -72,13 +77,23 @@ int lookup_nb(int dtype, int64_t m, int64_t n) {
       const double dist = dm * dm + dn * dn;
       if (dist < best) {
         best = dist;
-        nb = tab[k].nb;
+        pick = &tab[k];
       }
     }
-    if (nb > 0) return nb;
+    if (pick != nullptr) return *pick;
   }
-  return 128;
+  TuneEntry e{dtype, m, n, emu_key ? kHsmaEmulatedNb : 128};
+  return e;
 }
+
+bool valid_table_dtype(int d) {
+  return valid_dtype(d) || d == kEmulatedTableDtype(HSMA_R64) || d == kEmulatedTableDtype(HSMA_C128);
+}
+
+bool valid_tile(int t) { return t >= 0 && t <= HSMA_TILE_128x8; }
+bool valid_split(int v) { return v >= 0 && v <= HSMA_SPLITK_OFF; }
+bool valid_look(int v) { return v >= 0 && v <= HSMA_LOOK_LEFT; }
+bool valid_panel(int v) { return v == 0 || (v >= 512 && v <= 8192 && v % 64 == 0); }
 
 hsma_status_t make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts, hsma_plan_t *p) {
   std::memset(p, 0, sizeof(*p));
@@ -103,8 +118,19 @@ hsma_status_t make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts
   } else {
     int nb = opts ? opts->nb : 0;
     if (nb != 0 && (nb < 16 || nb > 512 || nb % 16 != 0)) return HSMA_ERR_INVALID_ARG;
-    if (nb == 0) nb = lookup_nb(dtype, m, n);
-    p->nb = nb;
+    if (opts && (!valid_tile(opts->tile) || !valid_split(opts->split_k) || !valid_look(opts->looking) ||
+                 !valid_panel(opts->panel_cols)))
+      return HSMA_ERR_INVALID_ARG;
+    // the table's entry for this scale (the emulated-products entries when the
+    // FP64 products are emulated: the option, or complex64's widened solve);
+    // every option the caller gives overrides its field
+    const bool emu = dtype == HSMA_C64 || ((dtype == HSMA_R64 || dtype == HSMA_C128) && opts && opts->fp64_products == 1);
+    const TuneEntry e = lookup(emu ? kEmulatedTableDtype(dtype == HSMA_C64 ? HSMA_C128 : dtype) : dtype, m, n);
+    p->nb = nb != 0 ? nb : e.nb;
+    p->tile = opts && opts->tile ? opts->tile : e.tile;
+    p->split_k = opts && opts->split_k ? opts->split_k : e.split_k;
+    p->looking = opts && opts->looking ? opts->looking : e.looking;
+    p->panel_cols = opts && opts->panel_cols ? opts->panel_cols : e.panel_cols;
   }
   return HSMA_OK;
 }
@@ -125,6 +151,14 @@ bool alpha_is_zero(int dtype, const void *alpha) {
 }
 
 }  // namespace
+
+extern "C" {
+
+}  // extern "C"
+
+hsma_status_t hsma_make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts, hsma_plan_t *out) {
+  return make_plan(dtype, m, n, opts, out);
+}
 
 extern "C" {
 
@@ -168,14 +202,15 @@ hsma_status_t hsma_tuning_load(const char *path) {
   char line[256];
   while (std::fgets(line, sizeof line, f)) {
     if (line[0] == '#' || line[0] == '\n') continue;
-    int d, nb;
+    int d, nb, tile = 0, split = HSMA_SPLITK_AUTO, look = HSMA_LOOK_RIGHT, panel = kEmuPanelColsDefault;
     long long m, n;
-    if (std::sscanf(line, "%d %lld %lld %d", &d, &m, &n, &nb) != 4 || !valid_dtype(d) || m < 1 || n < 1 ||
-        nb < 16 || nb > 512 || nb % 16 != 0) {
+    const int got = std::sscanf(line, "%d %lld %lld %d %d %d %d %d", &d, &m, &n, &nb, &tile, &split, &look, &panel);
+    if ((got != 4 && got != 8) || !valid_table_dtype(d) || m < 1 || n < 1 || nb < 16 || nb > 512 || nb % 16 != 0 ||
+        !valid_tile(tile) || split < 1 || split > 2 || look < 1 || look > 2 || panel == 0 || !valid_panel(panel)) {
       std::fclose(f);
       return HSMA_ERR_INVALID_ARG;
     }
-    t.push_back(TuneEntry{d, m, n, nb});
+    t.push_back(TuneEntry{d, m, n, nb, tile, split, look, panel});
   }
   std::fclose(f);
   if (t.empty()) return HSMA_ERR_INVALID_ARG;
@@ -211,12 +246,16 @@ hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const
     case HSMA_C128:
       if (plan.path == HSMA_PATH_SMALL)
         return hsma_small_single(dtype, plan.groups, A, lda, B, ldb, (int)m, (int)n, al, unit, st);
-      if (opts != nullptr && opts->fp64_products == 1) {
-        const int nb = opts->nb != 0 ? opts->nb : kHsmaEmulatedNb;
-        if (info) info->plan.nb = nb;
-        return hsma_blocked_emulated(dtype, nb, A, lda, B, ldb, m, n, al, unit, st);
+      if (opts != nullptr && opts->fp64_products == 1)
+        return hsma_blocked_emulated(dtype, plan.nb, plan.panel_cols, A, lda, B, ldb, m, n, al, unit, st);
+      {
+        HsmaBlockedCfg cfg;
+        cfg.nb = plan.nb;
+        cfg.tile = plan.tile;
+        cfg.split_k = plan.split_k;
+        cfg.looking = plan.looking;
+        return hsma_blocked_solve(dtype, cfg, A, lda, B, ldb, m, n, al, unit, st);
       }
-      return hsma_blocked_solve(dtype, plan.nb, A, lda, B, ldb, m, n, al, unit, st);
     case HSMA_R32_BF16:
       return hsma_mixed_r32(plan.nb, opts ? opts->bf16_terms : 0, static_cast<const float *>(A), lda,
                             static_cast<float *>(B), ldb, m, n, al[0], unit, st);
@@ -231,7 +270,7 @@ hsma_status_t hsma_trsm_llnn_ex(int dtype, int diag, int64_t m, int64_t n, const
     case HSMA_C64:
       if (plan.path == HSMA_PATH_SMALL)
         return hsma_small_single(dtype, plan.groups, A, lda, B, ldb, (int)m, (int)n, al, unit, st);
-      return hsma_c64_blocked(opts && opts->nb ? opts->nb : kHsmaEmulatedNb, A, lda, B, ldb, m, n, al, unit, st);
+      return hsma_c64_blocked(plan.nb, plan.panel_cols, A, lda, B, ldb, m, n, al, unit, st);
     default:
       return HSMA_ERR_INVALID_ARG;
   }

@@ -524,14 +524,17 @@ hsma_status_t gemm_tiled(const GemmArgs<T> &p0, const char *phase, cudaStream_t 
   return HSMA_OK;
 }
 
-// Launch one product (tile shape by n; K split across CTAs when the output
-// alone has too few tiles and a partial-product workspace P is given).
-// `phase` names it for the tracer.
+// Launch one product.  Tile shape: `tile` (HSMA_TILE_*), or by n when 0
+// (128 x 8 for n <= 8, 128 x 16 for n <= 48, else 64 x 64).  K is split across
+// CTAs when the output alone has too few tiles and a partial-product
+// workspace P is given (P = nullptr: never).  `phase` names it for the tracer.
 template <class T>
-hsma_status_t gemm(const GemmArgs<T> &p, const char *phase, cudaStream_t st, T *P = nullptr, size_t P_elems = 0) {
+hsma_status_t gemm(const GemmArgs<T> &p, const char *phase, cudaStream_t st, T *P = nullptr, size_t P_elems = 0,
+                   int tile = 0) {
   if (p.M <= 0 || p.N <= 0) return HSMA_OK;
-  if (p.N <= 8) return gemm_tiled<T, TileN8>(p, phase, st, P, P_elems);
-  if (p.N <= 48) return gemm_tiled<T, TileN16>(p, phase, st, P, P_elems);
+  if (tile == 0) tile = p.N <= 8 ? HSMA_TILE_128x8 : p.N <= 48 ? HSMA_TILE_128x16 : HSMA_TILE_64x64;
+  if (tile == HSMA_TILE_128x8) return gemm_tiled<T, TileN8>(p, phase, st, P, P_elems);
+  if (tile == HSMA_TILE_128x16) return gemm_tiled<T, TileN16>(p, phase, st, P, P_elems);
   return gemm_tiled<T, TileWide>(p, phase, st, P, P_elems);
 }
 
@@ -570,17 +573,28 @@ cplx make_scalar<cplx>(const double *a) {
   return cplx{a[0], a[1]};
 }
 
+// Blocked two-phase solve (Section 4.3).  Phase 1 inverts every diagonal
+// block; phase 2 walks the block rows r: X_r = D_r^{-1} W, where W holds the
+// block row's right-hand side after the updates, and the updates are either
+//   right-looking: after X_r, B_{r+1:} -= A_{r+1:, r} X_r (one product with
+//                  M = m - r0 - s_r rows, K = s_r; the next block row goes to W);
+//   left-looking:  before X_r, W = alpha B_r - A_{r, 0:r} X_{0:r} (one product
+//                  with M = s_r rows, K = r0, the paper's form of the update).
+// alpha is applied once, to each block row's first use.
 template <class T>
-hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, int64_t m, int64_t n,
-                           const double *alpha, int unit, cudaStream_t st) {
+hsma_status_t blocked_impl(const HsmaBlockedCfg &cfg, const T *A, int64_t lda, T *B, int64_t ldb, int64_t m,
+                           int64_t n, const double *alpha, int unit, cudaStream_t st) {
+  const int nb = cfg.nb;
+  const bool left = cfg.looking == HSMA_LOOK_LEFT;
   const int64_t nblk = (m + nb - 1) / nb;
   const T al = make_scalar<T>(alpha);
   const T one = make_scalar<T>((const double[2]){1.0, 0.0});
   void *ws = nullptr;
   const size_t dinv_bytes = sizeof(T) * (size_t)nblk * nb * nb;
   const size_t w_bytes = sizeof(T) * (size_t)nb * n;
-  // partial products of split-K launches (only when n is small)
-  const size_t p_elems = (size_t)n * 64 < (size_t)2 * sm_count() * 64 * 64 ? partial_elems_max() : 0;
+  // partial products of split-K launches (only when n is small, unless split K is off)
+  const size_t p_elems =
+      cfg.split_k != HSMA_SPLITK_OFF && (size_t)n * 64 < (size_t)2 * sm_count() * 64 * 64 ? partial_elems_max() : 0;
   hsma_status_t s = hsma_ws_alloc(&ws, dinv_bytes + w_bytes + sizeof(T) * p_elems, st);
   if (s != HSMA_OK) return s;
   T *Dinv = static_cast<T *>(ws);
@@ -600,6 +614,27 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
   for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
     const int64_t r0 = r * nb;
     const int sr = (int)std::min<int64_t>(nb, m - r0);
+    if (left && r > 0) {
+      // W = alpha B_r - A_{r, 0:r} X_{0:r}
+      GemmArgs<T> pl{};
+      pl.A = A + r0;
+      pl.lda = lda;
+      pl.Bm = B;
+      pl.ldb = ldb;
+      pl.C = B + r0;
+      pl.ldc = ldb;
+      pl.C2 = W;
+      pl.ldc2 = nb;
+      pl.split_rows = sr;
+      pl.M = sr;
+      pl.N = (int)n;
+      pl.K = (int)r0;
+      pl.mode = MODE_UPDATE;
+      pl.beta = al;
+      pl.tri = 0;
+      s = gemm<T>(pl, "update_gemm", st, Pw, p_elems, cfg.tile);
+      if (s != HSMA_OK) break;
+    }
     // X_r = D_r^{-1} (scale * W)
     GemmArgs<T> ps{};
     ps.A = Dinv + (size_t)r * nb * nb;
@@ -614,8 +649,9 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
     ps.mode = MODE_SCALE;
     ps.beta = r == 0 ? al : one;
     ps.tri = 1;
-    s = gemm<T>(ps, "solve_gemm", st, Pw, p_elems);
+    s = gemm<T>(ps, "solve_gemm", st, Pw, p_elems, cfg.tile);
     if (s != HSMA_OK || r0 + sr >= m) break;
+    if (left) continue;
     // B_{r+1:} = beta B_{r+1:} - A_{r+1:, r} X_r; the next block row goes to W
     GemmArgs<T> pu{};
     pu.A = A + (r0 + sr) + r0 * lda;
@@ -633,7 +669,7 @@ hsma_status_t blocked_impl(int nb, const T *A, int64_t lda, T *B, int64_t ldb, i
     pu.mode = MODE_UPDATE;
     pu.beta = r == 0 ? al : one;
     pu.tri = 0;
-    s = gemm<T>(pu, "update_gemm", st, Pw, p_elems);
+    s = gemm<T>(pu, "update_gemm", st, Pw, p_elems, cfg.tile);
   }
   hsma_status_t f = hsma_ws_free(ws, st);
   return s != HSMA_OK ? s : f;
@@ -723,13 +759,13 @@ bool hsma_make_map_2d(CUtensorMap *map, CUtensorMapDataType dt, int elem_bytes, 
   return r == CUDA_SUCCESS;
 }
 
-hsma_status_t hsma_blocked_solve(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
-                                 int64_t n, const double *alpha, int unit, cudaStream_t st) {
+hsma_status_t hsma_blocked_solve(int dtype, const HsmaBlockedCfg &cfg, const void *A, int64_t lda, void *B,
+                                 int64_t ldb, int64_t m, int64_t n, const double *alpha, int unit, cudaStream_t st) {
   if (n > INT32_MAX || m > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
   if (dtype == HSMA_C128)
-    return blocked_impl<cplx>(nb, static_cast<const cplx *>(A), lda, static_cast<cplx *>(B), ldb, m, n, alpha, unit,
-                              st);
-  return blocked_impl<double>(nb, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb, m, n, alpha,
+    return blocked_impl<cplx>(cfg, static_cast<const cplx *>(A), lda, static_cast<cplx *>(B), ldb, m, n, alpha,
+                              unit, st);
+  return blocked_impl<double>(cfg, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb, m, n, alpha,
                               unit, st);
 }
 

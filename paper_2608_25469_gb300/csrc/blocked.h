@@ -5,10 +5,20 @@
 
 #include "../../include/hsma.h"
 
-// Blocked two-phase solve (Section 4.3) for HSMA_R64 / HSMA_C128 with
-// diagonal block size nb.  Arguments already validated; alpha != 0.
-hsma_status_t hsma_blocked_solve(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
-                                 int64_t n, const double *alpha, int unit, cudaStream_t st);
+// Configuration of the blocked path: diagonal block size, FP64 product tile
+// shape (HSMA_TILE_*; 0 = by n), split K (HSMA_SPLITK_*) and the update
+// direction (HSMA_LOOK_*), as the planner picks them.
+struct HsmaBlockedCfg {
+  int nb = 256;
+  int tile = 0;
+  int split_k = HSMA_SPLITK_AUTO;
+  int looking = HSMA_LOOK_RIGHT;
+};
+
+// Blocked two-phase solve (Section 4.3) for HSMA_R64 / HSMA_C128.  Arguments
+// already validated; alpha != 0.
+hsma_status_t hsma_blocked_solve(int dtype, const HsmaBlockedCfg &cfg, const void *A, int64_t lda, void *B,
+                                 int64_t ldb, int64_t m, int64_t n, const double *alpha, int unit, cudaStream_t st);
 
 // Phase 1 alone: invert the N_B x N_B diagonal blocks of the lower triangle of
 // A (dtype HSMA_R64, HSMA_C128 or HSMA_R32_BF16 for float data) into Dinv

@@ -84,9 +84,11 @@ struct Elem<cplx> {
     s.im = fma(-a.im, x.re, s.im);
     return s;
   }
-  // 1/a, scaled by the larger component of a (Smith's division with numerator
-  // 1).  Written with selects rather than a branch: lanes of a warp that take
-  // different branches would otherwise run both branches' three divisions.
+  // 1/a, scaled by the larger component of a (Smith's algorithm with numerator
+  // 1), with two divisions: t/d is taken as t (1/d), one rounding more than a
+  // third division (relative error below 2 ulps instead of 1).  Written with
+  // selects rather than a branch: lanes of a warp that take different branches
+  // would otherwise run both branches' divisions.
   //   |re| >= |im|: t = im/re, d = re + im t, 1/a = (1/d, -t/d)
   //   otherwise:    t = re/im, d = re t + im, 1/a = (t/d, -1/d)
   __device__ __forceinline__ static cplx recip(cplx a) {
@@ -94,7 +96,7 @@ struct Elem<cplx> {
     const double p = big ? a.re : a.im, q = big ? a.im : a.re;  // larger, smaller
     const double t = q / p;
     const double d = fma(q, t, p);
-    const double u = 1.0 / d, v = t / d;
+    const double u = 1.0 / d, v = t * u;
     return big ? cplx{u, -v} : cplx{v, -u};
   }
   __device__ __forceinline__ static cplx shfl(cplx v, int src) {
@@ -134,13 +136,13 @@ struct Elem<cplxf> {
     s.im = fmaf(-a.im, x.re, s.im);
     return s;
   }
-  // Smith's division with numerator 1 (selects, as for cplx)
+  // Smith's algorithm with numerator 1 (selects, two divisions, as for cplx)
   __device__ __forceinline__ static cplxf recip(cplxf a) {
     const bool big = fabsf(a.re) >= fabsf(a.im);
     const float p = big ? a.re : a.im, q = big ? a.im : a.re;
     const float t = q / p;
     const float d = fmaf(q, t, p);
-    const float u = 1.0f / d, v = t / d;
+    const float u = 1.0f / d, v = t * u;
     return big ? cplxf{u, -v} : cplxf{v, -u};
   }
   __device__ __forceinline__ static cplxf shfl(cplxf v, int src) {

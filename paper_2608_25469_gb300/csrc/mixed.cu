@@ -956,14 +956,11 @@ __global__ void scale_kernel(double *B, int64_t ldb, int64_t rows, int64_t n, do
 // real columns): inside a panel, each solved block updates only the panel's
 // remaining rows; below the panel, one update with K = h N_B covers all h
 // blocks.  The result is the same product sum, grouped differently.
-// Real columns per update panel of the emulated blocked solve (the panel's
-// trailing update runs with K = this many real columns).  Measured on GB300
-// for m = 16384 FP64 / 8192 complex128: 1024 columns 217 / 112 ms, 2048
-// columns 208 / 105 ms, 3072 and 4096 columns slower again.
-#ifndef HSMA_EMU_PANEL_COLS
-#define HSMA_EMU_PANEL_COLS 2048
-#endif
-constexpr int kEmuPanelCols = HSMA_EMU_PANEL_COLS;
+// The panel width (real columns; the panel's trailing update runs with K =
+// that many real columns) comes from the planner: the autotuned table, else
+// kEmuPanelColsDefault.  Measured on GB300 for m = 16384 FP64 / 8192
+// complex128: 1024 columns 217 / 112 ms, 2048 columns 208 / 105 ms, 3072 and
+// 4096 columns slower again.
 
 // Workspace of blocked_emulated: the inverses, one block row of B, and the
 // slices of an update panel, of one inverse and of the right operand.
@@ -974,11 +971,11 @@ struct EmuLayout {
   size_t total() const { return dinv_b + w_b + pa_b + pd_b + px_b; }
 };
 
-EmuLayout emu_layout(bool cplx, int nb, int64_t m, int64_t n) {
+EmuLayout emu_layout(bool cplx, int nb, int panel_cols, int64_t m, int64_t n) {
   EmuLayout L;
   L.W = cplx ? 2 : 1;
   const int64_t nblk = (m + nb - 1) / nb;
-  L.h = std::max(1, kEmuPanelCols / (L.W * nb));
+  L.h = std::max(1, (panel_cols > 0 ? panel_cols : kEmuPanelColsDefault) / (L.W * nb));
   L.P = (int64_t)L.h * nb;  // panel width (source columns)
   L.Kpb = oz_kp((int64_t)L.W * nb);
   L.Kpp = oz_kp(L.W * L.P);
@@ -992,9 +989,10 @@ EmuLayout emu_layout(bool cplx, int nb, int64_t m, int64_t n) {
   return L;
 }
 
-hsma_status_t blocked_emulated(bool cplx, int nb, const double *A, int64_t lda, double *B, int64_t ldb, int64_t m,
+hsma_status_t blocked_emulated(bool cplx, int nb, int panel_cols, const double *A, int64_t lda, double *B,
+                               int64_t ldb, int64_t m,
                                int64_t n, const double *alpha, int unit, cudaStream_t st) {
-  const EmuLayout E = emu_layout(cplx, nb, m, n);
+  const EmuLayout E = emu_layout(cplx, nb, panel_cols, m, n);
   const int W = E.W;
   const int64_t P = E.P;
   const int Kpb = E.Kpb, Kpp = E.Kpp;
@@ -1222,15 +1220,16 @@ extern "C" HSMA_API hsma_status_t hsma_gemm_bf16_update(int64_t M, int64_t N, in
                      (int)K, beta, C, ldc, static_cast<cudaStream_t>(stream));
 }
 
-hsma_status_t hsma_blocked_emulated(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
-                                    int64_t n, const double *alpha, int unit, cudaStream_t st) {
+hsma_status_t hsma_blocked_emulated(int dtype, int nb, int panel_cols, const void *A, int64_t lda, void *B,
+                                    int64_t ldb, int64_t m, int64_t n, const double *alpha, int unit,
+                                    cudaStream_t st) {
   if (dtype != HSMA_R64 && dtype != HSMA_C128) return HSMA_ERR_INVALID_ARG;
-  return blocked_emulated(dtype == HSMA_C128, nb, static_cast<const double *>(A), lda, static_cast<double *>(B), ldb,
-                          m, n, alpha, unit, st);
+  return blocked_emulated(dtype == HSMA_C128, nb, panel_cols, static_cast<const double *>(A), lda,
+                          static_cast<double *>(B), ldb, m, n, alpha, unit, st);
 }
 
-size_t hsma_blocked_emulated_ws_bytes(int dtype, int nb, int64_t m, int64_t n) {
-  return emu_layout(dtype == HSMA_C128, nb, m, n).total();
+size_t hsma_blocked_emulated_ws_bytes(int dtype, int nb, int panel_cols, int64_t m, int64_t n) {
+  return emu_layout(dtype == HSMA_C128, nb, panel_cols, m, n).total();
 }
 
 extern "C" HSMA_API hsma_status_t hsma_gemm_f64_emulated(int64_t M, int64_t N, int64_t K, const double *A,
@@ -1281,8 +1280,8 @@ __global__ void c128_to_c64_kernel(const cplx *__restrict__ src, int64_t lds, cp
 
 }  // namespace
 
-hsma_status_t hsma_c64_blocked(int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m, int64_t n,
-                               const double *alpha, int unit, cudaStream_t st) {
+hsma_status_t hsma_c64_blocked(int nb, int panel_cols, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
+                               int64_t n, const double *alpha, int unit, cudaStream_t st) {
   auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
   const size_t a_b = al(sizeof(cplx) * (size_t)m * m), b_b = al(sizeof(cplx) * (size_t)m * n);
   void *ws = nullptr;
@@ -1296,7 +1295,7 @@ hsma_status_t hsma_c64_blocked(int nb, const void *A, int64_t lda, void *B, int6
     c64_to_c128_kernel<<<hsma_grid_rc(m, n), 256, 0, st>>>(static_cast<const cplxf *>(B), ldb, B2, m, m, n, 0);
     s = hsma_from_cuda(cudaGetLastError());
   }
-  if (s == HSMA_OK) s = blocked_emulated(true, nb, reinterpret_cast<const double *>(A2), m,
+  if (s == HSMA_OK) s = blocked_emulated(true, nb, panel_cols, reinterpret_cast<const double *>(A2), m,
                                          reinterpret_cast<double *>(B2), m, m, n, alpha, unit, st);
   if (s == HSMA_OK) {
     HsmaTraceScope ts("copy", st);

@@ -14,17 +14,28 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
                             int64_t m, int64_t n, double alpha, int unit, cudaStream_t st, hsma_info_t *info);
 
 // Blocked FP64 / complex FP64 solve with the solve and trailing-update
-// products emulated in FP64 on the BF16 tensor cores (exact integer slices).
-hsma_status_t hsma_blocked_emulated(int dtype, int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
-                                    int64_t n, const double *alpha, int unit, cudaStream_t st);
+// products emulated in FP64 on the BF16 tensor cores (exact integer slices);
+// trailing updates are applied per panel of about panel_cols real columns.
+hsma_status_t hsma_blocked_emulated(int dtype, int nb, int panel_cols, const void *A, int64_t lda, void *B,
+                                    int64_t ldb, int64_t m, int64_t n, const double *alpha, int unit,
+                                    cudaStream_t st);
 
 // Device workspace hsma_blocked_emulated takes from the pool (bytes).
-size_t hsma_blocked_emulated_ws_bytes(int dtype, int nb, int64_t m, int64_t n);
+size_t hsma_blocked_emulated_ws_bytes(int dtype, int nb, int panel_cols, int64_t m, int64_t n);
 
-// N_B of the emulated blocked path when the caller gives none.
+// N_B and panel width of the emulated blocked path when neither the caller
+// nor the table gives them.
 constexpr int kHsmaEmulatedNb = 512;
+constexpr int kEmuPanelColsDefault = 2048;
+
+// Table key of the emulated-products configuration of dtype (R64 or C128).
+constexpr int kEmulatedTableDtype(int dtype) { return dtype + 10; }
 
 // complex64 blocked solve (m > 64): widened to complex128, solved with emulated
 // FP64 products, rounded back into B.
-hsma_status_t hsma_c64_blocked(int nb, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m, int64_t n,
-                               const double *alpha, int unit, cudaStream_t st);
+hsma_status_t hsma_c64_blocked(int nb, int panel_cols, const void *A, int64_t lda, void *B, int64_t ldb, int64_t m,
+                               int64_t n, const double *alpha, int unit, cudaStream_t st);
+
+// The planner's choice for one solve with the given options (hsma_plan with
+// opts; api.cu).
+hsma_status_t hsma_make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts, hsma_plan_t *out);

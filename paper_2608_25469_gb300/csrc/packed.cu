@@ -210,48 +210,77 @@ __global__ void __launch_bounds__(kPkSchedThreads2) packed_place_kernel(
     tcsum[k] = g->csum[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // the group table, in schedule order (every CTA derives the same one)
-    int over = 0;
-    for (int m = 1; m <= 64; ++m) over |= tcsum[m] >= (1ull << kPkColBits) ? 1 : 0;
-    int ng = 0, pos = 0, tile = 0;
-    long long col = 0, stg = 0;
-    for (int k = 0; k < 64 && !over; ++k) {
-      const int m = order.m[k];
-      const int c = tcnt[m];
-      if (c == 0) continue;
-      const unsigned long long cs = tcsum[m];
-      const int gg = pk_groups(m, two);
-      const long long tiles = gg == 1 ? ((long long)cs + 31) >> 5 : ((long long)cs + 15) >> 4;
-      const int se = (int)pk_stage_elems(m, two);
-      if (blockIdx.x == 0) {
-        int32_t *e = grp + ng * kPkGroupWords;
+  // The group table, in schedule order (every CTA derives the same one): the
+  // first 64 threads take one schedule slot each and two warp scans give the
+  // running positions, tiles, columns and staged elements.
+  __shared__ long long wsum[2][4];
+  __shared__ int wng[2];
+  const int t = threadIdx.x;
+  int c = 0, tiles = 0, se = 0, gg = 1, m = 0;
+  unsigned long long cs = 0;
+  if (t < 64) {
+    m = order.m[t];
+    c = tcnt[m];
+    cs = tcsum[m];
+    gg = pk_groups(m, two);
+    tiles = c == 0 ? 0 : (int)(gg == 1 ? ((long long)cs + 31) >> 5 : ((long long)cs + 15) >> 4);
+    se = (int)pk_stage_elems(m, two);
+  }
+  const int over_t = (t < 64 && cs >= (1ull << kPkColBits)) ? 1 : 0;
+  const int over = __syncthreads_or(over_t);
+  long long v[4] = {c, tiles, (long long)cs, (long long)c * se};
+  int nz = c != 0 ? 1 : 0;
+  const int lane = t & 31, w = t >> 5;
+  if (t < 64) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scans
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long y = __shfl_up_sync(0xffffffffu, v[q], o);
+        if (lane >= o) v[q] += y;
+      }
+      const int y = __shfl_up_sync(0xffffffffu, nz, o);
+      if (lane >= o) nz += y;
+    }
+    if (lane == 31) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wsum[w][q] = v[q];
+      wng[w] = nz;
+    }
+  }
+  __syncthreads();
+  if (t < 64) {
+    // exclusive prefixes (warp 1 adds warp 0's totals)
+    long long ex[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ex[q] = v[q] - (q == 0 ? c : q == 1 ? tiles : q == 2 ? (long long)cs : (long long)c * se) +
+                                        (w == 1 ? wsum[0][q] : 0);
+    const int k = nz - (c != 0 ? 1 : 0) + (w == 1 ? wng[0] : 0);  // index among the non-empty groups
+    if (c != 0) {
+      gpos0[m] = (int)ex[0];
+      gcol0[m] = ex[2];
+      if (blockIdx.x == 0 && !over) {
+        int32_t *e = grp + k * kPkGroupWords;
         e[0] = m;
         e[1] = gg;
-        e[2] = tile;
-        e[3] = pos;
-        e[4] = pos + c;
+        e[2] = (int)ex[1];
+        e[3] = (int)ex[0];
+        e[4] = (int)ex[0] + c;
         e[5] = se;
-        *reinterpret_cast<long long *>(e + 6) = col;
-        *reinterpret_cast<long long *>(e + 8) = stg;
+        *reinterpret_cast<long long *>(e + 6) = ex[2];
+        *reinterpret_cast<long long *>(e + 8) = ex[3];
       }
-      gpos0[m] = pos;
-      gcol0[m] = col;
-      ++ng;
-      pos += c;
-      tile += (int)tiles;
-      col += (long long)cs;
-      stg += (long long)c * se;
     }
-    if (blockIdx.x == 0) {  // a column count beyond the cursor's low bits: nothing is solved
+    if (t == 63 && blockIdx.x == 0) {  // totals; a column count beyond the cursor's low bits: nothing is solved
+      const long long pos = v[0] + wsum[0][0], tile = v[1] + wsum[0][1], col = v[2] + wsum[0][2];
       hdr[0] = 0;
-      hdr[1] = over ? 0 : tile;
-      hdr[2] = over ? 0 : ng;
-      hdr[3] = over ? 0 : pos;
+      hdr[1] = over ? 0 : (int)tile;
+      hdr[2] = over ? 0 : nz + wng[0];
+      hdr[3] = over ? 0 : (int)pos;
       colpref[over ? 0 : pos] = over ? 0 : col;
     }
-    s_over = over;
   }
+  if (t == 0) s_over = over;
   __syncthreads();
   if (s_over) return;
   uint32_t err = 0;

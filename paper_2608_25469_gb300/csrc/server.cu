@@ -109,7 +109,14 @@ size_t request_bytes(const hsma_request_t &r, unsigned flags) {
     // triangular solves one after the other (their workspaces never coexist)
     b += sizeof(int32_t) * (size_t)r.m + es * (size_t)r.m * (size_t)r.n;
   }
-  if (use_emulated(r, flags)) return b + hsma_blocked_emulated_ws_bytes(r.dtype, kHsmaEmulatedNb, r.m, r.n);
+  if (use_emulated(r, flags)) {
+    hsma_opts_t o;
+    std::memset(&o, 0, sizeof o);
+    o.fp64_products = 1;
+    hsma_plan_t p;
+    if (hsma_make_plan(r.dtype, r.m, r.n, &o, &p) != HSMA_OK) p.nb = kHsmaEmulatedNb, p.panel_cols = 0;
+    return b + hsma_blocked_emulated_ws_bytes(r.dtype, p.nb, p.panel_cols, r.m, r.n);
+  }
   if (r.m > 64) {
     hsma_plan_t p;
     hsma_plan(r.dtype, r.m, r.n, &p);

@@ -51,13 +51,20 @@ class HsmaError(RuntimeError):
 
 class Plan(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32), ("groups", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("split_k", ctypes.c_int32), ("looking", ctypes.c_int32),
+                ("panel_cols", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+TILE_64x64, TILE_128x16, TILE_128x8 = 1, 2, 3
+SPLITK_AUTO, SPLITK_OFF = 1, 2
+LOOK_RIGHT, LOOK_LEFT = 1, 2
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("ir_max_iter", ctypes.c_int32), ("ir_tol", ctypes.c_double), ("bf16_terms", ctypes.c_int32),
-                ("ir_residual", ctypes.c_int32), ("fp64_products", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ir_residual", ctypes.c_int32), ("fp64_products", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("split_k", ctypes.c_int32), ("looking", ctypes.c_int32), ("panel_cols", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

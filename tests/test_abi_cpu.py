@@ -227,3 +227,44 @@ def test_header_is_plain_c(tmp_path):
         r = subprocess.run([gcc, "-x", lang, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                             "-I", os.path.dirname(hdr), str(src)], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_tuning_table_full_configuration(H, tmp_path):
+    """Section 4.3.2's table carries the whole blocked configuration: N_B, the FP64
+    product tile, split K and the update direction per (dtype, m, n), and N_B and the
+    update-panel width of the emulated-products path (table keys dtype + 10); the planner
+    reports the nearest entry's fields, options override them."""
+    f = tmp_path / "t.txt"
+    f.write_text("# dtype m n nb tile split_k looking panel_cols\n"
+                 "0 1000 1000 128 2 2 2 2048\n"
+                 "0 8000 8000 512 1 1 1 2048\n"
+                 "10 8000 8000 256 0 1 1 3072\n"
+                 "1 1000 100 64 3 1 2 2048\n")
+    try:
+        assert H.hsma_tuning_load(str(f)) == 0
+        p = H.hsma_plan(H.R64, 900, 1100)
+        assert (p.nb, p.tile, p.split_k, p.looking) == (128, H.TILE_128x16, H.SPLITK_OFF, H.LOOK_LEFT)
+        p = H.hsma_plan(H.R64, 9000, 9000)
+        assert (p.nb, p.tile, p.split_k, p.looking) == (512, H.TILE_64x64, H.SPLITK_AUTO, H.LOOK_RIGHT)
+        p = H.hsma_plan(H.C128, 1000, 100)
+        assert (p.nb, p.tile, p.looking) == (64, H.TILE_128x8, H.LOOK_LEFT)
+        # the emulated entries are not used by the plain FP64 plan
+        assert H.hsma_plan(H.R64, 8000, 8000).nb == 512
+        for bad in ("0 100 100 64 4 1 1 2048\n", "0 100 100 64 1 3 1 2048\n", "0 100 100 64 1 1 0 2048\n",
+                    "0 100 100 64 1 1 1 100\n", "0 100 100 64 1 1\n", "12 100 100 64\n"):
+            b = tmp_path / "bad.txt"
+            b.write_text(bad)
+            assert H.hsma_tuning_load(str(b)) == 1, bad
+        assert H.hsma_plan(H.R64, 900, 1100).nb == 128  # unchanged after rejected loads
+    finally:
+        assert H.hsma_tuning_load(None) == 0
+
+
+@pytest.mark.parametrize("field,value", [("tile", 4), ("tile", -1), ("split_k", 3), ("looking", 3),
+                                         ("panel_cols", 100), ("panel_cols", 8256), ("nb", 40)])
+def test_blocked_options_validated(H, field, value):
+    """Out-of-range blocked-path options are argument errors, found before any launch."""
+    o = H.Opts()
+    setattr(o, field, value)
+    s = H.hsma_trsm_llnn_ex(H.R64, 0, 200, 10, 1.0, 16, 200, 16, 200, 0, opts=o, check=False)
+    assert s == 1

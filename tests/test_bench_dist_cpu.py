@@ -56,13 +56,15 @@ def test_reference_arm_rank0_line():
 
 
 def test_bench_emulated_panel_width_matches_library():
-    """bench.py counts the emulated update work with the library's panel width."""
+    """bench.py counts the emulated update work with the panel width the plan reports,
+    and its fallback is the library's default width."""
     import re
     sys.path.insert(0, ROOT)
     import bench
-    src = open(os.path.join(ROOT, "paper_2608_25469_gb300", "csrc", "mixed.cu")).read()
-    lib = int(re.search(r"#define HSMA_EMU_PANEL_COLS (\d+)", src).group(1))
+    src = open(os.path.join(ROOT, "paper_2608_25469_gb300", "csrc", "mixed.h")).read()
+    lib = int(re.search(r"kEmuPanelColsDefault = (\d+);", src).group(1))
     assert bench.EMU_PANEL_COLS == lib
+    assert "info.plan.panel_cols" in open(os.path.join(ROOT, "bench.py")).read()
 
 
 def test_profile_traffic_follows_source_hash_and_scales_by_work(tmp_path, monkeypatch):

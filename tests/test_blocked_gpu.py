@@ -22,12 +22,14 @@ def _dt(code):
     return np.float64 if code == I.R64 else np.complex128
 
 
-def _run(H, code, A, B, alpha, nb, unit=False):
+def _run(H, code, A, B, alpha, nb, unit=False, **cfg):
     import torch
     dA, dB = H.to_device(A), H.to_device(B)
     opts = H.Opts()
     opts.path = H.PATH_BLOCKED
     opts.nb = nb
+    for k, v in cfg.items():
+        setattr(opts, k, v)
     info = H.Info()
     H.hsma_trsm_llnn_ex(code, int(unit), A.shape[1], B.shape[1], alpha, dA.data_ptr(), A.shape[0], dB.data_ptr(),
                         B.shape[0], H.stream_ptr(), opts=opts, info=info)
@@ -89,3 +91,39 @@ def test_planner_default_matches_oracle(H, code):
     X = H.from_device(dB)
     assert oracle.forward_error(X, oracle.solve(A, B, alpha)) <= TOL
     assert oracle.backward_error(A, B, X, alpha) <= 1e-14
+
+
+CFG_CASES = [(65, 7, 32), (300, 200, 128), (700, 50, 512), (1000, 9, 64), (513, 130, 256)]
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+@pytest.mark.parametrize("looking", [1, 2], ids=["right", "left"])
+@pytest.mark.parametrize("tile", [1, 2, 3], ids=["64x64", "128x16", "128x8"])
+@pytest.mark.parametrize("split_k", [1, 2], ids=["split", "nosplit"])
+@pytest.mark.parametrize("m,n,nb", CFG_CASES)
+def test_blocked_configurations_parity(H, code, looking, tile, split_k, m, n, nb):
+    """Every configuration the autotuner may choose (update direction, product tile, split
+    K) at ragged sizes, with NaN in the never-read upper triangle and padding rows."""
+    import torch
+    alpha = 1.25 if code == I.R64 else 0.5 - 1.5j
+    seed = m + 3 * n + nb
+    A0, B0 = I.gen_A(seed, m, code), I.gen_B(seed, m, n, code)
+    A = I.embed(A0, m + 2, fill=np.nan)
+    A[:m][np.triu_indices(m, 1)] = np.nan
+    B = I.embed(B0, m + 2, fill=np.nan)
+    X = _run(H, code, A, B, alpha, nb, looking=looking, tile=tile, split_k=split_k)
+    assert np.all(np.isnan(X[m:]))
+    assert oracle.forward_error(X[:m], oracle.solve(A0, B0, alpha)) <= TOL
+    assert H.hsma_device_status() == 0
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+def test_left_looking_unit_diagonal(H, code):
+    m, n, nb = 450, 33, 64
+    A0, B0 = I.gen_A(6, m, code), I.gen_B(6, m, n, code)
+    A = np.array(A0, order="F")
+    np.fill_diagonal(A, np.nan)
+    X = _run(H, code, A, B0, -2.0, nb, unit=True, looking=2)
+    A1 = np.array(A0, order="F")
+    np.fill_diagonal(A1, 1.0)
+    assert oracle.forward_error(X, oracle.solve(A1, B0, -2.0)) <= TOL

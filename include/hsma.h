@@ -213,10 +213,14 @@ HSMA_API hsma_status_t hsma_trsm(int dtype, int side, int uplo, int trans, int d
  * batch  number of instances (>= 0).
  * d_m, d_n, d_lda, d_ldb: DEVICE arrays of `batch` int32 sizes.
  * d_A, d_B: DEVICE arrays of `batch` device pointers.
- * max_m  host upper bound on every m_i: 1..64, or 0 for "unknown" (taken as
- *        64); it sizes the workspace, and an instance with m_i > max_m is
- *        skipped and flagged HSMA_DEVERR_BAD_SIZE; a larger value returns
- *        HSMA_ERR_UNSUPPORTED (use hsma_trsm_llnn per instance for m > 64).
+ * max_m  host upper bound on every m_i, or 0 for "unknown" (taken as 64); up
+ *        to 64 it sizes the workspace, and an instance with m_i > max_m is
+ *        skipped and flagged HSMA_DEVERR_BAD_SIZE.  max_m > 64 admits
+ *        instances of any size: the call then reads the batch's sizes and
+ *        pointers back to the host (it waits for the stream once, so it is
+ *        not capturable), runs the instances with m_i <= 64 as the batch and
+ *        solves each larger one on the same stream through the single-solve
+ *        path (hsma_trsm; blocked path, planner's configuration).
  * max_n  host upper bound on every n_i, or 0 if unknown (only a hint).
  * d_status: optional DEVICE uint32 word; the kernel ORs HSMA_DEVERR_* bits into
  *        it for instances it skips as invalid.  May be NULL.
@@ -272,7 +276,10 @@ HSMA_API hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int tra
  *        instance with a pivot outside [k, m_i] (that instance's B_i is left
  *        untouched).
  * Results equal two hsma_trsm_vbatched calls (unit lower, then upper) on the
- * interchanged B, bit for bit.  Errors as hsma_trsm_llnn_vbatched.
+ * interchanged B, bit for bit.  Errors as hsma_trsm_llnn_vbatched; with
+ * max_m > 64 the instances above 64 are solved one by one through hsma_getrs
+ * (hsma_potrs for the Cholesky batch below) after one read-back of the sizes,
+ * pointers and pivot pointers.
  */
 HSMA_API hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32_t *d_m, const int32_t *d_n,
                                            const void *alpha, const void *const *d_LU, const int32_t *d_lda,

@@ -289,6 +289,77 @@ hsma_status_t hsma_trsm_llnn_vbatched(int dtype, int diag, int32_t batch, const 
                             d_B, d_ldb, max_m, max_n, d_status, stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+__global__ void or_status_kernel(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
+
+// A batch whose host bound max_m exceeds 64, read back to the host: the sizes,
+// pointers and (factor solves) pivot pointers of every instance.  The stream
+// is waited for once.
+struct HostBatch {
+  std::vector<int32_t> m, n, lda, ldb;
+  std::vector<const void *> A;
+  std::vector<void *> B;
+  std::vector<const int32_t *> piv;
+};
+
+hsma_status_t read_batch(int32_t batch, const int32_t *d_m, const int32_t *d_n, const int32_t *d_lda,
+                         const int32_t *d_ldb, const void *const *d_A, void *const *d_B,
+                         const int32_t *const *d_ipiv, cudaStream_t st, HostBatch &h) {
+  const size_t b = (size_t)batch;
+  h.m.resize(b);
+  h.n.resize(b);
+  h.lda.resize(b);
+  h.ldb.resize(b);
+  h.A.resize(b);
+  h.B.resize(b);
+  h.piv.assign(b, nullptr);
+  HSMA_CUDA_TRY(cudaMemcpyAsync(h.m.data(), d_m, 4 * b, cudaMemcpyDeviceToHost, st));
+  HSMA_CUDA_TRY(cudaMemcpyAsync(h.n.data(), d_n, 4 * b, cudaMemcpyDeviceToHost, st));
+  HSMA_CUDA_TRY(cudaMemcpyAsync(h.lda.data(), d_lda, 4 * b, cudaMemcpyDeviceToHost, st));
+  HSMA_CUDA_TRY(cudaMemcpyAsync(h.ldb.data(), d_ldb, 4 * b, cudaMemcpyDeviceToHost, st));
+  HSMA_CUDA_TRY(cudaMemcpyAsync(h.A.data(), d_A, sizeof(void *) * b, cudaMemcpyDeviceToHost, st));
+  HSMA_CUDA_TRY(cudaMemcpyAsync(h.B.data(), d_B, sizeof(void *) * b, cudaMemcpyDeviceToHost, st));
+  if (d_ipiv != nullptr)
+    HSMA_CUDA_TRY(cudaMemcpyAsync(h.piv.data(), d_ipiv, sizeof(void *) * b, cudaMemcpyDeviceToHost, st));
+  HSMA_CUDA_TRY(cudaStreamSynchronize(st));
+  return HSMA_OK;
+}
+
+// Every instance with m > 64 through `solve1(b)` on the stream; invalid ones
+// (n < 0, ld < m, null pointer) are skipped and their HSMA_DEVERR_* bits ORed
+// into d_status.
+template <class F>
+hsma_status_t solve_large(const HostBatch &h, uint32_t *d_status, cudaStream_t st, F solve1) {
+  uint32_t bad = 0;
+  hsma_status_t s = HSMA_OK;
+  for (size_t b = 0; b < h.m.size() && s == HSMA_OK; ++b) {
+    const int32_t m = h.m[b];
+    if (m <= 64) continue;
+    if (h.n[b] < 0 || h.lda[b] < m || h.ldb[b] < m) {
+      bad |= HSMA_DEVERR_BAD_SIZE;
+      continue;
+    }
+    if (h.n[b] == 0) continue;
+    if (h.A[b] == nullptr || h.B[b] == nullptr) {
+      bad |= HSMA_DEVERR_NULL_PTR;
+      continue;
+    }
+    s = solve1(b);
+  }
+  if (s == HSMA_OK && bad != 0 && d_status != nullptr) {
+    or_status_kernel<<<1, 1, 0, st>>>(d_status, bad);
+    s = hsma_from_cuda(cudaGetLastError());
+  }
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
 hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int diag, int32_t batch,
                                  const int32_t *d_m, const int32_t *d_n, const void *alpha, const void *const *d_A,
                                  const int32_t *d_lda, void *const *d_B, const int32_t *d_ldb, int32_t max_m,
@@ -301,13 +372,18 @@ hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int d
     return HSMA_ERR_INVALID_ARG;
   if (side == HSMA_RIGHT) return HSMA_ERR_UNSUPPORTED;
   if (!valid_diag(diag) || batch < 0 || max_m < 0 || max_n < 0) return HSMA_ERR_INVALID_ARG;
-  if (max_m > 64) return HSMA_ERR_UNSUPPORTED;
   if (batch > (1 << 24) - 1) return HSMA_ERR_UNSUPPORTED;
   if (batch == 0) return HSMA_OK;
   if (alpha == nullptr || d_m == nullptr || d_n == nullptr || d_A == nullptr || d_lda == nullptr ||
       d_B == nullptr || d_ldb == nullptr)
     return HSMA_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool large = max_m > 64;
+  HostBatch hb;
+  if (large) {
+    hsma_status_t r = read_batch(batch, d_m, d_n, d_lda, d_ldb, d_A, d_B, nullptr, st, hb);
+    if (r != HSMA_OK) return r;
+  }
   void *scratch = nullptr;
   // the paper's case in complex128 runs the column-packed batch (the FP64
   // pipe binds, so full warp tiles pay); the other dtypes and variants the
@@ -323,8 +399,14 @@ hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int d
                                    d_B, d_ldb, diag == HSMA_UNIT, d_status, scratch, st);
   else
     s = hsma_small_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda, d_B, d_ldb,
-                            diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st, uplo, trans);
+                            diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st, uplo, trans,
+                            large ? 1 : 0);
   hsma_status_t f = hsma_ws_free(scratch, st);
+  if (s == HSMA_OK && f == HSMA_OK && large)
+    s = solve_large(hb, d_status, st, [&](size_t b) {
+      return hsma_trsm(dtype, HSMA_LEFT, uplo, trans, diag, hb.m[b], hb.n[b], alpha, hb.A[b], hb.lda[b], hb.B[b],
+                       hb.ldb[b], stream, nullptr, nullptr);
+    });
   return s != HSMA_OK ? s : f;
 }
 
@@ -337,19 +419,31 @@ static hsma_status_t factor_solve_vbatched(int dtype, int32_t batch, const int32
     return valid_dtype(dtype) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
   }
   if (batch < 0 || max_m < 0 || max_n < 0) return HSMA_ERR_INVALID_ARG;
-  if (max_m > 64) return HSMA_ERR_UNSUPPORTED;
   if (batch > (1 << 24) - 1) return HSMA_ERR_UNSUPPORTED;
   if (batch == 0) return HSMA_OK;
   if (alpha == nullptr || d_m == nullptr || d_n == nullptr || d_LU == nullptr || d_lda == nullptr ||
       d_B == nullptr || d_ldb == nullptr)
     return HSMA_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool large = max_m > 64;
+  HostBatch hb;
+  if (large) {
+    hsma_status_t r = read_batch(batch, d_m, d_n, d_lda, d_ldb, d_LU, d_B, chol ? nullptr : d_ipiv, st, hb);
+    if (r != HSMA_OK) return r;
+  }
   void *scratch = nullptr;
   hsma_status_t s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
   if (s != HSMA_OK) return s;
   s = hsma_small_getrs_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_LU, d_lda, d_ipiv,
-                                d_B, d_ldb, d_status, static_cast<int32_t *>(scratch), st, chol);
+                                d_B, d_ldb, d_status, static_cast<int32_t *>(scratch), st, chol, large ? 1 : 0);
   hsma_status_t f = hsma_ws_free(scratch, st);
+  if (s == HSMA_OK && f == HSMA_OK && large)
+    s = solve_large(hb, d_status, st, [&](size_t b) {
+      return chol ? hsma_potrs(dtype, hb.m[b], hb.n[b], alpha, hb.A[b], hb.lda[b], hb.B[b], hb.ldb[b], stream,
+                               nullptr)
+                  : hsma_getrs(dtype, hb.m[b], hb.n[b], alpha, hb.A[b], hb.lda[b], hb.piv[b], hb.B[b], hb.ldb[b],
+                               stream, nullptr);
+    });
   return s != HSMA_OK ? s : f;
 }
 

@@ -127,7 +127,8 @@ PkOrder pk_order(bool two_lanes, bool cplx_) {
 // thread).  Instances with m = 0 or n = 0 are valid and need no work; invalid
 // ones set a status bit and are skipped (as the per-instance kernel does).
 // An instance above mmax (the caller's bound, which sized the staging
-// workspace) counts as invalid.
+// workspace) counts as invalid, unless skip_large is set: then instances with
+// m > 64 are left to the caller (solved elsewhere) without a status bit.
 //   count: per m, the instances and their columns (CTA totals in shared
 //          memory, then one global atomic per m and CTA);
 //   place: every CTA derives the group table from the totals (CTA 0 writes
@@ -142,12 +143,13 @@ constexpr int kPkColBits = 40;
 __device__ __forceinline__ bool pk_valid(int b, const int32_t *__restrict__ dm, const int32_t *__restrict__ dn,
                                          const int32_t *__restrict__ dlda, const int32_t *__restrict__ dldb,
                                          const void *const *__restrict__ dA, void *const *__restrict__ dB, int mmax,
-                                         int &m, int &n, uint32_t &err) {
+                                         int skip_large, int &m, int &n, uint32_t &err) {
   m = dm[b];
   n = dn[b];
   const int lda = dlda[b], ldb = dldb[b];
   const bool nul = dA[b] == nullptr || dB[b] == nullptr;
   const int lo = m > 1 ? m : 1;
+  if (skip_large && m > 64) return false;
   if (m < 0 || n < 0 || m > mmax || lda < lo || ldb < lo) {
     err |= HSMA_DEVERR_BAD_SIZE;
     return false;
@@ -164,7 +166,7 @@ template <class T>
 __global__ void __launch_bounds__(kPkSchedThreads2) packed_count_kernel(
     int batch, const int32_t *__restrict__ dm, const int32_t *__restrict__ dn, const int32_t *__restrict__ dlda,
     const int32_t *__restrict__ dldb, const void *const *__restrict__ dA, void *const *__restrict__ dB,
-    unsigned char *scratch, PkLayout L, int mmax, uint32_t *status) {
+    unsigned char *scratch, PkLayout L, int mmax, int skip_large, uint32_t *status) {
   __shared__ int cnt[65];
   __shared__ unsigned long long csum[65];
   PkCounts *g = reinterpret_cast<PkCounts *>(scratch + L.counts);
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kPkSchedThreads2) packed_count_kernel(
   uint32_t err = 0;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x) {
     int m, n;
-    if (!pk_valid(b, dm, dn, dlda, dldb, dA, dB, mmax, m, n, err)) continue;
+    if (!pk_valid(b, dm, dn, dlda, dldb, dA, dB, mmax, skip_large, m, n, err)) continue;
     atomicAdd(&cnt[m], 1);
     atomicAdd(&csum[m], (unsigned long long)n);
   }
@@ -193,7 +195,7 @@ template <class T>
 __global__ void __launch_bounds__(kPkSchedThreads2) packed_place_kernel(
     int batch, const int32_t *__restrict__ dm, const int32_t *__restrict__ dn, const int32_t *__restrict__ dlda,
     const int32_t *__restrict__ dldb, const void *const *__restrict__ dA, void *const *__restrict__ dB,
-    unsigned char *scratch, PkLayout L, int mmax, PkOrder order) {
+    unsigned char *scratch, PkLayout L, int mmax, int skip_large, PkOrder order) {
   constexpr bool two = pk_two_lanes<T>();
   __shared__ int gpos0[65];
   __shared__ long long gcol0[65];
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kPkSchedThreads2) packed_place_kernel(
     __syncthreads();
     const int b = b0 + threadIdx.x;
     int m = 0, n = 0;
-    const bool ok = b < batch && pk_valid(b, dm, dn, dlda, dldb, dA, dB, mmax, m, n, err);
+    const bool ok = b < batch && pk_valid(b, dm, dn, dlda, dldb, dA, dB, mmax, skip_large, m, n, err);
     unsigned long long mine = 0;
     if (ok) mine = atomicAdd(&ccur[m], (1ull << kPkColBits) + (unsigned long long)n);
     __syncthreads();
@@ -551,15 +553,16 @@ hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int
   {
     static const PkOrder order = pk_order(pk_two_lanes<T>(), Elem<T>::kComplex);
     const int mmax = (max_m <= 0 || max_m > 64) ? 64 : max_m;
+    const int skip_large = max_m > 64 ? 1 : 0;
     const int nsm = sm_count(dev);
     int blocks = (batch + kPkSchedThreads2 - 1) / kPkSchedThreads2;
     if (blocks > 4 * nsm) blocks = 4 * nsm;
     HsmaTraceScope ts("vbatched_schedule", st);
     HSMA_CUDA_TRY(cudaMemsetAsync(scr + L.counts, 0, sizeof(PkCounts), st));
     packed_count_kernel<T><<<blocks, kPkSchedThreads2, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scr, L, mmax,
-                                                                status);
+                                                                skip_large, status);
     packed_place_kernel<T><<<blocks, kPkSchedThreads2, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scr, L, mmax,
-                                                                order);
+                                                                skip_large, order);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   if (!azero) {

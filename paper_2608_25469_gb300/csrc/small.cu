@@ -345,7 +345,8 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
                                                                  const int32_t *__restrict__ dldb,
                                                                  const void *const *__restrict__ dA,
                                                                  void *const *__restrict__ dB, int32_t *scratch,
-                                                                 uint32_t *status, const int32_t *__restrict__ tab) {
+                                                                 uint32_t *status, const int32_t *__restrict__ tab,
+                                                                 int skip_large) {
   __shared__ int hist[kBuckets];
   __shared__ int offs[kBuckets];
   const bool cplx_ = Elem<T>::kComplex;
@@ -355,6 +356,7 @@ __global__ void __launch_bounds__(1024) vbatched_schedule_kernel(int batch, cons
   for (int b = threadIdx.x; b < batch; b += blockDim.x) {
     const int m = dm[b], n = dn[b];
     const int lo = m > 1 ? m : 1;
+    if (skip_large && m > 64) continue;  // solved by the caller on the blocked path
     if (m < 0 || n < 0 || m > 64 || dlda[b] < lo || dldb[b] < lo) {
       err |= HSMA_DEVERR_BAD_SIZE;
       continue;
@@ -670,7 +672,7 @@ template <class T>
 static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32_t *dn, const double *alpha,
                                    const void *const *dA, const int32_t *dlda, void *const *dB,
                                    const int32_t *dldb, int unit, uint32_t *status, int32_t *scratch,
-                                   cudaStream_t st, SmallMap mp) {
+                                   cudaStream_t st, SmallMap mp, int skip_large) {
   int dev = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   static DeviceFlags attr_done;
@@ -683,7 +685,7 @@ static hsma_status_t vbatched_impl(int32_t batch, const int32_t *dm, const int32
   {
     HsmaTraceScope ts("vbatched_schedule", st);
     vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scratch, status,
-                                                    sched_table(st));
+                                                    sched_table(st), skip_large);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   // the identity map (the paper's case) runs a kernel without the remapping arithmetic
@@ -708,13 +710,17 @@ size_t hsma_vbatched_scratch_bytes(int32_t batch) { return sizeof(int32_t) * (2 
 hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
                                   void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
-                                  int32_t *scratch, cudaStream_t st, int uplo, int trans) {
+                                  int32_t *scratch, cudaStream_t st, int uplo, int trans, int skip_large) {
   const SmallMap mp = make_map(uplo, trans);
   switch (dtype) {
-    case HSMA_C128: return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
-    case HSMA_R32: return vbatched_impl<float>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
-    case HSMA_C64: return vbatched_impl<cplxf>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
-    default: return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp);
+    case HSMA_C128: return vbatched_impl<cplx>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp,
+                                    skip_large);
+    case HSMA_R32: return vbatched_impl<float>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp,
+                                    skip_large);
+    case HSMA_C64: return vbatched_impl<cplxf>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp,
+                                    skip_large);
+    default: return vbatched_impl<double>(batch, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st, mp,
+                                    skip_large);
   }
 }
 
@@ -722,7 +728,7 @@ template <class T>
 static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t *dn, const double *alpha,
                                 const void *const *dLU, const int32_t *dlda, const int32_t *const *dipiv,
                                 void *const *dB, const int32_t *dldb, uint32_t *status, int32_t *scratch,
-                                cudaStream_t st, int chol) {
+                                cudaStream_t st, int chol, int skip_large) {
   int dev = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   static DeviceFlags attr_done;
@@ -735,7 +741,7 @@ static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t 
   {
     HsmaTraceScope ts("vbatched_schedule", st);
     vbatched_schedule_kernel<T><<<1, 1024, 0, st>>>(batch, dm, dn, dlda, dldb, dLU, dB, scratch, status,
-                                                    sched_table(st));
+                                                    sched_table(st), skip_large);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   int grid = lu_grid<T>(dev);
@@ -753,17 +759,22 @@ static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t 
 hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                         const double *alpha, const void *const *dLU, const int32_t *dlda,
                                         const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,
-                                        uint32_t *status, int32_t *scratch, cudaStream_t st, int chol) {
+                                        uint32_t *status, int32_t *scratch, cudaStream_t st, int chol,
+                                        int skip_large) {
   if (chol) dipiv = nullptr;
   switch (dtype) {
     case HSMA_C128:
-      return getrs_impl<cplx>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
+      return getrs_impl<cplx>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol,
+                                 skip_large);
     case HSMA_R32:
-      return getrs_impl<float>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
+      return getrs_impl<float>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol,
+                                 skip_large);
     case HSMA_C64:
-      return getrs_impl<cplxf>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
+      return getrs_impl<cplxf>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol,
+                                 skip_large);
     default:
-      return getrs_impl<double>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol);
+      return getrs_impl<double>(batch, dm, dn, alpha, dLU, dlda, dipiv, dB, dldb, status, scratch, st, chol,
+                                 skip_large);
   }
 }
 

@@ -17,12 +17,14 @@ hsma_status_t hsma_small_single(int dtype, int g, const void *A, int64_t lda, vo
 size_t hsma_vbatched_scratch_bytes(int32_t batch);
 
 // Varlen batch (schedule pre-pass + persistent solve).  `scratch` holds
-// hsma_vbatched_scratch_bytes(batch) bytes of device memory.
+// hsma_vbatched_scratch_bytes(batch) bytes of device memory.  skip_large:
+// instances with m > 64 are skipped without a status bit (the caller solves
+// them on the blocked path); otherwise they are flagged HSMA_DEVERR_BAD_SIZE.
 hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                   const double *alpha, const void *const *dA, const int32_t *dlda,
                                   void *const *dB, const int32_t *dldb, int unit, uint32_t *status,
                                   int32_t *scratch, cudaStream_t st, int uplo = HSMA_LOWER,
-                                  int trans = HSMA_NO_TRANS);
+                                  int trans = HSMA_NO_TRANS, int skip_large = 0);
 
 // Varlen batch of factor solves in one launch (schedule pre-pass + fused
 // kernel): chol = 0, X = U^{-1} L^{-1} P^T (alpha B) from packed LU factors
@@ -31,13 +33,15 @@ hsma_status_t hsma_small_vbatched(int dtype, int32_t batch, const int32_t *dm, c
 hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                         const double *alpha, const void *const *dLU, const int32_t *dlda,
                                         const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,
-                                        uint32_t *status, int32_t *scratch, cudaStream_t st, int chol = 0);
+                                        uint32_t *status, int32_t *scratch, cudaStream_t st, int chol = 0,
+                                        int skip_large = 0);
 
 // Column-packed varlen batch for the left / lower / no-transpose solve in
 // HSMA_C128 (packed.cu): schedule, prep and solve passes;
 // `scratch` holds hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m)
-// bytes (max_m: a bound on every m_i, 0 = 64).  Results equal
-// hsma_small_vbatched's bit for bit.
+// bytes (max_m: a bound on every m_i, 0 = 64; above 64, instances with
+// m > 64 are skipped without a status bit, as skip_large below).  Results
+// equal hsma_small_vbatched's bit for bit.
 size_t hsma_vbatched_packed_scratch_bytes(int dtype, int32_t batch, int32_t max_m);
 // dtypes whose varlen batch runs the column-packed kernels (measured faster
 // than the per-instance kernel: complex128; real FP64 keeps the per-instance

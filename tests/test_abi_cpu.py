@@ -71,7 +71,8 @@ def test_vbatched_argument_checks(H):
     assert H.hsma_trsm_llnn_vbatched(2, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 2   # dtype unsupported
     assert H.hsma_trsm_llnn_vbatched(7, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 1   # dtype unknown
     assert H.hsma_trsm_llnn_vbatched(0, 0, -1, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 1  # batch < 0
-    assert H.hsma_trsm_llnn_vbatched(0, 0, 4, 1, 1, 1.0, 1, 1, 1, 1, max_m=65, check=False) == 2
+    # max_m > 64 admits large instances (read back from the device): argument errors still come first
+    assert H.hsma_trsm_llnn_vbatched(0, 0, 4, 0, 1, 1.0, 1, 1, 1, 1, max_m=65, check=False) == 1
     assert H.hsma_trsm_llnn_vbatched(0, 0, 4, 0, 1, 1.0, 1, 1, 1, 1, check=False) == 1   # NULL d_m
 
 
@@ -185,7 +186,7 @@ def test_getrs_argument_checks(H):
     f = H.hsma_getrs_vbatched
     assert f(2, 4, 1, 1, 1.0, 1, 1, 0, 1, 1, check=False) == 2              # dtype without a small path
     assert f(9, 4, 1, 1, 1.0, 1, 1, 0, 1, 1, check=False) == 1              # unknown dtype
-    assert f(0, 4, 1, 1, 1.0, 1, 1, 0, 1, 1, max_m=65, check=False) == 2    # m beyond the small path
+    assert f(0, 4, 1, 1, 1.0, 0, 1, 0, 1, 1, max_m=65, check=False) == 1    # NULL LU, large instances allowed
     assert f(0, -1, 1, 1, 1.0, 1, 1, 0, 1, 1, check=False) == 1             # negative batch
     assert f(0, 4, 1, 1, 1.0, 0, 1, 0, 1, 1, check=False) == 1              # NULL LU
     assert f(0, 0, 0, 0, 1.0, 0, 0, 0, 0, 0, check=False) == 0              # empty batch
@@ -194,7 +195,7 @@ def test_getrs_argument_checks(H):
 def test_potrs_argument_checks(H):
     f = H.hsma_potrs_vbatched
     assert f(3, 4, 1, 1, 1.0, 1, 1, 1, 1, check=False) == 2              # dtype without a small path
-    assert f(0, 4, 1, 1, 1.0, 1, 1, 1, 1, max_m=65, check=False) == 2    # m beyond the small path
+    assert f(0, 4, 1, 1, 1.0, 1, 1, 0, 1, max_m=65, check=False) == 1    # NULL B, large instances allowed
     assert f(1, 4, 1, 1, 1.0, 1, 1, 0, 1, check=False) == 1              # NULL B
     assert f(1, 0, 0, 0, 1.0, 0, 0, 0, 0, check=False) == 0              # empty batch
 

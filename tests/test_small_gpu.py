@@ -392,3 +392,71 @@ def test_packed_batch_instance_above_max_m_is_skipped(H):
     assert np.array_equal(X[1], Bs[1])
     for b in (0, 2):
         assert oracle.forward_error(X[b], oracle.solve(As[b], Bs[b], alpha)) <= TOL
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+def test_batch_with_instances_above_64(H, code):
+    """max_m > 64: instances of any size in one call.  The small ones run as the batch
+    (bit-equal to the batch without the large ones), each large one through the
+    single-solve path (bit-equal to hsma_trsm_llnn alone); all within the oracle's
+    tolerance.  A large instance with ldb < m is skipped and flagged."""
+    import torch
+    rng = np.random.default_rng(50)
+    sizes = [(int(m), int(n)) for m, n in rng.integers(1, 65, (120, 2))]
+    for k, mm in zip((3, 40, 77, 100), (65, 130, 300, 700)):
+        sizes[k] = (mm, int(rng.integers(1, 90)))
+    alpha = 1.5 if code == I.R64 else 1.5 - 0.5j
+    As, Bs = _mix(code, sizes, seed=51)
+    got = _run_batch(H, code, As, Bs, alpha, max_m=1000)
+    assert got.status() == 0
+    G = got.results()
+    small = [b for b, (m, _) in enumerate(sizes) if m <= 64]
+    only = _run_batch(H, code, [As[b] for b in small], [Bs[b] for b in small], alpha).results()
+    for k, b in enumerate(small):
+        assert np.array_equal(G[b], only[k]), b
+    for b, (m, n) in enumerate(sizes):
+        if m > 64:
+            dA, dB = H.to_device(As[b]), H.to_device(Bs[b])
+            H.hsma_trsm_llnn(code, 0, m, n, alpha, dA.data_ptr(), m, dB.data_ptr(), m, H.stream_ptr())
+            torch.cuda.synchronize()
+            assert np.array_equal(G[b], H.from_device(dB)), b
+        assert oracle.forward_error(G[b], oracle.solve(As[b], Bs[b], alpha)) <= TOL, b
+    # a large instance whose ldb is too small: skipped, flagged, B untouched
+    bt = U.Batch(As[:5], Bs[:5])
+    bt.d_ldb[3] = 10
+    H.hsma_trsm_llnn_vbatched(code, 0, 5, *bt.args()[:2], alpha, *bt.args()[2:], max_m=200, max_n=0,
+                              d_status=bt.d_status.data_ptr(), stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    assert bt.status() & H.DEVERR_BAD_SIZE
+    assert np.array_equal(bt.results()[3], Bs[3])
+
+
+def test_factor_batches_with_instances_above_64(H):
+    """LU- and Cholesky-factor batches with max_m > 64: large instances through hsma_getrs /
+    hsma_potrs, against the oracle's getrs / potrs."""
+    import torch
+    code = I.C128
+    rng = np.random.default_rng(52)
+    sizes = [(int(m), int(n)) for m, n in rng.integers(4, 65, (40, 2))] + [(90, 7), (257, 33)]
+    Fs = [I.gen_LU(53, m, code, inst=b) for b, (m, _) in enumerate(sizes)]
+    Bs = [I.gen_B(53, m, n, code, inst=b) for b, (m, n) in enumerate(sizes)]
+    pivs = [np.array([int(rng.integers(k, m)) + 1 for k in range(m)], dtype=np.int32) for m, _ in sizes]
+    dpiv = [torch.from_numpy(p).cuda() for p in pivs]
+    pp = torch.tensor([p.data_ptr() for p in dpiv], dtype=torch.int64, device="cuda")
+    bt = U.Batch(Fs, Bs)
+    H.hsma_getrs_vbatched(code, bt.batch, bt.d_m.data_ptr(), bt.d_n.data_ptr(), 0.5 + 0.5j, bt.d_ptrA.data_ptr(),
+                          bt.d_lda.data_ptr(), pp.data_ptr(), bt.d_ptrB.data_ptr(), bt.d_ldb.data_ptr(), 300, 0,
+                          bt.d_status.data_ptr(), H.stream_ptr())
+    torch.cuda.synchronize()
+    assert bt.status() == 0
+    for b, X in enumerate(bt.results()):
+        assert oracle.forward_error(X, oracle.getrs(Fs[b], pivs[b], Bs[b], 0.5 + 0.5j)) <= TOL, b
+    Ls = [I.gen_A(54, m, code, inst=b) for b, (m, _) in enumerate(sizes)]
+    bt = U.Batch(Ls, Bs)
+    H.hsma_potrs_vbatched(code, bt.batch, bt.d_m.data_ptr(), bt.d_n.data_ptr(), 2.0, bt.d_ptrA.data_ptr(),
+                          bt.d_lda.data_ptr(), bt.d_ptrB.data_ptr(), bt.d_ldb.data_ptr(), 300, 0,
+                          bt.d_status.data_ptr(), H.stream_ptr())
+    torch.cuda.synchronize()
+    assert bt.status() == 0
+    for b, X in enumerate(bt.results()):
+        assert oracle.forward_error(X, oracle.potrs(Ls[b], Bs[b], 2.0)) <= TOL, b

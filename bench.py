@@ -342,7 +342,9 @@ def run_batched(args, dist, device, c64=False):
     kernel_ms = solve_ms / max(solve_cnt, 1)
     achieved = flops / (kernel_ms * 1e-3) / 1e9
     name = "c64" if c64 else "c128"
-    traffic = profile_traffic(f"vbatched_solve_{name}_8192.txt", SMALL_SOURCES)
+    # complex128 runs the column-packed batch; complex64 the per-instance kernel
+    traffic = (profile_traffic("vbatched_solve_c64_8192.txt", SMALL_SOURCES) if c64 else
+               profile_traffic("packed_solve_c128_8192.txt", PACKED_SOURCES, work=flops))
     if c64:
         # FP32 work is cheap here: the algorithmic bytes bind (HBM roofline, measured copy bandwidth)
         peaks, src = load_peaks()
@@ -354,7 +356,7 @@ def run_batched(args, dist, device, c64=False):
     else:
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp64_peak_gflops(), 1),
                 "unit": "GFLOP/s", "frac": round(achieved / fp64_peak_gflops(), 4), "traffic": traffic,
-                "kernel": "vbatched_solve_kernel<cplx>", "kernel_ms": round(kernel_ms, 5),
+                "kernel": "packed_solve_kernel<cplx>", "kernel_ms": round(kernel_ms, 5),
                 "peak_source": FP64_PEAK_SOURCE,
                 "hbm_frac": round(abytes / (kernel_ms * 1e-3) / 1e9 / load_peaks()[0]["hbm_gbs"], 4)}
     out = {
@@ -873,7 +875,8 @@ def run_single64(args, dist, device):
         "replicated_8192": {"ms": round(rep_ms, 4), "gflops": round(R * flops / (rep_ms * 1e-3) / 1e9, 2),
                             "how": "the same 64 x 64 problem 8192 times in one varlen batched call"},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp64_peak_gflops(), 1),
-                     "unit": "GFLOP/s", "frac": round(achieved / fp64_peak_gflops(), 5), "traffic": None,
+                     "unit": "GFLOP/s", "frac": round(achieved / fp64_peak_gflops(), 5),
+                     "traffic": profile_traffic("small_single_fp64_64.txt", SMALL_SOURCES),
                      "kernel": "small_single_kernel<double>",
                      "peak_source": FP64_PEAK_SOURCE,
                      "note": "one 64 x 64 solve cannot fill the GPU: its bound is the 63-step dependent chain "
@@ -1179,7 +1182,7 @@ def run_mixed(args, dist, device, mode):
         pk = peaks["bf16_tflops"] * 1e3
         roof = {"bound": "tensor", "achieved": round(ach, 1), "peak": round(pk, 1), "unit": "GFLOP/s",
                 "frac": round(ach / pk, 4),
-                "traffic": profile_traffic("tc_f32_update_r32_8192x4096.txt", EMU_SOURCES),
+                "traffic": profile_traffic("tc_f32_update_r32_8192x4096.txt", EMU_SOURCES, work=upd / max(ups, 1)),
                 "kernel": "tc_gemm_kernel<TC_F32> (update_bf16: split-BF16 trailing update, FP32 accumulate)",
                 "kernel_ms": round(kernel_ms, 5), "peak_source": f"bf16 tensor (measured burst), {src}"}
     else:
@@ -1191,7 +1194,8 @@ def run_mixed(args, dist, device, mode):
         pk = peaks["bf16_tflops_sustained"] * 1e3
         roof = {"bound": "tensor", "achieved": round(ach, 1), "peak": round(pk, 1), "unit": "GFLOP/s",
                 "frac": round(ach / pk, 4),
-                "traffic": profile_traffic("residual_emulated_ir_8192x4096.txt", EMU_SOURCES),
+                "traffic": profile_traffic("residual_emulated_ir_8192x4096.txt", EMU_SOURCES,
+                                           work=res_fl * evals / max(rcnt, 1)),
                 "kernel": "tc_gemm_kernel<TC_OZ> (residual: 55 BF16 slice pairs per K chunk of 1024)",
                 "kernel_ms": round(kernel_ms, 5), "residual_evaluations": evals,
                 "peak_source": f"bf16 tensor (measured sustained), {src}"}

@@ -136,11 +136,13 @@ __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict
 }
 
 // One warp solves one column tile (up to 32/G columns starting at Bt).
-template <class T, int G, int MMAX, bool MAP>
-__device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, int64_t ldb, int m, int ncols,
+// FULL: m == MMAX, known at compile time (the bound checks fold away).
+template <class T, int G, int MMAX, bool MAP, bool FULL = false>
+__device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, int64_t ldb, int m_, int ncols,
                                            int rev) {
   using E = Elem<T>;
   constexpr int R = MMAX / G;
+  const int m = FULL ? MMAX : m_;
   const int lane = threadIdx.x & 31;
   const int g = lane % G, c = lane / G;
   const bool colok = c < ncols;
@@ -185,7 +187,7 @@ __device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, in
   }
 }
 
-template <class T, int G, int MMAX, bool MAP>
+template <class T, int G, int MMAX, bool MAP, bool FULL = false>
 __device__ __forceinline__ void solve_tiles(const T *sTri, const T *sC, T *B, int64_t ldb, int m, int n, int tile0,
                                             int tile_step, int rev) {
   constexpr int C = 32 / G;
@@ -194,7 +196,7 @@ __device__ __forceinline__ void solve_tiles(const T *sTri, const T *sC, T *B, in
   for (int t = tile0 + warp; t < ntiles; t += tile_step) {
     const int col0 = t * C;
     const int nc = (n - col0) < C ? (n - col0) : C;
-    warp_solve<T, G, MMAX, MAP>(sTri, sC, B + (int64_t)col0 * ldb, ldb, m, nc, rev);
+    warp_solve<T, G, MMAX, MAP, FULL>(sTri, sC, B + (int64_t)col0 * ldb, ldb, m, nc, rev);
   }
 }
 
@@ -263,18 +265,21 @@ __device__ __forceinline__ void smem_parts(unsigned char *smem, T *&sTri, T *&sC
 
 // ---------------------------------------------------------------------------
 // Single solve: CTA k stages the instance and its warps take column tiles
-// k*W, k*W+1, ... (W warps per CTA).
+// k*W, k*W+1, ... (W warps per CTA).  MAP = false is the paper's case (no
+// index remapping); FULL = true the m = MMAX case (no bound checks).
 // ---------------------------------------------------------------------------
-template <class T, int G, int MMAX>
+template <class T, int G, int MMAX, bool MAP, bool FULL>
 __global__ void __launch_bounds__(32 * kWarpsSingle) small_single_kernel(const T *__restrict__ A, int64_t lda, T *B,
-                                                                 int64_t ldb, int m, int n, T alpha, int unit,
+                                                                 int64_t ldb, int m_, int n, T alpha, int unit,
                                                                  SmallMap mp) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *sTri, *sC, *sR;
   smem_parts<T>(smem, sTri, sC, sR);
+  const int m = FULL ? MMAX : m_;
   const int rows_used = ((m + G - 1) / G) * G;
-  stage<T, MMAX, kWarpsSingle, true>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0, mp);
-  solve_tiles<T, G, MMAX, true>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsSingle, gridDim.x * kWarpsSingle, mp.rev);
+  stage<T, MMAX, kWarpsSingle, MAP>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0, mp);
+  solve_tiles<T, G, MMAX, MAP, FULL>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsSingle, gridDim.x * kWarpsSingle,
+                                     mp.rev);
 }
 
 // ---------------------------------------------------------------------------
@@ -591,6 +596,23 @@ hsma_status_t set_smem_attrs() {
   return HSMA_OK;
 }
 
+template <class T, int G, int MMAX, bool MAP, bool FULL>
+hsma_status_t launch_single_v(const T *A, int64_t lda, T *B, int64_t ldb, int m, int n, T alpha, int unit,
+                              int grid, cudaStream_t st, SmallMap mp) {
+  const size_t bytes = SmemLayout<T>::bytes(64);
+  static DeviceFlags attr_done;
+  if (!attr_done.test()) {
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(small_single_kernel<T, G, MMAX, MAP, FULL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    attr_done.set();
+  }
+  HsmaTraceScope ts("small_single", st);
+  small_single_kernel<T, G, MMAX, MAP, FULL><<<grid, 32 * kWarpsSingle, bytes, st>>>(A, lda, B, ldb, m, n, alpha,
+                                                                                       unit, mp);
+  HSMA_CUDA_TRY(cudaGetLastError());
+  return HSMA_OK;
+}
+
 template <class T, int G, int MMAX>
 hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m, int n, T alpha, int unit,
                               int nsm, cudaStream_t st, SmallMap mp) {
@@ -599,17 +621,12 @@ hsma_status_t launch_single_g(const T *A, int64_t lda, T *B, int64_t ldb, int m,
   int grid = (tiles + kWarpsSingle - 1) / kWarpsSingle;
   const int cap = nsm * 16;
   if (grid > cap) grid = cap;
-  const size_t bytes = SmemLayout<T>::bytes(64);
-  static DeviceFlags attr_done;
-  if (!attr_done.test()) {
-    HSMA_CUDA_TRY(cudaFuncSetAttribute(small_single_kernel<T, G, MMAX>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    attr_done.set();
+  const bool mapped = mp.rev != 0 || mp.tr != 0 || mp.cj != 0;
+  if (mapped) return launch_single_v<T, G, MMAX, true, false>(A, lda, B, ldb, m, n, alpha, unit, grid, st, mp);
+  if constexpr (G == 32 && MMAX == 64) {
+    if (m == MMAX) return launch_single_v<T, G, MMAX, false, true>(A, lda, B, ldb, m, n, alpha, unit, grid, st, mp);
   }
-  HsmaTraceScope ts("small_single", st);
-  small_single_kernel<T, G, MMAX><<<grid, 32 * kWarpsSingle, bytes, st>>>(A, lda, B, ldb, m, n, alpha, unit, mp);
-  HSMA_CUDA_TRY(cudaGetLastError());
-  return HSMA_OK;
+  return launch_single_v<T, G, MMAX, false, false>(A, lda, B, ldb, m, n, alpha, unit, grid, st, mp);
 }
 
 }  // namespace

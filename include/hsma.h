@@ -358,6 +358,22 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int diag, int32_t
                                                     void *hX, int32_t chunks, void *stream);
 
 /*
+ * As hsma_trsm_llnn_vbatched_host, with each A_i stored in host memory as a
+ * packed lower triangle (LAPACK's packed lower format: column j holds rows
+ * j .. m_i - 1, one column after the other, m_i (m_i + 1) / 2 elements from
+ * element offset h_offA[i]; offsets increase by at least that much).  Only
+ * the triangle crosses the link (about half the bytes of a square A for the
+ * batched sizes); it is expanded on the device into the square layout before
+ * each chunk's solve (device workspace: the packed copy and the squares).
+ * Results equal hsma_trsm_llnn_vbatched_host's on the same triangles, bit for
+ * bit.  Other arguments, asynchrony and errors as hsma_trsm_llnn_vbatched_host.
+ */
+HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host_tp(int dtype, int diag, int32_t batch, const int32_t *h_m,
+                                                       const int32_t *h_n, const void *alpha, const void *hAp,
+                                                       const int64_t *h_offA, const void *hB, const int64_t *h_offB,
+                                                       void *hX, int32_t chunks, void *stream);
+
+/*
  * Allocation-free form of hsma_trsm_llnn_vbatched (same arguments, same
  * results bit for bit).  It has no counterpart in the paper; it exists for
  * callers that cannot have the library allocate device memory during a

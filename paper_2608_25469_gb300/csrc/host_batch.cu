@@ -10,8 +10,10 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "../../include/hsma.h"
+#include "blocked.h"
 #include "common.cuh"
 #include "small.h"
 #include "trace.h"
@@ -56,21 +58,76 @@ __global__ void chunk_meta_kernel(int count, const int32_t *__restrict__ m, cons
   ld[i] = m[i] > 1 ? m[i] : 1;
 }
 
+// Packed lower triangles (column j holds rows j..m-1, m(m+1)/2 elements) of
+// instances [b0, b1) into their square device layout (ld = m): one warp per
+// instance; the strict upper triangle of a square is left as it is (never
+// read).  src offsets are the host's packed offsets minus baseP.
+template <class T>
+__global__ void unpack_tri_kernel(int b0, int b1, const int32_t *__restrict__ m, const int64_t *__restrict__ offP,
+                                  int64_t baseP, const int64_t *__restrict__ offS, const T *__restrict__ src, T *dst) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = b0 + w; b < b1; b += nw) {
+    const int mb = m[b];
+    const T *s = src + (offP[b] - baseP);
+    T *d = dst + offS[b];
+    int64_t q = 0;  // packed index of column j's diagonal
+    for (int j = 0; j < mb; ++j) {
+      for (int r = j + lane; r < mb; r += 32) d[r + (int64_t)j * mb] = s[q + (r - j)];
+      q += mb - j;
+    }
+  }
+}
+
+template <class T>
+void launch_unpack(int b0, int b1, const int32_t *m, const int64_t *offP, int64_t baseP, const int64_t *offS,
+                   const void *src, void *dst, cudaStream_t st) {
+  const int blocks = std::max(1, std::min((b1 - b0 + 7) / 8, 4 * hsma_sm_count()));
+  unpack_tri_kernel<T><<<blocks, 256, 0, st>>>(b0, b1, m, offP, baseP, offS, static_cast<const T *>(src),
+                                               static_cast<T *>(dst));
+}
+
+hsma_status_t unpack_chunk(int dtype, int b0, int b1, const int32_t *m, const int64_t *offP, int64_t baseP,
+                           const int64_t *offS, const void *src, void *dst, cudaStream_t st) {
+  HsmaTraceScope ts("host_unpack", st);
+  switch (hsma_small_esize(dtype)) {
+    case 16: launch_unpack<double2>(b0, b1, m, offP, baseP, offS, src, dst, st); break;
+    case 8: launch_unpack<double>(b0, b1, m, offP, baseP, offS, src, dst, st); break;
+    default: launch_unpack<float>(b0, b1, m, offP, baseP, offS, src, dst, st); break;
+  }
+  return hsma_from_cuda(cudaGetLastError());
+}
+
 // The whole batch's A and B get device buffers: the copy-in stream copies the
 // sizes and offsets, fills every instance's pointers, then copies A and B
 // chunk by chunk; each chunk's solve runs on one of two compute streams (so a
 // solve's tail overlaps the next one's start) once its copy has landed; the
 // copy-out stream returns each chunk's X as soon as it is solved.
+// tri = 1: A_i is stored as packed lower triangles on the host (m(m+1)/2
+// elements each); they are copied packed and expanded on the device.
+inline int64_t a_elems(int32_t m, int tri) { return tri ? (int64_t)m * (m + 1) / 2 : (int64_t)m * m; }
+
 hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h_m, const int32_t *h_n,
                             const void *alpha, const void *hA, const int64_t *h_offA, const void *hB,
                             const int64_t *h_offB, void *hX, int nch, int32_t per, int es, cudaStream_t caller,
-                            const cudaStream_t ss[kStreams]) {
+                            const cudaStream_t ss[kStreams], int tri) {
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const int64_t extA = h_offA[batch - 1] + (int64_t)h_m[batch - 1] * h_m[batch - 1] - h_offA[0];
+  const int64_t extA = h_offA[batch - 1] + a_elems(h_m[batch - 1], tri) - h_offA[0];
+  // square offsets of the expanded triangles (tri), computed here and copied once
+  std::vector<int64_t> sq;
+  int64_t extS = 0;
+  if (tri) {
+    sq.resize((size_t)batch);
+    for (int32_t i = 0; i < batch; ++i) {
+      sq[i] = extS;
+      extS += (int64_t)h_m[i] * h_m[i];
+    }
+  }
   const int64_t extB = h_offB[batch - 1] + (int64_t)h_m[batch - 1] * h_n[batch - 1] - h_offB[0];
   const size_t mi_b = al(sizeof(int32_t) * batch), oi_b = al(sizeof(int64_t) * batch);
   const size_t p_b = al(sizeof(void *) * batch);
-  const size_t a_b = al((size_t)extA * es), b_b = al((size_t)extB * es);
+  const size_t a_b = al((size_t)extA * es), b_b = al((size_t)extB * es), s_b = al((size_t)extS * es);
+  const size_t sq_b = tri ? al(sizeof(int64_t) * batch) : 0;
   // complex128 runs the column-packed batch, the others the per-instance
   // kernel; chunks on one compute stream run in order, so each stream needs
   // one scratch
@@ -80,7 +137,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
   const size_t scr_b = al(packed ? hsma_vbatched_packed_scratch_bytes(dtype, per, max_m)
                                  : hsma_vbatched_scratch_bytes(per));
   const int nscr = nch < 2 ? nch : 2;
-  const size_t total = a_b + b_b + 3 * mi_b + 2 * oi_b + 2 * p_b + scr_b * nscr;
+  const size_t total = a_b + b_b + s_b + sq_b + 3 * mi_b + 2 * oi_b + 2 * p_b + scr_b * nscr;
   std::unique_ptr<cudaEvent_t[]> evs(new (std::nothrow) cudaEvent_t[2 * nch]());  // copied-in, solved
   if (!evs) return HSMA_ERR_NO_MEMORY;
   cudaEvent_t *ev = evs.get();
@@ -88,8 +145,12 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
   hsma_status_t s = hsma_ws_alloc(&ws, total, caller);
   if (s != HSMA_OK) return s;
   char *q = static_cast<char *>(ws);
-  char *dA = q, *dB = q + a_b;
+  char *dA = q, *dB = q + a_b;  // dA: the host's layout of A (packed triangles when tri)
   q += a_b + b_b;
+  char *dS = tri ? q : dA;  // the square layout the kernels read
+  q += s_b;
+  int64_t *gSq = tri ? reinterpret_cast<int64_t *>(q) : nullptr;
+  q += sq_b;
   int32_t *gm = reinterpret_cast<int32_t *>(q), *gn = reinterpret_cast<int32_t *>(q + mi_b);
   int32_t *gld = reinterpret_cast<int32_t *>(q + 2 * mi_b);
   q += 3 * mi_b;
@@ -124,8 +185,14 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
           HSMA_OK)
         break;
     }
-    chunk_meta_kernel<<<(batch + 255) / 256, 256, 0, s_in>>>(batch, gm, goA, goB, h_offA[0], h_offB[0], dA, dB, es,
-                                                             pA, pB, gld);
+    if (tri) {
+      HsmaTraceScope ts("host_h2d", s_in);
+      if ((s = fail(cudaMemcpyAsync(gSq, sq.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice, s_in))) !=
+          HSMA_OK)
+        break;
+    }
+    chunk_meta_kernel<<<(batch + 255) / 256, 256, 0, s_in>>>(batch, gm, tri ? gSq : goA, goB, tri ? 0 : h_offA[0],
+                                                             h_offB[0], dS, dB, es, pA, pB, gld);
     if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     for (int c = 0; c < nch && s == HSMA_OK; ++c) {
       const int32_t b = c * per, e = std::min(batch, b + per), cnt = e - b;
@@ -135,7 +202,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
         continue;
       }
       const int64_t a0 = h_offA[b] - h_offA[0], b0 = h_offB[b] - h_offB[0];
-      const int64_t na = h_offA[e - 1] + (int64_t)h_m[e - 1] * h_m[e - 1] - h_offA[b];
+      const int64_t na = h_offA[e - 1] + a_elems(h_m[e - 1], tri) - h_offA[b];
       const int64_t nbx = h_offB[e - 1] + (int64_t)h_m[e - 1] * h_n[e - 1] - h_offB[b];
       {
         HsmaTraceScope ts("host_h2d", s_in);
@@ -149,6 +216,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
       if ((s = fail(cudaEventRecord(ev[2 * c], s_in))) != HSMA_OK) break;
       cudaStream_t sk = s_k[c & 1];
       if ((s = fail(cudaStreamWaitEvent(sk, ev[2 * c], 0))) != HSMA_OK) break;
+      if (tri && (s = unpack_chunk(dtype, b, e, gm, goA, h_offA[0], gSq, dA, dS, sk)) != HSMA_OK) break;
       int32_t *scr = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scr0) + scr_b * (c & 1));
       if (packed)
         s = hsma_small_vbatched_packed(dtype, cnt, max_m, gm + b, gn + b, static_cast<const double *>(alpha), pA + b,
@@ -183,12 +251,11 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
 
 }  // namespace
 
-extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int diag, int32_t batch,
-                                                                const int32_t *h_m, const int32_t *h_n,
-                                                                const void *alpha, const void *hA,
-                                                                const int64_t *h_offA, const void *hB,
-                                                                const int64_t *h_offB, void *hX, int32_t chunks,
-                                                                void *stream) {
+namespace {
+
+hsma_status_t host_batch_entry(int dtype, int diag, int32_t batch, const int32_t *h_m, const int32_t *h_n,
+                               const void *alpha, const void *hA, const int64_t *h_offA, const void *hB,
+                               const int64_t *h_offB, void *hX, int32_t chunks, void *stream, int tri) {
   if (!hsma_small_dtype(dtype)) {
     return (dtype == HSMA_R32_BF16 || dtype == HSMA_R64_IR) ? HSMA_ERR_UNSUPPORTED : HSMA_ERR_INVALID_ARG;
   }
@@ -200,7 +267,7 @@ extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int di
   for (int32_t i = 0; i < batch; ++i) {
     if (h_m[i] < 0 || h_n[i] < 0 || h_offA[i] < 0 || h_offB[i] < 0) return HSMA_ERR_INVALID_ARG;
     if (h_m[i] > 64) return HSMA_ERR_UNSUPPORTED;
-    if (i > 0 && (h_offA[i] < h_offA[i - 1] + (int64_t)h_m[i - 1] * h_m[i - 1] ||
+    if (i > 0 && (h_offA[i] < h_offA[i - 1] + a_elems(h_m[i - 1], tri) ||
                   h_offB[i] < h_offB[i - 1] + (int64_t)h_m[i - 1] * h_n[i - 1]))
       return HSMA_ERR_INVALID_ARG;
   }
@@ -211,5 +278,26 @@ extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int di
   cudaStream_t ss[kStreams];
   hsma_status_t s = pipe_streams(ss);
   if (s != HSMA_OK) return s;
-  return full_pipeline(dtype, diag, batch, h_m, h_n, alpha, hA, h_offA, hB, h_offB, hX, nch, per, es, caller, ss);
+  return full_pipeline(dtype, diag, batch, h_m, h_n, alpha, hA, h_offA, hB, h_offB, hX, nch, per, es, caller, ss,
+                       tri);
+}
+
+}  // namespace
+
+extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int diag, int32_t batch,
+                                                                const int32_t *h_m, const int32_t *h_n,
+                                                                const void *alpha, const void *hA,
+                                                                const int64_t *h_offA, const void *hB,
+                                                                const int64_t *h_offB, void *hX, int32_t chunks,
+                                                                void *stream) {
+  return host_batch_entry(dtype, diag, batch, h_m, h_n, alpha, hA, h_offA, hB, h_offB, hX, chunks, stream, 0);
+}
+
+extern "C" HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host_tp(int dtype, int diag, int32_t batch,
+                                                                   const int32_t *h_m, const int32_t *h_n,
+                                                                   const void *alpha, const void *hAp,
+                                                                   const int64_t *h_offA, const void *hB,
+                                                                   const int64_t *h_offB, void *hX, int32_t chunks,
+                                                                   void *stream) {
+  return host_batch_entry(dtype, diag, batch, h_m, h_n, alpha, hAp, h_offA, hB, h_offB, hX, chunks, stream, 1);
 }

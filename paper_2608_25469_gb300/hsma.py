@@ -37,7 +37,8 @@ EXPORTS = ["hsma_status_string", "hsma_version", "hsma_trsm_llnn", "hsma_trsm_ll
            "hsma_trsm_llnn_vbatched", "hsma_plan", "hsma_small_cost", "hsma_tuning_load", "hsma_gen_matrix",
            "hsma_trace_enable", "hsma_trace_read", "hsma_trace_launches", "hsma_trace_reset",
            "hsma_device_status", "hsma_gemm_bf16_update", "hsma_gemm_f64_emulated", "hsma_trsm_llnn_vbatched_noalloc",
-           "hsma_trsm_llnn_vbatched_host", "hsma_trsm", "hsma_trsm_vbatched", "hsma_check_wait_timeout",
+           "hsma_trsm_llnn_vbatched_host", "hsma_trsm_llnn_vbatched_host_tp", "hsma_trsm", "hsma_trsm_vbatched",
+           "hsma_check_wait_timeout",
            "hsma_getrs_vbatched", "hsma_potrs_vbatched", "hsma_getrs", "hsma_potrs",
            "hsma_server_create", "hsma_server_submit", "hsma_server_poll", "hsma_server_drain", "hsma_server_stats",
            "hsma_server_destroy"]
@@ -301,6 +302,19 @@ def hsma_trsm_llnn_vbatched_host(dtype, diag, batch, h_m, h_n, alpha, hA, h_offA
                                           ptr(hB), ptr(h_offB), ptr(hX), chunks, stream)
     if check:
         _check(s, "hsma_trsm_llnn_vbatched_host")
+    return s
+
+
+def hsma_trsm_llnn_vbatched_host_tp(dtype, diag, batch, h_m, h_n, alpha, hAp, h_offA, hB, h_offB, hX, chunks=0,
+                                    stream=0, check=True) -> int:
+    """As hsma_trsm_llnn_vbatched_host with each A_i as a packed lower triangle in host memory."""
+    def ptr(a):
+        return a.ctypes.data if isinstance(a, np.ndarray) else a
+    s = _lib.hsma_trsm_llnn_vbatched_host_tp(dtype, diag, batch, ptr(h_m), ptr(h_n),
+                                             ctypes.cast(_alpha_buf(alpha), ctypes.c_void_p), ptr(hAp), ptr(h_offA),
+                                             ptr(hB), ptr(h_offB), ptr(hX), chunks, stream)
+    if check:
+        _check(s, "hsma_trsm_llnn_vbatched_host_tp")
     return s
 
 

@@ -460,3 +460,58 @@ def test_factor_batches_with_instances_above_64(H):
     assert bt.status() == 0
     for b, X in enumerate(bt.results()):
         assert oracle.forward_error(X, oracle.potrs(Ls[b], Bs[b], 2.0)) <= TOL, b
+
+
+def _pack_lower(A):
+    """LAPACK's packed lower format: column j's rows j..m-1, one column after the other."""
+    m = A.shape[1]
+    return np.concatenate([A[j:m, j] for j in range(m)]) if m else np.zeros(0, A.dtype)
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128, C64])
+@pytest.mark.parametrize("chunks", [0, 3])
+def test_host_batch_packed_triangles_equal_square_layout(H, code, chunks):
+    """The host-buffer batch with A as packed lower triangles gives the square-layout call's
+    results bit for bit; gaps between instances and empty instances included."""
+    import torch
+    rng = np.random.default_rng(60 + code)
+    sizes = [(int(m), int(n)) for m, n in rng.integers(0, 65, (300, 2))]
+    As, Bs = _mix(code, [(max(m, 1), max(n, 1)) for m, n in sizes], seed=61)
+    As = [a[:m, :m] if m else np.zeros((0, 0), a.dtype) for a, (m, _) in zip(As, sizes)]
+    Bs = [b[:m, :n] for b, (m, n) in zip(Bs, sizes)]
+    alpha = 1.5 if code == I.R64 else 1.5 - 0.5j
+    ms = np.array([m for m, _ in sizes], dtype=np.int32)
+    ns = np.array([n for _, n in sizes], dtype=np.int32)
+    gap = 3
+    sqA = ms.astype(np.int64) ** 2
+    tpA = ms.astype(np.int64) * (ms + 1) // 2
+    nB = ms.astype(np.int64) * ns
+    offS = np.concatenate([[0], np.cumsum(sqA)[:-1]]).astype(np.int64)
+    offT = np.concatenate([[5], 5 + np.cumsum(tpA + gap)[:-1]]).astype(np.int64)
+    offB = np.concatenate([[0], np.cumsum(nB + gap)[:-1]]).astype(np.int64)
+    dt = As[0].dtype
+    hS = np.zeros(int(sqA.sum()) + 1, dt)
+    hT = np.full(int(offT[-1] + tpA[-1] + gap), np.nan, dt)
+    hB = np.zeros(int(offB[-1] + nB[-1] + gap), dt)
+    for b in range(len(sizes)):
+        m, n = sizes[b]
+        hS[offS[b]:offS[b] + m * m] = np.asfortranarray(As[b]).ravel(order="F")
+        hT[offT[b]:offT[b] + tpA[b]] = _pack_lower(As[b])
+        hB[offB[b]:offB[b] + m * n] = np.asfortranarray(Bs[b]).ravel(order="F")
+    X1, X2 = np.zeros_like(hB), np.zeros_like(hB)
+    H.hsma_trsm_llnn_vbatched_host(code, 0, len(sizes), ms, ns, alpha, hS.ctypes.data, offS, hB.ctypes.data, offB,
+                                   X1.ctypes.data, chunks=chunks, stream=H.stream_ptr())
+    H.hsma_trsm_llnn_vbatched_host_tp(code, 0, len(sizes), ms, ns, alpha, hT.ctypes.data, offT, hB.ctypes.data,
+                                      offB, X2.ctypes.data, chunks=chunks, stream=H.stream_ptr())
+    torch.cuda.synchronize()
+    for b in range(len(sizes)):
+        m, n = sizes[b]
+        sl = slice(offB[b], offB[b] + m * n)
+        assert np.array_equal(X1[sl], X2[sl]), b
+    # offsets that overlap the previous packed triangle are rejected before any copy
+    bad = offT.copy()
+    k = int(np.argmax(tpA > 1))
+    if k + 1 < len(bad):
+        bad[k + 1] = bad[k] + tpA[k] - 1
+        assert H.hsma_trsm_llnn_vbatched_host_tp(code, 0, len(sizes), ms, ns, alpha, hT.ctypes.data, bad,
+                                                 hB.ctypes.data, offB, X2.ctypes.data, check=False) == 1

@@ -116,6 +116,8 @@ def _load():
     lib.hsma_trsm_llnn_vbatched_noalloc.restype = c_int
     lib.hsma_trsm_llnn_vbatched_host.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     lib.hsma_trsm_llnn_vbatched_host.restype = c_int
+    lib.hsma_trsm_llnn_vbatched_host_tp.argtypes = [c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+    lib.hsma_trsm_llnn_vbatched_host_tp.restype = c_int
     lib.hsma_trsm.argtypes = [c_int, c_int, c_int, c_int, c_int, i64, i64, vp, vp, i64, vp, i64, vp, vp, vp]
     lib.hsma_trsm.restype = c_int
     lib.hsma_trsm_vbatched.argtypes = [c_int, c_int, c_int, c_int, c_int, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32,

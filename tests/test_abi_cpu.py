@@ -1,5 +1,6 @@
 """The C-ABI library loads, exports what include/hsma.h declares, and validates
 arguments on the host before touching the GPU (CPU only)."""
+import ctypes
 import os
 import re
 
@@ -32,6 +33,27 @@ def test_exports_match_header(H):
     assert sorted(H.EXPORTS) == declared, "binding and header disagree"
     for f in declared:
         assert hasattr(H.lib(), f)
+
+
+def header_arity():
+    """Parameter count of every function include/hsma.h declares."""
+    text = re.sub(r"/\*.*?\*/|//[^\n]*", "", open(os.path.join(ROOT, "include", "hsma.h")).read(), flags=re.S)
+    out = {}
+    for name, params in re.findall(r"HSMA_API[^;(]*?\b(hsma_\w+)\s*\(([^;]*?)\)\s*;", text, flags=re.S):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_declares_every_signature(H):
+    # without argtypes ctypes passes a Python int as a C int: a 64-bit pointer loses its upper half
+    arity = header_arity()
+    assert sorted(arity) == header_functions()
+    for f, n in arity.items():
+        fn = getattr(H.lib(), f)
+        if n:
+            assert fn.argtypes is not None and len(fn.argtypes) == n, f"{f}: argtypes {fn.argtypes}, header {n}"
+        assert fn.restype is not ctypes.c_int or f not in ("hsma_version", "hsma_status_string"), f
 
 
 def test_version_and_status_strings(H):

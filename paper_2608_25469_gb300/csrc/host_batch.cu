@@ -104,7 +104,8 @@ hsma_status_t unpack_chunk(int dtype, int b0, int b1, const int32_t *m, const in
 // solve's tail overlaps the next one's start) once its copy has landed; the
 // copy-out stream returns each chunk's X as soon as it is solved.
 // tri = 1: A_i is stored as packed lower triangles on the host (m(m+1)/2
-// elements each); they are copied packed and expanded on the device.
+// elements each); they are copied packed, and read packed by the complex128
+// batch or expanded on the device for the other dtypes.
 inline int64_t a_elems(int32_t m, int tri) { return tri ? (int64_t)m * (m + 1) / 2 : (int64_t)m * m; }
 
 hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h_m, const int32_t *h_n,
@@ -113,10 +114,15 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
                             const cudaStream_t ss[kStreams], int tri) {
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const int64_t extA = h_offA[batch - 1] + a_elems(h_m[batch - 1], tri) - h_offA[0];
-  // square offsets of the expanded triangles (tri), computed here and copied once
+  // complex128 runs the column-packed batch, whose prep pass reads packed
+  // triangles directly; the per-instance kernel of the other dtypes reads a
+  // square layout, so their packed triangles are expanded on the device
+  const bool packed = hsma_vbatched_packed_dtype(dtype);
+  const bool expand = tri && !packed;
+  // square offsets of the expanded triangles, computed here and copied once
   std::vector<int64_t> sq;
   int64_t extS = 0;
-  if (tri) {
+  if (expand) {
     sq.resize((size_t)batch);
     for (int32_t i = 0; i < batch; ++i) {
       sq[i] = extS;
@@ -127,11 +133,8 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
   const size_t mi_b = al(sizeof(int32_t) * batch), oi_b = al(sizeof(int64_t) * batch);
   const size_t p_b = al(sizeof(void *) * batch);
   const size_t a_b = al((size_t)extA * es), b_b = al((size_t)extB * es), s_b = al((size_t)extS * es);
-  const size_t sq_b = tri ? al(sizeof(int64_t) * batch) : 0;
-  // complex128 runs the column-packed batch, the others the per-instance
-  // kernel; chunks on one compute stream run in order, so each stream needs
-  // one scratch
-  const bool packed = hsma_vbatched_packed_dtype(dtype);
+  const size_t sq_b = expand ? al(sizeof(int64_t) * batch) : 0;
+  // chunks on one compute stream run in order, so each stream needs one scratch
   int32_t max_m = 0;
   for (int32_t i = 0; i < batch; ++i) max_m = std::max(max_m, h_m[i]);
   const size_t scr_b = al(packed ? hsma_vbatched_packed_scratch_bytes(dtype, per, max_m)
@@ -147,9 +150,9 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
   char *q = static_cast<char *>(ws);
   char *dA = q, *dB = q + a_b;  // dA: the host's layout of A (packed triangles when tri)
   q += a_b + b_b;
-  char *dS = tri ? q : dA;  // the square layout the kernels read
+  char *dS = expand ? q : dA;  // the layout the kernels read
   q += s_b;
-  int64_t *gSq = tri ? reinterpret_cast<int64_t *>(q) : nullptr;
+  int64_t *gSq = expand ? reinterpret_cast<int64_t *>(q) : nullptr;
   q += sq_b;
   int32_t *gm = reinterpret_cast<int32_t *>(q), *gn = reinterpret_cast<int32_t *>(q + mi_b);
   int32_t *gld = reinterpret_cast<int32_t *>(q + 2 * mi_b);
@@ -185,14 +188,15 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
           HSMA_OK)
         break;
     }
-    if (tri) {
+    if (expand) {
       HsmaTraceScope ts("host_h2d", s_in);
       if ((s = fail(cudaMemcpyAsync(gSq, sq.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice, s_in))) !=
           HSMA_OK)
         break;
     }
-    chunk_meta_kernel<<<(batch + 255) / 256, 256, 0, s_in>>>(batch, gm, tri ? gSq : goA, goB, tri ? 0 : h_offA[0],
-                                                             h_offB[0], dS, dB, es, pA, pB, gld);
+    chunk_meta_kernel<<<(batch + 255) / 256, 256, 0, s_in>>>(batch, gm, expand ? gSq : goA, goB,
+                                                             expand ? 0 : h_offA[0], h_offB[0], dS, dB, es, pA, pB,
+                                                             gld);
     if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     for (int c = 0; c < nch && s == HSMA_OK; ++c) {
       const int32_t b = c * per, e = std::min(batch, b + per), cnt = e - b;
@@ -216,11 +220,11 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
       if ((s = fail(cudaEventRecord(ev[2 * c], s_in))) != HSMA_OK) break;
       cudaStream_t sk = s_k[c & 1];
       if ((s = fail(cudaStreamWaitEvent(sk, ev[2 * c], 0))) != HSMA_OK) break;
-      if (tri && (s = unpack_chunk(dtype, b, e, gm, goA, h_offA[0], gSq, dA, dS, sk)) != HSMA_OK) break;
+      if (expand && (s = unpack_chunk(dtype, b, e, gm, goA, h_offA[0], gSq, dA, dS, sk)) != HSMA_OK) break;
       int32_t *scr = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scr0) + scr_b * (c & 1));
       if (packed)
         s = hsma_small_vbatched_packed(dtype, cnt, max_m, gm + b, gn + b, static_cast<const double *>(alpha), pA + b,
-                                       gld + b, pB + b, gld + b, diag == HSMA_UNIT, nullptr, scr, sk);
+                                       gld + b, pB + b, gld + b, diag == HSMA_UNIT, nullptr, scr, sk, tri);
       else
         s = hsma_small_vbatched(dtype, cnt, gm + b, gn + b, static_cast<const double *>(alpha), pA + b, gld + b,
                                 pB + b, gld + b, diag == HSMA_UNIT, nullptr, scr, sk);

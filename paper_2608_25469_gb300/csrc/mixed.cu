@@ -128,13 +128,9 @@ __global__ void __launch_bounds__(256) sgemm_scale_kernel(const float *__restric
 }
 
 // ---------------------------------------------------------------------------
-// Conversions to the tensor-core operand layouts.
+// Conversions to the tensor-core operand layouts (split_bf16 / split3_bf16
+// come from tc_gemm.cuh, whose FP32-result epilogue writes the same splits).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
-  hi = __float2bfloat16_rn(x);
-  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
-
 // A panel (rows x nb, column-major fp32, lda) -> A' rows x Kp row-major BF16:
 // terms 1: [hi], terms 3: [hi | hi | lo]; columns past terms*nb are zero.
 // One 32 x 32 tile (rows i0.., columns k0..) per CTA of 256 threads.
@@ -259,15 +255,6 @@ int r32_kd(int nb) { return round_up(nb, TC_BK); }
 
 size_t r32_dslices_elems(int nb, int64_t m) { return (size_t)((m + nb - 1) / nb) * 3 * nb * r32_kd(nb); }
 
-// x = a + b + c with a, b, c in BF16 (each remainder is exact in FP32)
-__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c) {
-  a = __float2bfloat16_rn(x);
-  float r = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r);
-  r -= __bfloat162float(b);
-  c = __float2bfloat16_rn(r);
-}
-
 // negated three-way slices of every diagonal-block inverse (column-major nb x nb
 // blocks, zeros outside the computed part) as out[blk][s][i][k]
 __global__ void r32_dslice_kernel(const float *__restrict__ Dinv, int nb, int64_t nblk, int Kd,
@@ -380,22 +367,39 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
       sa.pb[q] = ps[q][1];
     }
   }
+  // With the tensor-core solve products, the split of X_r that the update
+  // multiplies comes out of the solve product's epilogue, and the slices of
+  // the next block row out of the update's (the same values the separate
+  // conversion kernels give); the zero tails of both operands are set once.
+  if (P.tc_solve) {
+    cudaError_t e = cudaMemsetAsync(Xp, 0, x_b, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(X3, 0, x3_b, st);
+    if (e != cudaSuccess) s = hsma_from_cuda(e);
+  }
+  bool x3_ready = false;
   for (int64_t r = 0; r < nblk && s == HSMA_OK; ++r) {
     const int64_t r0 = r * nb;
     const int sr = (int)std::min<int64_t>(nb, m - r0);
+    const bool last = r0 + sr >= m;
     if (!P.tc_solve) {
       HsmaTraceScope ts("copy", st);
       copy_f32_kernel<<<hsma_grid_rc(sr, n), 256, 0, st>>>(B + r0, ldb, W, nb, sr, n, skip);
     }
     if (P.tc_solve) {
       // the product reads only the slices, so they are cut from B_r itself
-      // and X_r is written straight back into B_r
-      {
+      // (r = 0, or after a partial next block) and X_r is written straight
+      // back into B_r
+      if (!x3_ready) {
         HsmaTraceScope ts("convert", st);
         r32_xslice_kernel<<<hsma_grid_rc(Kd, n), 256, 0, st>>>(B + r0, ldb, sr, n, Kd, r == 0 ? alpha : 1.0f, X3,
                                                                 skip);
         if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
       }
+      sa.xs2 = last ? nullptr : Xp;
+      sa.ld2 = Kp;
+      sa.nb2 = nb;
+      sa.terms2 = P.terms;
+      sa.rows2 = sr;
       sa.C32 = B + r0;
       sa.ldc = ldb;
       sa.beta = 0.0f;
@@ -411,17 +415,17 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
       s = sgemm_scale(P.Dinv + (size_t)r * nb * nb, nb, W, nb, B + r0, ldb, sr, (int)n, sr, r == 0 ? alpha : 1.0f, 1,
                       skip, st);
     }
-    if (s != HSMA_OK || r0 + sr >= m) break;
+    if (s != HSMA_OK || last) break;
     const int rows = (int)(m - r0 - sr);
     const __nv_bfloat16 *panel = P.panels ? P.panels + panel_off(P, r) : Ap;
-    {
+    if (!P.panels || !P.tc_solve) {
       HsmaTraceScope ts("convert", st);
       if (!P.panels) {
         dim3 g1((rows + 31) / 32, (nb + 31) / 32);
         convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, nb, P.terms, Kp, Ap);
       }
-      convert_x_kernel<<<hsma_grid_rc(nb, n), 256, 0, st>>>(B + r0, ldb, nb, (int)n, P.terms, Kp, Xp,
-                                                                       skip);
+      if (!P.tc_solve)
+        convert_x_kernel<<<hsma_grid_rc(nb, n), 256, 0, st>>>(B + r0, ldb, nb, (int)n, P.terms, Kp, Xp, skip);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         s = hsma_from_cuda(e);
@@ -429,6 +433,15 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
       }
     }
     TcArgs a{};
+    // the next block row's slices for its solve product, when it is a full block
+    x3_ready = P.tc_solve && rows >= nb;
+    if (x3_ready) {
+      a.xs3 = X3;
+      a.per3 = n * (int64_t)Kd;
+      a.ld3 = Kd;
+      a.r3 = 0;
+      a.rows3 = nb;
+    }
     a.C32 = B + r0 + sr;
     a.ldc = ldb;
     a.beta = r == 0 ? alpha : 1.0f;
@@ -1214,7 +1227,7 @@ extern "C" HSMA_API hsma_status_t hsma_gemm_bf16_update(int64_t M, int64_t N, in
                                                         void *stream) {
   if (M < 0 || N < 0 || K < 0 || ldc < std::max<int64_t>(1, M)) return HSMA_ERR_INVALID_ARG;
   if (M == 0 || N == 0) return HSMA_OK;
-  if (A == nullptr || Bt == nullptr || C == nullptr || K == 0 || K % TC_BK != 0) return HSMA_ERR_INVALID_ARG;
+  if (A == nullptr || Bt == nullptr || C == nullptr || K == 0 || K % 64 != 0) return HSMA_ERR_INVALID_ARG;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return HSMA_ERR_UNSUPPORTED;
   return bf16_update(static_cast<const __nv_bfloat16 *>(A), static_cast<const __nv_bfloat16 *>(Bt), (int)M, (int)N,
                      (int)K, beta, C, ldc, static_cast<cudaStream_t>(stream));

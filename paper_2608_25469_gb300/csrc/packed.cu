@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
                                                                        const void *const *__restrict__ dA,
                                                                        const int32_t *__restrict__ dlda,
                                                                        const unsigned char *__restrict__ scratch,
-                                                                       PkLayout L, T *stage, T alpha, int unit) {
+                                                                       PkLayout L, T *stage, T alpha, int unit,
+                                                                       int a_packed) {
   using E = Elem<T>;
   __shared__ __align__(16) int32_t sgrp[64 * kPkGroupWords];
   __shared__ T sR[kPkPrepWarps][64];
@@ -352,12 +353,17 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
     const int b = inst[p];
     const T *A = static_cast<const T *>(dA[b]);
     const int64_t lda = dlda[b];
+    // element (r, c), r >= c: column-major with lda, or (a_packed) LAPACK's
+    // packed lower storage, column c holding rows c .. m-1 from c (2m - c + 1) / 2
+    auto at = [&](int r, int c) -> const T * {
+      return a_packed ? A + (int64_t)c * (2 * m - c + 1) / 2 + (r - c) : A + r + (int64_t)c * lda;
+    };
     T *tri = stage + off;
     T *sc = tri + pk_tri_elems(rows);
     __syncwarp();
     for (int r = lane; r < rows; r += 32) {  // warp-uniform trip count per 32 rows
       T rv = E::one();
-      if (r < m && !unit) rv = E::recip(E::ld(A + r + (int64_t)r * lda));
+      if (r < m && !unit) rv = E::recip(E::ld(at(r, r)));
       rinv[r] = rv;
       sc[r] = r < m ? E::mul(alpha, rv) : E::zero();
     }
@@ -381,7 +387,7 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
       for (int u = 0; u < 4; ++u) {
         const int q = q0 + u * 32 + lane;
         rr[u] = i + 1 + loc;
-        vv[u] = (q < total && rr[u] < m) ? E::ld(A + rr[u] + (int64_t)i * lda) : E::zero();
+        vv[u] = (q < total && rr[u] < m) ? E::ld(at(rr[u], i)) : E::zero();
         advance(32);
       }
 #pragma unroll
@@ -542,7 +548,7 @@ int sm_count(int dev) {
 template <class T>
 hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int32_t *dn, const double *alpha,
                           const void *const *dA, const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
-                          uint32_t *status, void *scratch, cudaStream_t st) {
+                          uint32_t *status, void *scratch, cudaStream_t st, int a_packed) {
   int dev = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   const PkLayout L = pk_layout(batch, max_m, (int)sizeof(T), pk_two_lanes<T>());
@@ -571,7 +577,7 @@ hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int
     int blocks = (batch + kPkPrepWarps - 1) / kPkPrepWarps;
     if (blocks > 4 * nsm) blocks = 4 * nsm;
     HsmaTraceScope ts("vbatched_prep", st);
-    packed_prep_kernel<T><<<blocks, 32 * kPkPrepWarps, 0, st>>>(dm, dA, dlda, scr, L, stage, al, unit);
+    packed_prep_kernel<T><<<blocks, 32 * kPkPrepWarps, 0, st>>>(dm, dA, dlda, scr, L, stage, al, unit, a_packed);
     HSMA_CUDA_TRY(cudaGetLastError());
   }
   {
@@ -592,10 +598,11 @@ size_t hsma_vbatched_packed_scratch_bytes(int dtype, int32_t batch, int32_t max_
 hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m, const int32_t *dm,
                                          const int32_t *dn, const double *alpha, const void *const *dA,
                                          const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
-                                         uint32_t *status, void *scratch, cudaStream_t st) {
+                                         uint32_t *status, void *scratch, cudaStream_t st, int a_packed) {
   switch (dtype) {
     case HSMA_C128:
-      return packed_impl<cplx>(batch, max_m, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st);
+      return packed_impl<cplx>(batch, max_m, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st,
+                               a_packed);
     default:
       return HSMA_ERR_UNSUPPORTED;
   }

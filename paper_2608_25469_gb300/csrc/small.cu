@@ -135,11 +135,34 @@ __device__ __forceinline__ void stage(T *sTri, T *sC, T *sR, const T *__restrict
   __syncthreads();
 }
 
-// One warp solves one column tile (up to 32/G columns starting at Bt).
+// The B entries of a lane's rows in one column tile (zero outside the
+// instance), loaded before the solve so that they can be in flight while the
+// triangle is staged.
+template <class T, int G, int MMAX, bool MAP, bool FULL = false>
+__device__ __forceinline__ void warp_load_b(T (&b)[MMAX / G], const T *Bt, int64_t ldb, int m_, int ncols, int rev) {
+  using E = Elem<T>;
+  constexpr int R = MMAX / G;
+  const int m = FULL ? MMAX : m_;
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G, c = lane / G;
+  const bool colok = c < ncols;
+  const T *Bp = Bt + (int64_t)(colok ? c : 0) * ldb;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int r = g + t * G;
+    b[t] = E::zero();
+    if (t * G < m) {
+      if (colok && r < m) b[t] = E::ld(Bp + (MAP && rev ? m - 1 - r : r));
+    }
+  }
+}
+
+// One warp solves one column tile (up to 32/G columns starting at Bt) whose
+// B entries warp_load_b has loaded.
 // FULL: m == MMAX, known at compile time (the bound checks fold away).
 template <class T, int G, int MMAX, bool MAP, bool FULL = false>
-__device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, int64_t ldb, int m_, int ncols,
-                                           int rev) {
+__device__ __forceinline__ void warp_solve_loaded(const T (&b)[MMAX / G], const T *sTri, const T *sC, T *Bt,
+                                                  int64_t ldb, int m_, int ncols, int rev) {
   using E = Elem<T>;
   constexpr int R = MMAX / G;
   const int m = FULL ? MMAX : m_;
@@ -154,7 +177,7 @@ __device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, in
     const int r = g + t * G;
     s[t] = E::zero();
     if (t * G < m) {
-      if (colok && r < m) s[t] = E::mul(sC[r], E::ld(Bp + (MAP && rev ? m - 1 - r : r)));
+      if (colok && r < m) s[t] = E::mul(sC[r], b[t]);
     }
   }
 
@@ -185,6 +208,14 @@ __device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, in
       if (colok && r < m) E::st(Bp + (MAP && rev ? m - 1 - r : r), s[t]);
     }
   }
+}
+
+template <class T, int G, int MMAX, bool MAP, bool FULL = false>
+__device__ __forceinline__ void warp_solve(const T *sTri, const T *sC, T *Bt, int64_t ldb, int m, int ncols,
+                                           int rev) {
+  T b[MMAX / G];
+  warp_load_b<T, G, MMAX, MAP, FULL>(b, Bt, ldb, m, ncols, rev);
+  warp_solve_loaded<T, G, MMAX, MAP, FULL>(b, sTri, sC, Bt, ldb, m, ncols, rev);
 }
 
 template <class T, int G, int MMAX, bool MAP, bool FULL = false>
@@ -276,10 +307,30 @@ __global__ void __launch_bounds__(32 * kWarpsSingle) small_single_kernel(const T
   T *sTri, *sC, *sR;
   smem_parts<T>(smem, sTri, sC, sR);
   const int m = FULL ? MMAX : m_;
-  const int rows_used = ((m + G - 1) / G) * G;
-  stage<T, MMAX, kWarpsSingle, MAP>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0, mp);
-  solve_tiles<T, G, MMAX, MAP, FULL>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsSingle, gridDim.x * kWarpsSingle,
-                                     mp.rev);
+  if constexpr (FULL && !MAP) {
+    // the warp's first column tile is loaded before staging, so its latency
+    // overlaps the staging (a one-pass staging with every triangle load in
+    // flight at once measured slower than this with warm caches: the kernel is
+    // bound by dependent FP64 work on one warp per sub-partition, not by memory)
+    constexpr int C = 32 / G;
+    const int ntiles = (n + C - 1) / C;
+    const int step = gridDim.x * kWarpsSingle;
+    const int t0 = blockIdx.x * kWarpsSingle + (threadIdx.x >> 5);
+    auto cols = [&](int t) { return (n - t * C) < C ? (n - t * C) : C; };
+    T b[MMAX / G];
+    if (t0 < ntiles) warp_load_b<T, G, MMAX, false, true>(b, B + (int64_t)t0 * C * ldb, ldb, m, cols(t0), 0);
+    stage<T, MMAX, kWarpsSingle, false>(sTri, sC, sR, A, lda, m, MMAX, alpha, unit != 0, mp);
+    for (int t = t0; t < ntiles; t += step) {
+      T *Bt = B + (int64_t)t * C * ldb;
+      if (t != t0) warp_load_b<T, G, MMAX, false, true>(b, Bt, ldb, m, cols(t), 0);
+      warp_solve_loaded<T, G, MMAX, false, true>(b, sTri, sC, Bt, ldb, m, cols(t), 0);
+    }
+  } else {
+    const int rows_used = ((m + G - 1) / G) * G;
+    stage<T, MMAX, kWarpsSingle, MAP>(sTri, sC, sR, A, lda, m, rows_used, alpha, unit != 0, mp);
+    solve_tiles<T, G, MMAX, MAP, FULL>(sTri, sC, B, ldb, m, n, blockIdx.x * kWarpsSingle,
+                                       gridDim.x * kWarpsSingle, mp.rev);
+  }
 }
 
 // ---------------------------------------------------------------------------

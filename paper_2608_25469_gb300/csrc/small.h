@@ -37,7 +37,9 @@ hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t 
                                         int skip_large = 0);
 
 // Column-packed varlen batch for the left / lower / no-transpose solve in
-// HSMA_C128 (packed.cu): schedule, prep and solve passes;
+// HSMA_C128 (packed.cu): schedule, prep and solve passes (a_packed: every A_i
+// is in LAPACK's packed lower storage, column c holding rows c .. m_i - 1, and
+// dlda is only validated, as for a square layout);
 // `scratch` holds hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m)
 // bytes (max_m: a bound on every m_i, 0 = 64; above 64, instances with
 // m > 64 are skipped without a status bit, as skip_large below).  Results
@@ -50,7 +52,7 @@ inline bool hsma_vbatched_packed_dtype(int dtype) { return dtype == HSMA_C128; }
 hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m, const int32_t *dm,
                                          const int32_t *dn, const double *alpha, const void *const *dA,
                                          const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
-                                         uint32_t *status, void *scratch, cudaStream_t st);
+                                         uint32_t *status, void *scratch, cudaStream_t st, int a_packed = 0);
 
 // dtypes the small kernels and the varlen batch handle
 inline bool hsma_small_dtype(int dtype) {

@@ -22,22 +22,37 @@ namespace {
 // tcgen05 BF16 x BF16 -> FP32 update:  C (M x N, column-major fp32) =
 // beta*C - A' B'^T with A' (M x K) and B' (N x K) row-major BF16 (K-major).
 // ---------------------------------------------------------------------------
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 4;
+// K-block of a pipeline stage: 64 BF16 values (128-byte rows, 128-byte
+// swizzle, four 48 KB stages), or 32 (64-byte rows and swizzle, nine 24 KB
+// stages: more bytes in flight behind the stage being multiplied).  Measured
+// on GB300 the 32-wide ring is 20-25% slower on every product (emulated FP64
+// 16384^2 solve 209 -> 258 ms, FP32-result 8192 x 4096 update 1.10 -> 1.20 ms),
+// so the products are not bound by how many bytes the ring keeps in flight.
+#ifndef HSMA_TC_BK
+#define HSMA_TC_BK 64
+#endif
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = HSMA_TC_BK;
+constexpr int TC_ROW_BYTES = TC_BK * 2;  // one K-row of a stage tile: the swizzle width
+static_assert(TC_ROW_BYTES == 64 || TC_ROW_BYTES == 128, "K-blocks of 32 or 64 BF16 values");
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_STAGES = TC_BK == 32 ? 9 : 4;
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;
+static_assert(TC_SMEM <= 227 * 1024 - 256, "stages fit the shared memory of one CTA");
+static_assert(TC_STAGE_BYTES % 1024 == 0, "every stage starts on a swizzle-pattern boundary");
 constexpr uint32_t TC_TMEM_COLS = 256;
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes in groups of 8 (1024 bytes apart).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major operand, rows of TC_ROW_BYTES in
+// groups of 8 (8 * TC_ROW_BYTES apart), swizzled over the row width
+// (layout codes: 2 = 128-byte, 4 = 64-byte swizzle).
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;              // leading-dimension offset (unused with this swizzle)
-  d |= (uint64_t)(1024u >> 4) << 32;    // stride between 8-row groups
-  d |= (uint64_t)1u << 46;              // descriptor version
-  d |= (uint64_t)2u << 61;              // 128-byte swizzle
+  d |= (uint64_t)1u << 16;                                // leading-dimension offset (unused when swizzled)
+  d |= (uint64_t)((8u * TC_ROW_BYTES) >> 4) << 32;        // stride between 8-row groups
+  d |= (uint64_t)1u << 46;                                // descriptor version
+  d |= (uint64_t)(TC_ROW_BYTES == 128 ? 2u : 4u) << 61;   // swizzle mode
   return d;
 }
 
@@ -81,7 +96,29 @@ struct TcArgs {
   const int *skip;  // device flag: when set, the launch does nothing
   unsigned int *err;
   uint64_t limit_ns;
+  // TC_F32 side outputs: BF16 splits of the stored values, the right operands
+  // of the next products (null: none)
+  __nv_bfloat16 *xs2;  // rows < rows2: [col][ld2] hi at k = row; terms2 = 3 adds lo at nb2 + row, hi at 2 nb2 + row
+  int ld2, nb2, terms2, rows2;
+  __nv_bfloat16 *xs3;  // rows r3 .. r3 + rows3 - 1: three exact slices [s][col][ld3] at k = row - r3, slice stride per3
+  int64_t per3;
+  int ld3, r3, rows3;
 };
+
+// x = hi + lo with hi, lo in BF16 (the split of the FP32-result products)
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// x = a + b + c exactly (24 bits in three BF16 slices)
+__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c) {
+  a = __float2bfloat16_rn(x);
+  float r = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r);
+  r -= __bfloat162float(b);
+  c = __float2bfloat16_rn(r);
+}
 
 // 32 lanes x 16 consecutive 32-bit tensor-memory columns into registers
 // (completion awaited separately with tcgen05.wait::ld).
@@ -226,7 +263,7 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
               }
               tc_fence_after();
               const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
-              const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TC_A_BYTES);
+              const uint64_t da = sw_desc(sa), db = sw_desc(sa + TC_A_BYTES);
 #pragma unroll
               for (int kk = 0; kk < TC_BK / 16; ++kk) {
                 asm volatile(
@@ -309,8 +346,26 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
               if (col < N) {
                 if constexpr (MODE == TC_F32) {
                   const float a = __uint_as_float(v[j]);
-                  __stcs(p.C32 + row + (int64_t)col * p.ldc,
-                         (p.beta == 1.0f) ? (old[j] - a) : fmaf(p.beta, old[j], -a));
+                  const float y = (p.beta == 1.0f) ? (old[j] - a) : fmaf(p.beta, old[j], -a);
+                  __stcs(p.C32 + row + (int64_t)col * p.ldc, y);
+                  if (p.xs2 != nullptr && row < p.rows2) {
+                    __nv_bfloat16 hi, lo;
+                    split_bf16(y, hi, lo);
+                    __nv_bfloat16 *o = p.xs2 + (int64_t)col * p.ld2 + row;
+                    o[0] = hi;
+                    if (p.terms2 == 3) {
+                      o[p.nb2] = lo;
+                      o[2 * p.nb2] = hi;
+                    }
+                  }
+                  if (p.xs3 != nullptr && row >= p.r3 && row < p.r3 + p.rows3) {
+                    __nv_bfloat16 x0, x1, x2;
+                    split3_bf16(y, x0, x1, x2);
+                    __nv_bfloat16 *o = p.xs3 + (int64_t)col * p.ld3 + (row - p.r3);
+                    o[0] = x0;
+                    o[p.per3] = x1;
+                    o[2 * p.per3] = x2;
+                  }
                 } else {
                   const double x = oz_scale(v[j], ushift + __ldg(p.cexp + col));
                   p.C64[row + (int64_t)col * p.ldc] = p.negate ? old[j] + x : old[j] - x;
@@ -336,7 +391,8 @@ __global__ void __launch_bounds__(32 * TC_WARPS, 1) tc_gemm_kernel(const __grid_
 }
 
 // 3-D tensor map over BF16 operand slices (K contiguous, rows, slice), one
-// box = 64 K-values x box_rows rows of one slice, 128-byte swizzle.
+// box = TC_BK K-values x box_rows rows of one slice, swizzled over its row
+// width as the shared-memory descriptor expects.
 bool make_slice_map(CUtensorMap *map, const void *base, uint64_t K, uint64_t rows, uint64_t slices,
                     uint32_t box_rows, uint64_t ld, uint64_t sst) {
   PFN_encodeTiled enc = hsma_encode_fn();
@@ -346,7 +402,8 @@ bool make_slice_map(CUtensorMap *map, const void *base, uint64_t K, uint64_t row
   const cuuint32_t box[3] = {(cuuint32_t)TC_BK, box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, TC_ROW_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

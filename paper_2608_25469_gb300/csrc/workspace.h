@@ -1,5 +1,7 @@
-// Internal workspace allocation: CUDA's stream-ordered allocator, with a
-// host-side fault injector for tests (HSMA_FAULT_ALLOC_AFTER=N makes every
+// Internal workspace allocation: CUDA's stream-ordered allocator, from a
+// per-device pool owned by the library that keeps up to 4 GiB of freed
+// workspace reserved between calls (the device's default pool under stream
+// capture), with a host-side fault injector for tests (HSMA_FAULT_ALLOC_AFTER=N makes every
 // allocation after the first N fail with HSMA_ERR_NO_MEMORY).
 #pragma once
 #include <cuda_runtime.h>

@@ -110,6 +110,42 @@ def test_poison_and_canaries(H, code):
     assert np.all(X0[:m] == 0) and np.all(np.isnan(X0[m:]))
 
 
+@pytest.mark.parametrize("code", [I.R64, I.C128, R32, C64])
+@pytest.mark.parametrize("unit", [False, True])
+def test_full_size_single_equals_other_variants(H, code, unit):
+    """m = 64 with the 32-row-group variant runs the full-size kernel (one-pass
+    staging, B loaded before it); every variant does the same multiply-adds per row in
+    the same order, so it equals the 8-row-group variant bit for bit.  Padding rows of
+    A and its upper triangle (and, for a unit diagonal, the diagonal) hold NaN and are
+    never read; padding rows of B are never written; n = 10000 gives some warps a
+    second column tile."""
+    m, pad = 64, 6
+    dt = {I.R64: np.float64, I.C128: np.complex128, R32: np.float32, C64: np.complex64}[code]
+    gcode = I.R64 if code in (I.R64, R32) else I.C128
+    alpha = 1.5 if gcode == I.R64 else 1.5 - 0.5j
+    A0 = I.gen_A(21, m, gcode).astype(dt)
+    A = np.full((m + pad, m), np.nan, dtype=dt, order="F")
+    A[:m] = A0
+    A[:m][np.triu_indices(m, 1)] = np.nan
+    if unit:
+        np.fill_diagonal(A[:m], np.nan)
+    for n in (1, 64, 300, 10000):
+        B0 = I.gen_B(21, m, n, gcode).astype(dt)
+        Bb = I.embed(B0, m + pad, fill=np.nan)
+        X = _solve_single(H, code, A, Bb, alpha, unit=unit, groups=32)
+        Y = _solve_single(H, code, A, Bb, alpha, unit=unit, groups=8)
+        assert np.all(np.isnan(X[m:])), n
+        assert np.array_equal(X[:m], Y[:m]), n
+        A1 = np.array(A0, order="F").astype(np.complex128 if gcode == I.C128 else np.float64)
+        A1[np.triu_indices(m, 1)] = 0
+        if unit:
+            np.fill_diagonal(A1, 1.0)
+        cols = slice(0, min(n, 300))
+        ref = oracle.solve(A1, np.asfortranarray(B0[:, cols].astype(A1.dtype)), alpha)
+        tol = TOL if code in (I.R64, I.C128) else 2e-5
+        assert oracle.forward_error(X[:m, cols].astype(ref.dtype), ref) <= tol, n
+
+
 def _config1(code=I.C128, batch=8192, seed=0):
     ms, ns = I.batched_sizes(seed, batch)
     As = [I.gen_A(seed, int(m), code, inst=b) for b, m in enumerate(ms)]

@@ -134,36 +134,44 @@ __global__ void __launch_bounds__(256) sgemm_scale_kernel(const float *__restric
 // A panel (rows x nb, column-major fp32, lda) -> A' rows x Kp row-major BF16:
 // terms 1: [hi], terms 3: [hi | hi | lo]; columns past terms*nb are zero.
 // One 32 x 32 tile (rows i0.., columns k0..) per CTA of 256 threads.
+// A tile of 32 rows x kPanelTileK columns of the panel: read as 32 columns
+// of 32 consecutive rows (128-byte loads), written as BF16 pairs of
+// consecutive K (128-byte stores; nb is even).
+constexpr int kPanelTileK = 64;
 __device__ __forceinline__ void convert_panel_tile(const float *__restrict__ A, int64_t lda, int rows, int nb,
                                                    int terms, int Kp, __nv_bfloat16 *out, int i0, int k0) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[kPanelTileK][33];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  for (int kk = ty; kk < 32; kk += 8) {
+  for (int kk = ty; kk < kPanelTileK; kk += 8) {
     const int i = i0 + tx, k = k0 + kk;
     tile[kk][tx] = (i < rows && k < nb) ? A[i + (int64_t)k * lda] : 0.0f;
   }
   __syncthreads();
+  const int k = k0 + 2 * tx;  // this lane's pair of K values
   for (int ii = ty; ii < 32; ii += 8) {
-    const int i = i0 + ii, k = k0 + tx;
+    const int i = i0 + ii;
     if (i >= rows) continue;
     __nv_bfloat16 *o = out + (int64_t)i * Kp;
     if (k < nb) {
-      __nv_bfloat16 hi, lo;
-      split_bf16(tile[tx][ii], hi, lo);
-      o[k] = hi;
+      __nv_bfloat16 h0, l0, h1, l1;
+      split_bf16(tile[2 * tx][ii], h0, l0);
+      split_bf16(tile[2 * tx + 1][ii], h1, l1);
+      const __nv_bfloat162 hi = __halves2bfloat162(h0, h1), lo = __halves2bfloat162(l0, l1);
+      *reinterpret_cast<__nv_bfloat162 *>(o + k) = hi;
       if (terms == 3) {
-        o[nb + k] = hi;
-        o[2 * nb + k] = lo;
+        *reinterpret_cast<__nv_bfloat162 *>(o + nb + k) = hi;
+        *reinterpret_cast<__nv_bfloat162 *>(o + 2 * nb + k) = lo;
       }
     }
     // zero padding columns [terms*nb, Kp)
-    for (int kp = terms * nb + k0 + tx; kp < Kp && k0 == 0; kp += 32) o[kp] = __float2bfloat16_rn(0.0f);
+    for (int kp = terms * nb + 2 * tx; kp < Kp && k0 == 0; kp += 64)
+      *reinterpret_cast<__nv_bfloat162 *>(o + kp) = __floats2bfloat162_rn(0.0f, 0.0f);
   }
 }
 
 __global__ void __launch_bounds__(256) convert_panel_kernel(const float *__restrict__ A, int64_t lda, int rows,
                                                             int nb, int terms, int Kp, __nv_bfloat16 *out) {
-  convert_panel_tile(A, lda, rows, nb, terms, Kp, out, blockIdx.x * 32, blockIdx.y * 32);
+  convert_panel_tile(A, lda, rows, nb, terms, Kp, out, blockIdx.x * 32, blockIdx.y * kPanelTileK);
 }
 
 // Every step's panel in one launch (blockIdx.z = step r < nblk - 1, whose
@@ -176,7 +184,8 @@ __global__ void __launch_bounds__(256) convert_panels_kernel(const float *__rest
   const int i0 = blockIdx.x * 32;
   if (i0 >= rows) return;  // uniform over the CTA
   const int64_t off = (r * m - (int64_t)nb * r * (r + 1) / 2) * Kp;
-  convert_panel_tile(A + (r0 + nb) + r0 * lda, lda, rows, nb, terms, Kp, panels + off, i0, blockIdx.y * 32);
+  convert_panel_tile(A + (r0 + nb) + r0 * lda, lda, rows, nb, terms, Kp, panels + off, i0,
+                     blockIdx.y * kPanelTileK);
 }
 
 // X_r (nb x n, column-major fp32, ldx) -> X' n x Kp row-major BF16:
@@ -251,6 +260,7 @@ struct R32Plan {
   __nv_bfloat16 *dslices = nullptr;
 };
 
+
 int r32_kd(int nb) { return round_up(nb, TC_BK); }
 
 size_t r32_dslices_elems(int nb, int64_t m) { return (size_t)((m + nb - 1) / nb) * 3 * nb * r32_kd(nb); }
@@ -315,8 +325,11 @@ __global__ void copy_f32_kernel(const float *__restrict__ src, int64_t lds, floa
   HSMA_FOR_RC(i, j, rows, cols) dst[i + j * ldd] = src[i + j * lds];
 }
 
+// Phase 1 of the FP32-result solve: the diagonal-block inverses, their
+// slices for the tensor-core solve products, and every update panel converted
+// to split BF16 in one launch.
 hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
-  hsma_status_t s = hsma_diag_inverse(HSMA_R32_BF16, P.nb, P.A, P.lda, P.m, P.unit, P.Dinv, st);
+  hsma_status_t s = hsma_r32_diag_inverse(P.nb, P.A, P.lda, P.m, P.unit, P.Dinv, st);
   if (s != HSMA_OK) return s;
   const int64_t nblk = (P.m + P.nb - 1) / P.nb;
   HsmaTraceScope ts("convert", st);
@@ -327,7 +340,8 @@ hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
   }
   if (!keep_panels || nblk < 2) return HSMA_OK;
   if (nblk - 1 > 65535) return HSMA_ERR_UNSUPPORTED;
-  const dim3 g((unsigned)((P.m - P.nb + 31) / 32), (unsigned)((P.nb + 31) / 32), (unsigned)(nblk - 1));
+  const dim3 g((unsigned)((P.m - P.nb + 31) / 32), (unsigned)((P.nb + kPanelTileK - 1) / kPanelTileK),
+               (unsigned)(nblk - 1));
   convert_panels_kernel<<<g, 256, 0, st>>>(P.A, P.lda, P.m, P.nb, P.terms, P.Kp, P.panels);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
@@ -421,7 +435,7 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
     if (!P.panels || !P.tc_solve) {
       HsmaTraceScope ts("convert", st);
       if (!P.panels) {
-        dim3 g1((rows + 31) / 32, (nb + 31) / 32);
+        dim3 g1((rows + 31) / 32, (nb + kPanelTileK - 1) / kPanelTileK);
         convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, nb, P.terms, Kp, Ap);
       }
       if (!P.tc_solve)

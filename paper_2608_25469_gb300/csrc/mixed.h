@@ -38,4 +38,11 @@ hsma_status_t hsma_c64_blocked(int nb, int panel_cols, const void *A, int64_t ld
 
 // The planner's choice for one solve with the given options (hsma_plan with
 // opts; api.cu).
+// FP32 inverses of the nb x nb diagonal blocks of L (m x m, lda) into Dinv
+// (ceil(m / nb) blocks of nb x nb, ld nb, zeros above each diagonal and
+// outside a partial block): 64 x 64 blocks by substitution, joined by doubling
+// when nb is a power of two >= 128 (r32_inverse.cu), else substitution at nb.
+hsma_status_t hsma_r32_diag_inverse(int nb, const float *A, int64_t lda, int64_t m, int unit, float *Dinv,
+                                    cudaStream_t st);
+
 hsma_status_t hsma_make_plan(int dtype, int64_t m, int64_t n, const hsma_opts_t *opts, hsma_plan_t *out);

@@ -90,3 +90,69 @@ def test_getrs_graph_replay_matches_eager():
             assert np.array_equal(got[b], ref[b]), b
     for b in range(0, bt.batch, 29):
         assert oracle.forward_error(got[b], oracle.getrs(LUs[b], pivs[b], Bs[b], alpha)) <= 1e-12, b
+
+
+def _capture_solve(H, code, A, B0, alpha, m, n, opts=None, info=None):
+    """The single solve on a copy of B0 captured into a CUDA graph; returns (graph, B)."""
+    import torch
+    B = B0.clone()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            H.hsma_trsm_llnn_ex(code, 0, m, n, alpha, A.data_ptr(), m, B.data_ptr(), m, int(s.cuda_stream),
+                                opts=opts, info=info)
+    torch.cuda.synchronize()
+    return g, B
+
+
+@pytest.mark.parametrize("m,n,nb", [(1500, 96, 512), (700, 33, 128)])
+def test_r32_mode_graph_replay_matches_eager(m, n, nb):
+    """The FP32-result solve captured into a CUDA graph: its panel conversion runs on
+    the library's side stream (forked and joined by events), its inverses by doubling;
+    every replay gives the eager result bit for bit."""
+    import torch
+    H = U.lib()
+    A64, B64 = I.gen_A(5, m, I.R64), I.gen_B(5, m, n, I.R64)
+    A = torch.from_numpy(np.ascontiguousarray(A64.T)).float().cuda()  # column-major m x m
+    B0 = torch.from_numpy(np.ascontiguousarray(B64.T)).float().cuda()
+    opts = H.Opts()
+    opts.nb = nb
+    eager = B0.clone()
+    H.hsma_trsm_llnn_ex(H.R32_BF16, 0, m, n, 1.5, A.data_ptr(), m, eager.data_ptr(), m, H.stream_ptr(), opts=opts)
+    torch.cuda.synchronize()
+    g, B = _capture_solve(H, H.R32_BF16, A, B0, 1.5, m, n, opts=opts)
+    for _ in range(2):
+        B.copy_(B0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(B, eager)
+    X = eager.double().cpu().numpy().T
+    assert oracle.forward_error(X, oracle.solve(A64.astype(np.float32).astype(np.float64),
+                                                B64.astype(np.float32).astype(np.float64), 1.5)) <= 2e-5
+
+
+def test_ir_mode_graph_replay_matches_eager():
+    """The FP64-result refinement captured into a CUDA graph: every refinement step is
+    recorded and the device skips those after convergence; a replay gives the eager
+    result bit for bit and FP64 accuracy."""
+    import torch
+    H = U.lib()
+    m, n = 900, 40
+    A64, B64 = I.gen_A(6, m, I.R64), I.gen_B(6, m, n, I.R64)
+    A = torch.from_numpy(np.ascontiguousarray(A64.T)).cuda()
+    B0 = torch.from_numpy(np.ascontiguousarray(B64.T)).cuda()
+    opts = H.Opts()
+    opts.ir_max_iter = 4
+    eager = B0.clone()
+    H.hsma_trsm_llnn_ex(H.R64_IR, 0, m, n, 1.0, A.data_ptr(), m, eager.data_ptr(), m, H.stream_ptr(), opts=opts)
+    torch.cuda.synchronize()
+    g, B = _capture_solve(H, H.R64_IR, A, B0, 1.0, m, n, opts=opts)
+    B.copy_(B0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(B, eager)
+    X = eager.cpu().numpy().T
+    assert oracle.forward_error(X, oracle.solve(A64, B64, 1.0)) <= 1e-12
+    assert H.hsma_device_status() == 0

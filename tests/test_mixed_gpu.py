@@ -67,7 +67,8 @@ def _r32(H, A64, B64, alpha, terms=0, nb=0):
     return H.from_device(dB).astype(np.float64)
 
 
-@pytest.mark.parametrize("m,n,nb", [(1000, 300, 128), (517, 77, 64), (64, 64, 64), (2048, 100, 256)])
+@pytest.mark.parametrize("m,n,nb", [(1000, 300, 128), (517, 77, 64), (64, 64, 64), (2048, 100, 256),
+                                     (1500, 37, 512), (777, 50, 256), (4096, 20, 512)])
 def test_r32_mode_accuracy(H, m, n, nb):
     A, B = I.gen_A(7, m, I.R64), I.gen_B(7, m, n, I.R64)
     X = _r32(H, A, B, 1.5, terms=3, nb=nb)

@@ -356,7 +356,14 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
   const int64_t rows_max = std::max<int64_t>(m - nb, 1);
   const size_t w_b = P.tc_solve ? 0 : sizeof(float) * (size_t)nb * n;
   const size_t a_b = P.panels ? 0 : sizeof(__nv_bfloat16) * (size_t)rows_max * Kp;
-  const size_t x_b = sizeof(__nv_bfloat16) * (size_t)n * Kp;
+  // Paired updates (tensor-core solve products with every panel converted up
+  // front): after an even block only the next block row takes X_r; after an
+  // odd block one product applies X_{r-1} and X_r to every row below (two
+  // slice pairs in one accumulator), so the trailing rows of B are read and
+  // written once per two blocks.  The two splits live in two buffers.
+  const bool pair = P.tc_solve && P.panels != nullptr;
+  const size_t x1_b = sizeof(__nv_bfloat16) * (size_t)n * Kp;
+  const size_t x_b = (pair ? 2 : 1) * x1_b;
   const int Kd = r32_kd(nb);
   const size_t x3_b = P.tc_solve ? sizeof(__nv_bfloat16) * 3 * (size_t)n * Kd : 0;
   auto al = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
@@ -409,7 +416,7 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
                                                                 skip);
         if ((s = hsma_from_cuda(cudaGetLastError())) != HSMA_OK) break;
       }
-      sa.xs2 = last ? nullptr : Xp;
+      sa.xs2 = last ? nullptr : Xp + (pair ? (r & 1) * (int64_t)n * Kp : 0);
       sa.ld2 = Kp;
       sa.nb2 = nb;
       sa.terms2 = P.terms;
@@ -447,8 +454,11 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
       }
     }
     TcArgs a{};
+    // paired: an even block updates its next block row only (the first rows
+    // of its panel), an odd one every row below with both blocks' products
+    const int upd_rows = pair && (r & 1) == 0 ? (int)std::min<int64_t>(nb, rows) : rows;
     // the next block row's slices for its solve product, when it is a full block
-    x3_ready = P.tc_solve && rows >= nb;
+    x3_ready = P.tc_solve && upd_rows >= nb;
     if (x3_ready) {
       a.xs3 = X3;
       a.per3 = n * (int64_t)Kd;
@@ -458,12 +468,37 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
     }
     a.C32 = B + r0 + sr;
     a.ldc = ldb;
-    a.beta = r == 0 ? alpha : 1.0f;
-    a.M = rows;
+    // alpha scales a row block at its first update: block 1 at r = 0, and
+    // (paired) the rows below block 1 at r = 1
+    a.beta = (r == 0 || (pair && r == 1)) ? alpha : 1.0f;
+    a.M = upd_rows;
     a.N = (int)n;
     a.K = Kp;
     a.skip = skip;
-    s = tc_gemm<TC_F32>(panel, 1, Xp, 1, a, "update_bf16", st);
+    if (pair && (r & 1) == 1) {
+      // panel r-1 from its row nb on and panel r cover the same rows, one
+      // uniform stride apart; X_{r-1} and X_r sit in the two split buffers
+      a.nunits = 1;
+      a.ubeg[0] = 0;
+      a.ubeg[1] = 2;
+      a.pa[0] = 0;
+      a.pb[0] = 0;
+      a.pa[1] = 1;
+      a.pb[1] = 1;
+      SliceLayout la, lb;
+      la.rows = rows;
+      la.kext = Kp;
+      la.ld = Kp;
+      la.sst = (int64_t)rows * Kp;
+      lb.rows = n;
+      lb.kext = Kp;
+      lb.ld = Kp;
+      lb.sst = n * (int64_t)Kp;
+      s = tc_gemm<TC_F32>(P.panels + panel_off(P, r - 1) + (size_t)nb * Kp, 2, Xp, 2, a, "update_bf16", st, la,
+                          lb);
+    } else {
+      s = tc_gemm<TC_F32>(panel, 1, Xp + (pair ? (r & 1) * (int64_t)n * Kp : 0), 1, a, "update_bf16", st);
+    }
   }
   hsma_status_t f = hsma_ws_free(ws, st);
   return s != HSMA_OK ? s : f;

@@ -356,12 +356,12 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
   const int64_t rows_max = std::max<int64_t>(m - nb, 1);
   const size_t w_b = P.tc_solve ? 0 : sizeof(float) * (size_t)nb * n;
   const size_t a_b = P.panels ? 0 : sizeof(__nv_bfloat16) * (size_t)rows_max * Kp;
-  // Paired updates (tensor-core solve products with every panel converted up
-  // front): after an even block only the next block row takes X_r; after an
-  // odd block one product applies X_{r-1} and X_r to every row below (two
-  // slice pairs in one accumulator), so the trailing rows of B are read and
-  // written once per two blocks.  The two splits live in two buffers.
-  const bool pair = P.tc_solve && P.panels != nullptr;
+  // Paired updates (every panel converted up front): after an even block only
+  // the next block row takes X_r; after an odd block one product applies
+  // X_{r-1} and X_r to every row below (two slice pairs in one accumulator),
+  // so the trailing rows of B are read and written once per two blocks.  The
+  // two splits live in two buffers.
+  const bool pair = P.panels != nullptr;
   const size_t x1_b = sizeof(__nv_bfloat16) * (size_t)n * Kp;
   const size_t x_b = (pair ? 2 : 1) * x1_b;
   const int Kd = r32_kd(nb);
@@ -446,7 +446,8 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
         convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, nb, P.terms, Kp, Ap);
       }
       if (!P.tc_solve)
-        convert_x_kernel<<<hsma_grid_rc(nb, n), 256, 0, st>>>(B + r0, ldb, nb, (int)n, P.terms, Kp, Xp, skip);
+        convert_x_kernel<<<hsma_grid_rc(nb, n), 256, 0, st>>>(B + r0, ldb, nb, (int)n, P.terms, Kp,
+                                                              Xp + (pair ? (r & 1) * (int64_t)n * Kp : 0), skip);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         s = hsma_from_cuda(e);

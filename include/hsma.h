@@ -33,9 +33,12 @@
  *  - A singular A (a zero on the diagonal) is not detected; IEEE infinities and
  *    NaNs propagate, as in BLAS.
  *  - Workspace (diagonal-block inverses, refinement copies, batch schedules)
- *    is taken from CUDA's stream-ordered allocator on `stream` and released on
- *    the same stream; HSMA_ERR_NO_MEMORY if that fails.  Nothing is allocated
- *    on the small path of hsma_trsm_llnn.
+ *    is taken from a stream-ordered memory pool the library keeps per device
+ *    (CUDA's default pool while `stream` is capturing a graph) on `stream`
+ *    and released on the same stream; released workspace stays reserved in
+ *    the pool, up to 4 GiB per device, for later calls.  HSMA_ERR_NO_MEMORY
+ *    if the allocation fails.  Nothing is allocated on the small path of
+ *    hsma_trsm_llnn.
  *  - CUDA errors surfacing at enqueue time return HSMA_ERR_CUDA.
  *  - Thread safety: calls on different streams may run concurrently; the
  *    tuning table is read-only after hsma_tuning_load.
@@ -363,10 +366,12 @@ HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host(int dtype, int diag, int32_t
  * j .. m_i - 1, one column after the other, m_i (m_i + 1) / 2 elements from
  * element offset h_offA[i]; offsets increase by at least that much).  Only
  * the triangle crosses the link (about half the bytes of a square A for the
- * batched sizes); it is expanded on the device into the square layout before
- * each chunk's solve (device workspace: the packed copy and the squares).
- * Results equal hsma_trsm_llnn_vbatched_host's on the same triangles, bit for
- * bit.  Other arguments, asynchrony and errors as hsma_trsm_llnn_vbatched_host.
+ * batched sizes).  HSMA_C128 batches read the packed triangles on the device
+ * as they are; the other dtypes expand them into the square layout before
+ * each chunk's solve (device workspace: the packed copy, and for those dtypes
+ * the squares).  Results equal hsma_trsm_llnn_vbatched_host's on the same
+ * triangles, bit for bit.  Other arguments, asynchrony and errors as
+ * hsma_trsm_llnn_vbatched_host.
  */
 HSMA_API hsma_status_t hsma_trsm_llnn_vbatched_host_tp(int dtype, int diag, int32_t batch, const int32_t *h_m,
                                                        const int32_t *h_n, const void *alpha, const void *hAp,

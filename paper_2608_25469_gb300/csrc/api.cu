@@ -385,18 +385,17 @@ hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int trans, int d
     if (r != HSMA_OK) return r;
   }
   void *scratch = nullptr;
-  // the paper's case in complex128 runs the column-packed batch (the FP64
-  // pipe binds, so full warp tiles pay); the other dtypes and variants the
-  // per-instance kernel (with its index map)
-  const bool packed = uplo == HSMA_LOWER && trans == HSMA_NO_TRANS && hsma_vbatched_packed_dtype(dtype) &&
-                      packed_enabled();
+  // complex128 runs the column-packed batch for every left-side variant (the
+  // FP64 pipe binds, so full warp tiles pay; the variants through the index
+  // map), the other dtypes the per-instance kernel (with the same map)
+  const bool packed = hsma_vbatched_packed_dtype(dtype) && packed_enabled();
   hsma_status_t s = hsma_ws_alloc(
       &scratch, packed ? hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m) : hsma_vbatched_scratch_bytes(batch),
       st);
   if (s != HSMA_OK) return s;
   if (packed)
     s = hsma_small_vbatched_packed(dtype, batch, max_m, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda,
-                                   d_B, d_ldb, diag == HSMA_UNIT, d_status, scratch, st);
+                                   d_B, d_ldb, diag == HSMA_UNIT, d_status, scratch, st, 0, uplo, trans);
   else
     s = hsma_small_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_A, d_lda, d_B, d_ldb,
                             diag == HSMA_UNIT, d_status, static_cast<int32_t *>(scratch), st, uplo, trans,
@@ -432,11 +431,41 @@ static hsma_status_t factor_solve_vbatched(int dtype, int32_t batch, const int32
     if (r != HSMA_OK) return r;
   }
   void *scratch = nullptr;
-  hsma_status_t s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
-  if (s != HSMA_OK) return s;
-  s = hsma_small_getrs_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_LU, d_lda, d_ipiv,
-                                d_B, d_ldb, d_status, static_cast<int32_t *>(scratch), st, chol, large ? 1 : 0);
-  hsma_status_t f = hsma_ws_free(scratch, st);
+  hsma_status_t s, f;
+  if (hsma_vbatched_packed_dtype(dtype) && packed_enabled()) {
+    // The row interchanges as their own pass, then the two triangular solves
+    // as separate launches of the column-packed batch: the lower factor (the
+    // paper's case), then the second factor through the index map (U, or
+    // L^H).  The same arithmetic as the fused kernel, bit for bit; faster,
+    // since the fused kernel cannot use the packed batch.
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const bool piv = !chol && d_ipiv != nullptr;
+    const size_t me_b = piv ? al(sizeof(int32_t) * (size_t)batch) : 0;
+    const size_t pk_b = al(hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m));
+    s = hsma_ws_alloc(&scratch, me_b + pk_b, st);
+    if (s != HSMA_OK) return s;
+    unsigned char *q = static_cast<unsigned char *>(scratch);
+    int32_t *m_eff = reinterpret_cast<int32_t *>(q);
+    const int32_t *ms = piv ? m_eff : d_m;
+    const double *al2 = static_cast<const double *>(alpha);
+    const bool azero = al2[0] == 0.0 && al2[1] == 0.0;
+    const double one[2] = {1.0, 0.0};
+    if (piv)
+      s = hsma_small_lu_pivots(dtype, batch, d_m, d_n, d_lda, d_ldb, d_LU, d_B, d_ipiv, m_eff, d_status, st);
+    if (s == HSMA_OK)
+      s = hsma_small_vbatched_packed(dtype, batch, max_m, ms, d_n, al2, d_LU, d_lda, d_B, d_ldb, chol ? 0 : 1,
+                                     d_status, q + me_b, st);
+    if (s == HSMA_OK && !azero)  // alpha = 0: X = 0 without reading the factors
+      s = hsma_small_vbatched_packed(dtype, batch, max_m, ms, d_n, one, d_LU, d_lda, d_B, d_ldb, 0, d_status,
+                                     q + me_b, st, 0, chol ? HSMA_LOWER : HSMA_UPPER,
+                                     chol ? HSMA_CONJ_TRANS : HSMA_NO_TRANS);
+  } else {
+    s = hsma_ws_alloc(&scratch, hsma_vbatched_scratch_bytes(batch), st);
+    if (s != HSMA_OK) return s;
+    s = hsma_small_getrs_vbatched(dtype, batch, d_m, d_n, static_cast<const double *>(alpha), d_LU, d_lda, d_ipiv,
+                                  d_B, d_ldb, d_status, static_cast<int32_t *>(scratch), st, chol, large ? 1 : 0);
+  }
+  f = hsma_ws_free(scratch, st);
   if (s == HSMA_OK && f == HSMA_OK && large)
     s = solve_large(hb, d_status, st, [&](size_t b) {
       return chol ? hsma_potrs(dtype, hb.m[b], hb.n[b], alpha, hb.A[b], hb.lda[b], hb.B[b], hb.ldb[b], stream,

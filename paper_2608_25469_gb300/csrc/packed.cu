@@ -33,6 +33,14 @@ namespace {
 
 constexpr int kPkWarps = 4;     // warps per CTA of the solve kernel (independent)
 constexpr int kPkMinBlocks = 3;  // resident CTAs per SM (register cap of the solve kernel)
+
+// Index map from the solved lower-triangular form onto the caller's operand
+// for the other left-side variants (the per-instance kernel's map): with rev,
+// row r of the form is row m-1-r of the operand and of B; with tr, A is read
+// transposed; with cj, conjugated.  The identity is the paper's case.
+struct PkMap {
+  int rev, tr, cj;
+};
 constexpr int kPkHeaderWords = 8;
 
 // Rows per lane group G of the packed solve: FP64 complex values take four
@@ -327,13 +335,13 @@ __device__ __forceinline__ int pk_load_groups(const unsigned char *scratch, cons
 // ---------------------------------------------------------------------------
 constexpr int kPkPrepWarps = 8;
 
-template <class T>
+template <class T, bool MAP>
 __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const int32_t *__restrict__ dm,
                                                                        const void *const *__restrict__ dA,
                                                                        const int32_t *__restrict__ dlda,
                                                                        const unsigned char *__restrict__ scratch,
                                                                        PkLayout L, T *stage, T alpha, int unit,
-                                                                       int a_packed) {
+                                                                       int a_packed, PkMap mp) {
   using E = Elem<T>;
   __shared__ __align__(16) int32_t sgrp[64 * kPkGroupWords];
   __shared__ T sR[kPkPrepWarps][64];
@@ -353,17 +361,31 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
     const int b = inst[p];
     const T *A = static_cast<const T *>(dA[b]);
     const int64_t lda = dlda[b];
-    // element (r, c), r >= c: column-major with lda, or (a_packed) LAPACK's
-    // packed lower storage, column c holding rows c .. m-1 from c (2m - c + 1) / 2
-    auto at = [&](int r, int c) -> const T * {
-      return a_packed ? A + (int64_t)c * (2 * m - c + 1) / 2 + (r - c) : A + r + (int64_t)c * lda;
+    // element (r, c), r >= c, of the lower-triangular form: from the operand
+    // through the index map (column-major with lda), or (a_packed, identity
+    // map only) LAPACK's packed lower storage, column c holding rows c .. m-1
+    // from c (2m - c + 1) / 2
+    auto at = [&](int r, int c) -> T {
+      if (a_packed) return E::ld(A + (int64_t)c * (2 * m - c + 1) / 2 + (r - c));
+      if constexpr (!MAP) return E::ld(A + r + (int64_t)c * lda);
+      int pr = mp.rev ? m - 1 - r : r, pc = mp.rev ? m - 1 - c : c;
+      if (mp.tr) {
+        const int t = pr;
+        pr = pc;
+        pc = t;
+      }
+      T v = E::ld(A + pr + (int64_t)pc * lda);
+      if constexpr (E::kComplex) {
+        if (mp.cj) v.im = -v.im;
+      }
+      return v;
     };
     T *tri = stage + off;
     T *sc = tri + pk_tri_elems(rows);
     __syncwarp();
     for (int r = lane; r < rows; r += 32) {  // warp-uniform trip count per 32 rows
       T rv = E::one();
-      if (r < m && !unit) rv = E::recip(E::ld(at(r, r)));
+      if (r < m && !unit) rv = E::recip(at(r, r));
       rinv[r] = rv;
       sc[r] = r < m ? E::mul(alpha, rv) : E::zero();
     }
@@ -387,7 +409,7 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
       for (int u = 0; u < 4; ++u) {
         const int q = q0 + u * 32 + lane;
         rr[u] = i + 1 + loc;
-        vv[u] = (q < total && rr[u] < m) ? E::ld(at(rr[u], i)) : E::zero();
+        vv[u] = (q < total && rr[u] < m) ? at(rr[u], i) : E::zero();
         advance(32);
       }
 #pragma unroll
@@ -414,18 +436,22 @@ __device__ __forceinline__ cplx pk_ld<cplx>(const cplx *p) {
 // 3. Solve.  A warp tile: C = 32/G columns of one m's stream; lane l holds
 // column c = l / G of the tile, rows g + t*G (g = l % G) in register slot t.
 // ---------------------------------------------------------------------------
-template <class T, int G, int MMAX>
+template <class T, int G, int MMAX, bool REV>
 __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bool active, int m, int rows,
                                             bool azero) {
   using E = Elem<T>;
   constexpr int R = MMAX / G;
   const int lane = threadIdx.x & 31;
   const int g = lane % G, c = lane / G;
+  // row r = g + t G of the form is row r of B, or (REV) row m - 1 - r: one
+  // base per lane and a compile-time step per slot t
+  T *const Bg = REV ? Bp + (m - 1 - g) : Bp + g;
+  constexpr int kStep = REV ? -G : G;
   if (azero) {
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       const int r = g + t * G;
-      if (t * G < m && active && r < m) E::st(Bp + r, E::zero());
+      if (t * G < m && active && r < m) E::st(Bg + t * kStep, E::zero());
     }
     return;
   }
@@ -435,7 +461,7 @@ __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bo
     const int r = g + t * G;
     s[t] = E::zero();
     if (t * G < m) {
-      if (active && r < m) s[t] = E::mul(pk_ld(sc + r), E::ld(Bp + r));
+      if (active && r < m) s[t] = E::mul(pk_ld(sc + r), E::ld(Bg + t * kStep));
     }
   }
   int64_t base = -1;  // column i of the staged triangle starts at tri + base + i + 1
@@ -463,12 +489,12 @@ __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bo
   for (int t = 0; t < R; ++t) {
     const int r = g + t * G;
     if (t * G < m) {
-      if (active && r < m) E::st(Bp + r, s[t]);
+      if (active && r < m) E::st(Bg + t * kStep, s[t]);
     }
   }
 }
 
-template <class T>
+template <class T, bool REV>
 __global__ void __launch_bounds__(32 * kPkWarps, kPkMinBlocks) packed_solve_kernel(
     void *const *__restrict__ dB, const int32_t *__restrict__ dldb, unsigned char *scratch, PkLayout L,
     const T *__restrict__ stage, int azero) {
@@ -515,22 +541,22 @@ __global__ void __launch_bounds__(32 * kPkWarps, kPkMinBlocks) packed_solve_kern
     const T *sc = tri + pk_tri_elems(rows);
     if constexpr (two) {
       if (G == 1)
-        packed_tile<T, 1, 32>(tri, sc, Bp, active, m, rows, azero != 0);
+        packed_tile<T, 1, 32, REV>(tri, sc, Bp, active, m, rows, azero != 0);
       else
-        packed_tile<T, 2, 64>(tri, sc, Bp, active, m, rows, azero != 0);
+        packed_tile<T, 2, 64, REV>(tri, sc, Bp, active, m, rows, azero != 0);
     } else {
-      packed_tile<T, 1, 64>(tri, sc, Bp, active, m, rows, azero != 0);
+      packed_tile<T, 1, 64, REV>(tri, sc, Bp, active, m, rows, azero != 0);
     }
   }
 }
 
-template <class T>
+template <class T, bool REV>
 int packed_grid(int dev) {
   static int cached[64] = {0};
   if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
   int nsm = 0, per_sm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, packed_solve_kernel<T>, 32 * kPkWarps, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, packed_solve_kernel<T, REV>, 32 * kPkWarps, 0);
   const int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (dev >= 0 && dev < 64) cached[dev] = grid;
   return grid;
@@ -548,7 +574,7 @@ int sm_count(int dev) {
 template <class T>
 hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int32_t *dn, const double *alpha,
                           const void *const *dA, const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
-                          uint32_t *status, void *scratch, cudaStream_t st, int a_packed) {
+                          uint32_t *status, void *scratch, cudaStream_t st, int a_packed, PkMap mp) {
   int dev = 0;
   HSMA_CUDA_TRY(cudaGetDevice(&dev));
   const PkLayout L = pk_layout(batch, max_m, (int)sizeof(T), pk_two_lanes<T>());
@@ -577,12 +603,23 @@ hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int
     int blocks = (batch + kPkPrepWarps - 1) / kPkPrepWarps;
     if (blocks > 4 * nsm) blocks = 4 * nsm;
     HsmaTraceScope ts("vbatched_prep", st);
-    packed_prep_kernel<T><<<blocks, 32 * kPkPrepWarps, 0, st>>>(dm, dA, dlda, scr, L, stage, al, unit, a_packed);
+    const bool mapped = mp.rev || mp.tr || mp.cj;
+    if (mapped)
+      packed_prep_kernel<T, true><<<blocks, 32 * kPkPrepWarps, 0, st>>>(dm, dA, dlda, scr, L, stage, al, unit,
+                                                                        a_packed, mp);
+    else
+      packed_prep_kernel<T, false><<<blocks, 32 * kPkPrepWarps, 0, st>>>(dm, dA, dlda, scr, L, stage, al, unit,
+                                                                         a_packed, mp);
     HSMA_CUDA_TRY(cudaGetLastError());
   }
   {
     HsmaTraceScope ts("vbatched_solve", st);
-    packed_solve_kernel<T><<<packed_grid<T>(dev), 32 * kPkWarps, 0, st>>>(dB, dldb, scr, L, stage, azero ? 1 : 0);
+    if (mp.rev)
+      packed_solve_kernel<T, true><<<packed_grid<T, true>(dev), 32 * kPkWarps, 0, st>>>(dB, dldb, scr, L, stage,
+                                                                                     azero ? 1 : 0);
+    else
+      packed_solve_kernel<T, false><<<packed_grid<T, false>(dev), 32 * kPkWarps, 0, st>>>(dB, dldb, scr, L, stage,
+                                                                                       azero ? 1 : 0);
   }
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
@@ -598,11 +635,17 @@ size_t hsma_vbatched_packed_scratch_bytes(int dtype, int32_t batch, int32_t max_
 hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m, const int32_t *dm,
                                          const int32_t *dn, const double *alpha, const void *const *dA,
                                          const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
-                                         uint32_t *status, void *scratch, cudaStream_t st, int a_packed) {
+                                         uint32_t *status, void *scratch, cudaStream_t st, int a_packed, int uplo,
+                                         int trans) {
+  // the per-instance kernel's map: an upper operand (after op) is solved with
+  // its rows and columns reversed
+  const bool op_lower = (uplo == HSMA_LOWER) != (trans != HSMA_NO_TRANS);
+  const PkMap mp{op_lower ? 0 : 1, trans != HSMA_NO_TRANS ? 1 : 0, trans == HSMA_CONJ_TRANS ? 1 : 0};
+  if (a_packed && (mp.rev || mp.tr)) return HSMA_ERR_UNSUPPORTED;
   switch (dtype) {
     case HSMA_C128:
       return packed_impl<cplx>(batch, max_m, dm, dn, alpha, dA, dlda, dB, dldb, unit, status, scratch, st,
-                               a_packed);
+                               a_packed, mp);
     default:
       return HSMA_ERR_UNSUPPORTED;
   }

@@ -824,6 +824,78 @@ static hsma_status_t getrs_impl(int32_t batch, const int32_t *dm, const int32_t 
   return HSMA_OK;
 }
 
+namespace {
+
+// Row interchanges of a batch of LU-factor solves ahead of their two
+// triangular solves (one warp per instance): P^T B by LAPACK's ipiv (row k
+// swapped with row ipiv[k] - 1, k = 0, 1, ... in order), and the instance's
+// size for the solves in m_eff: its m, or 0 when a pivot is out of range
+// (HSMA_DEVERR_BAD_PIVOT; B untouched and both solves skip the instance).
+// Instances the solves reject (sizes, pointers) or leave to the blocked path
+// (m > 64) are not permuted here.
+template <class T>
+__global__ void __launch_bounds__(256) lu_pivots_kernel(int32_t batch, const int32_t *__restrict__ dm,
+                                                        const int32_t *__restrict__ dn,
+                                                        const int32_t *__restrict__ dlda,
+                                                        const int32_t *__restrict__ dldb,
+                                                        const void *const *__restrict__ dA, void *const *dB,
+                                                        const int32_t *const *__restrict__ dipiv, int32_t *m_eff,
+                                                        uint32_t *status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < batch; b += nw) {
+    const int m = dm[b], n = dn[b];
+    if (lane == 0) m_eff[b] = m;
+    const int32_t *ipiv = dipiv != nullptr ? dipiv[b] : nullptr;
+    if (ipiv == nullptr || m <= 0 || n <= 0 || m > 64 || dlda[b] < m || dldb[b] < m || dA[b] == nullptr ||
+        dB[b] == nullptr)
+      continue;
+    bool bad = false;
+    for (int k = lane; k < m; k += 32) bad |= ipiv[k] <= k || ipiv[k] > m;  // LAPACK: ipiv[k] in [k+1, m]
+    if (__any_sync(0xffffffffu, bad)) {
+      if (lane == 0) {
+        m_eff[b] = 0;
+        if (status != nullptr) atomicOr(status, HSMA_DEVERR_BAD_PIVOT);
+      }
+      continue;
+    }
+    T *B = static_cast<T *>(dB[b]);
+    const int64_t ldb = dldb[b];
+    for (int k = 0; k < m; ++k) {
+      const int p = ipiv[k] - 1;
+      if (p == k) continue;
+      for (int j = lane; j < n; j += 32) {
+        const T t = B[k + j * ldb];
+        B[k + j * ldb] = B[p + j * ldb];
+        B[p + j * ldb] = t;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+hsma_status_t hsma_small_lu_pivots(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
+                                   const int32_t *dlda, const int32_t *dldb, const void *const *dA,
+                                   void *const *dB, const int32_t *const *dipiv, int32_t *m_eff, uint32_t *status,
+                                   cudaStream_t st) {
+  if (batch <= 0) return HSMA_OK;
+  int dev = 0, nsm = 0;
+  HSMA_CUDA_TRY(cudaGetDevice(&dev));
+  HSMA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = (int)std::min<int64_t>(((int64_t)batch + 7) / 8, 4 * (int64_t)nsm);
+  HsmaTraceScope ts("vbatched_schedule", st);
+  if (dtype == HSMA_C128)
+    lu_pivots_kernel<cplx><<<grid, 256, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, dipiv, m_eff, status);
+  else if (dtype == HSMA_C64)
+    lu_pivots_kernel<cplxf><<<grid, 256, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, dipiv, m_eff, status);
+  else if (dtype == HSMA_R32)
+    lu_pivots_kernel<float><<<grid, 256, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, dipiv, m_eff, status);
+  else
+    lu_pivots_kernel<double><<<grid, 256, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, dipiv, m_eff, status);
+  return hsma_from_cuda(cudaGetLastError());
+}
+
 hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
                                         const double *alpha, const void *const *dLU, const int32_t *dlda,
                                         const int32_t *const *dipiv, void *const *dB, const int32_t *dldb,

@@ -36,10 +36,22 @@ hsma_status_t hsma_small_getrs_vbatched(int dtype, int32_t batch, const int32_t 
                                         uint32_t *status, int32_t *scratch, cudaStream_t st, int chol = 0,
                                         int skip_large = 0);
 
+// Row interchanges of a varlen batch of LU-factor solves (LAPACK ipiv, one
+// pointer per instance, dipiv may be NULL) applied to B ahead of two separate
+// triangular-solve launches, and the sizes those launches take: m_eff[b] is
+// m_b, or 0 when a pivot of instance b is out of range (flagged
+// HSMA_DEVERR_BAD_PIVOT, B untouched).  m_eff: batch int32 of device memory.
+hsma_status_t hsma_small_lu_pivots(int dtype, int32_t batch, const int32_t *dm, const int32_t *dn,
+                                   const int32_t *dlda, const int32_t *dldb, const void *const *dA,
+                                   void *const *dB, const int32_t *const *dipiv, int32_t *m_eff, uint32_t *status,
+                                   cudaStream_t st);
+
 // Column-packed varlen batch for the left / lower / no-transpose solve in
 // HSMA_C128 (packed.cu): schedule, prep and solve passes (a_packed: every A_i
 // is in LAPACK's packed lower storage, column c holding rows c .. m_i - 1, and
-// dlda is only validated, as for a square layout);
+// dlda is only validated, as for a square layout; uplo / trans select the
+// left-side variant through the per-instance kernel's index map, identity
+// only with a_packed);
 // `scratch` holds hsma_vbatched_packed_scratch_bytes(dtype, batch, max_m)
 // bytes (max_m: a bound on every m_i, 0 = 64; above 64, instances with
 // m > 64 are skipped without a status bit, as skip_large below).  Results
@@ -52,7 +64,8 @@ inline bool hsma_vbatched_packed_dtype(int dtype) { return dtype == HSMA_C128; }
 hsma_status_t hsma_small_vbatched_packed(int dtype, int32_t batch, int32_t max_m, const int32_t *dm,
                                          const int32_t *dn, const double *alpha, const void *const *dA,
                                          const int32_t *dlda, void *const *dB, const int32_t *dldb, int unit,
-                                         uint32_t *status, void *scratch, cudaStream_t st, int a_packed = 0);
+                                         uint32_t *status, void *scratch, cudaStream_t st, int a_packed = 0,
+                                         int uplo = HSMA_LOWER, int trans = HSMA_NO_TRANS);
 
 // dtypes the small kernels and the varlen batch handle
 inline bool hsma_small_dtype(int dtype) {

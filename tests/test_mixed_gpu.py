@@ -185,3 +185,31 @@ def test_ir_mode_config3_sampled(H):
     err = oracle.forward_error(X[:, cols], ref)
     assert err <= 1e-12, err
     assert H.hsma_device_status() == 0
+
+
+def test_workspace_pool_does_not_grow(H):
+    """Workspace comes from the library's stream-ordered pool: after the first call,
+    repeated FP32-result and refinement solves with a synchronisation between them
+    take no further device memory (released workspace is reused, nothing leaks)."""
+    import torch
+    m, n = 1536, 200
+    A64, B64 = I.gen_A(9, m, I.R64), I.gen_B(9, m, n, I.R64)
+    A32 = torch.from_numpy(np.ascontiguousarray(A64.T)).float().cuda()
+    B32 = torch.from_numpy(np.ascontiguousarray(B64.T)).float().cuda()
+    A = torch.from_numpy(np.ascontiguousarray(A64.T)).cuda()
+    B0 = torch.from_numpy(np.ascontiguousarray(B64.T)).cuda()
+    X32, X = B32.clone(), B0.clone()
+
+    def solve_both():
+        X32.copy_(B32)
+        X.copy_(B0)
+        H.hsma_trsm_llnn_ex(H.R32_BF16, 0, m, n, 1.0, A32.data_ptr(), m, X32.data_ptr(), m, H.stream_ptr())
+        H.hsma_trsm_llnn_ex(H.R64_IR, 0, m, n, 1.0, A.data_ptr(), m, X.data_ptr(), m, H.stream_ptr())
+        torch.cuda.synchronize()
+
+    solve_both()
+    free_after_first = torch.cuda.mem_get_info()[0]
+    for _ in range(8):
+        solve_both()
+    assert torch.cuda.mem_get_info()[0] >= free_after_first - (64 << 20)
+    assert oracle.forward_error(X.cpu().numpy().T, oracle.solve(A64, B64, 1.0)) <= 1e-12

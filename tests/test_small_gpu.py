@@ -379,6 +379,53 @@ def test_packed_batch_equals_per_instance_kernel(H, code, mix):
         assert oracle.forward_error(G[b].astype(refs[k].dtype), refs[k]) <= tol, (mix, b)
 
 
+def _trsm_vbatched(H, code, uplo, trans, unit, As, Bs, alpha):
+    import torch
+    bt = U.Batch(As, Bs)
+    a = bt.args()
+    H.hsma_trsm_vbatched(code, H.LEFT, uplo, trans, int(unit), bt.batch, a[0], a[1], alpha, a[2], a[3], a[4], a[5],
+                         64, 0, bt.d_status.data_ptr(), H.stream_ptr())
+    torch.cuda.synchronize()
+    assert bt.status() == 0
+    return bt.results()
+
+
+@pytest.mark.parametrize("code", [I.R64, I.C128])
+@pytest.mark.parametrize("uplo,trans", [(1, 0), (0, 1), (0, 2), (1, 1), (1, 2)])
+@pytest.mark.parametrize("unit", [False, True])
+def test_mapped_batch_equals_explicit_lower_system(H, code, uplo, trans, unit):
+    """Every left-side variant of the varlen batch reads A and B through an index map: op(A)
+    (transpose, conjugate transpose), reversed in rows and columns when op(A) is upper.  Its
+    results equal the lower / no-transpose batch on that system written out explicitly
+    (J op(A) J, J B; X = J X'), bit for bit.  The triangle the variant does not reference
+    holds NaN, so it is never read."""
+    rng = np.random.default_rng(60 + 10 * uplo + 3 * trans + unit)
+    sizes = [(int(m), int(n)) for m, n in rng.integers(1, 65, (700, 2))] + [(m, 3) for m in range(1, 65)]
+    alpha = 1.25 if code == I.R64 else 1.25 - 0.75j
+    As, Bs = _mix(code, sizes, seed=61 + uplo + trans)
+    op_lower = (uplo == 0) != (trans != 0)
+    Am, Ae, Be = [], [], []
+    for A, B in zip(As, Bs):
+        T = A if uplo == 0 else np.asfortranarray(A.T)  # the referenced triangle in place
+        T = np.array(T, order="F")
+        T[np.triu_indices(T.shape[0], 1) if uplo == 0 else np.tril_indices(T.shape[0], -1)] = np.nan
+        Am.append(T)
+        op = T if trans == 0 else (T.T if trans == 1 else T.conj().T)
+        Ae.append(np.asfortranarray(op if op_lower else op[::-1, ::-1]))
+        Be.append(np.asfortranarray(B if op_lower else B[::-1]))
+    got = _trsm_vbatched(H, code, uplo, trans, unit, Am, Bs, alpha)
+    ref = _noalloc(H, code, Ae, Be, alpha, unit=unit)
+    assert ref.status() == 0
+    R = ref.results()
+    for b in range(len(As)):
+        X = R[b] if op_lower else R[b][::-1]
+        assert np.array_equal(got[b], X), (b, sizes[b])
+        assert not np.isnan(got[b]).any(), b
+    for b in range(0, len(As), 97):
+        refo = oracle.solve_general(np.nan_to_num(Am[b]), Bs[b], alpha, 0, uplo, trans, unit)
+        assert oracle.forward_error(got[b], refo) <= TOL, b
+
+
 @pytest.mark.parametrize("code", [I.R64, I.C128])
 def test_packed_batch_padding_unit_and_zero_alpha(H, code):
     """lda, ldb > m: padding rows of B stay untouched and padding rows of A are never
@@ -504,7 +551,7 @@ def _pack_lower(A):
     return np.concatenate([A[j:m, j] for j in range(m)]) if m else np.zeros(0, A.dtype)
 
 
-@pytest.mark.parametrize("code", [I.R64, I.C128, C64])
+@pytest.mark.parametrize("code", [I.R64, I.C128, C64, R32])
 @pytest.mark.parametrize("chunks", [0, 3])
 def test_host_batch_packed_triangles_equal_square_layout(H, code, chunks):
     """The host-buffer batch with A as packed lower triangles gives the square-layout call's
@@ -515,7 +562,7 @@ def test_host_batch_packed_triangles_equal_square_layout(H, code, chunks):
     As, Bs = _mix(code, [(max(m, 1), max(n, 1)) for m, n in sizes], seed=61)
     As = [a[:m, :m] if m else np.zeros((0, 0), a.dtype) for a, (m, _) in zip(As, sizes)]
     Bs = [b[:m, :n] for b, (m, n) in zip(Bs, sizes)]
-    alpha = 1.5 if code == I.R64 else 1.5 - 0.5j
+    alpha = 1.5 if code in (I.R64, R32) else 1.5 - 0.5j
     ms = np.array([m for m, _ in sizes], dtype=np.int32)
     ns = np.array([n for _, n in sizes], dtype=np.int32)
     gap = 3

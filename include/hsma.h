@@ -258,16 +258,19 @@ HSMA_API hsma_status_t hsma_trsm_vbatched(int dtype, int side, int uplo, int tra
                                           void *stream);
 
 /*
- * Varlen batch of LU-factor solves in ONE launch: the small solve fused with
- * its consumer, for the LU factorisations that motivate the paper (Section 1;
- * fusion at small scales is its future work, Section 6).  Instance i holds
+ * Varlen batch of LU-factor solves: the small solve fused with its consumer,
+ * for the LU factorisations that motivate the paper (Section 1; fusion at
+ * small scales is its future work, Section 6).  Instance i holds
  * A_i = P_i L_i U_i as LAPACK getrf leaves it: one m_i x m_i column-major
  * array (ld d_lda[i]) with L_i's multipliers below the diagonal (unit
  * diagonal, not stored) and U_i on and above it.  Then
  *     X_i = U_i^{-1} L_i^{-1} P_i^T (alpha B_i)   overwrites B_i,
- * i.e. A_i X_i = alpha B_i.  Per instance one CTA applies the row
- * interchanges, solves with L_i and then with U_i (the upper solve through
- * the left / upper index map); the intermediate stays in that CTA's cache.
+ * i.e. A_i X_i = alpha B_i.  HSMA_C128: one pass applies the row
+ * interchanges, then the two triangular solves run as two launches of the
+ * column-packed batch (the upper solve through the left / upper index map).
+ * The other dtypes: per instance one CTA applies the interchanges, solves
+ * with L_i and then with U_i, in ONE launch for the batch; the intermediate
+ * stays in that CTA's cache.
  *
  * d_ipiv: NULL (no interchanges) or a DEVICE array of `batch` DEVICE pointers,
  *        each to instance i's m_i int32 pivots in LAPACK's convention
@@ -307,8 +310,8 @@ HSMA_API hsma_status_t hsma_getrs_vbatched(int dtype, int32_t batch, const int32
  * asynchronous on `stream`; errors as hsma_trsm.
  */
 /*
- * Varlen batch of Cholesky-factor solves in ONE launch (the same fused
- * kernel): instance i holds A_i = L_i L_i^H's lower factor L_i as LAPACK
+ * Varlen batch of Cholesky-factor solves (the same kernels as
+ * hsma_getrs_vbatched without its interchange pass): instance i holds A_i = L_i L_i^H's lower factor L_i as LAPACK
  * potrf leaves it (uplo = lower; the strict upper triangle is not read), and
  *     X_i = L_i^{-H} L_i^{-1} (alpha B_i)   overwrites B_i
  * (L_i^T for the real dtypes).  The second solve reads L_i through the

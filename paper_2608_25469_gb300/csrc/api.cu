@@ -18,6 +18,7 @@
 #include "gen.h"
 #include "mixed.h"
 #include "small.h"
+#include "trace.h"
 #include "workspace.h"
 
 namespace {
@@ -351,6 +352,7 @@ hsma_status_t solve_large(const HostBatch &h, uint32_t *d_status, cudaStream_t s
   }
   if (s == HSMA_OK && bad != 0 && d_status != nullptr) {
     or_status_kernel<<<1, 1, 0, st>>>(d_status, bad);
+    hsma_count_launches(1);
     s = hsma_from_cuda(cudaGetLastError());
   }
   return s;

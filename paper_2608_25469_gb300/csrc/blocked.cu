@@ -605,7 +605,7 @@ hsma_status_t blocked_impl(const HsmaBlockedCfg &cfg, const T *A, int64_t lda, T
   // first block, written by the previous trailing update for the others, so
   // the solve product can write X_r straight into B_r.
   if (s == HSMA_OK) {
-    HsmaTraceScope ts("copy", st);
+    HsmaTraceScope ts("copy", st, 0);
     const int s0 = (int)std::min<int64_t>(nb, m);
     cudaError_t e = cudaMemcpy2DAsync(W, sizeof(T) * nb, B, sizeof(T) * ldb, sizeof(T) * s0, n,
                                       cudaMemcpyDeviceToDevice, st);

@@ -72,7 +72,7 @@ hsma_status_t permute_rows(const int32_t *ipiv, int64_t m, int64_t n, T *B, int6
   int32_t *perm = static_cast<int32_t *>(ws);
   T *W = reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + perm_b);
   {
-    HsmaTraceScope ts("interchange", st);
+    HsmaTraceScope ts("interchange", st, 2);
     const size_t smem = m <= kPermSmemMax ? sizeof(int32_t) * 2 * (size_t)m : 0;
     static DeviceFlags attr;
     if (!attr.test()) {

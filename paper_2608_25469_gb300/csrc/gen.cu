@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "gen.h"
+#include "trace.h"
 
 namespace {
 
@@ -84,6 +85,7 @@ hsma_status_t hsma_gen_launch(int dtype, int kind, uint64_t seed, int64_t inst, 
   if (blocks > (int64_t)nsm[dev] * 64) blocks = (int64_t)nsm[dev] * 64;
   gen_kernel<<<(unsigned)blocks, 256, 0, st>>>(dtype == HSMA_C128, kind, kre, kim, ukre, ukim, m, cols,
                                                static_cast<double *>(dst), ld);
+  hsma_count_launches(1);
   HSMA_CUDA_TRY(cudaGetLastError());
   return HSMA_OK;
 }

@@ -176,7 +176,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
     for (int k = 0; k < kStreams && s == HSMA_OK; ++k) s = fail(cudaStreamWaitEvent(ss[k], start, 0));
     if (s != HSMA_OK) break;
     {
-      HsmaTraceScope ts("host_h2d", s_in);
+      HsmaTraceScope ts("host_h2d", s_in, 0);
       if ((s = fail(cudaMemcpyAsync(gm, h_m, sizeof(int32_t) * batch, cudaMemcpyHostToDevice, s_in))) != HSMA_OK)
         break;
       if ((s = fail(cudaMemcpyAsync(gn, h_n, sizeof(int32_t) * batch, cudaMemcpyHostToDevice, s_in))) != HSMA_OK)
@@ -189,7 +189,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
         break;
     }
     if (expand) {
-      HsmaTraceScope ts("host_h2d", s_in);
+      HsmaTraceScope ts("host_h2d", s_in, 0);
       if ((s = fail(cudaMemcpyAsync(gSq, sq.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice, s_in))) !=
           HSMA_OK)
         break;
@@ -197,6 +197,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
     chunk_meta_kernel<<<(batch + 255) / 256, 256, 0, s_in>>>(batch, gm, expand ? gSq : goA, goB,
                                                              expand ? 0 : h_offA[0], h_offB[0], dS, dB, es, pA, pB,
                                                              gld);
+    hsma_count_launches(1);
     if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     for (int c = 0; c < nch && s == HSMA_OK; ++c) {
       const int32_t b = c * per, e = std::min(batch, b + per), cnt = e - b;
@@ -209,7 +210,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
       const int64_t na = h_offA[e - 1] + a_elems(h_m[e - 1], tri) - h_offA[b];
       const int64_t nbx = h_offB[e - 1] + (int64_t)h_m[e - 1] * h_n[e - 1] - h_offB[b];
       {
-        HsmaTraceScope ts("host_h2d", s_in);
+        HsmaTraceScope ts("host_h2d", s_in, 0);
         if ((s = fail(cudaMemcpyAsync(dA + a0 * es, static_cast<const char *>(hA) + h_offA[b] * es, (size_t)na * es,
                                       cudaMemcpyHostToDevice, s_in))) != HSMA_OK)
           break;
@@ -232,7 +233,7 @@ hsma_status_t full_pipeline(int dtype, int diag, int32_t batch, const int32_t *h
       if ((s = fail(cudaEventRecord(ev[2 * c + 1], sk))) != HSMA_OK) break;
       if ((s = fail(cudaStreamWaitEvent(s_out, ev[2 * c + 1], 0))) != HSMA_OK) break;
       {
-        HsmaTraceScope ts("host_d2h", s_out);
+        HsmaTraceScope ts("host_d2h", s_out, 0);
         if ((s = fail(cudaMemcpyAsync(static_cast<char *>(hX) + h_offB[b] * es, dB + b0 * es, (size_t)nbx * es,
                                       cudaMemcpyDeviceToHost, s_out))) != HSMA_OK)
           break;

@@ -332,7 +332,7 @@ hsma_status_t r32_prepare(R32Plan &P, bool keep_panels, cudaStream_t st) {
   hsma_status_t s = hsma_r32_diag_inverse(P.nb, P.A, P.lda, P.m, P.unit, P.Dinv, st);
   if (s != HSMA_OK) return s;
   const int64_t nblk = (P.m + P.nb - 1) / P.nb;
-  HsmaTraceScope ts("convert", st);
+  HsmaTraceScope ts("convert", st, (P.tc_solve ? 1 : 0) + (keep_panels && nblk >= 2 ? 1 : 0));
   if (P.tc_solve) {
     r32_dslice_kernel<<<hsma_grid_rc(r32_kd(P.nb), nblk * P.nb), 256, 0, st>>>(P.Dinv, P.nb, nblk, r32_kd(P.nb),
                                                                                  P.dslices);
@@ -440,7 +440,7 @@ hsma_status_t r32_apply(const R32Plan &P, float *B, int64_t ldb, int64_t n, floa
     const int rows = (int)(m - r0 - sr);
     const __nv_bfloat16 *panel = P.panels ? P.panels + panel_off(P, r) : Ap;
     if (!P.panels || !P.tc_solve) {
-      HsmaTraceScope ts("convert", st);
+      HsmaTraceScope ts("convert", st, (P.panels ? 0 : 1) + (P.tc_solve ? 0 : 1));
       if (!P.panels) {
         dim3 g1((rows + 31) / 32, (nb + kPanelTileK - 1) / kPanelTileK);
         convert_panel_kernel<<<g1, 256, 0, st>>>(P.A + (r0 + sr) + r0 * P.lda, P.lda, rows, nb, P.terms, Kp, Ap);
@@ -1082,7 +1082,7 @@ hsma_status_t blocked_emulated(bool cplx, int nb, int panel_cols, const double *
     OzOperand Pa = view(pa_mem, (int64_t)W * m, Kp, (int64_t)W * rows);
     OzOperand Px = view(px_mem, n, Kp, n);
     {
-      HsmaTraceScope ts("slices", st);
+      HsmaTraceScope ts("slices", st, 4);  // oz_slice_a: 3 kernels, oz_slice_x: 1
       hsma_status_t e = oz_slice_a(cplx, A + W * (rb + c0 * lda), lda, (int)rows, k, 0, Pa, st);
       if (e == HSMA_OK) e = oz_slice_x(B + W * c0, (int64_t)W * ldb, W * k, Pa.kexp, Px, nullptr, st);
       if (e != HSMA_OK) return e;
@@ -1102,7 +1102,7 @@ hsma_status_t blocked_emulated(bool cplx, int nb, int panel_cols, const double *
         const int64_t r = r0 / nb;
         const int sr = (int)std::min<int64_t>(nb, m - r0);
         {
-          HsmaTraceScope ts("copy", st);
+          HsmaTraceScope ts("copy", st, 0);
           cudaError_t e =
               cudaMemcpy2DAsync(Wb, eb * nb, B + W * r0, eb * ldb, eb * sr, n, cudaMemcpyDeviceToDevice, st);
           if ((s = hsma_from_cuda(e)) != HSMA_OK) break;
@@ -1111,7 +1111,7 @@ hsma_status_t blocked_emulated(bool cplx, int nb, int panel_cols, const double *
         Pd.rows = W * sr;
         OzOperand Px = view(px_mem, n, Kpb, n);
         {
-          HsmaTraceScope ts("slices", st);
+          HsmaTraceScope ts("slices", st, 4);
           if ((s = oz_slice_a(cplx, Dinv + (size_t)W * r * nb * nb, nb, sr, sr, 1, Pd, st)) != HSMA_OK) break;
           if ((s = oz_slice_x(Wb, (int64_t)W * nb, W * sr, Pd.kexp, Px, nullptr, st)) != HSMA_OK) break;
         }
@@ -1196,7 +1196,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
                                     cudaMemcpyDeviceToDevice, st))) != HSMA_OK)
       break;
     {
-      HsmaTraceScope ts("convert", st);
+      HsmaTraceScope ts("convert", st, 4);
       f64_to_f32_kernel<<<hsma_grid_rc(m, m), 256, 0, st>>>(A, lda, A32, m, m, m, 1, nullptr);
       f64_to_f32_kernel<<<grid, 256, 0, st>>>(B, ldb, R32, m, m, n, 0, nullptr);
       sumsq_kernel<<<hsma_grid_rc(m, m), 256, 0, st>>>(A, lda, m, m, 1, unit, sums, 0, nullptr);
@@ -1204,7 +1204,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
       if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
     }
     if (emulated) {
-      HsmaTraceScope ts("residual_slices", st);
+      HsmaTraceScope ts("residual_slices", st, 3);
       if ((s = oz_slice_a(false, A, lda, (int)m, (int)m, unit ? 2 : 1, Lsl, st)) != HSMA_OK) break;
     }
     // X_0 from the FP32-result solve of the rounded data
@@ -1235,7 +1235,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
         if ((s = hsma_residual_f64(A, lda, unit, B, ldb, R64, m, m, n, alpha, state, st)) != HSMA_OK) break;
       }
       {
-        HsmaTraceScope ts("refine", st);
+        HsmaTraceScope ts("refine", st, 3);
         sumsq_kernel<<<grid, 256, 0, st>>>(R64, m, m, n, 0, 0, sums, 2, state);
         sumsq_kernel<<<grid, 256, 0, st>>>(B, ldb, m, n, 0, 0, sums, 3, state);
         check_kernel<<<1, 1, 0, st>>>(sums, state, std::fabs(alpha), tol, it, it == itmax ? 1 : 0,
@@ -1248,6 +1248,7 @@ hsma_status_t hsma_mixed_ir(int nb, const hsma_opts_t *opts, const double *A, in
           if (conv) break;
         }
         f64_to_f32_kernel<<<grid, 256, 0, st>>>(R64, m, R32, m, m, n, 0, state);
+        hsma_count_launches(1);
         if ((s = fail(cudaGetLastError())) != HSMA_OK) break;
       }
       // correction C from the FP32-result solve of L C = R (alpha = 1), X += C
@@ -1353,7 +1354,7 @@ hsma_status_t hsma_c64_blocked(int nb, int panel_cols, const void *A, int64_t ld
   cplx *A2 = static_cast<cplx *>(ws);
   cplx *B2 = reinterpret_cast<cplx *>(static_cast<unsigned char *>(ws) + a_b);
   {
-    HsmaTraceScope ts("copy", st);
+    HsmaTraceScope ts("copy", st, 2);
     c64_to_c128_kernel<<<hsma_grid_rc(m, m), 256, 0, st>>>(static_cast<const cplxf *>(A), lda, A2, m, m, m, 1);
     c64_to_c128_kernel<<<hsma_grid_rc(m, n), 256, 0, st>>>(static_cast<const cplxf *>(B), ldb, B2, m, m, n, 0);
     s = hsma_from_cuda(cudaGetLastError());

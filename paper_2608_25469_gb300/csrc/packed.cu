@@ -589,7 +589,7 @@ hsma_status_t packed_impl(int32_t batch, int max_m, const int32_t *dm, const int
     const int nsm = sm_count(dev);
     int blocks = (batch + kPkSchedThreads2 - 1) / kPkSchedThreads2;
     if (blocks > 4 * nsm) blocks = 4 * nsm;
-    HsmaTraceScope ts("vbatched_schedule", st);
+    HsmaTraceScope ts("vbatched_schedule", st, 2);
     HSMA_CUDA_TRY(cudaMemsetAsync(scr + L.counts, 0, sizeof(PkCounts), st));
     packed_count_kernel<T><<<blocks, kPkSchedThreads2, 0, st>>>(batch, dm, dn, dlda, dldb, dA, dB, scr, L, mmax,
                                                                 skip_large, status);

@@ -139,7 +139,9 @@ hsma_status_t hsma_r32_diag_inverse(int nb, const float *A, int64_t lda, int64_t
   float *W = reinterpret_cast<float *>(static_cast<unsigned char *>(ws) + base_b);
   do {
     if ((s = hsma_diag_inverse(HSMA_R32_BF16, kInvBase, A, lda, m, unit, base, st)) != HSMA_OK) break;
-    HsmaTraceScope ts("diag_inverse", st);
+    int levels = 0;
+    for (int h = kInvBase; h < nb; h *= 2) ++levels;
+    HsmaTraceScope ts("diag_inverse", st, 1 + 2 * levels);
     if ((s = hsma_from_cuda(cudaMemsetAsync(Dinv, 0, sizeof(float) * (size_t)nblk * nb * nb, st))) != HSMA_OK) break;
     inv_place_kernel<<<(unsigned)nbase, 256, 0, st>>>(base, m, nb, Dinv);
     for (int h = kInvBase; h < nb; h *= 2) {

@@ -6,6 +6,7 @@
 #include "blocked.h"
 #include "common.cuh"
 #include "tma.cuh"
+#include "trace.h"
 
 namespace {
 // One thread waits, with the library's bounded wait, on an mbarrier that
@@ -26,5 +27,6 @@ extern "C" HSMA_API hsma_status_t hsma_check_wait_timeout(uint64_t limit_ns, int
   unsigned int *err = hsma_dev_error_ptr();
   if (err == nullptr) return HSMA_ERR_CUDA;
   wait_timeout_check_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(limit_ns, err, d_returned);
+  hsma_count_launches(1);
   return hsma_from_cuda(cudaGetLastError());
 }

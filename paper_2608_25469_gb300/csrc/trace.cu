@@ -24,7 +24,7 @@ struct Totals {
 
 std::mutex g_mu;
 std::atomic<int> g_enabled{-1};  // -1: not yet read from the environment
-std::atomic<long long> g_launches{0};  // every launch site, traced or not
+std::atomic<long long> g_launches{0};  // every kernel launched, traced or not
 std::vector<Pending> g_open;  // indexed by slot
 std::vector<int> g_free_slots;
 std::vector<int> g_done;  // slots recorded, not yet folded into totals
@@ -55,8 +55,11 @@ void drain_locked() {
 
 }  // namespace
 
-HsmaTraceScope::HsmaTraceScope(const char *phase, cudaStream_t st) : phase_(phase), st_(st), slot_(-1) {
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+void hsma_count_launches(int kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
+
+HsmaTraceScope::HsmaTraceScope(const char *phase, cudaStream_t st, int kernels)
+    : phase_(phase), st_(st), slot_(-1) {
+  g_launches.fetch_add(kernels, std::memory_order_relaxed);
   if (g_enabled.load(std::memory_order_relaxed) == 0) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!enabled_locked()) return;

@@ -3,10 +3,16 @@
 #pragma once
 #include <cuda_runtime.h>
 
+// `kernels`: the kernels the scope launches (0 for a scope around copies);
+// the library's launch counter (hsma_trace_launches) adds them up.
 struct HsmaTraceScope {
-  HsmaTraceScope(const char *phase, cudaStream_t st);
+  HsmaTraceScope(const char *phase, cudaStream_t st, int kernels = 1);
   ~HsmaTraceScope();
   const char *phase_;
   cudaStream_t st_;
   int slot_;
 };
+
+// Kernel launches made outside any HsmaTraceScope, or beyond the count a
+// scope was given.
+void hsma_count_launches(int kernels);

@@ -80,7 +80,7 @@ hsma_status_t variant_impl(int dtype, int side, int uplo, int trans, int diag, i
   T *L = static_cast<T *>(ws);
   T *Bp = reinterpret_cast<T *>(static_cast<unsigned char *>(ws) + l_b);
   {
-    HsmaTraceScope ts("remap", st);
+    HsmaTraceScope ts("remap", st, 2);
     remap_a_kernel<T><<<hsma_grid_rc(mE, mE), 256, 0, st>>>(A, lda, mE, rev, tsrc, cj, L);
     remap_b_kernel<T><<<hsma_grid_rc(mE, nE), 256, 0, st>>>(B, ldb, Bp, mE, nE, rev, right ? 1 : 0, 0);
     s = hsma_from_cuda(cudaGetLastError());

@@ -464,6 +464,10 @@ __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bo
       if (active && r < m) s[t] = E::mul(pk_ld(sc + r), E::ld(Bg + t * kStep));
     }
   }
+  // slots below kSafe hold rows below m for every m this form serves (G = 2
+  // serves m > 32 only), so their loads need no run-time bound check and the
+  // compiler may issue them together
+  constexpr int kSafe = (G == 2 && MMAX == 64) ? 17 : 1;
   int64_t base = -1;  // column i of the staged triangle starts at tri + base + i + 1
 #pragma unroll
   for (int i = 0; i < MMAX - 1; ++i) {
@@ -480,7 +484,7 @@ __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bo
     }
 #pragma unroll
     for (int t = tb + 1; t < R; ++t) {
-      if (t * G >= m) break;  // warp-uniform
+      if (t >= kSafe && t * G >= m) break;  // warp-uniform
       s[t] = E::fms(pk_ld(col + g + t * G), x, s[t]);
     }
     base += rows - 2 - i;

@@ -436,7 +436,7 @@ __device__ __forceinline__ cplx pk_ld<cplx>(const cplx *p) {
 // 3. Solve.  A warp tile: C = 32/G columns of one m's stream; lane l holds
 // column c = l / G of the tile, rows g + t*G (g = l % G) in register slot t.
 // ---------------------------------------------------------------------------
-template <class T, int G, int MMAX, bool REV>
+template <class T, int G, int MMAX, bool REV, int KS>
 __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bool active, int m, int rows,
                                             bool azero) {
   using E = Elem<T>;
@@ -464,10 +464,9 @@ __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bo
       if (active && r < m) s[t] = E::mul(pk_ld(sc + r), E::ld(Bg + t * kStep));
     }
   }
-  // slots below kSafe hold rows below m for every m this form serves (G = 2
-  // serves m > 32 only), so their loads need no run-time bound check and the
+  // slots below KS hold rows below m for every m the caller sends to this
+  // form (KS G < m), so their loads need no run-time bound check and the
   // compiler may issue them together
-  constexpr int kSafe = (G == 2 && MMAX == 64) ? 17 : 1;
   int64_t base = -1;  // column i of the staged triangle starts at tri + base + i + 1
 #pragma unroll
   for (int i = 0; i < MMAX - 1; ++i) {
@@ -484,7 +483,7 @@ __device__ __forceinline__ void packed_tile(const T *tri, const T *sc, T *Bp, bo
     }
 #pragma unroll
     for (int t = tb + 1; t < R; ++t) {
-      if (t >= kSafe && t * G >= m) break;  // warp-uniform
+      if (t >= KS && t * G >= m) break;  // warp-uniform
       s[t] = E::fms(pk_ld(col + g + t * G), x, s[t]);
     }
     base += rows - 2 - i;
@@ -544,12 +543,17 @@ __global__ void __launch_bounds__(32 * kPkWarps, kPkMinBlocks) packed_solve_kern
     const T *tri = stage + *reinterpret_cast<const long long *>(e + 8) + (int64_t)(p - pos0) * e[5];
     const T *sc = tri + pk_tri_elems(rows);
     if constexpr (two) {
-      if (G == 1)
-        packed_tile<T, 1, 32, REV>(tri, sc, Bp, active, m, rows, azero != 0);
-      else
-        packed_tile<T, 2, 64, REV>(tri, sc, Bp, active, m, rows, azero != 0);
+      // the bound-check-free slot prefix by m: KS slots with KS G < m
+      if (G == 1) {
+        if (m > 8)
+          packed_tile<T, 1, 32, REV, 9>(tri, sc, Bp, active, m, rows, azero != 0);
+        else
+          packed_tile<T, 1, 32, REV, 1>(tri, sc, Bp, active, m, rows, azero != 0);
+      } else {
+        packed_tile<T, 2, 64, REV, 17>(tri, sc, Bp, active, m, rows, azero != 0);
+      }
     } else {
-      packed_tile<T, 1, 64, REV>(tri, sc, Bp, active, m, rows, azero != 0);
+      packed_tile<T, 1, 64, REV, 1>(tri, sc, Bp, active, m, rows, azero != 0);
     }
   }
 }

@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
     }
     __syncwarp();
     // element q of the packed triangle: column i, row i + 1 + local index;
-    // four elements per lane in flight (loads first)
+    // eight elements per lane in flight (loads first)
     const int total = (int)pk_tri_elems(rows);
     int i = 0, loc = lane;
     auto advance = [&](int by) {
@@ -402,18 +402,18 @@ __global__ void __launch_bounds__(32 * kPkPrepWarps) packed_prep_kernel(const in
       }
     };
     advance(0);
-    for (int q0 = 0; q0 < total; q0 += 4 * 32) {
-      int rr[4];
-      T vv[4];
+    for (int q0 = 0; q0 < total; q0 += 8 * 32) {
+      int rr[8];
+      T vv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int q = q0 + u * 32 + lane;
         rr[u] = i + 1 + loc;
         vv[u] = (q < total && rr[u] < m) ? at(rr[u], i) : E::zero();
         advance(32);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int q = q0 + u * 32 + lane;
         if (q < total) tri[q] = E::mul(rinv[rr[u]], vv[u]);
       }

@@ -134,13 +134,19 @@ def test_getrs_fp32_dtypes(H, cx):
         assert oracle.forward_error(out[b].astype(wide), ref) <= 2e-5, b
 
 
-def test_getrs_alpha_zero_and_empty_instances(H):
-    LUs, pivs, Bs = _instances(36, 30, False)
-    LUs[3], pivs[3], Bs[3] = np.zeros((0, 0)), np.zeros(0, np.int32), np.zeros((0, 0))
-    Bs[4] = np.zeros((LUs[4].shape[0], 0))
-    out = _run(H, I.R64, LUs, pivs, Bs, 0.0).results()
+@pytest.mark.parametrize("cx", [False, True])
+def test_getrs_alpha_zero_and_empty_instances(H, cx):
+    """alpha = 0 gives X = 0 (complex128: the interchange pass, then one packed launch writing
+    zeros; the second is skipped); empty instances (m = 0, n = 0) are valid no-ops."""
+    LUs, pivs, Bs = _instances(36, 30, cx)
+    dt = np.complex128 if cx else np.float64
+    LUs[3], pivs[3], Bs[3] = np.zeros((0, 0), dt), np.zeros(0, np.int32), np.zeros((0, 0), dt)
+    Bs[4] = np.zeros((LUs[4].shape[0], 0), dt)
+    bt = _run(H, I.C128 if cx else I.R64, LUs, pivs, Bs, 0.0)
+    assert bt.status() == 0
+    out = bt.results()
     for b in range(len(LUs)):
-        assert np.all(out[b] == 0.0), b
+        assert out[b].shape == Bs[b].shape and np.all(out[b] == 0.0), b
 
 
 

@@ -332,7 +332,8 @@ HSMA_API hsma_status_t hsma_potrs_vbatched(int dtype, int32_t batch, const int32
 /*
  * The varlen batch with its matrices in HOST memory (no paper counterpart:
  * the paper's solves are device-resident).  The batch is cut into `chunks`
- * groups of consecutive instances (0 = 8, at most 256).  The sizes and
+ * groups of consecutive instances (0 = 8; 6 for the packed-triangle entry
+ * point below; at most 256).  The sizes and
  * offsets are copied once; then the groups' host-to-device copies run in
  * order on an internal copy-in stream, each group's batched solve starts (on
  * one of two internal compute streams) as soon as its copy has landed, and

@@ -411,47 +411,61 @@ def run_batched(args, dist, device, c64=False):
 
 
 def run_batched_lu(args, dist, device):
-    """LU-factor solve as a second batched workload (the paper's motivation): 8192 complex128
-    instances, m,n ~ U{8..64}; packed factors P = tril(L, -1) + triu(U); each step solves
-    X = U^{-1} L^{-1} (alpha B) with the LU-solve batch (complex128: two launches of the
-    column-packed batch, unit lower then upper through the index map); the same work as two
-    hsma_trsm_vbatched calls is timed beside it."""
+    """LU-factor solve as a second batched workload (the paper's motivation): 8192 instances,
+    m,n ~ U{8..64}; packed factors P = tril(L, -1) + triu(U) with getrf-style row interchanges
+    (seeded LAPACK pivots, ipiv[k] uniform on k+1..m); each step solves X = U^{-1} L^{-1} P^T
+    (alpha B) with the LU-solve batch (complex128: the interchange pass, then two launches of
+    the column-packed batch, unit lower then upper through the index map; --lu-dtype f64:
+    the fused one-launch kernel); the two triangular solves as hsma_trsm_vbatched calls are
+    timed beside it."""
     import torch
     from paper_2608_25469_gb300 import hsma as H
     from paper_2608_25469_gb300 import inputs as I
-    alpha = 1.5 - 0.5j
+    cx = args.lu_dtype == "c128"
+    code = H.C128 if cx else H.R64
+    es = 16 if cx else 8
+    alpha = (1.5 - 0.5j) if cx else 1.5
     seed = shard_seed(args.seed, dist.rank)
     ms, ns = I.batched_sizes(seed, 8192)
     Ps = []
     for b, m in enumerate(ms):
-        Lf = I.gen_A(seed, int(m), I.C128, inst=b)
-        Uf = I.gen_A(seed + 1, int(m), I.C128, inst=b).T
+        Lf = I.gen_A(seed, int(m), I.C128 if cx else I.R64, inst=b)
+        Uf = I.gen_A(seed + 1, int(m), I.C128 if cx else I.R64, inst=b).T
         Ps.append(np.asfortranarray(np.tril(Lf, -1) + np.triu(Uf)))
-    Bs = [I.gen_B(seed, int(m), int(n), I.C128, inst=b) for b, (m, n) in enumerate(zip(ms, ns))]
+    Bs = [I.gen_B(seed, int(m), int(n), I.C128 if cx else I.R64, inst=b) for b, (m, n) in enumerate(zip(ms, ns))]
+    prng = np.random.default_rng(seed + 7)
+    pivs = [(np.arange(int(m)) + (prng.random(int(m)) * (int(m) - np.arange(int(m)))).astype(np.int64) + 1)
+            .astype(np.int32) for m in ms]
     batch = len(Ps)
-    flops = float(sum(2 * 4.0 * float(m) * m * n for m, n in zip(ms, ns)))
-    abytes = float(sum(2 * (16 * (m * (m + 1) // 2) + 2 * 16 * m * n) for m, n in zip(ms, ns)))
+    k = 4.0 if cx else 1.0
+    flops = float(sum(2 * k * float(m) * m * n for m, n in zip(ms, ns)))
+    abytes = float(sum(2 * (es * (m * (m + 1) // 2) + 2 * es * m * n) for m, n in zip(ms, ns)))
     offA = np.concatenate([[0], np.cumsum(ms.astype(np.int64) ** 2)[:-1]])
     offB = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns)[:-1]])
     pinA = torch.from_numpy(np.concatenate([a.ravel(order="F") for a in Ps])).pin_memory()
     pinB = torch.from_numpy(np.concatenate([b.ravel(order="F") for b in Bs])).pin_memory()
     outB = torch.empty_like(pinB).pin_memory()
     dA, dB = pinA.to(device), pinB.to(device)
-    pa = torch.from_numpy((dA.data_ptr() + offA * 16).astype(np.int64)).to(device)
-    pb = torch.from_numpy((dB.data_ptr() + offB * 16).astype(np.int64)).to(device)
+    pa = torch.from_numpy((dA.data_ptr() + offA * es).astype(np.int64)).to(device)
+    pb = torch.from_numpy((dB.data_ptr() + offB * es).astype(np.int64)).to(device)
     dm = torch.from_numpy(ms.astype(np.int32)).to(device)
     dn = torch.from_numpy(ns.astype(np.int32)).to(device)
+    # the pivots: one pinned array, copied with A and B every end-to-end step
+    offP = np.concatenate([[0], np.cumsum(ms.astype(np.int64))[:-1]])
+    pinP = torch.from_numpy(np.concatenate(pivs).astype(np.int32)).pin_memory()
+    dP = pinP.to(device)
+    pp = torch.from_numpy((dP.data_ptr() + offP * 4).astype(np.int64)).to(device)
     st = torch.cuda.current_stream()
     sp = int(st.cuda_stream)
 
     def step():
-        H.hsma_getrs_vbatched(H.C128, batch, dm.data_ptr(), dn.data_ptr(), alpha, pa.data_ptr(), dm.data_ptr(), 0,
-                              pb.data_ptr(), dm.data_ptr(), 64, 64, 0, sp)
+        H.hsma_getrs_vbatched(code, batch, dm.data_ptr(), dn.data_ptr(), alpha, pa.data_ptr(), dm.data_ptr(),
+                              pp.data_ptr(), pb.data_ptr(), dm.data_ptr(), 64, 64, 0, sp)
 
-    def step_two_launches():
-        H.hsma_trsm_vbatched(H.C128, H.LEFT, H.LOWER, H.NO_TRANS, H.UNIT, batch, dm.data_ptr(), dn.data_ptr(), alpha,
+    def step_two_launches():  # the two triangular solves alone (no interchanges)
+        H.hsma_trsm_vbatched(code, H.LEFT, H.LOWER, H.NO_TRANS, H.UNIT, batch, dm.data_ptr(), dn.data_ptr(), alpha,
                              pa.data_ptr(), dm.data_ptr(), pb.data_ptr(), dm.data_ptr(), 64, 64, 0, sp)
-        H.hsma_trsm_vbatched(H.C128, H.LEFT, H.UPPER, H.NO_TRANS, H.NON_UNIT, batch, dm.data_ptr(), dn.data_ptr(),
+        H.hsma_trsm_vbatched(code, H.LEFT, H.UPPER, H.NO_TRANS, H.NON_UNIT, batch, dm.data_ptr(), dn.data_ptr(),
                              1.0, pa.data_ptr(), dm.data_ptr(), pb.data_ptr(), dm.data_ptr(), 64, 64, 0, sp)
 
     for _ in range(args.warmup):
@@ -473,7 +487,8 @@ def run_batched_lu(args, dist, device):
     t1 = time.time()
     H.hsma_trace_enable(False)
     ms_max = dist.max(e0.elapsed_time(e1), device=device)
-    solve_ms, solve_cnt = H.hsma_trace_read("vbatched_solve")
+    # complex128: two packed solve launches per step; the other dtypes: one fused launch
+    solve_ms, solve_cnt = H.hsma_trace_read("vbatched_solve" if cx else "vbatched_lu")
     launches = H.hsma_trace_launches()
     clocks = None
     if sampler:
@@ -490,10 +505,11 @@ def run_batched_lu(args, dist, device):
     torch.cuda.synchronize()
     two_ms = dist.max(e0.elapsed_time(e1), device=device) / args.steps
 
-    # end to end: A and B copied in, the fused solve, X copied out, every step
+    # end to end: A, B and the pivots copied in, the solve, X copied out, every step
     def e2e_step():
         dA.copy_(pinA, non_blocking=True)
         dB.copy_(pinB, non_blocking=True)
+        dP.copy_(pinP, non_blocking=True)
         step()
         outB.copy_(dB, non_blocking=True)
 
@@ -507,13 +523,14 @@ def run_batched_lu(args, dist, device):
     torch.cuda.synchronize()
     e2e_ms = dist.max(e0.elapsed_time(e1), device=device)
     total = dist.sum(flops, device=device)
-    kernel_ms = solve_ms / max(solve_cnt, 1)  # two solve launches per step, half the flops each
-    achieved = flops / 2 / (kernel_ms * 1e-3) / 1e9
+    kernel_ms = solve_ms / max(solve_cnt, 1)
+    per_launch = flops / 2 if cx else flops  # complex128: two solve launches a step, half the flops each
+    achieved = per_launch / (kernel_ms * 1e-3) / 1e9
     # the last end-to-end step solved the original data: every instance against the oracle's getrs
-    # (no row interchanges), which is also the timed CPU baseline
+    # with the same pivots, which is also the timed CPU baseline
     import oracle
     t_or = time.perf_counter()
-    refs = [oracle.getrs(P, None, B, alpha) for P, B in zip(Ps, Bs)]
+    refs = [oracle.getrs(P, piv, B, alpha) for P, piv, B in zip(Ps, pivs, Bs)]
     el_or = time.perf_counter() - t_or
     errs = batch_forward_errors(outB.numpy(), ms, ns, refs, offB)
     extra = {"forward_error": fwd_error_record(errs, 1e-12, "every instance of the batch (end-to-end result), "
@@ -526,22 +543,30 @@ def run_batched_lu(args, dist, device):
     return {
         "metric": METRIC, "value": round(total * args.steps / (ms_max * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": "batched_lu_c128: 8192 complex128 LU-factor solves per GPU (unit lower then upper: "
-                               "two launches of the column-packed batch), m,n ~ U{8..64}, alpha=(1.5,-0.5)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.lu_dtype, "data": "synthetic",
+        "config": {"workload": (f"batched_lu_{args.lu_dtype}: 8192 "
+                                f"{'complex128' if cx else 'fp64'} LU-factor solves per GPU with row "
+                                "interchanges (ipiv[k] ~ U{k+1..m}; "
+                                + ("the interchange pass, then unit lower and upper as two launches of the "
+                                   "column-packed batch" if cx else "one fused launch: interchanges, unit lower, "
+                                   "upper") + f"), m,n ~ U{{8..64}}, alpha={alpha}"),
                    "l2": f"inputs larger than L2 ({abytes / 1e6:.0f} MB algorithmic per step)"},
         "two_launches": {"ms_per_step": round(two_ms, 5),
-                         "value": round(total / (two_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s"},
+                         "value": round(total / (two_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                         "what": "the two triangular solves as hsma_trsm_vbatched calls, no interchanges"},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp64_peak_gflops(), 1),
                      "unit": "GFLOP/s", "frac": round(achieved / fp64_peak_gflops(), 4),
-                     "traffic": profile_traffic("packed_solve_lu_upper_c128_8192.txt", PACKED_SOURCES,
-                                                work=flops / 2),
-                     "kernel": "packed_solve_kernel<cplx> (two launches a step: unit lower, then upper "
-                               "through the index map; achieved over both)", "kernel_ms": round(kernel_ms, 5),
+                     "traffic": (profile_traffic("packed_solve_lu_upper_c128_8192.txt", PACKED_SOURCES,
+                                                 work=flops / 2) if cx else
+                                 profile_traffic("vbatched_lu_f64_8192.txt", SMALL_SOURCES)),
+                     "kernel": ("packed_solve_kernel<cplx> (two launches a step: unit lower, then upper "
+                                "through the index map; achieved over both)" if cx else
+                                "vbatched_lu_kernel<double> (interchanges, unit lower and upper in one launch)"),
+                     "kernel_ms": round(kernel_ms, 5),
                      "peak_source": FP64_PEAK_SOURCE},
         "e2e": {"value": round(total * e2e_steps / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
-                "h2d_bytes_per_step": int(pinA.numel() * 16 + pinB.numel() * 16),
-                "d2h_bytes_per_step": int(outB.numel() * 16)},
+                "h2d_bytes_per_step": int(pinA.numel() * es + pinB.numel() * es + pinP.numel() * 4),
+                "d2h_bytes_per_step": int(outB.numel() * es)},
         "gpu_launches": int(launches), "clocks": clocks,
         **extra,
     }
@@ -1339,6 +1364,8 @@ def main(argv=None):
                     help="large_*, serve: FP64 tensor products, or FP64 emulated on the BF16 tensor cores")
     ap.add_argument("--nb", type=int, default=0, help="large_*: force N_B (0 = planner)")
     ap.add_argument("--e2e-chunks", type=int, default=0, help="batched e2e: host-buffer chunks (0 = library default)")
+    ap.add_argument("--lu-dtype", default="c128", choices=["c128", "f64"],
+                    help="batched_lu_c128: element type of the LU-factor batch (f64 runs the fused kernel)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -831,6 +831,9 @@ namespace {
 // swapped with row ipiv[k] - 1, k = 0, 1, ... in order), and the instance's
 // size for the solves in m_eff: its m, or 0 when a pivot is out of range
 // (HSMA_DEVERR_BAD_PIVOT; B untouched and both solves skip the instance).
+// The swaps are composed into one permutation first (row r of P^T B is row
+// perm[r] of B), so each column is one gather: loads of the column's rows,
+// then stores, four columns in flight per step.
 // Instances the solves reject (sizes, pointers) or leave to the blocked path
 // (m > 64) are not permuted here.
 template <class T>
@@ -841,7 +844,10 @@ __global__ void __launch_bounds__(256) lu_pivots_kernel(int32_t batch, const int
                                                         const void *const *__restrict__ dA, void *const *dB,
                                                         const int32_t *const *__restrict__ dipiv, int32_t *m_eff,
                                                         uint32_t *status) {
+  constexpr int kCols = 4;
+  __shared__ int s_perm[8][64];
   const int lane = threadIdx.x & 31;
+  int *perm = s_perm[threadIdx.x >> 5];
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < batch; b += nw) {
     const int m = dm[b], n = dn[b];
@@ -859,16 +865,38 @@ __global__ void __launch_bounds__(256) lu_pivots_kernel(int32_t batch, const int
       }
       continue;
     }
+    for (int r = lane; r < m; r += 32) perm[r] = r;
+    __syncwarp();
+    if (lane == 0) {
+      for (int k = 0; k < m; ++k) {
+        const int p = ipiv[k] - 1;
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+      }
+    }
+    __syncwarp();
+    const int r0 = lane, r1 = lane + 32;
+    const int q0 = r0 < m ? perm[r0] : 0, q1 = r1 < m ? perm[r1] : 0;
+    __syncwarp();  // perm is rewritten by this warp's next instance
     T *B = static_cast<T *>(dB[b]);
     const int64_t ldb = dldb[b];
-    for (int k = 0; k < m; ++k) {
-      const int p = ipiv[k] - 1;
-      if (p == k) continue;
-      for (int j = lane; j < n; j += 32) {
-        const T t = B[k + j * ldb];
-        B[k + j * ldb] = B[p + j * ldb];
-        B[p + j * ldb] = t;
+    for (int j0 = 0; j0 < n; j0 += kCols) {
+      T v0[kCols], v1[kCols];
+#pragma unroll
+      for (int u = 0; u < kCols; ++u) {
+        const T *col = B + (int64_t)(j0 + u) * ldb;
+        if (j0 + u < n && r0 < m) v0[u] = col[q0];
+        if (j0 + u < n && r1 < m) v1[u] = col[q1];
       }
+      __syncwarp();  // every lane's loads of these columns before any store
+#pragma unroll
+      for (int u = 0; u < kCols; ++u) {
+        T *col = B + (int64_t)(j0 + u) * ldb;
+        if (j0 + u < n && r0 < m) col[r0] = v0[u];
+        if (j0 + u < n && r1 < m) col[r1] = v1[u];
+      }
+      __syncwarp();
     }
   }
 }

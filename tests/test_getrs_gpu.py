@@ -92,14 +92,18 @@ def test_getrs_without_pivots_equals_two_launches(H):
         assert oracle.forward_error(fused[b], oracle.getrs(LUs[b], None, Bs[b], alpha)) <= 1e-12, b
 
 
-def test_getrs_null_pivot_entries_and_alone(H):
-    LUs, pivs, Bs = _instances(33, 300, False)
-    mix = _run(H, I.R64, LUs, pivs, Bs, -1.25, null_every=3).results()
+@pytest.mark.parametrize("cx", [False, True])
+def test_getrs_null_pivot_entries_and_alone(H, cx):
+    """NULL pivot pointers mean no interchanges for that instance; an instance alone equals it
+    in the mix, bit for bit (complex128: the interchange pass's permutation gather)."""
+    code = I.C128 if cx else I.R64
+    LUs, pivs, Bs = _instances(33, 300, cx)
+    mix = _run(H, code, LUs, pivs, Bs, -1.25, null_every=3).results()
     for b in range(len(LUs)):
         ref = oracle.getrs(LUs[b], None if b % 3 == 0 else pivs[b], Bs[b], -1.25)
         assert oracle.forward_error(mix[b], ref) <= 1e-12, b
     for b in range(1, len(LUs), 41):  # alone = in the mix, bit for bit
-        alone = _run(H, I.R64, [LUs[b]], None if b % 3 == 0 else [pivs[b]], [Bs[b]], -1.25).results()[0]
+        alone = _run(H, code, [LUs[b]], None if b % 3 == 0 else [pivs[b]], [Bs[b]], -1.25).results()[0]
         assert np.array_equal(alone, mix[b]), b
 
 
